@@ -1,0 +1,114 @@
+"""Seeded synthetic inputs shaped like the paper's mock LISA streams.
+
+This module is the one piece shared by the CUDA path's tests/bench and the
+CPU oracle: it draws random numbers and builds the data grid, the noise PSD
+and particle populations.  It holds none of the statistic's arithmetic (no
+waveform, no response, no inner product); injections are added by whoever
+owns a template (the oracle in tests, the library's own injection call in the
+benchmark).
+
+Workload shapes follow Sec. IV of arXiv:2408.13170 (analytic instrumental
+PSD, stationary Gaussian noise generated directly in the frequency domain,
+one injected inspiral whose amplitude sets the SNR, uniform priors) and the
+benchmark configurations listed in the design doc.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+CLIGHT = 299792458.0
+ARM_M = 2.5e9
+
+
+def grid(f_min: float, f_max: float, T_obs: float):
+    """FFT frequency grid f_k = f_first + k df, df = 1/T_obs, covering the
+    Fourier frequencies j/T_obs with ceil(f_min T) <= j <= floor(f_max T)."""
+    j0 = math.ceil(f_min * T_obs - 1e-9)
+    j1 = math.floor(f_max * T_obs + 1e-9)
+    df = 1.0 / T_obs
+    return j0 * df, df, j1 - j0 + 1
+
+
+def psd_AE(f):
+    """Analytic instrumental one-sided PSD of TDI A (= E), first generation,
+    in the SciRD form (Babak et al. 2021, the model the paper cites in
+    Sec. IV).  Fractional-frequency units; only ratios matter here."""
+    f = np.asarray(f, dtype=np.float64)
+    L = ARM_M / CLIGHT
+    x = 2.0 * np.pi * f * L
+    s_oms = (15e-12) ** 2 * (1.0 + (2e-3 / f) ** 4) * (2.0 * np.pi * f / CLIGHT) ** 2
+    s_acc = ((3e-15) ** 2 * (1.0 + (4e-4 / f) ** 2) * (1.0 + (f / 8e-3) ** 4)
+             / (2.0 * np.pi * f * CLIGHT) ** 2)
+    return 8.0 * np.sin(x) ** 2 * ((2.0 + np.cos(x)) * s_oms
+                                   + 2.0 * (3.0 + 2.0 * np.cos(x) + np.cos(2.0 * x)) * s_acc)
+
+
+def noise(S, T_obs, rng):
+    """Stationary Gaussian FD noise: Re, Im ~ N(0, S T_obs / 4) per bin, so
+    that E|n|^2 = S T_obs / 2 (one-sided PSD convention)."""
+    S = np.asarray(S, dtype=np.float64)
+    sig = np.sqrt(S * T_obs / 4.0)
+    return rng.normal(size=S.shape) * sig + 1j * (rng.normal(size=S.shape) * sig)
+
+
+PRIOR_BOX = {
+    # Mc [Msun], q, f0 [Hz], lambda, beta, iota, psi, e0
+    "lo": np.array([10.0, 1.0, 0.012, 0.0, -np.pi / 2, 0.0, 0.0, 0.0]),
+    "hi": np.array([100.0, 8.0, 0.03, 2 * np.pi, np.pi / 2, np.pi, np.pi, 0.0]),
+}
+
+
+def draw_particles(P: int, rng, lo=None, hi=None):
+    """P particles uniform in the prior box (uniform-in-parameter priors,
+    Table I); e0 = 0."""
+    lo = PRIOR_BOX["lo"] if lo is None else np.asarray(lo, dtype=np.float64)
+    hi = PRIOR_BOX["hi"] if hi is None else np.asarray(hi, dtype=np.float64)
+    u = rng.random((P, 8))
+    th = lo + u * (hi - lo)
+    th[:, 7] = 0.0
+    return th
+
+
+def injection_params(rng, Mc, q, f0):
+    """Injected source: intrinsic parameters fixed, sky / inclination /
+    polarisation uniform (the phase is maximised away)."""
+    return np.array([Mc, q, f0, rng.uniform(0, 2 * np.pi),
+                     rng.uniform(-np.pi / 2, np.pi / 2), rng.uniform(0, np.pi),
+                     rng.uniform(0, np.pi), 0.0])
+
+
+# Benchmark / test configurations (sizes, segment counts, seeds).
+CONFIGS = {
+    "C1": dict(T_obs=3.0e6, f_min=0.015, f_max=0.030, P=256, N=8,
+               mode="equal_width", inj=(30.0, 1.5, 0.018), snr=20.0, seed=0),
+    "C2": dict(T_obs=3.15e7, f_min=0.01, f_max=0.05, P=4096, N=2048,
+               mode="equal_snr2", inj=(30.0, 1.5, 0.018), snr=17.0, seed=0),
+    "C3": dict(T_obs=1.26e8, f_min=0.01, f_max=0.05, P=16384,
+               N=(16384, 4096, 1024, 256, 64, 16, 1), mode="equal_snr2",
+               inj=(30.0, 1.5, 0.018), snr=25.0, seed=0),
+}
+
+
+def make_stream(name_or_cfg, seed=None, noise_free=False):
+    """Noise-only data stream of a configuration.
+
+    Returns a dict: f_first, df, K, T_obs, A, E (complex128[K]), SA, SE
+    (float64[K]), rng (the generator, positioned after the noise draws, for
+    drawing the injection and the particles), cfg.
+    """
+    cfg = CONFIGS[name_or_cfg] if isinstance(name_or_cfg, str) else name_or_cfg
+    seed = cfg["seed"] if seed is None else seed
+    rng = np.random.Generator(np.random.PCG64(seed))
+    f_first, df, K = grid(cfg["f_min"], cfg["f_max"], cfg["T_obs"])
+    f = f_first + np.arange(K) * df
+    S = psd_AE(f)
+    if noise_free:
+        A = np.zeros(K, np.complex128)
+        E = np.zeros(K, np.complex128)
+    else:
+        A = noise(S, cfg["T_obs"], rng)
+        E = noise(S, cfg["T_obs"], rng)
+    return dict(f_first=f_first, df=df, K=K, T_obs=cfg["T_obs"], A=A, E=E,
+                SA=S, SE=S.copy(), rng=rng, cfg=cfg)
