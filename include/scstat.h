@@ -1,0 +1,154 @@
+/*
+ * scstat.h -- C ABI of the GB300 (sm_103a) library that evaluates the
+ * semi-coherent search statistic Upsilon_N of Bandopadhyay & Moore,
+ * "A GPU-accelerated semi-coherent hierarchical search for stellar-mass
+ * binary inspiral signals in LISA", arXiv:2408.13170.
+ *
+ * What one evaluation computes, for every particle theta_p
+ * (Sec. II.A Eq. inner_prod, Sec. II.B Eq. semi-coherent_O and Upsilon_N):
+ *
+ *   z_{p,n}  = sum_{k in segment n} sum_{alpha in {A,E}}
+ *                  4 df d_alpha(f_k) conj(h_alpha(theta_p, f_k)) / S_alpha(f_k)
+ *   hh_{p,n} = sum_{k in segment n} sum_alpha 4 df |h_alpha|^2 / S_alpha
+ *   x_{p,n}  = max_phi Re{z e^{-i phi}} = |z_{p,n}|
+ *   Upsilon_N(p) = sum_n x_{p,n}^2 / hh_{p,n}      (terms with hh = 0 add 0)
+ *
+ * with h_alpha the (2,2)-mode frequency-domain inspiral (circular TaylorF2
+ * to 2PN) times the LISA TDI A/E transfer function at t = t(f) (Sec. IV).
+ *
+ * Conventions shared by all calls
+ *  - Every function returns 0 (SCS_OK) or a negative SCS_E* code; the text
+ *    of the last error of a context is returned by scs_last_error().
+ *  - Pointers may be host or device memory; the library detects which with
+ *    cudaPointerGetAttributes.  Host arrays are copied and the call returns
+ *    after the result has been copied back (synchronous); when every array
+ *    of a call is device memory the call is asynchronous on the given stream.
+ *  - A context is bound to one device and is not thread-safe.
+ *  - Particle layout: params is row-major P x 8:
+ *      {Mc [Msun, detector frame], q = m1/m2 >= 1, f0 [Hz, GW frequency at
+ *       t = 0, the start of the observation], lambda, beta [ecliptic
+ *       longitude/latitude, rad], iota [inclination, rad], psi
+ *       [polarisation, rad], e0 [initial eccentricity; must be 0]}.
+ *  - Non-physical particles (Mc <= 0, q < 1, f0 <= 0, a non-finite entry,
+ *    e0 != 0, or f0 already past the last stable orbit v = 6^{-1/2}) get
+ *    stat = -inf; a particle whose support misses the data band gets 0.
+ *  - Support of a particle: grid bins k with f_k >= f0, t(f_k) <= T_obs and
+ *    v(f_k) <= 6^{-1/2}.
+ */
+#ifndef SCSTAT_H
+#define SCSTAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SCS_OK 0
+#define SCS_EINVAL (-1)       /* bad argument (size, pointer, value) */
+#define SCS_ENOMEM (-2)       /* device allocation failed */
+#define SCS_ECUDA (-3)        /* a CUDA runtime call or kernel failed */
+#define SCS_ENODATA (-4)      /* stream has no data or no segments yet */
+#define SCS_ETIMEOUT (-5)     /* a bounded device-side wait gave up */
+#define SCS_EUNSUPPORTED (-6) /* valid request the library does not do */
+
+/* evaluation paths */
+#define SCS_FP64 0   /* every bin in FP64, double-double phase */
+#define SCS_MIXED 1  /* FP64 anchors + FP32 split-phase bins, Kahan sums */
+
+/* segmentations */
+#define SCS_EQUAL_WIDTH 0 /* n-th edge floor(n K / N) over the whole grid */
+#define SCS_EQUAL_SNR2 1  /* equal squared SNR per segment, per particle */
+
+typedef struct scs_ctx scs_ctx; /* opaque, owned by the library */
+
+/* Create a context on CUDA device `device` using evaluation path `path`
+ * (SCS_FP64 or SCS_MIXED).  *out receives the context (NULL on failure).
+ * Errors: SCS_EINVAL (bad device/path/out), SCS_ECUDA, SCS_ENOMEM. */
+int scs_create(scs_ctx **out, int device, int path);
+
+/* Release every device buffer of the context.  NULL is ignored. */
+void scs_destroy(scs_ctx *ctx);
+
+/* NUL-terminated text of the last error on this context (owned by the
+ * context, valid until the next call on it). */
+const char *scs_last_error(const scs_ctx *ctx);
+
+/* Switch the evaluation path of later calls (SCS_FP64 or SCS_MIXED). */
+int scs_set_path(scs_ctx *ctx, int path);
+
+/* Load one data stream (Sec. II.A: data d_alpha on the FFT grid with
+ * one-sided PSD S_alpha; Sec. IV: grid f_k = f_first + k df, k = 0..K-1,
+ * df = 1/T_obs).
+ *   stream_id  0 <= stream_id < 1024, slot to (re)fill.
+ *   A, E       K complex values each, interleaved (re, im), FP64.
+ *   S_A, S_E   K one-sided PSD values each (> 0, finite); S_E may be NULL
+ *              (then S_E = S_A).
+ *   f_first, df, K, T_obs   grid; requires K >= 1, df > 0, f_first > 0 and
+ *              |df T_obs - 1| <= 1e-12.
+ * The library copies and pre-whitens the data (d~ = 4 df d / S,
+ * w = 4 df / S) in FP64 and FP32; the caller keeps ownership of its
+ * buffers and may free them on return.  Any segmentation previously set on
+ * the stream is kept if N <= K.
+ * Errors: SCS_EINVAL (sizes, non-positive or non-finite PSD), SCS_ENOMEM,
+ * SCS_ECUDA. */
+int scs_set_data(scs_ctx *ctx, int stream_id, const double *A, const double *E,
+                 const double *S_A, const double *S_E, double f_first,
+                 double df, int64_t K, double T_obs);
+
+/* Choose the segmentation of a stream (Sec. II.B): N segments, 1 <= N <= K,
+ * mode SCS_EQUAL_WIDTH (edges floor(n K/N) shared by all particles) or
+ * SCS_EQUAL_SNR2 (per particle: the cumulative template power
+ * sum_alpha w |h_alpha|^2, evaluated exactly on the anchor bins
+ * k_lo, k_lo + 1024, ..., k_hi and integrated by the trapezoid rule, is cut
+ * at n/N of its total by linear inverse interpolation; bin k belongs to
+ * segment n iff kappa_n <= k < kappa_{n+1}).
+ * Errors: SCS_EINVAL, SCS_ENODATA (no data on the stream). */
+int scs_set_segments(scs_ctx *ctx, int stream_id, int N, int mode);
+
+/* Evaluate Upsilon_N for P particles on one stream (Sec. II.B).
+ *   params   P x 8 doubles (layout above), host or device.
+ *   P        number of particles, 1 <= P <= 2^24.
+ *   stat     P doubles: Upsilon_N per particle.
+ *   seg_x    NULL, or P x N doubles: x_{p,n} = |z_{p,n}| (row-major).
+ *   seg_hh   NULL, or P x N doubles: hh_{p,n} = [h|h]_n.
+ *   cuda_stream  cudaStream_t to run on (NULL: the context's stream).
+ * Errors: SCS_EINVAL, SCS_ENODATA, SCS_ENOMEM, SCS_ECUDA, SCS_ETIMEOUT. */
+int scs_eval_stat(scs_ctx *ctx, int stream_id, const double *params,
+                  int64_t P, double *stat, double *seg_x, double *seg_hh,
+                  void *cuda_stream);
+
+/* Template h_A, h_E (Sec. IV: h_alpha = T_alpha(theta, f) A(f) e^{-i Psi(f)},
+ * A(f) = f^{-7/6}) of one particle on the stream's grid, FP64, complex
+ * interleaved, zero outside the support.
+ *   theta  8 doubles; hA, hE  2K doubles each (host or device).
+ * Errors: SCS_EINVAL (also for a non-physical theta), SCS_ENODATA,
+ * SCS_ECUDA. */
+int scs_waveform(scs_ctx *ctx, int stream_id, const double *theta, double *hA,
+                 double *hE, void *cuda_stream);
+
+/* Add an injection to the loaded data of a stream: d += snr h/sqrt(<h|h>)
+ * with h the template of theta (Sec. IV: injected signals scaled to a target
+ * SNR).  *hh_out (may be NULL) receives <h|h> of the un-normalised
+ * template.  Synchronous.
+ * Errors: SCS_EINVAL, SCS_ENODATA, SCS_ECUDA. */
+int scs_inject(scs_ctx *ctx, int stream_id, const double *theta, double snr,
+               double *hh_out);
+
+/* Support and anchor stride of P particles (diagnostics): k_lo[P], k_hi[P]
+ * (k_hi < k_lo: empty; both -1: non-physical) and log2 of the anchor
+ * stride of the mixed path (may be NULL).  Host or device pointers. */
+int scs_support(scs_ctx *ctx, int stream_id, const double *params, int64_t P,
+                int64_t *k_lo, int64_t *k_hi, int32_t *log2_stride,
+                void *cuda_stream);
+
+/* Segment edges of P particles under the stream's segmentation: e[P x (N+1)]
+ * with segment n = [e_n, e_{n+1}) in grid bins (int64, host or device). */
+int scs_segment_edges(scs_ctx *ctx, int stream_id, const double *params,
+                      int64_t P, int64_t *edges, void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SCSTAT_H */

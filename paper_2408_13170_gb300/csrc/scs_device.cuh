@@ -1,0 +1,362 @@
+// scs_device.cuh -- device-side model of the semi-coherent statistic
+// (arXiv:2408.13170): particle derivation, waveform phase, LISA response.
+//
+// Everything here is written for sm_103a.  FP64 appears only where the
+// accuracy needs it (the absolute inspiral phase, t(f), anchors); the
+// per-bin work of the mixed path is FP32 (see scs_mixed.cu).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace scs {
+
+// ---------------------------------------------------------------- constants
+constexpr double kTsun = 4.925490947641267e-6;             // G Msun / c^3 [s]
+constexpr double kC = 299792458.0;
+constexpr double kArm = 2.5e9 / kC;                         // L [s]
+constexpr double kAU = 149597870700.0 / kC;                 // R [s]
+constexpr double kOmega = 6.283185307179586476925 / 3.15581497632e7;  // orbit
+constexpr double kPi = 3.141592653589793116;
+constexpr double kPiLo = 1.224646799147353207e-16;
+constexpr double kTwoPi = 6.283185307179586232;
+constexpr double kIscoV3 = 0.06804138174397717;             // 6^{-3/2}
+constexpr int kMaxLog2B = 12;                               // anchor stride <= 4096
+constexpr int kChunk = 4096;                                // bins per work chunk
+constexpr int kSnr2Stride = 1024;                           // equal-SNR^2 anchor grid
+
+enum : int { kOk = 0, kInvalid = 1, kEmpty = 2 };
+
+// ---------------------------------------------------------- double-double
+// Error-free transformations (Knuth two-sum, FMA two-product); explicit _rn
+// intrinsics keep nvcc from contracting them.
+struct dd {
+  double hi, lo;
+};
+__host__ __device__ inline dd mkdd(double h, double l = 0.0) { return dd{h, l}; }
+
+__device__ inline dd dd_two_sum(double a, double b) {
+  double s = __dadd_rn(a, b);
+  double bb = __dsub_rn(s, a);
+  double err = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
+  return dd{s, err};
+}
+__device__ inline dd dd_fast(double a, double b) {
+  double s = __dadd_rn(a, b);
+  return dd{s, __dsub_rn(b, __dsub_rn(s, a))};
+}
+__device__ inline dd dd_prod(double a, double b) {
+  double p = __dmul_rn(a, b);
+  return dd{p, __fma_rn(a, b, -p)};
+}
+__device__ inline dd operator+(dd a, dd b) {
+  dd s = dd_two_sum(a.hi, b.hi);
+  dd t = dd_two_sum(a.lo, b.lo);
+  s = dd_fast(s.hi, __dadd_rn(s.lo, t.hi));
+  return dd_fast(s.hi, __dadd_rn(s.lo, t.lo));
+}
+__device__ inline dd operator-(dd a) { return dd{-a.hi, -a.lo}; }
+__device__ inline dd operator-(dd a, dd b) { return a + (-b); }
+__device__ inline dd operator*(dd a, dd b) {
+  dd p = dd_prod(a.hi, b.hi);
+  double c = __fma_rn(a.hi, b.lo, __dmul_rn(a.lo, b.hi));
+  return dd_fast(p.hi, __dadd_rn(p.lo, c));
+}
+__device__ inline dd operator*(dd a, double b) {
+  dd p = dd_prod(a.hi, b);
+  return dd_fast(p.hi, __fma_rn(a.lo, b, p.lo));
+}
+__device__ inline dd dd_div(dd a, dd b) {
+  double q1 = __ddiv_rn(a.hi, b.hi);
+  dd r = a - b * q1;
+  double q2 = __ddiv_rn(r.hi, b.hi);
+  r = r - b * q2;
+  double q3 = __ddiv_rn(r.hi, b.hi);
+  return dd_fast(q1, q2) + mkdd(q3);
+}
+__device__ inline double dd_val(dd a) { return a.hi + a.lo; }
+// x^{-1/3}: double estimate refined by one Newton step on u^3 x = 1
+__device__ inline dd dd_rcbrt(dd x) {
+  double u0 = rcbrt(x.hi);
+  dd u = mkdd(u0);
+  dd r = mkdd(1.0) - (u * u) * u * x;
+  return u + u * r * (1.0 / 3.0);
+}
+// f_k = f_first + k df exactly
+__device__ inline dd grid_freq_dd(double f_first, double df, int64_t k) {
+  return dd_prod((double)k, df) + mkdd(f_first);
+}
+
+// ------------------------------------------------------------- the particle
+// Phase in turns: F(f) = Psi(f)/(2 pi) = t_c f - 1/8 + sum_k A_k u^{n_k},
+// u = f^{-1/3}, n = {5, 3, 2, 1} for PN orders k = {0, 2, 3, 4}.  Then
+// d u^n / df = -(n/3) u^{n+3}, so t(f) = F'(f) = t_c - u^3 sum (n_k/3) A_k u^{n_k}.
+struct Part {
+  int status;
+  int k_lo, k_hi;   // support in grid bins (k_hi < k_lo: empty)
+  int log2B;        // mixed-path anchor stride
+  double f0;
+  double piMs;      // pi G M / c^3 [s]
+  dd tc;            // coalescence time [s]
+  dd A[4];          // PN phase coefficients for u^5, u^3, u^2, u^1 [turns]
+  double kx, ky, kz;            // propagation direction
+  double Pr[6], Pi[6];          // polarisation tensor xx, yy, zz, xy, xz, yz
+  double Rcb, lam;              // R cos(beta) [s], lambda
+  float Pr32[6], Pi32[6], k32[3];   // FP32 copies for the mixed path
+};
+
+__device__ constexpr int kPow[4] = {5, 3, 2, 1};
+
+// FP64 t(f) (accurate to ~1e-8 s; enough for the response and the support)
+__device__ inline double time_of_freq(const Part& p, double f) {
+  double u = rcbrt(f);
+  double u2 = u * u;
+  double s = u * (-(1.0 / 3.0) * p.A[3].hi +
+                  u * (-(2.0 / 3.0) * p.A[2].hi +
+                       u * (-p.A[1].hi + u2 * (-(5.0 / 3.0) * p.A[0].hi))));
+  return p.tc.hi + (p.tc.lo + u2 * u * s);
+}
+
+// Derive a particle from theta (8 doubles).  Support is not set here.
+__device__ inline void part_init(Part& p, const double* th) {
+  p.status = kInvalid;
+  p.k_lo = 0;
+  p.k_hi = -1;
+  p.log2B = 0;
+  bool fin = true;
+  for (int i = 0; i < 8; ++i) fin = fin && isfinite(th[i]);
+  double Mc = th[0], q = th[1], f0 = th[2];
+  p.f0 = f0;
+  if (!fin || !(Mc > 0.0) || !(q >= 1.0) || !(f0 > 0.0) || th[7] != 0.0) return;
+  // eta = q/(1+q)^2 ; M = Mc eta^{-3/5}
+  dd onepq = dd_two_sum(1.0, q);
+  dd eta = dd_div(mkdd(q), onepq * onepq);
+  // eta^{-3/5}: Newton on y^5 eta^3 = 1
+  dd y = mkdd(pow(eta.hi, -0.6));
+  dd e3 = eta * eta * eta;
+  {
+    dd y2 = y * y;
+    dd r = mkdd(1.0) - y2 * y2 * y * e3;
+    y = y + y * r * 0.2;
+  }
+  dd Ms = y * Mc * kTsun;
+  dd piMs = Ms * mkdd(kPi, kPiLo);
+  p.piMs = dd_val(piMs);
+  if (p.piMs * f0 > kIscoV3) return;   // already past the last stable orbit
+  // c = (pi Ms)^{-1/3};  v^{k-5} = c^{5-k} u^{5-k}
+  dd c = dd_rcbrt(piMs);
+  dd c2 = c * c, c3 = c2 * c, c5 = c3 * c2;
+  // phi_k (TaylorF2, circular, 2PN)
+  dd phi0 = mkdd(1.0);
+  dd phi2 = dd_div(mkdd(3715.0), mkdd(756.0)) + dd_div(mkdd(55.0), mkdd(9.0)) * eta;
+  dd phi3 = mkdd(kPi, kPiLo) * -16.0;
+  dd phi4 = dd_div(mkdd(15293365.0), mkdd(508032.0)) +
+            dd_div(mkdd(27145.0), mkdd(504.0)) * eta +
+            dd_div(mkdd(3085.0), mkdd(72.0)) * (eta * eta);
+  // 3/(256 pi eta)
+  dd pre = dd_div(mkdd(3.0), mkdd(kPi, kPiLo) * 256.0 * eta);
+  p.A[0] = pre * phi0 * c5;
+  p.A[1] = pre * phi2 * c3;
+  p.A[2] = pre * phi3 * c2;
+  p.A[3] = pre * phi4 * c;
+  // t_c: t(f0) = 0  =>  t_c = u0^3 sum (n_k/3) A_k u0^{n_k}
+  dd u0 = dd_rcbrt(mkdd(f0));
+  dd u02 = u0 * u0;
+  dd s = u0 * (dd_div(p.A[3], mkdd(3.0)) +
+            u0 * (dd_div(p.A[2] * 2.0, mkdd(3.0)) +
+                  u0 * (p.A[1] + u02 * dd_div(p.A[0] * 5.0, mkdd(3.0)))));
+  p.tc = u02 * u0 * s;
+  // sky and polarisation
+  double lam = th[3], bet = th[4], inc = th[5], psi = th[6];
+  double cb = cos(bet), sb = sin(bet), cl = cos(lam), sl = sin(lam);
+  p.kx = -cb * cl;
+  p.ky = -cb * sl;
+  p.kz = -sb;
+  double u[3] = {sl, -cl, 0.0};
+  double v[3] = {-sb * cl, -sb * sl, cb};
+  double c2p = cos(2.0 * psi), s2p = sin(2.0 * psi);
+  double ap = 0.5 * (1.0 + cos(inc) * cos(inc)), ax = cos(inc);
+  const int ii[6] = {0, 1, 2, 0, 0, 1}, jj[6] = {0, 1, 2, 1, 2, 2};
+  for (int m = 0; m < 6; ++m) {
+    int i = ii[m], j = jj[m];
+    double ep = u[i] * u[j] - v[i] * v[j];
+    double ex = u[i] * v[j] + v[i] * u[j];
+    p.Pr[m] = ap * (c2p * ep + s2p * ex);
+    p.Pi[m] = -ax * (-s2p * ep + c2p * ex);
+  }
+  p.Rcb = kAU * cb;
+  p.lam = lam;
+  for (int m = 0; m < 6; ++m) {
+    p.Pr32[m] = (float)p.Pr[m];
+    p.Pi32[m] = (float)p.Pi[m];
+  }
+  p.k32[0] = (float)p.kx;
+  p.k32[1] = (float)p.ky;
+  p.k32[2] = (float)p.kz;
+  p.status = kOk;
+}
+
+// Support [k_lo, k_hi] on the grid (same rules as the definition: f_k >= f0,
+// pi M f_k <= 6^{-3/2}, t(f_k) <= T_obs; t and M f increase with f).
+__device__ inline void part_support(Part& p, double f_first, double df, int64_t K,
+                                    double T_obs) {
+  if (p.status != kOk) return;
+  double g = ceil((p.f0 - f_first) / df);
+  int64_t k = g < 0.0 ? 0 : (g > (double)K ? K : (int64_t)g);
+  while (k > 0 && (grid_freq_dd(f_first, df, k - 1) - mkdd(p.f0)).hi >= 0.0) --k;
+  while (k < K && (grid_freq_dd(f_first, df, k) - mkdd(p.f0)).hi < 0.0) ++k;
+  int64_t lo = k;
+  auto inb = [&](int64_t kk) {
+    double f = dd_val(grid_freq_dd(f_first, df, kk));
+    return p.piMs * f <= kIscoV3 && time_of_freq(p, f) <= T_obs;
+  };
+  int64_t hi = lo - 1;
+  if (lo < K && inb(lo)) {
+    int64_t good = lo, bad = K;
+    while (bad - good > 1) {
+      int64_t mid = good + (bad - good) / 2;
+      if (inb(mid)) good = mid; else bad = mid;
+    }
+    hi = good;
+  }
+  p.k_lo = (int)lo;
+  p.k_hi = (int)hi;
+  if (hi < lo) p.status = kEmpty;
+}
+
+// ------------------------------------------------------------ the response
+// Residual transfer functions: the TDI A, E response of the rigid-adiabatic
+// link model with the guiding-centre Doppler factor e^{-2 pi i f k.p0(t)}
+// taken out (it is carried by the phase).  With delta_i = p_i - p0:
+//   G~_{s->r} = -i pi f L sinc(pi f L (1 - k.n)) e^{-i pi f (L + k.(d_s + d_r))} n.P.n
+//   X = (1 - D^2)[(G31 + D G13) - (G21 + D G12)], Y, Z cyclic, D = e^{-2 pi i f L}
+//   A = (Z - X)/sqrt2, E = (X - 2Y + Z)/sqrt6.
+template <typename T>
+struct Cx {
+  T re, im;
+};
+template <typename T>
+__device__ inline Cx<T> cmul(Cx<T> a, Cx<T> b) {
+  return Cx<T>{a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename T>
+__device__ inline Cx<T> cadd(Cx<T> a, Cx<T> b) { return Cx<T>{a.re + b.re, a.im + b.im}; }
+template <typename T>
+__device__ inline Cx<T> csub(Cx<T> a, Cx<T> b) { return Cx<T>{a.re - b.re, a.im - b.im}; }
+
+__device__ inline void sc_(double x, double* s, double* c) { sincos(x, s, c); }
+__device__ inline void sc_(float x, float* s, float* c) { sincosf(x, s, c); }
+__device__ inline double sin_(double x) { return sin(x); }
+__device__ inline float sin_(float x) { return sinf(x); }
+
+// ca, sa: cos/sin of the orbital angle alpha = Omega t (any precision T);
+// f in Hz; P: polarisation tensor (re/im of xx,yy,zz,xy,xz,yz); k: direction.
+template <typename T>
+__device__ inline void response_residual(T f, T ca, T sa, const T* Pr, const T* Pi,
+                                         const T* kv, Cx<T>& RA, Cx<T>& RE) {
+  const T L = (T)kArm;
+  const T eR2 = (T)(kArm / (4.0 * 1.7320508075688772));   // e R / 2 = L/(4 sqrt3)
+  const T s3 = (T)1.7320508075688772;
+  // cos/sin of 2 alpha
+  T c2a = ca * ca - sa * sa, s2a = (T)2 * ca * sa;
+  // craft offsets from the centre, beta_i = 0, 2pi/3, 4pi/3
+  const T cb[3] = {(T)1, (T)-0.5, (T)-0.5};
+  const T sbv[3] = {(T)0, (T)0.8660254037844386, (T)-0.8660254037844386};
+  T d[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    T c2 = c2a * cb[i] + s2a * sbv[i];     // cos(2a - b)
+    T s2 = s2a * cb[i] - c2a * sbv[i];     // sin(2a - b)
+    T c1 = ca * cb[i] + sa * sbv[i];       // cos(a - b)
+    d[i][0] = eR2 * (c2 - (T)3 * cb[i]);
+    d[i][1] = eR2 * (s2 - (T)3 * sbv[i]);
+    d[i][2] = -(T)2 * s3 * eR2 * c1;
+  }
+  const T pfl = (T)kPi * f * L;
+  // links on the three arms; G[s][r] for s != r
+  Cx<T> G[3][3];
+  const int as[3] = {0, 0, 1}, ar[3] = {1, 2, 2};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    int s = as[a], r = ar[a];
+    T n0 = (d[r][0] - d[s][0]) / L, n1 = (d[r][1] - d[s][1]) / L, n2 = (d[r][2] - d[s][2]) / L;
+    T kn = kv[0] * n0 + kv[1] * n1 + kv[2] * n2;
+    T kd = kv[0] * (d[s][0] + d[r][0]) + kv[1] * (d[s][1] + d[r][1]) + kv[2] * (d[s][2] + d[r][2]);
+    T q0 = n0 * n0, q1 = n1 * n1, q2 = n2 * n2, q3 = (T)2 * n0 * n1, q4 = (T)2 * n0 * n2,
+      q5 = (T)2 * n1 * n2;
+    Cx<T> nPn{Pr[0] * q0 + Pr[1] * q1 + Pr[2] * q2 + Pr[3] * q3 + Pr[4] * q4 + Pr[5] * q5,
+              Pi[0] * q0 + Pi[1] * q1 + Pi[2] * q2 + Pi[3] * q3 + Pi[4] * q4 + Pi[5] * q5};
+    T sph, cph;
+    sc_(-(T)kPi * f * (L + kd), &sph, &cph);
+    Cx<T> ph{cph, sph};
+    // s -> r uses n, r -> s uses -n
+    T xf = pfl * ((T)1 - kn), xb = pfl * ((T)1 + kn);
+    T sincf = xf == (T)0 ? (T)1 : sin_(xf) / xf;
+    T sincb = xb == (T)0 ? (T)1 : sin_(xb) / xb;
+    Cx<T> base = cmul(ph, nPn);
+    // -i * pfl * sinc * base
+    G[s][r] = Cx<T>{pfl * sincf * base.im, -pfl * sincf * base.re};
+    G[r][s] = Cx<T>{pfl * sincb * base.im, -pfl * sincb * base.re};
+  }
+  T sD, cD;
+  sc_(-(T)2 * (T)kPi * f * L, &sD, &cD);
+  Cx<T> D{cD, sD};
+  Cx<T> D2 = cmul(D, D);
+  Cx<T> W{(T)1 - D2.re, -D2.im};
+  auto arm = [&](int a, int b, int c) {   // vertex a, far craft b (first), c
+    Cx<T> t1 = cadd(G[c][a], cmul(D, G[a][c]));
+    Cx<T> t2 = cadd(G[b][a], cmul(D, G[a][b]));
+    return cmul(W, csub(t1, t2));
+  };
+  Cx<T> X = arm(0, 1, 2), Y = arm(1, 2, 0), Z = arm(2, 0, 1);
+  const T is2 = (T)0.70710678118654752, is6 = (T)0.40824829046386302;
+  RA = Cx<T>{(Z.re - X.re) * is2, (Z.im - X.im) * is2};
+  RE = Cx<T>{(X.re - (T)2 * Y.re + Z.re) * is6, (X.im - (T)2 * Y.im + Z.im) * is6};
+}
+
+// orbital angle reduced to [-pi, pi] in FP64
+__device__ inline double orbit_angle(double t) {
+  double a = kOmega * t;
+  return a - kTwoPi * rint(a * (1.0 / kTwoPi));
+}
+
+// Guiding-centre Doppler delay k.p0(t) = -R cos(beta) cos(Omega t - lambda)
+__device__ inline double doppler_delay(const Part& p, double t) {
+  return -p.Rcb * cos(kOmega * t - p.lam);
+}
+
+// ------------------------------------------------------ per-bin FP64 model
+// Reduced total phase (turns, in [-1/2, 1/2)) of bin f (dd) together with
+// t(f): Phi = F(f) + f k.p0(t(f)); the large F is summed in double-double.
+__device__ inline double phase_turns_fp64(const Part& p, dd f, double& t_out) {
+  dd u = dd_rcbrt(f);
+  dd u2 = u * u;
+  dd Fp = u * (p.A[3] + u * (p.A[2] + u * (p.A[1] + u2 * p.A[0])));
+  dd F = f * p.tc + Fp - mkdd(0.125);
+  double n = rint(F.hi);
+  double fr = dd_val(F - mkdd(n));
+  double fd = dd_val(f);
+  double t = time_of_freq(p, fd);
+  t_out = t;
+  double tot = fr + fd * doppler_delay(p, t);
+  return tot - rint(tot);
+}
+
+// Full per-bin FP64 template factors: G_alpha = f^{-7/6} R_alpha (residual
+// response) and the total phase Phi, so that h_alpha = G_alpha e^{-2 pi i Phi}.
+__device__ inline void bin_fp64(const Part& p, double f_first, double df, int64_t k,
+                                Cx<double>& GA, Cx<double>& GE, double& phi) {
+  dd f = grid_freq_dd(f_first, df, k);
+  double t;
+  phi = phase_turns_fp64(p, f, t);
+  double fd = dd_val(f);
+  double sa, ca;
+  sincos(orbit_angle(t), &sa, &ca);
+  const double kv[3] = {p.kx, p.ky, p.kz};
+  Cx<double> RA, RE;
+  response_residual<double>(fd, ca, sa, p.Pr, p.Pi, kv, RA, RE);
+  double amp = pow(fd, -7.0 / 6.0);
+  GA = Cx<double>{amp * RA.re, amp * RA.im};
+  GE = Cx<double>{amp * RE.re, amp * RE.im};
+}
+
+}  // namespace scs

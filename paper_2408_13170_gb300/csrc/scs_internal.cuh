@@ -1,0 +1,108 @@
+// scs_internal.cuh -- structures shared by the host code and the kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "scs_device.cuh"
+
+namespace scs {
+
+// Partial sums of one (particle, chunk) work unit.  A chunk is kChunk grid
+// bins; a particle's segments may straddle chunk edges, so each unit reports
+// the segment its first support bin of the chunk falls in (head), the one
+// its last bin falls in (tail, if different), and the statistic of all
+// segments that start and end inside the chunk.
+struct Rec {
+  int n_head, n_tail;            // segment indices, -1: none
+  double zr_h, zi_h, hh_h;
+  double zr_t, zi_t, hh_t;
+  double ups;
+};
+
+// Everything a main kernel needs; all pointers are device memory.
+struct EvalArgs {
+  double f_first, df, T_obs;
+  int K;
+  // pre-whitened data d~ = 4 df d / S and weights w = 4 df / S
+  const float4* d32;     // (A.re, A.im, E.re, E.im)
+  const float2* w32;     // (w_A, w_E)
+  const double2* dA64;
+  const double2* dE64;
+  const double2* w64;
+  // segmentation: edges[p * edge_stride + n], n = 0..N
+  int N;
+  const int* edges;
+  int64_t edge_stride;   // 0 when all particles share one edge table
+  // particles
+  const Part* part;
+  int P;
+  // work list: chunk c holds list[list_off[c] .. list_off[c] + cnt[c]),
+  // processed by warp items item_off[c] .. item_off[c+1]
+  int n_chunks;
+  const int* cnt;
+  const int* list_off;
+  const int* list;
+  const int* item_off;   // n_chunks + 1 entries
+  const int64_t* rec_off;
+  Rec* rec;
+  int* item_counter;
+  // outputs (optional)
+  double* seg_x;
+  double* seg_hh;
+  int* err;
+};
+
+void launch_main_mixed(const EvalArgs& a, int grid, cudaStream_t s);
+void launch_main_fp64(const EvalArgs& a, int grid, cudaStream_t s);
+void launch_waveform_fp64(const Part* part, double f_first, double df, int K,
+                          double2* hA, double2* hE, cudaStream_t s);
+// resident 128-thread blocks per SM of the main kernels (0 on success)
+int occupancy_mixed(int* blocks_per_sm);
+int occupancy_fp64(int* blocks_per_sm);
+
+// chunk index of a grid bin
+__host__ __device__ inline int chunk_of(int k) { return k / kChunk; }
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kNoEdge = 0x7fffffff;
+
+__device__ inline int warp_min(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(kFull, v, o));
+  return v;
+}
+__device__ inline int warp_max(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(kFull, v, o));
+  return v;
+}
+
+// segment of bin k: the largest n in [0, N) with e[n] <= k (e non-decreasing,
+// e[0] <= k)
+__device__ inline int segment_of(const int* e, int N, int k) {
+  int lo = 0, hi = N;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (__ldg(e + mid) <= k) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// chunk of a warp item: the c with item_off[c] <= item < item_off[c + 1]
+__device__ inline int find_item_chunk(const int* item_off, int n_chunks, int item) {
+  int lo = 0, hi = n_chunks;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (__ldg(item_off + mid) <= item) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// after closing segment n at bin k (a boundary), the segment bin k is in
+__device__ inline int advance_segment(const int* e, int N, int n, int k) {
+  ++n;
+  while (n + 1 <= N && __ldg(e + n + 1) <= k) ++n;
+  return n;
+}
+
+}  // namespace scs

@@ -1,0 +1,408 @@
+// scs_setup.cu -- per-call preparation kernels: particle derivation and
+// support, the mixed path's anchor stride, equal-SNR^2 segment edges, the
+// chunk work list, the cross-chunk fix-up, and data pre-whitening.
+#include "scs_anchor.cuh"
+#include "scs_internal.cuh"
+#include "scs_setup.cuh"
+
+namespace scs {
+
+namespace {
+
+// ---------------------------------------------------------- anchor stride
+// Largest power-of-two stride B <= kChunk for which the degree-4 phase
+// polynomial stays within kTolPhase turns and the quadratic G within
+// kTolG (relative) of the exact FP64 model, checked at three spans of the
+// support (first, middle, last) and three offsets per span.
+constexpr double kTolPhase = 2e-8;   // turns
+constexpr double kTolG = 3e-7;       // relative to |G_A| + |G_E|
+
+__device__ bool span_ok(const Part& p, int B, int ka, double f_first, double df) {
+  Anchor an;
+  anchor_build(p, ka, B, f_first, df, an);
+  double fa = f_first + (double)ka * df;
+  int jlo = max(0, p.k_lo - ka), jhi = min(B - 1, p.k_hi - ka);
+  if (jhi < jlo) return true;
+  const int js[3] = {B / 4, (3 * B) / 4, B - 1};
+  for (int t = 0; t < 3; ++t) {
+    int j = min(max(js[t], jlo), jhi);
+    int k = ka + j;
+    Cx<double> GA, GE;
+    double phi;
+    bin_fp64(p, f_first, df, k, GA, GE, phi);
+    double pj = anchor_poly_turns(p, fa, df, (double)j);
+    double dphi = pj - phi;
+    dphi -= rint(dphi);
+    if (!(fabs(dphi) <= kTolPhase)) return false;
+    float jf = (float)j;
+    double q[4];
+    for (int c = 0; c < 4; ++c) q[c] = fmaf(jf, fmaf(jf, an.g2[c], an.g1[c]), an.g0[c]);
+    double err = fabs(q[0] - GA.re) + fabs(q[1] - GA.im) + fabs(q[2] - GE.re) + fabs(q[3] - GE.im);
+    double mag = hypot(GA.re, GA.im) + hypot(GE.re, GE.im);
+    if (!(err <= kTolG * mag)) return false;
+  }
+  return true;
+}
+
+__device__ int choose_log2B(const Part& p, double f_first, double df) {
+  // analytic start: Taylor remainder of the PN phase and of the Doppler
+  // phase at the low end of the support (where both are largest)
+  double flo = f_first + (double)p.k_lo * df;
+  double fhi = f_first + (double)p.k_hi * df;
+  double u = rcbrt(flo), u3 = u * u * u;
+  double d5 = 0.0, tp = 0.0;
+  double upow[4] = {u3 * u * u, u3, u * u, u};
+  for (int m = 0; m < 4; ++m) {
+    double n = (double)kPow[m];
+    double val = p.A[m].hi * upow[m];
+    for (int r = 0; r < 5; ++r) {
+      if (r == 2) tp += val;   // F'' = dt/df
+      val *= -(n + 3.0 * r) * (1.0 / 3.0) * u3;
+    }
+    d5 += val;
+  }
+  double Bpn = pow(120.0 * 0.5 * kTolPhase / fmax(fabs(d5), 1e-300), 0.2) / df;
+  double x = pow(120.0 * 0.5 * kTolPhase / (fhi * p.Rcb + 1e-30), 0.2);
+  double Bdop = x / (kOmega * fabs(tp) * df + 1e-300);
+  double Bs = fmin(fmin(Bpn, Bdop), (double)kChunk);
+  int l = 0;
+  while (l < kMaxLog2B && (double)(2 << l) <= Bs) ++l;
+  for (; l > 0; --l) {
+    int B = 1 << l;
+    int k0 = (p.k_lo / B) * B, k2 = (p.k_hi / B) * B;
+    int k1 = (((p.k_lo + p.k_hi) / 2) / B) * B;
+    if (span_ok(p, B, k0, f_first, df) && span_ok(p, B, k1, f_first, df) &&
+        span_ok(p, B, k2, f_first, df))
+      break;
+  }
+  return l;
+}
+
+}  // namespace
+
+// One thread per particle: derive, find the support, choose the stride,
+// count the chunks the particle touches.
+__global__ void k_setup(const double* params, int P, double f_first, double df, int K,
+                        double T_obs, int want_stride, Part* part, int2* crange,
+                        int64_t* nrec, int* diff) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P) return;
+  Part p;
+  part_init(p, params + 8 * (int64_t)i);
+  part_support(p, f_first, df, K, T_obs);
+  int2 cr = make_int2(0, -1);
+  if (p.status == kOk) {
+    if (want_stride) p.log2B = choose_log2B(p, f_first, df);
+    cr = make_int2(chunk_of(p.k_lo), chunk_of(p.k_hi));
+    atomicAdd(diff + cr.x, 1);
+    atomicAdd(diff + cr.y + 1, -1);
+  }
+  part[i] = p;
+  crange[i] = cr;
+  nrec[i] = cr.y - cr.x + 1;
+}
+
+// Single-block exclusive scan of n int64 values in place; total in *total.
+__global__ void k_scan64(int64_t* v, int64_t n, int64_t* total) {
+  __shared__ int64_t part[1024];
+  int t = threadIdx.x;
+  int64_t per = (n + 1023) / 1024;
+  int64_t b = t * per, e = min(n, b + per);
+  int64_t s = 0;
+  for (int64_t i = b; i < e; ++i) s += v[i];
+  part[t] = s;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    int64_t x = t >= o ? part[t - o] : 0;
+    __syncthreads();
+    part[t] += x;
+    __syncthreads();
+  }
+  int64_t run = part[t] - s;
+  for (int64_t i = b; i < e; ++i) {
+    int64_t x = v[i];
+    v[i] = run;
+    run += x;
+  }
+  if (t == 1023) *total = part[1023];
+}
+
+// Chunk table from the difference array: active counts, list offsets and
+// warp-item offsets (single block).
+__global__ void k_chunk_table(const int* diff, int n_chunks, int* cnt, int* list_off,
+                              int* item_off) {
+  __shared__ int s_cnt[1024], s_items[1024];
+  int t = threadIdx.x;
+  int per = (n_chunks + 1023) / 1024;
+  int b = t * per, e = min(n_chunks, b + per);
+  // pass 1: local sums of diff (-> counts need a prefix over diff)
+  int sd = 0;
+  for (int i = b; i < e; ++i) sd += diff[i];
+  s_cnt[t] = sd;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    int x = t >= o ? s_cnt[t - o] : 0;
+    __syncthreads();
+    s_cnt[t] += x;
+    __syncthreads();
+  }
+  int c_run = s_cnt[t] - sd;   // count at chunk b-1 level prefix
+  int lsum = 0, isum = 0;
+  for (int i = b; i < e; ++i) {
+    c_run += diff[i];
+    cnt[i] = c_run;
+    lsum += c_run;
+    isum += (c_run + 31) / 32;
+  }
+  __syncthreads();
+  s_cnt[t] = lsum;
+  s_items[t] = isum;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    int x = t >= o ? s_cnt[t - o] : 0;
+    int y = t >= o ? s_items[t - o] : 0;
+    __syncthreads();
+    s_cnt[t] += x;
+    s_items[t] += y;
+    __syncthreads();
+  }
+  int lo = s_cnt[t] - lsum, io = s_items[t] - isum;
+  for (int i = b; i < e; ++i) {
+    list_off[i] = lo;
+    item_off[i] = io;
+    lo += cnt[i];
+    io += (cnt[i] + 31) / 32;
+  }
+  if (t == 1023) {
+    list_off[n_chunks] = s_cnt[1023];
+    item_off[n_chunks] = s_items[1023];
+  }
+}
+
+__global__ void k_fill(const int2* crange, int P, const int* list_off, int* fill, int* list) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P) return;
+  int2 cr = crange[i];
+  for (int c = cr.x; c <= cr.y; ++c) {
+    int pos = atomicAdd(fill + c, 1);
+    list[list_off[c] + pos] = i;
+  }
+}
+
+// Equal-SNR^2 edges (one warp per particle).  The cumulative template power
+// is the trapezoid sum over the anchor bins k_lo, k_lo + 1024, ..., k_hi of
+// hh(k) = sum_alpha w_alpha(k) |h_alpha(f_k)|^2, evaluated exactly in FP64;
+// target c_n = n C/N; kappa_n by linear inverse interpolation; segment n
+// starts at bin ceil(kappa_n).  The double operations follow that order
+// explicitly (no contraction) so that the rounding is the definition's.
+__global__ void k_bounds(const Part* part, int P, double f_first, double df,
+                         const double2* w64, int N, int64_t amax, double* Hs, double* Cs,
+                         int* edges) {
+  int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (gw >= P) return;
+  const Part& p = part[gw];
+  int* e = edges + (int64_t)gw * (N + 1);
+  if (p.status != kOk) {
+    for (int n = lane; n <= N; n += 32) e[n] = 0;
+    return;
+  }
+  int span = p.k_hi - p.k_lo;
+  int nanch = span / kSnr2Stride + 1 + (span % kSnr2Stride != 0 ? 1 : 0);
+  double* H = Hs + (int64_t)gw * amax;
+  double* C = Cs + (int64_t)gw * amax;
+  const double kv[3] = {p.kx, p.ky, p.kz};
+  for (int a = lane; a < nanch; a += 32) {
+    int ka = min(p.k_lo + a * kSnr2Stride, p.k_hi);
+    double f = dd_val(grid_freq_dd(f_first, df, ka));
+    double t = time_of_freq(p, f);
+    double sa, ca;
+    sincos(orbit_angle(t), &sa, &ca);
+    Cx<double> RA, RE;
+    response_residual<double>(f, ca, sa, p.Pr, p.Pi, kv, RA, RE);
+    double amp = pow(f, -7.0 / 6.0);
+    double2 w = w64[ka];
+    double hA = (amp * RA.re) * (amp * RA.re) + (amp * RA.im) * (amp * RA.im);
+    double hE = (amp * RE.re) * (amp * RE.re) + (amp * RE.im) * (amp * RE.im);
+    H[a] = __dadd_rn(__dmul_rn(w.x, hA), __dmul_rn(w.y, hE));
+  }
+  __syncwarp();
+  if (lane == 0) {
+    C[0] = 0.0;
+    int kprev = p.k_lo;
+    for (int a = 1; a < nanch; ++a) {
+      int ka = min(p.k_lo + a * kSnr2Stride, p.k_hi);
+      double s2 = __dadd_rn(H[a - 1], H[a]);
+      double tr = __ddiv_rn(__dmul_rn((double)(ka - kprev), s2), 2.0);
+      C[a] = __dadd_rn(C[a - 1], tr);
+      kprev = ka;
+    }
+  }
+  __syncwarp();
+  double Cl = C[nanch - 1];
+  for (int n = lane; n <= N; n += 32) {
+    int en;
+    if (n == 0) {
+      en = p.k_lo;
+    } else if (n == N) {
+      en = p.k_hi + 1;
+    } else if (!(Cl > 0.0)) {
+      en = p.k_lo;
+    } else {
+      double cn = __ddiv_rn(__dmul_rn((double)n, Cl), (double)N);
+      // first a in [1, nanch-1] with C[a] >= cn (else nanch-1)
+      int lo = 1, hi = nanch - 1;
+      while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (C[mid] >= cn) hi = mid; else lo = mid + 1;
+      }
+      int a = lo;
+      int k1 = min(p.k_lo + (a - 1) * kSnr2Stride, p.k_hi);
+      int k2 = min(p.k_lo + a * kSnr2Stride, p.k_hi);
+      double fr = __ddiv_rn(__dsub_rn(cn, C[a - 1]), __dsub_rn(C[a], C[a - 1]));
+      double kap = __dadd_rn((double)k1, __dmul_rn(fr, (double)(k2 - k1)));
+      en = (int)ceil(kap);
+    }
+    e[n] = en;
+  }
+}
+
+// Merge the (particle, chunk) records into Upsilon_N (Sec. II.B).
+__global__ void k_fixup(const Part* part, const int2* crange, const int64_t* rec_off,
+                        const Rec* rec, int P, int N, double* stat, double* seg_x,
+                        double* seg_hh) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P) return;
+  const Part& p = part[i];
+  if (p.status == kInvalid) {
+    stat[i] = -__longlong_as_double(0x7ff0000000000000LL);
+    return;
+  }
+  if (p.status == kEmpty) {
+    stat[i] = 0.0;
+    return;
+  }
+  int2 cr = crange[i];
+  double ups = 0.0;
+  int n_run = -1;
+  double zr = 0.0, zi = 0.0, hh = 0.0;
+  auto close = [&]() {
+    if (n_run < 0) return;
+    double x2 = zr * zr + zi * zi;
+    if (hh > 0.0) ups += x2 / hh;
+    if (seg_x) {
+      seg_x[(int64_t)i * N + n_run] = sqrt(x2);
+      seg_hh[(int64_t)i * N + n_run] = hh;
+    }
+  };
+  const Rec* r = rec + rec_off[i];
+  for (int c = cr.x; c <= cr.y; ++c, ++r) {
+    ups += r->ups;
+    if (r->n_head >= 0) {
+      if (r->n_head == n_run) {
+        zr += r->zr_h; zi += r->zi_h; hh += r->hh_h;
+      } else {
+        close();
+        n_run = r->n_head;
+        zr = r->zr_h; zi = r->zi_h; hh = r->hh_h;
+      }
+    }
+    if (r->n_tail >= 0) {
+      close();
+      n_run = r->n_tail;
+      zr = r->zr_t; zi = r->zi_t; hh = r->hh_t;
+    }
+  }
+  close();
+  stat[i] = ups;
+}
+
+// d~ = w d with w = 4 df / S, FP64 and FP32 copies.
+__global__ void k_prewhiten(const double2* A, const double2* E, const double* SA,
+                            const double* SE, double df, int K, double2* dA64, double2* dE64,
+                            double2* w64, float4* d32, float2* w32) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
+    double wa = 4.0 * df / SA[k];
+    double we = 4.0 * df / (SE ? SE[k] : SA[k]);
+    double2 a = A[k], e = E[k];
+    double2 da = make_double2(wa * a.x, wa * a.y), de = make_double2(we * e.x, we * e.y);
+    dA64[k] = da;
+    dE64[k] = de;
+    w64[k] = make_double2(wa, we);
+    d32[k] = make_float4((float)da.x, (float)da.y, (float)de.x, (float)de.y);
+    w32[k] = make_float2((float)wa, (float)we);
+  }
+}
+
+// Counts PSD entries that are not finite and positive.
+__global__ void k_check_psd(const double* S, int K, int* bad) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
+    double s = S[k];
+    if (!(s > 0.0) || !isfinite(s)) atomicAdd(bad, 1);
+  }
+}
+
+// <h|h> partial sums of a template (block sums into out[blockIdx])
+__global__ void k_hh(const double2* hA, const double2* hE, const double2* w64, int K,
+                     double* out) {
+  __shared__ double sm[256];
+  double s = 0.0;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
+    double2 a = hA[k], e = hE[k], w = w64[k];
+    s += w.x * (a.x * a.x + a.y * a.y) + w.y * (e.x * e.x + e.y * e.y);
+  }
+  sm[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = sm[0];
+}
+
+// d~ += s w h (injection) and refresh the FP32 copy
+__global__ void k_add_template(const double2* hA, const double2* hE, double s, int K,
+                               double2* dA64, double2* dE64, const double2* w64, float4* d32) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
+    double2 w = w64[k], a = hA[k], e = hE[k];
+    double2 da = dA64[k], de = dE64[k];
+    da.x += s * w.x * a.x;
+    da.y += s * w.x * a.y;
+    de.x += s * w.y * e.x;
+    de.y += s * w.y * e.y;
+    dA64[k] = da;
+    dE64[k] = de;
+    d32[k] = make_float4((float)da.x, (float)da.y, (float)de.x, (float)de.y);
+  }
+}
+
+__global__ void k_width_edges(int64_t K, int N, int* e) {
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n <= N; n += gridDim.x * blockDim.x)
+    e[n] = (int)((int64_t)n * K / N);
+}
+
+__global__ void k_support_out(const Part* part, int P, int64_t* klo, int64_t* khi, int32_t* l2b) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P) return;
+  const Part& p = part[i];
+  if (p.status == kInvalid) {
+    klo[i] = -1;
+    khi[i] = -1;
+  } else {
+    klo[i] = p.k_lo;
+    khi[i] = p.k_hi;
+  }
+  if (l2b) l2b[i] = p.log2B;
+}
+
+__global__ void k_edges_out(const Part* part, const int* edges, int64_t stride, int P, int N,
+                            int64_t* out) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t tot = (int64_t)P * (N + 1);
+  if (idx >= tot) return;
+  int64_t p = idx / (N + 1);
+  int n = (int)(idx % (N + 1));
+  out[idx] = part[p].status == kInvalid ? -1 : edges[p * stride + n];
+}
+
+}  // namespace scs

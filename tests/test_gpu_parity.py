@@ -1,0 +1,225 @@
+"""Parity of the CUDA paths with the FP64 CPU oracle, through the C ABI.
+
+Tolerances (relative to max(|Upsilon_oracle|, 1), the statistic's natural
+scale: noise alone gives Upsilon ~ 2N >= 2):
+  FP64 path  1e-10   (both use double-double phases)
+  mixed path 1e-5    (FP32 split phase; the bound stated for the method)
+Integer outputs (supports, segment edges) must be identical.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2408_13170_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+TOL32 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def scstat():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_2408_13170_gb300 import scstat as m
+    return m
+
+
+def rel_err(got, ref):
+    ref = np.asarray(ref)
+    return np.max(np.abs(np.asarray(got) - ref) / np.maximum(np.abs(ref), 1.0))
+
+
+def stream(T=3e6, fmin=0.0175, fmax=0.0200, seed=21, snr=18.0, inj=(30.0, 1.5, 0.018)):
+    d = synth.make_stream(dict(T_obs=T, f_min=fmin, f_max=fmax, seed=seed))
+    th = synth.injection_params(d["rng"], *inj)
+    oracle.inject(th, d["f_first"], d["df"], d["K"], d["T_obs"], d["SA"], d["SE"], snr,
+                  d["A"], d["E"])
+    return d, th
+
+
+def particles(rng, n, f_lo=0.0176, f_hi=0.019, mc=(10, 100), q=(1, 8)):
+    return synth.draw_particles(n, rng, lo=[mc[0], q[0], f_lo, 0, -1.5, 0, 0, 0],
+                                hi=[mc[1], q[1], f_hi, 6.28, 1.5, 3.14, 3.14, 0])
+
+
+@pytest.fixture(scope="module")
+def small(scstat):
+    d, inj = stream()
+    rng = np.random.default_rng(4)
+    th = np.vstack([inj, particles(rng, 70)])
+    ctx = scstat.Context(0, scstat.SCS_FP64)
+    ctx.set_data(0, d)
+    yield d, th, ctx
+    ctx.close()
+
+
+def test_waveform_matches_oracle(scstat, small):
+    d, th, ctx = small
+    for p in th[:6]:
+        hA, hE = ctx.waveform(0, p, d["K"])
+        _, oA, oE = oracle.template(p, d["f_first"], d["df"], d["K"], d["T_obs"])
+        scale = max(np.abs(oA).max(), np.abs(oE).max())
+        assert np.max(np.abs(hA - oA)) <= 1e-11 * scale
+        assert np.max(np.abs(hE - oE)) <= 1e-11 * scale
+
+
+def test_support_is_exact(scstat, small):
+    d, th, ctx = small
+    rng = np.random.default_rng(9)
+    extra = synth.draw_particles(200, rng)            # full prior box
+    bad = np.array([[-1, 1.5, .018, 0, 0, 0, 0, 0], [30, .5, .018, 0, 0, 0, 0, 0],
+                    [30, 1.5, .05, 0, 0, 0, 0, 0], [2e5, 1, .018, 0, 0, 0, 0, 0],
+                    [30, 1.5, .018, 0, 0, 0, 0, 0.1]], float)
+    allp = np.vstack([th, extra, bad])
+    lo, hi, _ = ctx.support(0, allp)
+    for i, p in enumerate(allp):
+        st, olo, ohi = oracle.support(p, d["f_first"], d["df"], d["K"], d["T_obs"])
+        if st == oracle.INVALID:
+            assert lo[i] == -1 and hi[i] == -1, i
+        elif st == oracle.EMPTY:
+            assert hi[i] < lo[i], i
+        else:
+            assert (lo[i], hi[i]) == (olo, ohi), i
+
+
+@pytest.mark.parametrize("N", [1, 7, 64])
+def test_snr2_edges_are_exact(scstat, small, N):
+    d, th, ctx = small
+    ctx.set_segments(0, N, scstat.SCS_EQUAL_SNR2)
+    e = ctx.edges(0, th, N)
+    _, kap = oracle.evaluate(d, th, N, mode=oracle.EQUAL_SNR2, want_kappa=True)
+    np.testing.assert_array_equal(e, np.ceil(kap).astype(np.int64))
+
+
+@pytest.mark.parametrize("path", ["fp64", "mixed"])
+@pytest.mark.parametrize("mode", [oracle.EQUAL_WIDTH, oracle.EQUAL_SNR2])
+@pytest.mark.parametrize("N", [1, 8, 100])
+def test_stat_parity(scstat, small, path, mode, N):
+    d, th, ctx = small
+    ctx.set_path(scstat.SCS_FP64 if path == "fp64" else scstat.SCS_MIXED)
+    ctx.set_segments(0, N, mode)
+    stat, sx, sh = ctx.eval(0, th, N, segments=True)
+    ref, rx, rh = oracle.evaluate(d, th, N, mode=mode, want_segments=True)
+    tol = TOL64 if path == "fp64" else TOL32
+    assert rel_err(stat, ref) <= tol
+    scale = np.maximum(rh.max(axis=1, keepdims=True), 1e-300)
+    assert np.max(np.abs(sh - rh) / scale) <= tol
+    xs = np.maximum(rx.max(axis=1, keepdims=True), 1e-300)
+    assert np.max(np.abs(sx - rx) / xs) <= 10 * tol
+    # the injected particle is the best one on both sides
+    assert np.argmax(stat) == np.argmax(ref)
+
+
+def test_edge_cases(scstat, small):
+    """Non-physical particles -> -inf, empty support -> 0, single particle,
+    a ragged particle count, and the largest segment count N = K."""
+    d, th, ctx = small
+    ctx.set_path(scstat.SCS_MIXED)
+    bad = np.array([[-1, 1.5, .018, 0, 0, 0, 0, 0], [30, 1.5, np.inf, 0, 0, 0, 0, 0],
+                    [30, 1.5, 0.025, 0, 0, 0, 0, 0], [30, 1.5, .018, 0, 0, 0, 0, 0.2]])
+    ctx.set_segments(0, 4, scstat.SCS_EQUAL_WIDTH)
+    s = ctx.eval(0, bad)
+    assert np.isneginf(s[0]) and np.isneginf(s[1]) and s[2] == 0.0 and np.isneginf(s[3])
+    for path in (scstat.SCS_FP64, scstat.SCS_MIXED):
+        ctx.set_path(path)
+        one = ctx.eval(0, th[:1])
+        ref = oracle.evaluate(d, th[:1], 4)
+        assert rel_err(one, ref) <= (TOL64 if path == scstat.SCS_FP64 else TOL32)
+    # N = K: every bin its own segment (equal width)
+    small_d = synth.make_stream(dict(T_obs=3e6, f_min=0.0179, f_max=0.01815, seed=5))
+    ctx.set_data(1, small_d)
+    K = small_d["K"]
+    ctx.set_segments(1, K, scstat.SCS_EQUAL_WIDTH)
+    p = np.array([[30.0, 1.5, 0.018, 1.0, 0.2, 0.5, 0.3, 0.0]])
+    ref = oracle.evaluate(small_d, p, K)
+    for path in (scstat.SCS_FP64, scstat.SCS_MIXED):
+        ctx.set_path(path)
+        got = ctx.eval(1, p)
+        assert rel_err(got, ref) <= (TOL64 if path == scstat.SCS_FP64 else TOL32)
+
+
+def test_slow_and_fast_chirps(scstat):
+    """Particles from the whole prior box (slow chirps with a few bins of
+    support up to signals reaching the last stable orbit) over a band that
+    spans several work chunks."""
+    d, inj = stream(T=4e6, fmin=0.012, fmax=0.03, seed=33)
+    rng = np.random.default_rng(12)
+    th = np.vstack([inj, synth.draw_particles(96, rng)])
+    with scstat.Context(0, scstat.SCS_MIXED) as ctx:
+        ctx.set_data(0, d)
+        for mode, N in ((scstat.SCS_EQUAL_SNR2, 16), (scstat.SCS_EQUAL_WIDTH, 32)):
+            ctx.set_segments(0, N, mode)
+            ref = oracle.evaluate(d, th, N, mode=mode)
+            ctx.set_path(scstat.SCS_MIXED)
+            assert rel_err(ctx.eval(0, th), ref) <= TOL32
+            ctx.set_path(scstat.SCS_FP64)
+            assert rel_err(ctx.eval(0, th), ref) <= TOL64
+
+
+def test_device_pointers_and_streams(scstat, small):
+    """torch CUDA tensors in, results on the device, on a user stream; the
+    same numbers as the host-pointer call."""
+    import torch
+    d, th, ctx = small
+    ctx.set_path(scstat.SCS_MIXED)
+    ctx.set_segments(0, 8, scstat.SCS_EQUAL_SNR2)
+    host = ctx.eval(0, th)
+    dev_th = torch.tensor(th, device="cuda")
+    out = torch.empty(len(th), dtype=torch.float64, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        scstat.scs_eval_stat(ctx.h, 0, dev_th, len(th), out, cuda_stream=s)
+    s.synchronize()
+    np.testing.assert_array_equal(out.cpu().numpy(), host)
+
+
+def test_argument_errors(scstat):
+    ctx = scstat.Context(0, scstat.SCS_MIXED)
+    with pytest.raises(scstat.ScsError) as e:
+        ctx.eval(0, np.zeros((1, 8)))
+    assert e.value.code == scstat.SCS_ENODATA
+    d = synth.make_stream(dict(T_obs=3e6, f_min=0.0179, f_max=0.0181, seed=5))
+    bad = dict(d)
+    bad["SA"] = d["SA"].copy()
+    bad["SA"][3] = -1.0
+    with pytest.raises(scstat.ScsError) as e:
+        ctx.set_data(0, bad)
+    assert e.value.code == scstat.SCS_EINVAL
+    bad = dict(d)
+    bad["df"] = d["df"] * 1.001
+    with pytest.raises(scstat.ScsError):
+        ctx.set_data(0, bad)
+    ctx.set_data(0, d)
+    with pytest.raises(scstat.ScsError):
+        ctx.set_segments(0, d["K"] + 1, scstat.SCS_EQUAL_WIDTH)
+    with pytest.raises(scstat.ScsError):
+        ctx.set_segments(0, 4, 9)
+    with pytest.raises(scstat.ScsError) as e:
+        ctx.eval(0, np.zeros((1, 8)))
+    assert e.value.code == scstat.SCS_ENODATA
+    ctx.close()
+
+
+def test_c1_full(scstat):
+    """The small published configuration in full: 256 particles, 45 001 bins,
+    N = 8 equal-width segments; both paths against the oracle."""
+    d = synth.make_stream("C1")
+    cfg = d["cfg"]
+    inj = synth.injection_params(d["rng"], *cfg["inj"])
+    oracle.inject(inj, d["f_first"], d["df"], d["K"], d["T_obs"], d["SA"], d["SE"],
+                  cfg["snr"], d["A"], d["E"])
+    th = synth.draw_particles(cfg["P"], d["rng"])
+    th[0] = inj
+    ref = oracle.evaluate(d, th, cfg["N"], mode=oracle.EQUAL_WIDTH)
+    with scstat.Context(0, scstat.SCS_FP64) as ctx:
+        ctx.set_data(0, d)
+        ctx.set_segments(0, cfg["N"], scstat.SCS_EQUAL_WIDTH)
+        s64 = ctx.eval(0, th)
+        ctx.set_path(scstat.SCS_MIXED)
+        s32 = ctx.eval(0, th)
+    assert rel_err(s64, ref) <= TOL64
+    assert rel_err(s32, ref) <= TOL32
+    assert np.argmax(s32) == np.argmax(ref) == 0
