@@ -43,6 +43,8 @@ struct DataStream {
   double f_first = 0, df = 0, T_obs = 0;
   int K = 0;
   DevBuf dA64, dE64, w64, d32, w32;
+  DevBuf wmax;          // max w as the bits of a double (FP32 scale W0)
+  double W0 = 1.0;
   int N = 0, mode = -1;
   DevBuf width_edges;   // N + 1 ints (equal-width segmentation)
 };
@@ -209,6 +211,7 @@ void scs_destroy(scs_ctx* ctx) {
   for (auto& kv : ctx->streams) {
     DataStream& d = kv.second;
     d.dA64.release(); d.dE64.release(); d.w64.release(); d.d32.release(); d.w32.release();
+    d.wmax.release();
     d.width_edges.release();
   }
   DevBuf* bufs[] = {&ctx->params, &ctx->part, &ctx->crange, &ctx->nrec, &ctx->total,
@@ -290,13 +293,22 @@ int scs_set_data(scs_ctx* ctx, int sid, const double* A, const double* E, const 
       din[i] = tmp[i]->ptr;
     }
   }
+  CK(ds.wmax.reserve(sizeof(unsigned long long)));
+  CK(cudaMemsetAsync(ds.wmax.ptr, 0, sizeof(unsigned long long), s));
   k_prewhiten<<<2048, 256, 0, s>>>((const double2*)din[0], (const double2*)din[1],
                                    (const double*)din[2], (const double*)din[3], df, (int)K,
                                    ds.dA64.as<double2>(), ds.dE64.as<double2>(),
-                                   ds.w64.as<double2>(), ds.d32.as<float4>(),
-                                   ds.w32.as<float2>());
+                                   ds.w64.as<double2>(), ds.wmax.as<unsigned long long>());
   CKLAUNCH();
+  k_to_fp32<<<2048, 256, 0, s>>>(ds.dA64.as<double2>(), ds.dE64.as<double2>(),
+                                 ds.w64.as<double2>(), (int)K,
+                                 ds.wmax.as<unsigned long long>(), ds.d32.as<float4>(),
+                                 ds.w32.as<float2>());
+  CKLAUNCH();
+  unsigned long long wbits = 0;
+  CK(cudaMemcpyAsync(&wbits, ds.wmax.ptr, sizeof wbits, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  std::memcpy(&ds.W0, &wbits, sizeof(double));
   ds.has_data = true;
   ds.f_first = f_first;
   ds.df = df;
@@ -431,6 +443,7 @@ int scs_eval_stat(scs_ctx* ctx, int sid, const double* params, int64_t P, double
   a.dA64 = ds.dA64.as<double2>();
   a.dE64 = ds.dE64.as<double2>();
   a.w64 = ds.w64.as<double2>();
+  a.W0 = ds.W0;
   a.N = N;
   a.edges = edges;
   a.edge_stride = stride;
@@ -590,7 +603,7 @@ int scs_inject(scs_ctx* ctx, int sid, const double* theta, double snr, double* h
   double scale = hh > 0.0 ? snr / std::sqrt(hh) : 0.0;
   k_add_template<<<2048, 256, 0, s>>>(tA, tE, scale, ds->K, ds->dA64.as<double2>(),
                                       ds->dE64.as<double2>(), ds->w64.as<double2>(),
-                                      ds->d32.as<float4>());
+                                      ds->wmax.as<unsigned long long>(), ds->d32.as<float4>());
   CKLAUNCH();
   CK(cudaStreamSynchronize(s));
   return SCS_OK;

@@ -29,6 +29,7 @@ struct EvalArgs {
   const double2* dA64;
   const double2* dE64;
   const double2* w64;
+  double W0;             // FP32 copies hold d~/sqrt(W0) and w/W0
   // segmentation: edges[p * edge_stride + n], n = 0..N
   int N;
   const int* edges;

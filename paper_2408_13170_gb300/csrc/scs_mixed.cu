@@ -31,6 +31,7 @@ __device__ inline float kval(const Kahan& k) { return k.s - k.c; }
 __global__ void __launch_bounds__(128) k_main_mixed(EvalArgs a) {
   const int lane = threadIdx.x & 31;
   const int total = a.item_off[a.n_chunks];
+  const double zs = sqrt(a.W0);   // FP32 sums -> physical units
   for (;;) {
     int item = 0;
     if (lane == 0) item = atomicAdd(a.item_counter, 1);
@@ -91,14 +92,14 @@ __global__ void __launch_bounds__(128) k_main_mixed(EvalArgs a) {
             float zr = kval(szr) + bzr, zi = kval(szi) + bzi, hh = kval(shh) + bhh;
             if (head) {
               r.n_head = n_cur;
-              r.zr_h = zr; r.zi_h = zi; r.hh_h = hh;
+              r.zr_h = zr * zs; r.zi_h = zi * zs; r.hh_h = hh * a.W0;
               head = false;
             } else {
               float x2 = zr * zr + zi * zi;
               if (hh > 0.f) r.ups += (double)(x2 / hh);
               if (a.seg_x) {
-                a.seg_x[(int64_t)p * a.N + n_cur] = (double)sqrtf(x2);
-                a.seg_hh[(int64_t)p * a.N + n_cur] = (double)hh;
+                a.seg_x[(int64_t)p * a.N + n_cur] = (double)sqrtf(x2) * zs;
+                a.seg_hh[(int64_t)p * a.N + n_cur] = (double)hh * a.W0;
               }
             }
             szr = Kahan{0.f, 0.f};
@@ -144,10 +145,10 @@ __global__ void __launch_bounds__(128) k_main_mixed(EvalArgs a) {
       float zr = kval(szr) + bzr, zi = kval(szi) + bzi, hh = kval(shh) + bhh;
       if (head) {
         r.n_head = n_cur;
-        r.zr_h = zr; r.zi_h = zi; r.hh_h = hh;
+        r.zr_h = zr * zs; r.zi_h = zi * zs; r.hh_h = hh * a.W0;
       } else {
         r.n_tail = n_cur;
-        r.zr_t = zr; r.zi_t = zi; r.hh_t = hh;
+        r.zr_t = zr * zs; r.zi_t = zi * zs; r.hh_t = hh * a.W0;
       }
     }
     if (has && pp.status == kOk) a.rec[a.rec_off[p] + (c - chunk_of(pp.k_lo))] = r;

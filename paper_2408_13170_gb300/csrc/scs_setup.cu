@@ -317,20 +317,36 @@ __global__ void k_fixup(const Part* part, const int2* crange, const int64_t* rec
   stat[i] = ups;
 }
 
-// d~ = w d with w = 4 df / S, FP64 and FP32 copies.
+// d~ = w d with w = 4 df / S (FP64); the largest w goes to *wmax (positive
+// doubles order like their bit patterns).
 __global__ void k_prewhiten(const double2* A, const double2* E, const double* SA,
                             const double* SE, double df, int K, double2* dA64, double2* dE64,
-                            double2* w64, float4* d32, float2* w32) {
+                            double2* w64, unsigned long long* wmax) {
+  double m = 0.0;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
     double wa = 4.0 * df / SA[k];
     double we = 4.0 * df / (SE ? SE[k] : SA[k]);
     double2 a = A[k], e = E[k];
-    double2 da = make_double2(wa * a.x, wa * a.y), de = make_double2(we * e.x, we * e.y);
-    dA64[k] = da;
-    dE64[k] = de;
+    dA64[k] = make_double2(wa * a.x, wa * a.y);
+    dE64[k] = make_double2(we * e.x, we * e.y);
     w64[k] = make_double2(wa, we);
-    d32[k] = make_float4((float)da.x, (float)da.y, (float)de.x, (float)de.y);
-    w32[k] = make_float2((float)wa, (float)we);
+    m = fmax(m, fmax(wa, we));
+  }
+  atomicMax(wmax, (unsigned long long)__double_as_longlong(m));
+}
+
+// FP32 copies for the mixed path, scaled so that FP32 sums cannot overflow:
+// w' = w / W0, d~' = d~ / sqrt(W0) with W0 = max w.  Then z' = z / sqrt(W0)
+// and hh' = hh / W0, so every x_n^2 / hh_n (hence Upsilon_N) is unchanged.
+__global__ void k_to_fp32(const double2* dA64, const double2* dE64, const double2* w64, int K,
+                          const unsigned long long* wmax, float4* d32, float2* w32) {
+  double W0 = __longlong_as_double((long long)*wmax);
+  double iw = 1.0 / W0, isq = 1.0 / sqrt(W0);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
+    double2 da = dA64[k], de = dE64[k], w = w64[k];
+    d32[k] = make_float4((float)(da.x * isq), (float)(da.y * isq), (float)(de.x * isq),
+                         (float)(de.y * isq));
+    w32[k] = make_float2((float)(w.x * iw), (float)(w.y * iw));
   }
 }
 
@@ -360,9 +376,11 @@ __global__ void k_hh(const double2* hA, const double2* hE, const double2* w64, i
   if (threadIdx.x == 0) out[blockIdx.x] = sm[0];
 }
 
-// d~ += s w h (injection) and refresh the FP32 copy
+// d~ += s w h (injection) and refresh the scaled FP32 copy
 __global__ void k_add_template(const double2* hA, const double2* hE, double s, int K,
-                               double2* dA64, double2* dE64, const double2* w64, float4* d32) {
+                               double2* dA64, double2* dE64, const double2* w64,
+                               const unsigned long long* wmax, float4* d32) {
+  double isq = 1.0 / sqrt(__longlong_as_double((long long)*wmax));
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
     double2 w = w64[k], a = hA[k], e = hE[k];
     double2 da = dA64[k], de = dE64[k];
@@ -372,7 +390,8 @@ __global__ void k_add_template(const double2* hA, const double2* hE, double s, i
     de.y += s * w.y * e.y;
     dA64[k] = da;
     dE64[k] = de;
-    d32[k] = make_float4((float)da.x, (float)da.y, (float)de.x, (float)de.y);
+    d32[k] = make_float4((float)(da.x * isq), (float)(da.y * isq), (float)(de.x * isq),
+                         (float)(de.y * isq));
   }
 }
 

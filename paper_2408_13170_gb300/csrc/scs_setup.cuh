@@ -19,12 +19,15 @@ __global__ void k_fixup(const Part* part, const int2* crange, const int64_t* rec
                         double* seg_hh);
 __global__ void k_prewhiten(const double2* A, const double2* E, const double* SA,
                             const double* SE, double df, int K, double2* dA64, double2* dE64,
-                            double2* w64, float4* d32, float2* w32);
+                            double2* w64, unsigned long long* wmax);
+__global__ void k_to_fp32(const double2* dA64, const double2* dE64, const double2* w64, int K,
+                          const unsigned long long* wmax, float4* d32, float2* w32);
 __global__ void k_check_psd(const double* S, int K, int* bad);
 __global__ void k_hh(const double2* hA, const double2* hE, const double2* w64, int K,
                      double* out);
 __global__ void k_add_template(const double2* hA, const double2* hE, double s, int K,
-                               double2* dA64, double2* dE64, const double2* w64, float4* d32);
+                               double2* dA64, double2* dE64, const double2* w64,
+                               const unsigned long long* wmax, float4* d32);
 __global__ void k_width_edges(int64_t K, int N, int* e);
 __global__ void k_support_out(const Part* part, int P, int64_t* klo, int64_t* khi,
                               int32_t* l2b);
