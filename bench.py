@@ -1,0 +1,335 @@
+"""Benchmark: batched evaluation of the semi-coherent statistic Upsilon_N.
+
+One step = one scs_eval_stat call over one batch of particles on the
+one-year stream (T = 3.15e7 s, 0.01-0.05 Hz -> K = 1 260 001 bins x TDI A, E;
+P = 4096 particles uniform in the prior box; N = 2048 equal-SNR^2 segments;
+Gaussian noise from the analytic A/E PSD plus one injection at SNR 17).
+Prints one JSON line.  `--impl reference` times the FP64 CPU oracle instead.
+
+Multi-GPU: the statistic shards over independent streams/particle batches
+with no exchange, so N GPUs run N replicas (different seeds, weak scaling);
+the timed region is max-reduced over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SC-stat particle-evals/s, mixed vs plain FP64 path on GB300, at rel err ≤1e-5"
+WORKLOAD = "C2"
+# Algorithmic FP32/INT32 lane-operations of the mixed path per support bin and
+# particle (itemised in the design doc): phase advance 8, phase->angle 2,
+# G interpolation 8, channel products 8, rotate-accumulate 4, |G|^2 w 6.
+ALG_OPS_PER_BIN = 36
+LAUNCHES_PER_STEP = 7   # setup, scan, chunk table, fill, edges, main, fix-up
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison")
+    ap.add_argument("--cpu-sample", type=int, default=48,
+                    help="particles in the CPU-oracle sample")
+    ap.add_argument("--workload", default=WORKLOAD)
+    return ap.parse_args()
+
+
+def dist_init(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if (args.impl == "ours" and torch.cuda.is_available()) else "gloo"
+        dist.init_process_group(backend, init_method="env://")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world, device=None):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = f"/tmp/scs_clocks_{os.getpid()}.csv"
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5], f[6], f[7], f[8]))
+            except ValueError:
+                continue
+        os.remove(self.path)
+        if not rows:
+            return None
+        sm = np.array([r[0] for r in rows])
+        reasons = set()
+        for r in rows:
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                                "sw_power_cap"), r[2:]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(rows[0][1]),
+                "samples": len(rows), "reasons": sorted(reasons)}
+
+
+def make_workload(seed_offset=0):
+    from paper_2408_13170_gb300 import synth
+    cfg = dict(synth.CONFIGS[WORKLOAD])
+    cfg["seed"] = cfg["seed"] + seed_offset
+    d = synth.make_stream(cfg)
+    inj = synth.injection_params(d["rng"], *cfg["inj"])
+    return cfg, d, inj
+
+
+def run_reference(args, rank, world):
+    """The FP64 CPU oracle, as it stands, on the host cores: each step
+    evaluates a bounded sample of the workload's particles."""
+    import oracle
+    from paper_2408_13170_gb300 import synth
+    if rank != 0:
+        return
+    cfg, d, inj = make_workload()
+    oracle.inject(inj, d["f_first"], d["df"], d["K"], d["T_obs"], d["SA"], d["SE"],
+                  cfg["snr"], d["A"], d["E"])
+    per_step = max(1, args.cpu_sample // 2)
+    batches = [synth.draw_particles(per_step, d["rng"]) for _ in range(args.warmup + args.steps)]
+    for b in batches[:args.warmup]:
+        oracle.evaluate(d, b, cfg["N"], mode=oracle.EQUAL_SNR2)
+    t0 = time.perf_counter()
+    for b in batches[args.warmup:]:
+        oracle.evaluate(d, b, cfg["N"], mode=oracle.EQUAL_SNR2)
+    dt = time.perf_counter() - t0
+    v = per_step * args.steps / dt
+    cores = os.cpu_count()
+    sample = (f"{per_step} particles per step of the {WORKLOAD} workload "
+              f"(P={cfg['P']}, K={d['K']}, N={cfg['N']} equal-SNR^2), all bins of each")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "particle-evals/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD}: one-year stream, {cfg['P']} particles, "
+                               f"K={d['K']} bins x 2 channels, N={cfg['N']} equal-SNR^2",
+                   "sample_per_step": per_step},
+        "cpu_baseline": {"value": v, "unit": "particle-evals/s", "cores": cores,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "particle-evals/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+    from paper_2408_13170_gb300 import scstat, synth
+    assert torch.cuda.is_available(), "bench needs a CUDA device"
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cfg, d, inj = make_workload(seed_offset=rank)
+    P, N = cfg["P"], cfg["N"]
+    ctx = scstat.Context(local, scstat.SCS_MIXED)
+    ctx.set_data(0, d)
+    ctx.inject(0, inj, cfg["snr"])
+    ctx.set_segments(0, N, scstat.SCS_EQUAL_SNR2)
+    nb = args.warmup + args.steps
+    host_batches = [synth.draw_particles(P, d["rng"]) for _ in range(nb)]
+    host_batches[0][0] = inj
+    batches = torch.tensor(np.stack(host_batches), device=dev)
+    stat = torch.empty((nb, P), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(i):
+        scstat.scs_eval_stat(ctx.h, 0, batches[i], P, stat[i], cuda_stream=stream)
+
+    scstat.scs_set_profiling(ctx.h, True)
+    for i in range(args.warmup):
+        flush.zero_()
+        step(i)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    main_ms = []
+    barrier(world)
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for j in range(args.steps):
+        flush.zero_()
+        ev[j][0].record(stream)
+        step(args.warmup + j)
+        ev[j][1].record(stream)
+        main_ms.append(scstat.scs_last_timings(ctx.h))
+    torch.cuda.synchronize()
+    barrier(world)
+    wall = time.perf_counter() - wall0
+    ck = clocks.stop()
+    step_ms = np.array([a.elapsed_time(b) for a, b in ev])
+    t_dev = max_over_ranks(step_ms.sum() / 1e3, world, dev)
+    value = world * P * args.steps / t_dev
+    stages = np.array(main_ms)            # steps x 4
+    scstat.scs_set_profiling(ctx.h, False)
+
+    # supports of the timed batches: bin-evals (algorithmic units)
+    bin_evals = []
+    for j in range(args.steps):
+        lo, hi, _ = ctx.support(0, host_batches[args.warmup + j])
+        bin_evals.append(float(np.sum(np.maximum(hi - lo + 1, 0))))
+    bin_evals = np.array(bin_evals)
+    t_main = stages[:, 2] / 1e3
+    ops = bin_evals * ALG_OPS_PER_BIN
+    sm_mhz = (ck or {}).get("sm_mhz") or 2070.0
+    props = torch.cuda.get_device_properties(dev)
+    peak = props.multi_processor_count * 128 * sm_mhz * 1e6   # lane-ops/s
+    achieved = float(np.mean(ops / t_main))
+
+    # end to end through the public API with host buffers (pinned params in,
+    # stat out; the library copies both ways inside the call)
+    pinned = torch.from_numpy(np.stack(host_batches[:args.steps])).pin_memory()
+    host_stat = np.empty(P)
+    ctx_params = [pinned[j].numpy() for j in range(args.steps)]
+    barrier(world)
+    t0 = time.perf_counter()
+    for j in range(args.steps):
+        scstat.scs_eval_stat(ctx.h, 0, ctx_params[j], P, host_stat)
+    e2e_t = max_over_ranks(time.perf_counter() - t0, world, dev)
+    e2e = {"value": world * P * args.steps / e2e_t, "unit": "particle-evals/s",
+           "h2d_bytes_per_step": P * 8 * 8, "d2h_bytes_per_step": P * 8}
+
+    # the plain FP64 path on one batch: throughput and agreement
+    fp64 = None
+    acc = {}
+    if not args.no_fp64:
+        ctx.set_path(scstat.SCS_FP64)
+        s64 = torch.empty(P, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        scstat.scs_eval_stat(ctx.h, 0, batches[args.warmup], P, s64, cuda_stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t64 = a.elapsed_time(b) / 1e3
+        ctx.set_path(scstat.SCS_MIXED)
+        m = stat[args.warmup].cpu().numpy()
+        r = s64.cpu().numpy()
+        rel = np.abs(m - r) / np.maximum(np.abs(r), 1.0)
+        fp64 = {"value": P / t64, "unit": "particle-evals/s", "ms_per_step": 1e3 * t64,
+                "mixed_speedup": (P / t64) and value / world / (P / t64)}
+        acc = {"max_rel_err_mixed_vs_fp64": float(rel.max()),
+               "argmax_agrees": bool(np.argmax(m) == np.argmax(r))}
+
+    # CPU oracle on a bounded sample of the same workload (rank 0 only)
+    cpu = None
+    if rank == 0 and world == 1 and args.cpu_sample > 0:
+        import oracle
+        dh = dict(d)
+        dh["A"] = d["A"].copy()
+        dh["E"] = d["E"].copy()
+        oracle.inject(inj, d["f_first"], d["df"], d["K"], d["T_obs"], d["SA"], d["SE"],
+                      cfg["snr"], dh["A"], dh["E"])
+        sample = host_batches[args.warmup][:args.cpu_sample]
+        t0 = time.perf_counter()
+        ref = oracle.evaluate(dh, sample, N, mode=oracle.EQUAL_SNR2)
+        tc = time.perf_counter() - t0
+        m = stat[args.warmup, :args.cpu_sample].cpu().numpy()
+        acc["max_rel_err_mixed_vs_oracle_sample"] = float(
+            np.max(np.abs(m - ref) / np.maximum(np.abs(ref), 1.0)))
+        cpu = {"value": len(sample) / tc, "unit": "particle-evals/s",
+               "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"first {len(sample)} particles of a timed batch, every support bin "
+                         f"({WORKLOAD}, N={N} equal-SNR^2); {tc:.1f} s wall"}
+
+    if rank != 0:
+        return
+    out = {
+        "metric": METRIC, "value": value, "unit": "particle-evals/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (f64 anchors and segment totals)", "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD}: one-year stream T=3.15e7 s, K={d['K']} bins x "
+                               f"TDI A,E; P={P} particles uniform in the prior box; "
+                               f"N={N} equal-SNR^2 segments; injection SNR {cfg['snr']}",
+                   "P": P, "K": int(d["K"]), "N": N, "path": "mixed",
+                   "l2": "256 MB buffer written between timed steps",
+                   "parallelism": f"replicas x{world}"},
+        "bin_evals_per_s": float(world * bin_evals.sum() / t_dev),
+        "stage_ms": {k: float(v) for k, v in zip(
+            ("setup_worklist", "segment_edges", "main", "fixup"), stages.mean(axis=0))},
+        "roofline": {"bound": "alu", "kernel": "k_main_mixed", "achieved": achieved / 1e12,
+                     "peak": peak / 1e12, "unit": "Tops/s", "frac": achieved / peak,
+                     "traffic": None,
+                     "note": f"{ALG_OPS_PER_BIN} lane-ops per support bin-eval; peak = "
+                             f"{props.multi_processor_count} SMs x 128 lanes x "
+                             f"{sm_mhz:.0f} MHz (median SM clock under load)"},
+        "e2e": e2e,
+        "gpu_launches": LAUNCHES_PER_STEP * args.steps,
+        "clocks": ck,
+        "fp64_path": fp64,
+        "accuracy": acc,
+        "cpu_baseline": cpu,
+        "wall_s_timed_region": wall,
+    }
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

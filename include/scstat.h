@@ -148,6 +148,15 @@ int scs_support(scs_ctx *ctx, int stream_id, const double *params, int64_t P,
 int scs_segment_edges(scs_ctx *ctx, int stream_id, const double *params,
                       int64_t P, int64_t *edges, void *cuda_stream);
 
+/* Stage timing of scs_eval_stat (CUDA events recorded on the call's
+ * stream while enabled; adds no synchronisation to the call itself).
+ * scs_last_timings blocks until the last profiled call has finished and
+ * writes ms[4]: particle set-up and work list, segment edges, main
+ * evaluation kernel, cross-chunk fix-up.
+ * Errors: SCS_EINVAL, SCS_ENODATA (nothing profiled yet), SCS_ECUDA. */
+int scs_set_profiling(scs_ctx *ctx, int enable);
+int scs_last_timings(scs_ctx *ctx, double *ms);
+
 #ifdef __cplusplus
 }
 #endif

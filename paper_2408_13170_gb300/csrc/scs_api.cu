@@ -68,6 +68,9 @@ struct scs_ctx {
   int grid_mixed = 0, grid_fp64 = 0;
   cudaStream_t stream = nullptr;
   std::string err;
+  bool prof = false;               // record stage events in scs_eval_stat
+  bool prof_valid = false;
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   std::map<int, DataStream> streams;
   // per-call scratch
   DevBuf params, part, crange, nrec, total, diff, cnt, list_off, item_off, fill, list, rec,
@@ -220,6 +223,8 @@ void scs_destroy(scs_ctx* ctx) {
                     &ctx->stat, &ctx->segx, &ctx->segh, &ctx->tmpA, &ctx->tmpE, &ctx->red,
                     &ctx->misc};
   for (DevBuf* b : bufs) b->release();
+  for (cudaEvent_t& e : ctx->ev)
+    if (e) cudaEventDestroy(e);
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }
@@ -401,12 +406,15 @@ int scs_eval_stat(scs_ctx* ctx, int sid, const double* params, int64_t P, double
   cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : ctx->stream;
   const bool mixed = ctx->path == SCS_MIXED;
   const double* dparams = nullptr;
+  ctx->prof_valid = false;
+  if (ctx->prof) CK(cudaEventRecord(ctx->ev[0], s));
   rc = stage_params(ctx, params, P, s, &dparams);
   if (rc) return rc;
   int n_chunks = 0;
   int64_t max_rec = 0;
   rc = prepare(ctx, ds, dparams, (int)P, mixed, s, &n_chunks, &max_rec);
   if (rc) return rc;
+  if (ctx->prof) CK(cudaEventRecord(ctx->ev[1], s));
   const int* edges = nullptr;
   int64_t stride = 0;
   rc = build_edges(ctx, ds, (int)P, s, &edges, &stride);
@@ -460,13 +468,19 @@ int scs_eval_stat(scs_ctx* ctx, int sid, const double* params, int64_t P, double
   a.seg_x = dsx;
   a.seg_hh = dsh;
   a.err = ctx->counter.as<int>() + 1;
+  if (ctx->prof) CK(cudaEventRecord(ctx->ev[2], s));
   if (mixed) launch_main_mixed(a, ctx->grid_mixed, s);
   else launch_main_fp64(a, ctx->grid_fp64, s);
   CKLAUNCH();
+  if (ctx->prof) CK(cudaEventRecord(ctx->ev[3], s));
   k_fixup<<<(int)((P + 127) / 128), 128, 0, s>>>(ctx->part.as<Part>(), ctx->crange.as<int2>(),
                                                  ctx->nrec.as<int64_t>(), ctx->rec.as<Rec>(),
                                                  (int)P, N, dstat, dsx, dsh);
   CKLAUNCH();
+  if (ctx->prof) {
+    CK(cudaEventRecord(ctx->ev[4], s));
+    ctx->prof_valid = true;
+  }
   if (!stat_dev) CK(cudaMemcpyAsync(stat, dstat, sizeof(double) * P, cudaMemcpyDeviceToHost, s));
   if (seg_x && !seg_dev) {
     CK(cudaMemcpyAsync(seg_x, dsx, sizeof(double) * (size_t)P * N, cudaMemcpyDeviceToHost, s));
@@ -606,6 +620,32 @@ int scs_inject(scs_ctx* ctx, int sid, const double* theta, double snr, double* h
                                       ds->wmax.as<unsigned long long>(), ds->d32.as<float4>());
   CKLAUNCH();
   CK(cudaStreamSynchronize(s));
+  return SCS_OK;
+}
+
+int scs_set_profiling(scs_ctx* ctx, int enable) {
+  if (!ctx) return SCS_EINVAL;
+  int rc = bind(ctx);
+  if (rc) return rc;
+  if (enable && !ctx->ev[0])
+    for (cudaEvent_t& e : ctx->ev) CK(cudaEventCreate(&e));
+  ctx->prof = enable != 0;
+  ctx->prof_valid = false;
+  return SCS_OK;
+}
+
+int scs_last_timings(scs_ctx* ctx, double* ms) {
+  if (!ctx || !ms) return SCS_EINVAL;
+  if (!ctx->prof_valid)
+    return fail(ctx, SCS_ENODATA, "no profiled scs_eval_stat since profiling was enabled");
+  int rc = bind(ctx);
+  if (rc) return rc;
+  CK(cudaEventSynchronize(ctx->ev[4]));
+  for (int i = 0; i < 4; ++i) {
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, ctx->ev[i], ctx->ev[i + 1]));
+    ms[i] = t;
+  }
   return SCS_OK;
 }
 

@@ -61,6 +61,10 @@ def lib():
         L.scs_support.restype = I
         L.scs_segment_edges.argtypes = [P, I, P, I64, P, P]
         L.scs_segment_edges.restype = I
+        L.scs_set_profiling.argtypes = [P, I]
+        L.scs_set_profiling.restype = I
+        L.scs_last_timings.argtypes = [P, P]
+        L.scs_last_timings.restype = I
         _lib = L
         return L
 
@@ -146,6 +150,17 @@ def scs_support(ctx, stream_id, params, P, k_lo, k_hi, log2_stride=None, cuda_st
 def scs_segment_edges(ctx, stream_id, params, P, edges, cuda_stream=None):
     _check(ctx, lib().scs_segment_edges(ctx, stream_id, _ptr(params), int(P), _ptr(edges),
                                         _stream(cuda_stream)))
+
+
+def scs_set_profiling(ctx, enable: bool):
+    _check(ctx, lib().scs_set_profiling(ctx, 1 if enable else 0))
+
+
+def scs_last_timings(ctx):
+    """ms of (set-up + work list, segment edges, main kernel, fix-up)."""
+    out = np.zeros(4)
+    _check(ctx, lib().scs_last_timings(ctx, out.ctypes.data))
+    return out
 
 
 # ------------------------------------------------------ numpy convenience
