@@ -195,7 +195,8 @@ def main():
     batches = torch.tensor(np.stack(host_batches), device=dev)
     stat = torch.empty((nb, P), dtype=torch.float64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream(dev)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
 
     def step(i):
         scstat.scs_eval_stat(ctx.h, 0, batches[i], P, stat[i], cuda_stream=stream)

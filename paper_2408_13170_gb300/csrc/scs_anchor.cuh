@@ -77,6 +77,23 @@ __device__ inline void phase_derivs(const Part& p, double fa, double Phi[5], dou
   T[3] = t3;
 }
 
+// G_alpha at frequency offset df_off from the anchor, FP64 (stride checks).
+__device__ inline void g_node64(const Part& p, double fa, double df_off, const double T[4],
+                                double out[4]) {
+  double t = T[0] + df_off * (T[1] + df_off * (0.5 * T[2] + df_off * (T[3] * (1.0 / 6.0))));
+  double sa, ca;
+  sincos(orbit_angle(t), &sa, &ca);
+  double f = fa + df_off;
+  const double kv[3] = {p.kx, p.ky, p.kz};
+  Cx<double> RA, RE;
+  response_residual<double>(f, ca, sa, p.Pr, p.Pi, kv, RA, RE);
+  double amp = pow(f, -7.0 / 6.0);
+  out[0] = amp * RA.re;
+  out[1] = amp * RA.im;
+  out[2] = amp * RE.re;
+  out[3] = amp * RE.im;
+}
+
 // G_alpha at frequency offset df_off from the anchor (FP32 response).
 __device__ inline void g_node(const Part& p, double fa, double df_off, const double T[4],
                               float out[4]) {

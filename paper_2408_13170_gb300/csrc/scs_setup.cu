@@ -10,19 +10,28 @@ namespace scs {
 namespace {
 
 // ---------------------------------------------------------- anchor stride
-// Largest power-of-two stride B <= kChunk for which the degree-4 phase
-// polynomial stays within kTolPhase turns and the quadratic G within
-// kTolG (relative) of the exact FP64 model, checked at three spans of the
-// support (first, middle, last) and three offsets per span.
+// Largest power-of-two stride B <= kChunk for which, over a span, the
+// degree-4 phase polynomial stays within kTolPhase turns of the exact FP64
+// phase and the quadratic through j = 0, B/2, B (built here from FP64 node
+// values, so that only the truncation is measured) stays within kTolG of
+// the exact G relative to |G_A| + |G_E|.  Checked at three spans of the
+// support (first, middle, last) and three offsets per span.  The FP32
+// rounding of the kernel's own node values (~1e-7 to 1e-6 relative) does not
+// depend on B and is bounded by the parity tests instead.
 constexpr double kTolPhase = 2e-8;   // turns
 constexpr double kTolG = 3e-7;       // relative to |G_A| + |G_E|
 
 __device__ bool span_ok(const Part& p, int B, int ka, double f_first, double df) {
-  Anchor an;
-  anchor_build(p, ka, B, f_first, df, an);
   double fa = f_first + (double)ka * df;
   int jlo = max(0, p.k_lo - ka), jhi = min(B - 1, p.k_hi - ka);
   if (jhi < jlo) return true;
+  double Pd[5], Td[4];
+  phase_derivs(p, fa, Pd, Td);
+  double h = 0.5 * (double)B;
+  double y0[4], y1[4], y2[4];
+  g_node64(p, fa, 0.0, Td, y0);
+  g_node64(p, fa, h * df, Td, y1);
+  g_node64(p, fa, 2.0 * h * df, Td, y2);
   const int js[3] = {B / 4, (3 * B) / 4, B - 1};
   for (int t = 0; t < 3; ++t) {
     int j = min(max(js[t], jlo), jhi);
@@ -34,12 +43,16 @@ __device__ bool span_ok(const Part& p, int B, int ka, double f_first, double df)
     double dphi = pj - phi;
     dphi -= rint(dphi);
     if (!(fabs(dphi) <= kTolPhase)) return false;
-    float jf = (float)j;
+    // Lagrange quadratic through (0, y0), (h, y1), (2h, y2) at x = j
+    double x = (double)j;
+    double l0 = (x - h) * (x - 2.0 * h) / (2.0 * h * h);
+    double l1 = -x * (x - 2.0 * h) / (h * h);
+    double l2 = x * (x - h) / (2.0 * h * h);
     double q[4];
-    for (int c = 0; c < 4; ++c) q[c] = fmaf(jf, fmaf(jf, an.g2[c], an.g1[c]), an.g0[c]);
-    double err = fabs(q[0] - GA.re) + fabs(q[1] - GA.im) + fabs(q[2] - GE.re) + fabs(q[3] - GE.im);
+    for (int c = 0; c < 4; ++c) q[c] = l0 * y0[c] + l1 * y1[c] + l2 * y2[c];
     double mag = hypot(GA.re, GA.im) + hypot(GE.re, GE.im);
-    if (!(err <= kTolG * mag)) return false;
+    double ierr = fabs(q[0] - GA.re) + fabs(q[1] - GA.im) + fabs(q[2] - GE.re) + fabs(q[3] - GE.im);
+    if (!(ierr <= kTolG * mag)) return false;
   }
   return true;
 }

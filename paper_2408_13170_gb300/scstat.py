@@ -84,10 +84,18 @@ def _ptr(x):
     raise TypeError(f"unsupported array type {type(x)}")
 
 
+_CUDA_STREAM_LEGACY = 1   # cudaStreamLegacy: the legacy default stream
+
+
 def _stream(s):
+    """cudaStream_t handle of a torch stream (or an int).  torch reports the
+    default stream as handle 0, which the C ABI reads as "the context's own
+    stream"; it is passed as cudaStreamLegacy so the work stays ordered with
+    torch's default stream."""
     if s is None:
         return None
-    return getattr(s, "cuda_stream", s)
+    h = getattr(s, "cuda_stream", s)
+    return _CUDA_STREAM_LEGACY if h == 0 else h
 
 
 def _check(ctx, rc):
