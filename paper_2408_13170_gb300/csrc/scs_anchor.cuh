@@ -1,23 +1,36 @@
 // scs_anchor.cuh -- anchors of the mixed-precision path.
 //
 // Over a span of B bins starting at anchor bin k_a the total phase
-// Phi(f) = Psi(f)/(2 pi) + f k.p0(t(f)) (turns) is replaced by its degree-4
-// Taylor polynomial in the bin offset j, and the smooth factor
-// G_alpha(f) = f^{-7/6} R_alpha(f, t(f)) (amplitude times residual TDI
-// response, Sec. IV) by the quadratic through j = 0, B/2, B.
+// Phi(f) = Psi(f)/(2 pi) + f k.p0(t(f)) (turns) is replaced by its
+// degree-kOrd Taylor polynomial in the bin offset j, advanced bin by bin
+// with its forward differences in 64-bit fixed point (2^64 = one turn):
+// the additions wrap modulo one turn exactly, so the phase error is the
+// anchor's rounding (~1e-9 turns) plus the Taylor remainder, which the
+// stride B is chosen to bound.  Orders 0-3 of the polynomial are computed in
+// FP64; orders 4-6, whose contribution over a span is far below a turn, in
+// FP32.
 //
-// The phase polynomial is advanced bin by bin with its forward differences
-// in 64-bit fixed point (2^64 = one turn): the additions wrap modulo one turn
-// exactly, so the only phase error is the FP64 anchor value (~1e-9 turns)
-// plus the Taylor remainder, which the anchor stride B is chosen to bound.
+// The smooth factor G_alpha(f) = f^{-7/6} R_alpha(f, t(f)) (amplitude times
+// residual TDI response, Sec. IV) is replaced, over response sub-spans of
+// Br <= B bins, by the quadratic through j = 0, Br/2, Br; its nodes are
+// evaluated in FP32 from the anchor's orbit angle and t(f) expansion.
 #pragma once
 #include "scs_device.cuh"
 
 namespace scs {
 
-struct Anchor {
-  uint64_t ph, d1, d2, d3, d4;   // phase and its forward differences
-  float g0[4], g1[4], g2[4];     // G_A.re, G_A.im, G_E.re, G_E.im = g0 + j (g1 + j g2)
+constexpr int kOrd = 6;   // phase polynomial degree
+
+// phase state and the FP32 hand-off for the response nodes of the span
+struct PhaseAnchor {
+  uint64_t d[kOrd + 1];   // phase and its forward differences (fixed point)
+  float al0;              // orbit angle at the anchor, reduced
+  float tq1, tq2, tq3;    // t(k_a + x) - t(k_a) = x (tq1 + x (tq2 + x tq3)), x in bins
+  float fa32, df32;
+};
+
+struct RespQuad {
+  float g0[4], g1[4], g2[4];   // G_A.re, G_A.im, G_E.re, G_E.im = g0 + j (g1 + j g2)
 };
 
 // x (turns) -> fixed point modulo one turn
@@ -25,65 +38,173 @@ __device__ inline uint64_t turns_to_fixed(double x) {
   x -= rint(x);
   return (uint64_t)__double2ll_rn(x * 18446744073709551616.0);
 }
+__device__ inline uint64_t small_turns_to_fixed(float x) {   // normally |x| << 1/2
+  x -= rintf(x);
+  return (uint64_t)__float2ll_rn(x * 18446744073709551616.0f);
+}
 
-// Derivatives of the phase at f_a: Phi^{(r)}, r = 0..4 (Phi^{(0)} reduced to
-// [-1/2, 1/2]), and t(f_a) with its first three f-derivatives.
-__device__ inline void phase_derivs(const Part& p, double fa, double Phi[5], double T[4]) {
+// Taylor coefficients of the phase in the bin offset j about k_a:
+// c[r] = Phi^{(r)} df^r / r!  (c[0] reduced modulo one turn), orders 0-3 in
+// FP64 (c64) and 4-6 in FP32 (c32), plus the node hand-off.
+__device__ inline void phase_taylor(const Part& p, double fa, double df, double c64[4],
+                                    float c32[7], PhaseAnchor& an) {
+  const double rdf = df / fa;   // d/df of u^n = -(n/3) u^n / f: one bin = df
   double u = rcbrt(fa);
-  double u3 = u * u * u;
-  double F[6] = {0, 0, 0, 0, 0, 0};
-  double upow[4] = {u3 * u * u, u3, u * u, u};
+  double u2 = u * u;
+  double upow[4] = {u2 * u2 * u, u2 * u, u2, u};
+  // PN part F_pn: bin-unit derivatives F[r] = F_pn^{(r)} df^r
+  double F[5] = {0, 0, 0, 0, 0};
+  float F32[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
     double n = (double)kPow[m];
     double val = p.A[m].hi * upow[m];
 #pragma unroll
-    for (int r = 0; r < 6; ++r) {
+    for (int r = 0; r < 5; ++r) {
       F[r] += val;
-      val *= -(n + 3.0 * r) * (1.0 / 3.0) * u3;
+      val *= -(n + 3.0 * r) * (1.0 / 3.0) * rdf;
+    }
+    float v32 = (float)val;
+    const float rdf32 = (float)rdf;
+#pragma unroll
+    for (int r = 5; r < 8; ++r) {
+      F32[r] += v32;
+      v32 *= -((float)n + 3.0f * r) * (1.0f / 3.0f) * rdf32;
     }
   }
-  // F(f) = t_c f - 1/8 + F_pn(f): reduce the two large terms separately
+  // t(f) and its bin derivatives T[r] = t^{(r)} df^r (t = F'):  T[r] = F[r+1]/df
+  const double idf = 1.0 / df;
+  double t0 = p.tc.hi + (p.tc.lo + F[1] * idf);
+  double T1 = F[2] * idf, T2 = F[3] * idf, T3 = F[4] * idf;
+  // F(f) = t_c f - 1/8 + F_pn: reduce the large terms separately
   double lin = p.tc.hi * fa;
   double lin_err = fma(p.tc.hi, fa, -lin) + p.tc.lo * fa;
   double F0 = (lin - rint(lin)) + (F[0] - rint(F[0])) + lin_err - 0.125;
-  double t0 = p.tc.hi + (p.tc.lo + F[1]);
-  double t1 = F[2], t2 = F[3], t3 = F[4], t4 = F[5];
-  // guiding-centre Doppler D(f) = f q(t(f)), q(t) = -R cos(beta) cos(Omega t - lambda)
+  // Doppler D(f) = f q(t(f)), q(t) = -R cos(beta) cos(Omega t - lambda)
   double th = kOmega * t0 - p.lam;
   th -= kTwoPi * rint(th * (1.0 / kTwoPi));
   double sn, cs;
   sincos(th, &sn, &cs);
   const double R = p.Rcb, W = kOmega;
-  double q0 = -R * cs, q1 = R * W * sn, q2 = R * W * W * cs, q3 = -R * W * W * W * sn,
-         q4 = -R * W * W * W * W * cs;
-  // chain rule through t(f)
-  double Q0 = q0;
-  double Q1 = q1 * t1;
-  double Q2 = q2 * t1 * t1 + q1 * t2;
-  double Q3 = q3 * t1 * t1 * t1 + 3.0 * q2 * t1 * t2 + q1 * t3;
-  double Q4 = q4 * t1 * t1 * t1 * t1 + 6.0 * q3 * t1 * t1 * t2 +
-              q2 * (3.0 * t2 * t2 + 4.0 * t1 * t3) + q1 * t4;
-  double D0 = fa * Q0;
-  Phi[0] = F0 + (D0 - rint(D0));
-  Phi[0] -= rint(Phi[0]);
-  Phi[1] = t0 + fa * Q1 + Q0;
-  Phi[2] = F[2] + fa * Q2 + 2.0 * Q1;
-  Phi[3] = F[3] + fa * Q3 + 3.0 * Q2;
-  Phi[4] = F[4] + fa * Q4 + 4.0 * Q3;
-  T[0] = t0;
-  T[1] = t1;
-  T[2] = t2;
-  T[3] = t3;
+  // q derivatives in bins (chain rule through t, orders <= 3)
+  double q0 = -R * cs, q1 = R * W * sn, q2 = R * W * W * cs, q3 = -R * W * W * W * sn;
+  double Q1 = q1 * T1;
+  double Q2 = q2 * T1 * T1 + q1 * T2;
+  double Q3 = q3 * T1 * T1 * T1 + 3.0 * q2 * T1 * T2 + q1 * T3;
+  // D^{(r)} in bins: (f_a + x df) q(x):  D_r = f_a Q_r + r df Q_{r-1}
+  double D0 = fa * q0;
+  c64[0] = F0 + (D0 - rint(D0));
+  c64[0] -= rint(c64[0]);
+  c64[1] = (p.tc.hi + p.tc.lo) * df + F[1] + fa * Q1 + df * q0;
+  c64[2] = (F[2] + fa * Q2 + 2.0 * df * Q1) * 0.5;
+  c64[3] = (F[3] + fa * Q3 + 3.0 * df * Q2) * (1.0 / 6.0);
+  // orders 4-6 in FP32.  Doppler: exp of the series i Omega (t(x) - t0) =
+  // sum_k s_k x^k gives e^{i Omega (t - t0)} = sum_n e_n x^n with
+  // e_n = (1/n) sum_k k s_k e_{n-k}; q_n = -R Re(e^{i theta} e_n).
+  float tk[7];
+  tk[1] = (float)T1;
+  tk[2] = (float)(T2 * 0.5);
+  tk[3] = (float)(T3 * (1.0 / 6.0));
+  tk[4] = F32[5] * (float)idf * (1.0f / 24.0f);
+  tk[5] = F32[6] * (float)idf * (1.0f / 120.0f);
+  tk[6] = F32[7] * (float)idf * (1.0f / 720.0f);
+  const float Wf = (float)kOmega;
+  float er[7], ei[7];
+  er[0] = 1.f;
+  ei[0] = 0.f;
+#pragma unroll
+  for (int nn = 1; nn <= 6; ++nn) {
+    float sr = 0.f, si = 0.f;
+#pragma unroll
+    for (int k = 1; k <= nn; ++k) {
+      // (i Omega k tk[k]) * e_{n-k}
+      float a = Wf * (float)k * tk[k];
+      sr -= a * ei[nn - k];
+      si += a * er[nn - k];
+    }
+    er[nn] = sr / (float)nn;
+    ei[nn] = si / (float)nn;
+  }
+  const float csf = (float)cs, snf = (float)sn, Rf = (float)R;
+  float qn[7];
+#pragma unroll
+  for (int nn = 0; nn <= 6; ++nn) qn[nn] = -Rf * (csf * er[nn] - snf * ei[nn]);
+  const float fa32 = (float)fa, df32 = (float)df;
+  c32[4] = (float)(F[4] * (1.0 / 24.0)) + fa32 * qn[4] + df32 * qn[3];
+  c32[5] = F32[5] * (1.0f / 120.0f) + fa32 * qn[5] + df32 * qn[4];
+  c32[6] = F32[6] * (1.0f / 720.0f) + fa32 * qn[6] + df32 * qn[5];
+  // node hand-off (FP32): orbit angle and t offsets in bins
+  double al = kOmega * t0;
+  al -= kTwoPi * rint(al * (1.0 / kTwoPi));
+  an.al0 = (float)al;
+  an.tq1 = (float)T1;
+  an.tq2 = (float)(T2 * 0.5);
+  an.tq3 = (float)(T3 * (1.0 / 6.0));
+  an.fa32 = fa32;
+  an.df32 = df32;
 }
 
-// G_alpha at frequency offset df_off from the anchor, FP64 (stride checks).
-__device__ inline void g_node64(const Part& p, double fa, double df_off, const double T[4],
-                                double out[4]) {
-  double t = T[0] + df_off * (T[1] + df_off * (0.5 * T[2] + df_off * (T[3] * (1.0 / 6.0))));
+// Build the phase state of the span starting at k_a.
+__device__ inline void phase_anchor(const Part& p, int ka, double f_first, double df,
+                                    PhaseAnchor& an) {
+  double fa = f_first + (double)ka * df;
+  double c64[4];
+  float c32[7];
+  phase_taylor(p, fa, df, c64, c32, an);
+  // forward differences Delta_r = sum_{s>=r} c_s r! S(s, r), with r! S(s, r)
+  // (S: Stirling numbers of the second kind) the r-th forward difference at
+  // 0 of j^s
+  double hi[4];
+  hi[1] = c64[1] + c64[2] + c64[3] + (double)(c32[4] + c32[5] + c32[6]);
+  hi[2] = 2.0 * c64[2] + 6.0 * c64[3] +
+          (double)(14.f * c32[4] + 30.f * c32[5] + 62.f * c32[6]);
+  hi[3] = 6.0 * c64[3] + (double)(36.f * c32[4] + 150.f * c32[5] + 540.f * c32[6]);
+  an.d[0] = turns_to_fixed(c64[0]);
+  an.d[1] = turns_to_fixed(hi[1]);
+  an.d[2] = turns_to_fixed(hi[2]);
+  an.d[3] = turns_to_fixed(hi[3]);
+  an.d[4] = small_turns_to_fixed(24.f * c32[4] + 240.f * c32[5] + 1560.f * c32[6]);
+  an.d[5] = small_turns_to_fixed(120.f * c32[5] + 1800.f * c32[6]);
+  an.d[6] = small_turns_to_fixed(720.f * c32[6]);
+}
+
+// Phase polynomial of the anchor at bin offset j (fixed point, exact modular
+// Newton form sum_r Delta_r binom(j, r)); for the stride checks.
+__device__ inline uint64_t phase_anchor_at(const PhaseAnchor& an, int j) {
+  uint64_t acc = an.d[0], b = 1;
+#pragma unroll
+  for (int r = 1; r <= kOrd; ++r) {
+    if (j - r + 1 <= 0) break;
+    // binom(j, r) = binom(j, r-1) (j-r+1)/r, exact in 128-bit
+    unsigned __int128 t = (unsigned __int128)b * (uint64_t)(j - r + 1);
+    b = (uint64_t)(t / (uint64_t)r);
+    acc += an.d[r] * b;
+  }
+  return acc;
+}
+
+// G_alpha at bin offset x from the phase anchor (FP32 node).
+__device__ inline void g_node32(const Part& p, const PhaseAnchor& an, float x, float out[4]) {
+  float dt = x * (an.tq1 + x * (an.tq2 + x * an.tq3));
+  float al = an.al0 + (float)kOmega * dt;
+  float sa, ca;
+  sincosf(al, &sa, &ca);
+  float f = an.fa32 + x * an.df32;
+  Cx<float> RA, RE;
+  response_residual<float>(f, ca, sa, p.Pr32, p.Pi32, p.k32, RA, RE);
+  float amp = powf(f, -7.0f / 6.0f);
+  out[0] = amp * RA.re;
+  out[1] = amp * RA.im;
+  out[2] = amp * RE.re;
+  out[3] = amp * RE.im;
+}
+
+// G_alpha at bin offset x from k_a, FP64 with the exact t(f) (stride checks).
+__device__ inline void g_exact64(const Part& p, double fa, double df, double x, double out[4]) {
+  double f = fa + x * df;
+  double t = time_of_freq(p, f);
   double sa, ca;
   sincos(orbit_angle(t), &sa, &ca);
-  double f = fa + df_off;
   const double kv[3] = {p.kx, p.ky, p.kz};
   Cx<double> RA, RE;
   response_residual<double>(f, ca, sa, p.Pr, p.Pi, kv, RA, RE);
@@ -94,61 +215,17 @@ __device__ inline void g_node64(const Part& p, double fa, double df_off, const d
   out[3] = amp * RE.im;
 }
 
-// G_alpha at frequency offset df_off from the anchor (FP32 response).
-__device__ inline void g_node(const Part& p, double fa, double df_off, const double T[4],
-                              float out[4]) {
-  double t = T[0] + df_off * (T[1] + df_off * (0.5 * T[2] + df_off * (T[3] * (1.0 / 6.0))));
-  double al = orbit_angle(t);
-  float sa, ca;
-  sincosf((float)al, &sa, &ca);
-  float f = (float)(fa + df_off);
-  Cx<float> RA, RE;
-  response_residual<float>(f, ca, sa, p.Pr32, p.Pi32, p.k32, RA, RE);
-  float amp = powf(f, -7.0f / 6.0f);
-  out[0] = amp * RA.re;
-  out[1] = amp * RA.im;
-  out[2] = amp * RE.re;
-  out[3] = amp * RE.im;
-}
-
-// Build the anchor of the span [ka, ka + B).
-__device__ inline void anchor_build(const Part& p, int ka, int B, double f_first, double df,
-                                    Anchor& an) {
-  double fa = f_first + (double)ka * df;
-  double Phi[5], T[4];
-  phase_derivs(p, fa, Phi, T);
-  double c1 = Phi[1] * df;
-  double c2 = Phi[2] * df * df * 0.5;
-  double c3 = Phi[3] * df * df * df * (1.0 / 6.0);
-  double c4 = Phi[4] * df * df * df * df * (1.0 / 24.0);
-  an.ph = turns_to_fixed(Phi[0]);
-  an.d1 = turns_to_fixed(c1 + c2 + c3 + c4);
-  an.d2 = turns_to_fixed(2.0 * c2 + 6.0 * c3 + 14.0 * c4);
-  an.d3 = turns_to_fixed(6.0 * c3 + 36.0 * c4);
-  an.d4 = turns_to_fixed(24.0 * c4);
-  float y0[4], y1[4], y2[4];
-  double h = 0.5 * (double)B;
-  g_node(p, fa, 0.0, T, y0);
-  g_node(p, fa, h * df, T, y1);
-  g_node(p, fa, 2.0 * h * df, T, y2);
-  float ih = (float)(1.0 / h);
+// Quadratic through nodes (0, y0), (h, y1), (2h, y2) as g0 + j (g1 + j g2).
+__device__ inline void quad_from_nodes(const float y0[4], const float y1[4], const float y2[4],
+                                       float h, RespQuad& q) {
+  float ih = 1.0f / h;
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     float g2 = 0.5f * (y0[c] - 2.0f * y1[c] + y2[c]) * ih * ih;
-    an.g0[c] = y0[c];
-    an.g1[c] = (y1[c] - y0[c]) * ih - g2 * (float)h;
-    an.g2[c] = g2;
+    q.g0[c] = y0[c];
+    q.g1[c] = (y1[c] - y0[c]) * ih - g2 * h;
+    q.g2[c] = g2;
   }
-}
-
-// Phase of the span polynomial at offset j (turns, FP64; for error checks)
-__device__ inline double anchor_poly_turns(const Part& p, double fa, double df, double j) {
-  double Phi[5], T[4];
-  phase_derivs(p, fa, Phi, T);
-  double x = j * df;
-  double v = Phi[0] + x * (Phi[1] + x * (0.5 * Phi[2] + x * (Phi[3] * (1.0 / 6.0) +
-                                                             x * (Phi[4] * (1.0 / 24.0)))));
-  return v;
 }
 
 }  // namespace scs

@@ -93,7 +93,8 @@ __device__ inline dd grid_freq_dd(double f_first, double df, int64_t k) {
 struct Part {
   int status;
   int k_lo, k_hi;   // support in grid bins (k_hi < k_lo: empty)
-  int log2B;        // mixed-path anchor stride
+  int log2B;        // mixed-path phase-anchor stride
+  int log2Br;       // mixed-path response sub-span (<= log2B)
   double f0;
   double piMs;      // pi G M / c^3 [s]
   dd tc;            // coalescence time [s]
@@ -122,6 +123,7 @@ __device__ inline void part_init(Part& p, const double* th) {
   p.k_lo = 0;
   p.k_hi = -1;
   p.log2B = 0;
+  p.log2Br = 0;
   bool fin = true;
   for (int i = 0; i < 8; ++i) fin = fin && isfinite(th[i]);
   double Mc = th[0], q = th[1], f0 = th[2];

@@ -3,13 +3,15 @@
 // Layout: one warp takes a work item (one chunk of kChunk grid bins x up to
 // 32 particles active in it), one lane per particle.  All lanes walk the
 // same bins, so each bin's pre-whitened data (float4 d~ and float2 w) is one
-// warp-uniform load shared by 32 templates.  Per bin and lane, in FP32:
-//   phase:     64-bit fixed-point forward differences (exact mod one turn)
+// warp-uniform load shared by 32 templates.  Per bin and lane, in FP32/INT32:
+//   phase:     degree-6 forward differences in 64-bit fixed point
+//              (exact modulo one turn), re-seeded at each phase anchor
 //   e^{i Phi}: MUFU sin/cos of the top 32 bits
-//   G_alpha:   quadratic in the bin offset (amplitude x residual response)
+//   G_alpha:   quadratic in the bin offset over a response sub-span
 //   z += d~ conj(G) e^{+2 pi i Phi},  hh += w |G|^2   (Sec. II.B [a|b]_n)
-// Sums run in 32-bin FP32 blocks flushed into Kahan accumulators; a
-// segment's x^2/hh (Sec. II.B, Upsilon_N) is added in FP64 when it closes.
+// Sums run in 32-bin FP32 blocks flushed into Kahan accumulators; when a
+// segment closes its x^2/hh (Sec. II.B, Upsilon_N) goes into a per-item
+// Kahan sum, written to the work unit's record in FP64.
 #include "scs_anchor.cuh"
 #include "scs_internal.cuh"
 
@@ -20,13 +22,91 @@ namespace {
 struct Kahan {
   float s, c;
 };
-__device__ inline void kadd(Kahan& k, float x) {
+__device__ __forceinline__ void kadd(Kahan& k, float x) {
   float y = x - k.c;
   float t = k.s + y;
   k.c = (t - k.s) - y;
   k.s = t;
 }
-__device__ inline float kval(const Kahan& k) { return k.s - k.c; }
+__device__ __forceinline__ float kval(const Kahan& k) { return k.s - k.c; }
+
+// per-lane state of one work item
+struct Lane {
+  int p, kb, ke, B, Br;
+  int n_cur, e_next;
+  int next_phase, next_resp, phase_k;
+  bool act, head, fresh, done;
+  const int* e;
+  float jf;
+  PhaseAnchor an;
+  RespQuad rq;
+  float yend[4];
+  Kahan szr, szi, shh, ups;
+  float bzr, bzi, bhh;
+  Rec r;
+};
+
+__device__ __forceinline__ void close_segment(Lane& L, const EvalArgs& a, double zs, int k) {
+  float zr = kval(L.szr) + L.bzr, zi = kval(L.szi) + L.bzi, hh = kval(L.shh) + L.bhh;
+  if (L.head) {
+    L.r.n_head = L.n_cur;
+    L.r.zr_h = zr * zs;
+    L.r.zi_h = zi * zs;
+    L.r.hh_h = hh * a.W0;
+    L.head = false;
+  } else {
+    float x2 = zr * zr + zi * zi;
+    if (hh > 0.f) kadd(L.ups, __fdividef(x2, hh));
+    if (a.seg_x) {
+      a.seg_x[(int64_t)L.p * a.N + L.n_cur] = (double)sqrtf(x2) * zs;
+      a.seg_hh[(int64_t)L.p * a.N + L.n_cur] = (double)hh * a.W0;
+    }
+  }
+  L.szr = Kahan{0.f, 0.f};
+  L.szi = Kahan{0.f, 0.f};
+  L.shh = Kahan{0.f, 0.f};
+  L.bzr = L.bzi = L.bhh = 0.f;
+  L.n_cur = advance_segment(L.e, a.N, L.n_cur, k);
+  L.e_next = __ldg(L.e + L.n_cur + 1);
+}
+
+// nb bins from k0; MASKED: some lane is only partly inside [kb, ke)
+template <bool MASKED>
+__device__ __forceinline__ void run_block(Lane& L, const EvalArgs& a, double zs, int k0,
+                                          int nb) {
+  for (int i = 0; i < nb; ++i) {
+    const int k = k0 + i;
+    const bool m = !MASKED || (L.act && (unsigned)(k - L.kb) < (unsigned)(L.ke - L.kb));
+    const bool hit = m && k == L.e_next;
+    if (__any_sync(kFull, hit)) {
+      if (hit) close_segment(L, a, zs, k);
+    }
+    const float4 dv = __ldg(a.d32 + k);
+    const float2 wv = __ldg(a.w32 + k);
+    // e^{+2 pi i Phi} from the top 32 bits of the fixed-point phase
+    const float turns = (float)(int)(L.an.d[0] >> 32) * 2.3283064365386963e-10f;
+    float sp, cp;
+    __sincosf(turns * 6.283185307179586f, &sp, &cp);
+    float G[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) G[q] = fmaf(L.jf, fmaf(L.jf, L.rq.g2[q], L.rq.g1[q]), L.rq.g0[q]);
+    // q = d~_A conj(G_A) + d~_E conj(G_E)
+    const float qr = dv.x * G[0] + dv.y * G[1] + dv.z * G[2] + dv.w * G[3];
+    const float qi = dv.y * G[0] - dv.x * G[1] + dv.w * G[2] - dv.z * G[3];
+    const float hb = wv.x * (G[0] * G[0] + G[1] * G[1]) + wv.y * (G[2] * G[2] + G[3] * G[3]);
+    float zr = qr * cp - qi * sp, zi = qr * sp + qi * cp;
+    if (MASKED && !m) {
+      zr = 0.f;
+      zi = 0.f;
+    }
+    L.bzr += zr;
+    L.bzi += zi;
+    L.bhh += (MASKED && !m) ? 0.f : hb;
+#pragma unroll
+    for (int r = 0; r < kOrd; ++r) L.an.d[r] += L.an.d[r + 1];
+    L.jf += 1.f;
+  }
+}
 
 __global__ void __launch_bounds__(128) k_main_mixed(EvalArgs a) {
   const int lane = threadIdx.x & 31;
@@ -41,117 +121,107 @@ __global__ void __launch_bounds__(128) k_main_mixed(EvalArgs a) {
     const int g = item - a.item_off[c];
     const int slot = g * 32 + lane;
     const bool has = slot < a.cnt[c];
-    const int p = has ? a.list[a.list_off[c] + slot] : -1;
     const int kc0 = c * kChunk;
     const int kc1 = min(kc0 + kChunk, a.K);
+    Lane L;
+    L.p = has ? a.list[a.list_off[c] + slot] : -1;
     Part pp;
-    int kb = 0, ke = 0, B = kChunk, first_anchor = kNoEdge;
+    L.kb = 0;
+    L.ke = 0;
+    L.B = kChunk;
+    L.Br = kChunk;
+    int first = kNoEdge;
     if (has) {
-      pp = a.part[p];
-      kb = max(kc0, pp.k_lo);
-      ke = min(kc1, pp.k_hi + 1);
-      B = 1 << pp.log2B;
-      first_anchor = (kb / B) * B;
+      pp = a.part[L.p];
+      L.kb = max(kc0, pp.k_lo);
+      L.ke = min(kc1, pp.k_hi + 1);
+      L.B = 1 << pp.log2B;
+      L.Br = 1 << pp.log2Br;
+      first = (L.kb / L.B) * L.B;
     }
-    const bool act = has && kb < ke;
-    if (!act) first_anchor = kNoEdge;
-    const int* e = act ? a.edges + (int64_t)p * a.edge_stride : a.edges;
-    int n_cur = act ? segment_of(e, a.N, kb) : 0;
-    int e_next = act ? __ldg(e + n_cur + 1) : kNoEdge;
-    bool head = true;
-    Rec r;
-    r.n_head = -1;
-    r.n_tail = -1;
-    r.zr_h = r.zi_h = r.hh_h = 0.0;
-    r.zr_t = r.zi_t = r.hh_t = 0.0;
-    r.ups = 0.0;
-    Kahan szr{0.f, 0.f}, szi{0.f, 0.f}, shh{0.f, 0.f};
-    float bzr = 0.f, bzi = 0.f, bhh = 0.f;
-    Anchor an;
-    an.ph = an.d1 = an.d2 = an.d3 = an.d4 = 0;
+    L.act = has && L.kb < L.ke;
+    if (!L.act) first = kNoEdge;
+    L.e = L.act ? a.edges + (int64_t)L.p * a.edge_stride : a.edges;
+    L.n_cur = L.act ? segment_of(L.e, a.N, L.kb) : 0;
+    L.e_next = L.act ? __ldg(L.e + L.n_cur + 1) : kNoEdge;
+    L.head = true;
+    L.fresh = true;
+    L.done = false;
+    L.r.n_head = -1;
+    L.r.n_tail = -1;
+    L.r.zr_h = L.r.zi_h = L.r.hh_h = 0.0;
+    L.r.zr_t = L.r.zi_t = L.r.hh_t = 0.0;
+    L.r.ups = 0.0;
+    L.szr = L.szi = L.shh = L.ups = Kahan{0.f, 0.f};
+    L.bzr = L.bzi = L.bhh = 0.f;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) an.g0[q] = an.g1[q] = an.g2[q] = 0.f;
-    float jf = 0.f;
-    int next_anchor = first_anchor;
-    const int kw0 = warp_min(first_anchor);
-    const int kw1 = warp_max(act ? ke : -1);
-    const int BW = min(32, warp_min(act ? B : kChunk));
+    for (int r = 0; r <= kOrd; ++r) L.an.d[r] = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) L.rq.g0[q] = L.rq.g1[q] = L.rq.g2[q] = L.yend[q] = 0.f;
+    L.jf = 0.f;
+    L.next_phase = first;
+    L.next_resp = first;
+    L.phase_k = first;
+    const int kw0 = warp_min(first);
+    const int kw1 = warp_max(L.act ? L.ke : -1);
+    const int BW = min(32, warp_min(L.act ? L.Br : kChunk));
     for (int k0 = kw0; k0 < kw1; k0 += BW) {
-      if (act && k0 == next_anchor && k0 < ke) {
-        anchor_build(pp, k0, B, a.f_first, a.df, an);
-        next_anchor += B;
-        jf = 0.f;
+      if (L.act && k0 == L.next_phase && k0 < L.ke) {
+        phase_anchor(pp, k0, a.f_first, a.df, L.an);
+        L.phase_k = k0;
+        L.next_phase += L.B;
+        L.fresh = true;
+      }
+      if (L.act && k0 == L.next_resp && k0 < L.ke) {
+        const float x0 = (float)(k0 - L.phase_k), h = 0.5f * (float)L.Br;
+        float y0[4], y1[4];
+        if (L.fresh) {
+          g_node32(pp, L.an, x0, y0);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) y0[q] = L.yend[q];
+        }
+        g_node32(pp, L.an, x0 + h, y1);
+        g_node32(pp, L.an, x0 + 2.0f * h, L.yend);
+        quad_from_nodes(y0, y1, L.yend, h, L.rq);
+        L.fresh = false;
+        L.jf = 0.f;
+        L.next_resp += L.Br;
+      }
+      if (L.act && !L.done && k0 >= L.ke) {
+        // past the support: contribute exact zeros from here on
+#pragma unroll
+        for (int q = 0; q < 4; ++q) L.rq.g0[q] = L.rq.g1[q] = L.rq.g2[q] = 0.f;
+        L.e_next = kNoEdge;
+        L.done = true;
       }
       const int nb = min(BW, kw1 - k0);
-      for (int i = 0; i < nb; ++i) {
-        const int k = k0 + i;
-        const bool m = act && (unsigned)(k - kb) < (unsigned)(ke - kb);
-        const bool hit = m && k == e_next;
-        if (__any_sync(kFull, hit)) {
-          if (hit) {
-            float zr = kval(szr) + bzr, zi = kval(szi) + bzi, hh = kval(shh) + bhh;
-            if (head) {
-              r.n_head = n_cur;
-              r.zr_h = zr * zs; r.zi_h = zi * zs; r.hh_h = hh * a.W0;
-              head = false;
-            } else {
-              float x2 = zr * zr + zi * zi;
-              if (hh > 0.f) r.ups += (double)(x2 / hh);
-              if (a.seg_x) {
-                a.seg_x[(int64_t)p * a.N + n_cur] = (double)sqrtf(x2) * zs;
-                a.seg_hh[(int64_t)p * a.N + n_cur] = (double)hh * a.W0;
-              }
-            }
-            szr = Kahan{0.f, 0.f};
-            szi = Kahan{0.f, 0.f};
-            shh = Kahan{0.f, 0.f};
-            bzr = bzi = bhh = 0.f;
-            n_cur = advance_segment(e, a.N, n_cur, k);
-            e_next = __ldg(e + n_cur + 1);
-          }
-        }
-        const float4 dv = __ldg(a.d32 + k);
-        const float2 wv = __ldg(a.w32 + k);
-        // e^{+2 pi i Phi} from the top 32 bits of the fixed-point phase
-        const float turns = (float)(int)(an.ph >> 32) * 2.3283064365386963e-10f;
-        float sp, cp;
-        __sincosf(turns * 6.283185307179586f, &sp, &cp);
-        float G[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) G[q] = fmaf(jf, fmaf(jf, an.g2[q], an.g1[q]), an.g0[q]);
-        // q = d~_A conj(G_A) + d~_E conj(G_E)
-        const float qr = dv.x * G[0] + dv.y * G[1] + dv.z * G[2] + dv.w * G[3];
-        const float qi = dv.y * G[0] - dv.x * G[1] + dv.w * G[2] - dv.z * G[3];
-        const float hb = wv.x * (G[0] * G[0] + G[1] * G[1]) + wv.y * (G[2] * G[2] + G[3] * G[3]);
-        if (m) {
-          bzr += qr * cp - qi * sp;
-          bzi += qr * sp + qi * cp;
-          bhh += hb;
-        }
-        an.ph += an.d1;
-        an.d1 += an.d2;
-        an.d2 += an.d3;
-        an.d3 += an.d4;
-        jf += 1.f;
-      }
+      const bool partial = L.act && !L.done && !(L.kb <= k0 && k0 + nb <= L.ke);
+      if (__any_sync(kFull, partial)) run_block<true>(L, a, zs, k0, nb);
+      else run_block<false>(L, a, zs, k0, nb);
       if (((k0 + BW) & 31) == 0) {
-        kadd(szr, bzr);
-        kadd(szi, bzi);
-        kadd(shh, bhh);
-        bzr = bzi = bhh = 0.f;
+        kadd(L.szr, L.bzr);
+        kadd(L.szi, L.bzi);
+        kadd(L.shh, L.bhh);
+        L.bzr = L.bzi = L.bhh = 0.f;
       }
     }
-    if (act) {
-      float zr = kval(szr) + bzr, zi = kval(szi) + bzi, hh = kval(shh) + bhh;
-      if (head) {
-        r.n_head = n_cur;
-        r.zr_h = zr * zs; r.zi_h = zi * zs; r.hh_h = hh * a.W0;
+    if (L.act) {
+      float zr = kval(L.szr) + L.bzr, zi = kval(L.szi) + L.bzi, hh = kval(L.shh) + L.bhh;
+      if (L.head) {
+        L.r.n_head = L.n_cur;
+        L.r.zr_h = zr * zs;
+        L.r.zi_h = zi * zs;
+        L.r.hh_h = hh * a.W0;
       } else {
-        r.n_tail = n_cur;
-        r.zr_t = zr * zs; r.zi_t = zi * zs; r.hh_t = hh * a.W0;
+        L.r.n_tail = L.n_cur;
+        L.r.zr_t = zr * zs;
+        L.r.zi_t = zi * zs;
+        L.r.hh_t = hh * a.W0;
       }
+      L.r.ups = (double)L.ups.s - (double)L.ups.c;
     }
-    if (has && pp.status == kOk) a.rec[a.rec_off[p] + (c - chunk_of(pp.k_lo))] = r;
+    if (has && pp.status == kOk) a.rec[a.rec_off[L.p] + (c - chunk_of(pp.k_lo))] = L.r;
   }
 }
 

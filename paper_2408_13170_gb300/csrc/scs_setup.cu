@@ -10,85 +10,110 @@ namespace scs {
 namespace {
 
 // ---------------------------------------------------------- anchor stride
-// Largest power-of-two stride B <= kChunk for which, over a span, the
-// degree-4 phase polynomial stays within kTolPhase turns of the exact FP64
-// phase and the quadratic through j = 0, B/2, B (built here from FP64 node
-// values, so that only the truncation is measured) stays within kTolG of
-// the exact G relative to |G_A| + |G_E|.  Checked at three spans of the
-// support (first, middle, last) and three offsets per span.  The FP32
-// rounding of the kernel's own node values (~1e-7 to 1e-6 relative) does not
-// depend on B and is bounded by the parity tests instead.
+// Strides of the mixed path, chosen per particle:
+//  - phase: the largest power of two B <= kChunk for which the kernel's own
+//    degree-6 fixed-point phase polynomial stays within kTolPhase turns of
+//    the exact (double-double) phase;
+//  - response: the largest Br <= B for which the quadratic through FP64
+//    nodes at 0, Br/2, Br stays within kTolG of the exact G relative to
+//    |G_A| + |G_E| (so only the truncation is measured; the FP32 rounding of
+//    the kernel's nodes does not depend on Br and is bounded by the parity
+//    tests).
+// Both start from an analytic estimate of the remainder at the low end of
+// the support (where the derivatives are largest) and are verified at three
+// spans (first, middle, last) and three offsets per span, halving on failure.
 constexpr double kTolPhase = 2e-8;   // turns
 constexpr double kTolG = 3e-7;       // relative to |G_A| + |G_E|
 
-__device__ bool span_ok(const Part& p, int B, int ka, double f_first, double df) {
-  double fa = f_first + (double)ka * df;
-  int jlo = max(0, p.k_lo - ka), jhi = min(B - 1, p.k_hi - ka);
-  if (jhi < jlo) return true;
-  double Pd[5], Td[4];
-  phase_derivs(p, fa, Pd, Td);
-  double h = 0.5 * (double)B;
-  double y0[4], y1[4], y2[4];
-  g_node64(p, fa, 0.0, Td, y0);
-  g_node64(p, fa, h * df, Td, y1);
-  g_node64(p, fa, 2.0 * h * df, Td, y2);
-  const int js[3] = {B / 4, (3 * B) / 4, B - 1};
-  for (int t = 0; t < 3; ++t) {
-    int j = min(max(js[t], jlo), jhi);
-    int k = ka + j;
-    Cx<double> GA, GE;
-    double phi;
-    bin_fp64(p, f_first, df, k, GA, GE, phi);
-    double pj = anchor_poly_turns(p, fa, df, (double)j);
-    double dphi = pj - phi;
-    dphi -= rint(dphi);
-    if (!(fabs(dphi) <= kTolPhase)) return false;
-    // Lagrange quadratic through (0, y0), (h, y1), (2h, y2) at x = j
-    double x = (double)j;
-    double l0 = (x - h) * (x - 2.0 * h) / (2.0 * h * h);
-    double l1 = -x * (x - 2.0 * h) / (h * h);
-    double l2 = x * (x - h) / (2.0 * h * h);
-    double q[4];
-    for (int c = 0; c < 4; ++c) q[c] = l0 * y0[c] + l1 * y1[c] + l2 * y2[c];
-    double mag = hypot(GA.re, GA.im) + hypot(GE.re, GE.im);
-    double ierr = fabs(q[0] - GA.re) + fabs(q[1] - GA.im) + fabs(q[2] - GE.re) + fabs(q[3] - GE.im);
-    if (!(ierr <= kTolG * mag)) return false;
+__device__ inline int span_start(int k, int B) { return (k / B) * B; }
+
+__device__ bool phase_ok(const Part& p, int B, double f_first, double df) {
+  const int starts[3] = {span_start(p.k_lo, B), span_start((p.k_lo + p.k_hi) / 2, B),
+                         span_start(p.k_hi, B)};
+  for (int s = 0; s < 3; ++s) {
+    int ka = starts[s];
+    int jlo = max(0, p.k_lo - ka), jhi = min(B - 1, p.k_hi - ka);
+    if (jhi < jlo) continue;
+    PhaseAnchor an;
+    phase_anchor(p, ka, f_first, df, an);
+    const int js[3] = {B / 4, (3 * B) / 4, B - 1};
+    for (int t = 0; t < 3; ++t) {
+      int j = min(max(js[t], jlo), jhi);
+      double tt;
+      double exact = phase_turns_fp64(p, grid_freq_dd(f_first, df, ka + j), tt);
+      double got = (double)(int64_t)phase_anchor_at(an, j) * 5.421010862427522e-20;
+      double d = got - exact;
+      d -= rint(d);
+      if (!(fabs(d) <= kTolPhase)) return false;
+    }
   }
   return true;
 }
 
-__device__ int choose_log2B(const Part& p, double f_first, double df) {
-  // analytic start: Taylor remainder of the PN phase and of the Doppler
-  // phase at the low end of the support (where both are largest)
+__device__ bool resp_ok(const Part& p, int Br, double f_first, double df) {
+  const int starts[3] = {span_start(p.k_lo, Br), span_start((p.k_lo + p.k_hi) / 2, Br),
+                         span_start(p.k_hi, Br)};
+  const double h = 0.5 * (double)Br;
+  for (int s = 0; s < 3; ++s) {
+    int ka = starts[s];
+    int jlo = max(0, p.k_lo - ka), jhi = min(Br - 1, p.k_hi - ka);
+    if (jhi < jlo) continue;
+    double fa = f_first + (double)ka * df;
+    double y0[4], y1[4], y2[4];
+    g_exact64(p, fa, df, 0.0, y0);
+    g_exact64(p, fa, df, h, y1);
+    g_exact64(p, fa, df, 2.0 * h, y2);
+    const int js[3] = {Br / 4, (3 * Br) / 4, Br - 1};
+    for (int t = 0; t < 3; ++t) {
+      double x = (double)min(max(js[t], jlo), jhi);
+      double g[4];
+      g_exact64(p, fa, df, x, g);
+      double l0 = (x - h) * (x - 2.0 * h) / (2.0 * h * h);
+      double l1 = -x * (x - 2.0 * h) / (h * h);
+      double l2 = x * (x - h) / (2.0 * h * h);
+      double err = 0.0, mag = hypot(g[0], g[1]) + hypot(g[2], g[3]);
+      for (int c = 0; c < 4; ++c) err += fabs(l0 * y0[c] + l1 * y1[c] + l2 * y2[c] - g[c]);
+      if (!(err <= kTolG * mag)) return false;
+    }
+  }
+  return true;
+}
+
+__device__ int log2_floor_clamp(double x) {
+  int l = 0;
+  while (l < kMaxLog2B && (double)(2 << l) <= x) ++l;
+  return l;
+}
+
+__device__ void choose_strides(Part& p, double f_first, double df) {
   double flo = f_first + (double)p.k_lo * df;
   double fhi = f_first + (double)p.k_hi * df;
-  double u = rcbrt(flo), u3 = u * u * u;
-  double d5 = 0.0, tp = 0.0;
-  double upow[4] = {u3 * u * u, u3, u * u, u};
+  // analytic starting points at f_lo: 7th bin-derivative of the PN phase and
+  // the Doppler remainder f R (Omega dt/dk B)^7 / 7!, and the response
+  // rate ~ 4 Omega dt/dk per bin (orbital harmonics of the residual response)
+  double rdf = df / flo, u = rcbrt(flo), u2 = u * u;
+  double upow[4] = {u2 * u2 * u, u2 * u, u2, u};
+  double d7 = 0.0, T1 = 0.0;
   for (int m = 0; m < 4; ++m) {
     double n = (double)kPow[m];
     double val = p.A[m].hi * upow[m];
-    for (int r = 0; r < 5; ++r) {
-      if (r == 2) tp += val;   // F'' = dt/df
-      val *= -(n + 3.0 * r) * (1.0 / 3.0) * u3;
+    for (int r = 0; r < 7; ++r) {
+      if (r == 2) T1 += val / df;   // t' df = F'' df^2 / df
+      val *= -(n + 3.0 * r) * (1.0 / 3.0) * rdf;
     }
-    d5 += val;
+    d7 += val;
   }
-  double Bpn = pow(120.0 * 0.5 * kTolPhase / fmax(fabs(d5), 1e-300), 0.2) / df;
-  double x = pow(120.0 * 0.5 * kTolPhase / (fhi * p.Rcb + 1e-30), 0.2);
-  double Bdop = x / (kOmega * fabs(tp) * df + 1e-300);
-  double Bs = fmin(fmin(Bpn, Bdop), (double)kChunk);
-  int l = 0;
-  while (l < kMaxLog2B && (double)(2 << l) <= Bs) ++l;
-  for (; l > 0; --l) {
-    int B = 1 << l;
-    int k0 = (p.k_lo / B) * B, k2 = (p.k_hi / B) * B;
-    int k1 = (((p.k_lo + p.k_hi) / 2) / B) * B;
-    if (span_ok(p, B, k0, f_first, df) && span_ok(p, B, k1, f_first, df) &&
-        span_ok(p, B, k2, f_first, df))
-      break;
-  }
-  return l;
+  double Bpn = pow(5040.0 * 0.5 * kTolPhase / fmax(fabs(d7), 1e-300), 1.0 / 7.0);
+  double wdop = kOmega * fabs(T1);
+  double Bdop = pow(5040.0 * 0.5 * kTolPhase / (fhi * p.Rcb + 1e-30), 1.0 / 7.0) /
+                fmax(wdop, 1e-300);
+  int l = log2_floor_clamp(fmin(fmin(Bpn, Bdop), (double)kChunk));
+  while (l > 0 && !phase_ok(p, 1 << l, f_first, df)) --l;
+  double Br = 0.033 / fmax(4.0 * wdop, 1e-12);
+  int lr = min(l, log2_floor_clamp(Br));
+  while (lr > 0 && !resp_ok(p, 1 << lr, f_first, df)) --lr;
+  p.log2B = l;
+  p.log2Br = lr;
 }
 
 }  // namespace
@@ -105,7 +130,7 @@ __global__ void k_setup(const double* params, int P, double f_first, double df, 
   part_support(p, f_first, df, K, T_obs);
   int2 cr = make_int2(0, -1);
   if (p.status == kOk) {
-    if (want_stride) p.log2B = choose_log2B(p, f_first, df);
+    if (want_stride) choose_strides(p, f_first, df);
     cr = make_int2(chunk_of(p.k_lo), chunk_of(p.k_hi));
     atomicAdd(diff + cr.x, 1);
     atomicAdd(diff + cr.y + 1, -1);
