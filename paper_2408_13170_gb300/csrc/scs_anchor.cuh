@@ -183,20 +183,22 @@ __device__ inline uint64_t phase_anchor_at(const PhaseAnchor& an, int j) {
   return acc;
 }
 
-// G_alpha at bin offset x from the phase anchor (FP32 node).
-__device__ inline void g_node32(const Part& p, const PhaseAnchor& an, float x, float out[4]) {
-  float dt = x * (an.tq1 + x * (an.tq2 + x * an.tq3));
-  float al = an.al0 + (float)kOmega * dt;
+// G_alpha at bin offset x from the phase anchor (FP32 node).  Not inlined:
+// called once or twice per response sub-span, so one copy of the response
+// code keeps the hot loop's instruction footprint small.
+static __device__ __noinline__ void g_node32(const Part* __restrict__ pp, float al0, float tq1,
+                                      float tq2, float tq3, float fa32, float df32, float x,
+                                      float4* out) {
+  const Part& p = *pp;
+  float dt = x * (tq1 + x * (tq2 + x * tq3));
+  float al = al0 + (float)kOmega * dt;
   float sa, ca;
   sincosf(al, &sa, &ca);
-  float f = an.fa32 + x * an.df32;
+  float f = fa32 + x * df32;
   Cx<float> RA, RE;
   response_residual<float>(f, ca, sa, p.Pr32, p.Pi32, p.k32, RA, RE);
   float amp = powf(f, -7.0f / 6.0f);
-  out[0] = amp * RA.re;
-  out[1] = amp * RA.im;
-  out[2] = amp * RE.re;
-  out[3] = amp * RE.im;
+  *out = make_float4(amp * RA.re, amp * RA.im, amp * RE.re, amp * RE.im);
 }
 
 // G_alpha at bin offset x from k_a, FP64 with the exact t(f) (stride checks).
@@ -216,14 +218,15 @@ __device__ inline void g_exact64(const Part& p, double fa, double df, double x, 
 }
 
 // Quadratic through nodes (0, y0), (h, y1), (2h, y2) as g0 + j (g1 + j g2).
-__device__ inline void quad_from_nodes(const float y0[4], const float y1[4], const float y2[4],
-                                       float h, RespQuad& q) {
+__device__ inline void quad_from_nodes(float4 y0, float4 y1, float4 y2, float h, RespQuad& q) {
+  const float a0[4] = {y0.x, y0.y, y0.z, y0.w}, a1[4] = {y1.x, y1.y, y1.z, y1.w},
+              a2[4] = {y2.x, y2.y, y2.z, y2.w};
   float ih = 1.0f / h;
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
-    float g2 = 0.5f * (y0[c] - 2.0f * y1[c] + y2[c]) * ih * ih;
-    q.g0[c] = y0[c];
-    q.g1[c] = (y1[c] - y0[c]) * ih - g2 * h;
+    float g2 = 0.5f * (a0[c] - 2.0f * a1[c] + a2[c]) * ih * ih;
+    q.g0[c] = a0[c];
+    q.g1[c] = (a1[c] - a0[c]) * ih - g2 * h;
     q.g2[c] = g2;
   }
 }

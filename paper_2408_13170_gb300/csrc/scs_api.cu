@@ -277,8 +277,11 @@ int scs_set_data(scs_ctx* ctx, int sid, const double* A, const double* E, const 
   CK(ds.dA64.reserve(sizeof(double2) * Kz));
   CK(ds.dE64.reserve(sizeof(double2) * Kz));
   CK(ds.w64.reserve(sizeof(double2) * Kz));
-  CK(ds.d32.reserve(sizeof(float4) * Kz));
-  CK(ds.w32.reserve(sizeof(float2) * Kz));
+  // FP32 copies carry a zeroed tail: the hot loop loads one bin ahead
+  CK(ds.d32.reserve(sizeof(float4) * (Kz + 32)));
+  CK(ds.w32.reserve(sizeof(float2) * (Kz + 32)));
+  CK(cudaMemsetAsync(ds.d32.as<float4>() + Kz, 0, sizeof(float4) * 32, s));
+  CK(cudaMemsetAsync(ds.w32.as<float2>() + Kz, 0, sizeof(float2) * 32, s));
   // raw inputs on the device (reuse scratch)
   const void* in[4] = {A, E, S_A, S_E};
   size_t sz[4] = {sizeof(double2) * Kz, sizeof(double2) * Kz, sizeof(double) * Kz,

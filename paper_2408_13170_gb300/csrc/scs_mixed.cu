@@ -30,29 +30,33 @@ __device__ __forceinline__ void kadd(Kahan& k, float x) {
 }
 __device__ __forceinline__ float kval(const Kahan& k) { return k.s - k.c; }
 
-// per-lane state of one work item
+// per-lane state of one work item (kept in registers)
 struct Lane {
-  int p, kb, ke, B, Br;
+  int kb, ke;
   int n_cur, e_next;
   int next_phase, next_resp, phase_k;
+  int log2B, log2Br;
   bool act, head, fresh, done;
   const int* e;
+  const Part* pp;
+  Rec* rec;          // this (particle, chunk) unit's record
+  int p;
   float jf;
-  PhaseAnchor an;
+  uint64_t d[kOrd + 1];
+  float al0, tq1, tq2, tq3, fa32;
   RespQuad rq;
-  float yend[4];
+  float4 yend;
   Kahan szr, szi, shh, ups;
   float bzr, bzi, bhh;
-  Rec r;
 };
 
 __device__ __forceinline__ void close_segment(Lane& L, const EvalArgs& a, double zs, int k) {
   float zr = kval(L.szr) + L.bzr, zi = kval(L.szi) + L.bzi, hh = kval(L.shh) + L.bhh;
   if (L.head) {
-    L.r.n_head = L.n_cur;
-    L.r.zr_h = zr * zs;
-    L.r.zi_h = zi * zs;
-    L.r.hh_h = hh * a.W0;
+    L.rec->n_head = L.n_cur;
+    L.rec->zr_h = zr * zs;
+    L.rec->zi_h = zi * zs;
+    L.rec->hh_h = hh * a.W0;
     L.head = false;
   } else {
     float x2 = zr * zr + zi * zi;
@@ -70,23 +74,29 @@ __device__ __forceinline__ void close_segment(Lane& L, const EvalArgs& a, double
   L.e_next = __ldg(L.e + L.n_cur + 1);
 }
 
-// nb bins from k0; MASKED: some lane is only partly inside [kb, ke)
+// nb bins from k0; MASKED: some lane is only partly inside [kb, ke).  The
+// data of bin k+1 is loaded while bin k is computed (the FP32 arrays carry a
+// zeroed tail for the last prefetch).
 template <bool MASKED>
 __device__ __forceinline__ void run_block(Lane& L, const EvalArgs& a, double zs, int k0,
                                           int nb) {
+  float4 dn = __ldg(a.d32 + k0);
+  float2 wn = __ldg(a.w32 + k0);
   for (int i = 0; i < nb; ++i) {
     const int k = k0 + i;
+    const float4 dv = dn;
+    const float2 wv = wn;
+    dn = __ldg(a.d32 + k + 1);
+    wn = __ldg(a.w32 + k + 1);
     const bool m = !MASKED || (L.act && (unsigned)(k - L.kb) < (unsigned)(L.ke - L.kb));
     const bool hit = m && k == L.e_next;
     if (__any_sync(kFull, hit)) {
       if (hit) close_segment(L, a, zs, k);
     }
-    const float4 dv = __ldg(a.d32 + k);
-    const float2 wv = __ldg(a.w32 + k);
     // e^{+2 pi i Phi} from the top 32 bits of the fixed-point phase
-    const float turns = (float)(int)(L.an.d[0] >> 32) * 2.3283064365386963e-10f;
+    const float ang = (float)(int)(L.d[0] >> 32) * 1.4629180792671596e-09f;   // 2 pi / 2^32
     float sp, cp;
-    __sincosf(turns * 6.283185307179586f, &sp, &cp);
+    __sincosf(ang, &sp, &cp);
     float G[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) G[q] = fmaf(L.jf, fmaf(L.jf, L.rq.g2[q], L.rq.g1[q]), L.rq.g0[q]);
@@ -103,15 +113,16 @@ __device__ __forceinline__ void run_block(Lane& L, const EvalArgs& a, double zs,
     L.bzi += zi;
     L.bhh += (MASKED && !m) ? 0.f : hb;
 #pragma unroll
-    for (int r = 0; r < kOrd; ++r) L.an.d[r] += L.an.d[r + 1];
+    for (int r = 0; r < kOrd; ++r) L.d[r] += L.d[r + 1];
     L.jf += 1.f;
   }
 }
 
-__global__ void __launch_bounds__(128) k_main_mixed(EvalArgs a) {
+__global__ void __launch_bounds__(128, 4) k_main_mixed(EvalArgs a) {
   const int lane = threadIdx.x & 31;
   const int total = a.item_off[a.n_chunks];
   const double zs = sqrt(a.W0);   // FP32 sums -> physical units
+  const float df32 = (float)a.df;
   for (;;) {
     int item = 0;
     if (lane == 0) item = atomicAdd(a.item_counter, 1);
@@ -124,20 +135,22 @@ __global__ void __launch_bounds__(128) k_main_mixed(EvalArgs a) {
     const int kc0 = c * kChunk;
     const int kc1 = min(kc0 + kChunk, a.K);
     Lane L;
-    L.p = has ? a.list[a.list_off[c] + slot] : -1;
-    Part pp;
+    L.p = has ? a.list[a.list_off[c] + slot] : 0;
+    L.pp = a.part + L.p;
     L.kb = 0;
     L.ke = 0;
-    L.B = kChunk;
-    L.Br = kChunk;
+    L.log2B = 12;
+    L.log2Br = 12;
     int first = kNoEdge;
+    L.rec = a.rec;
     if (has) {
-      pp = a.part[L.p];
-      L.kb = max(kc0, pp.k_lo);
-      L.ke = min(kc1, pp.k_hi + 1);
-      L.B = 1 << pp.log2B;
-      L.Br = 1 << pp.log2Br;
-      first = (L.kb / L.B) * L.B;
+      const int klo = L.pp->k_lo, khi = L.pp->k_hi;
+      L.kb = max(kc0, klo);
+      L.ke = min(kc1, khi + 1);
+      L.log2B = L.pp->log2B;
+      L.log2Br = L.pp->log2Br;
+      first = (L.kb >> L.log2B) << L.log2B;
+      L.rec = a.rec + a.rec_off[L.p] + (c - chunk_of(klo));
     }
     L.act = has && L.kb < L.ke;
     if (!L.act) first = kNoEdge;
@@ -147,46 +160,47 @@ __global__ void __launch_bounds__(128) k_main_mixed(EvalArgs a) {
     L.head = true;
     L.fresh = true;
     L.done = false;
-    L.r.n_head = -1;
-    L.r.n_tail = -1;
-    L.r.zr_h = L.r.zi_h = L.r.hh_h = 0.0;
-    L.r.zr_t = L.r.zi_t = L.r.hh_t = 0.0;
-    L.r.ups = 0.0;
     L.szr = L.szi = L.shh = L.ups = Kahan{0.f, 0.f};
     L.bzr = L.bzi = L.bhh = 0.f;
 #pragma unroll
-    for (int r = 0; r <= kOrd; ++r) L.an.d[r] = 0;
+    for (int r = 0; r <= kOrd; ++r) L.d[r] = 0;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) L.rq.g0[q] = L.rq.g1[q] = L.rq.g2[q] = L.yend[q] = 0.f;
+    for (int q = 0; q < 4; ++q) L.rq.g0[q] = L.rq.g1[q] = L.rq.g2[q] = 0.f;
+    L.yend = make_float4(0.f, 0.f, 0.f, 0.f);
+    L.al0 = L.tq1 = L.tq2 = L.tq3 = L.fa32 = 0.f;
     L.jf = 0.f;
     L.next_phase = first;
     L.next_resp = first;
     L.phase_k = first;
     const int kw0 = warp_min(first);
     const int kw1 = warp_max(L.act ? L.ke : -1);
-    const int BW = min(32, warp_min(L.act ? L.Br : kChunk));
+    const int BW = min(32, 1 << warp_min(L.act ? L.log2Br : 12));
     for (int k0 = kw0; k0 < kw1; k0 += BW) {
       if (L.act && k0 == L.next_phase && k0 < L.ke) {
-        phase_anchor(pp, k0, a.f_first, a.df, L.an);
+        PhaseAnchor an;
+        phase_anchor(*L.pp, k0, a.f_first, a.df, an);
+#pragma unroll
+        for (int r = 0; r <= kOrd; ++r) L.d[r] = an.d[r];
+        L.al0 = an.al0;
+        L.tq1 = an.tq1;
+        L.tq2 = an.tq2;
+        L.tq3 = an.tq3;
+        L.fa32 = an.fa32;
         L.phase_k = k0;
-        L.next_phase += L.B;
+        L.next_phase += 1 << L.log2B;
         L.fresh = true;
       }
       if (L.act && k0 == L.next_resp && k0 < L.ke) {
-        const float x0 = (float)(k0 - L.phase_k), h = 0.5f * (float)L.Br;
-        float y0[4], y1[4];
-        if (L.fresh) {
-          g_node32(pp, L.an, x0, y0);
-        } else {
-#pragma unroll
-          for (int q = 0; q < 4; ++q) y0[q] = L.yend[q];
-        }
-        g_node32(pp, L.an, x0 + h, y1);
-        g_node32(pp, L.an, x0 + 2.0f * h, L.yend);
+        const float x0 = (float)(k0 - L.phase_k), h = 0.5f * (float)(1 << L.log2Br);
+        float4 y0, y1;
+        if (L.fresh) g_node32(L.pp, L.al0, L.tq1, L.tq2, L.tq3, L.fa32, df32, x0, &y0);
+        else y0 = L.yend;
+        g_node32(L.pp, L.al0, L.tq1, L.tq2, L.tq3, L.fa32, df32, x0 + h, &y1);
+        g_node32(L.pp, L.al0, L.tq1, L.tq2, L.tq3, L.fa32, df32, x0 + 2.0f * h, &L.yend);
         quad_from_nodes(y0, y1, L.yend, h, L.rq);
         L.fresh = false;
         L.jf = 0.f;
-        L.next_resp += L.Br;
+        L.next_resp += 1 << L.log2Br;
       }
       if (L.act && !L.done && k0 >= L.ke) {
         // past the support: contribute exact zeros from here on
@@ -209,19 +223,20 @@ __global__ void __launch_bounds__(128) k_main_mixed(EvalArgs a) {
     if (L.act) {
       float zr = kval(L.szr) + L.bzr, zi = kval(L.szi) + L.bzi, hh = kval(L.shh) + L.bhh;
       if (L.head) {
-        L.r.n_head = L.n_cur;
-        L.r.zr_h = zr * zs;
-        L.r.zi_h = zi * zs;
-        L.r.hh_h = hh * a.W0;
+        L.rec->n_head = L.n_cur;
+        L.rec->zr_h = zr * zs;
+        L.rec->zi_h = zi * zs;
+        L.rec->hh_h = hh * a.W0;
+        L.rec->n_tail = -1;
+        L.rec->zr_t = L.rec->zi_t = L.rec->hh_t = 0.0;
       } else {
-        L.r.n_tail = L.n_cur;
-        L.r.zr_t = zr * zs;
-        L.r.zi_t = zi * zs;
-        L.r.hh_t = hh * a.W0;
+        L.rec->n_tail = L.n_cur;
+        L.rec->zr_t = zr * zs;
+        L.rec->zi_t = zi * zs;
+        L.rec->hh_t = hh * a.W0;
       }
-      L.r.ups = (double)L.ups.s - (double)L.ups.c;
+      L.rec->ups = (double)L.ups.s - (double)L.ups.c;
     }
-    if (has && pp.status == kOk) a.rec[a.rec_off[L.p] + (c - chunk_of(pp.k_lo))] = L.r;
   }
 }
 
