@@ -157,6 +157,33 @@ int scs_segment_edges(scs_ctx *ctx, int stream_id, const double *params,
 int scs_set_profiling(scs_ctx *ctx, int enable);
 int scs_last_timings(scs_ctx *ctx, double *ms);
 
+/* scs_eval_stat without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc at evaluation time -- code being captured into a CUDA graph
+ * (allocation is not a capturable operation), services whose device memory
+ * is entirely owned by another allocator, and loops that must not pay an
+ * allocation's latency or implicit synchronisation.
+ *   Same evaluation as scs_eval_stat (path and segmentation of the context
+ *   and stream), without per-segment outputs.  params (P x 8) and stat (P)
+ *   must be device memory.  Asynchronous on cuda_stream (NULL: the
+ *   context's stream).
+ *   Scratch: a fixed 64 MiB device array inside the library, held by every
+ *   GPU that loads it until the process exits; no cudaMalloc, cudaFree or
+ *   allocating library routine is called.  Calls whose scratch would exceed
+ *   it are rejected with SCS_EINVAL and a message giving the bytes needed
+ *   (roughly 20 + 68 C bytes per particle, C = ceil(K/4096) chunks, plus
+ *   4 (N+1) + 16 (K/1024 + 2) bytes per particle for equal-SNR^2 segments).
+ *   The first call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   Every call shares the array and it keeps the previous call's contents:
+ *   calls that overlap on the GPU (different streams, or different contexts
+ *   on one device) race and must be serialised by the caller.
+ * The stream's data (scs_set_data) and segmentation must already be set.
+ * Errors: SCS_EINVAL (sizes, host pointers), SCS_ENODATA, SCS_ECUDA,
+ * SCS_EUNSUPPORTED (device index >= 64). */
+int scs_eval_stat_noalloc(scs_ctx *ctx, int stream_id, const double *params,
+                          int64_t P, double *stat, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -653,3 +653,151 @@ int scs_last_timings(scs_ctx* ctx, double* ms) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Evaluation without device allocation (scs_eval_stat_noalloc).
+//
+// All per-call scratch comes from one file-scope device array of
+// kNoAllocBytes that every GPU loading this library holds until the process
+// exits.  Host code cannot use the array's name as a device address, so the
+// first call on each device looks the address up with cudaGetSymbolAddress
+// (with that device current) and caches it.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocBytes = size_t(64) << 20;   // 64 MiB
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+static void* g_noalloc_ptr[kNoAllocMaxDevices] = {nullptr};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// carves consecutive 256-byte aligned pieces out of the static array
+struct Carve {
+  unsigned char* base;
+  size_t used, cap;
+  void* take(size_t bytes) {
+    void* p = base + used;
+    used += align256(bytes);
+    return used <= cap ? p : nullptr;
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+int scs_eval_stat_noalloc(scs_ctx* ctx, int sid, const double* params, int64_t P,
+                          double* stat, void* cuda_stream) {
+  if (!ctx) return SCS_EINVAL;
+  if (!params || !stat) return fail(ctx, SCS_EINVAL, "null params or stat");
+  if (P < 1 || P > (1 << 24)) return fail(ctx, SCS_EINVAL, "P = %lld out of range", (long long)P);
+  int rc = bind(ctx);
+  if (rc) return rc;
+  if (ctx->device < 0 || ctx->device >= kNoAllocMaxDevices)
+    return fail(ctx, SCS_EUNSUPPORTED, "device %d beyond the no-alloc device table", ctx->device);
+  if (!is_device_ptr(params) || !is_device_ptr(stat))
+    return fail(ctx, SCS_EINVAL, "scs_eval_stat_noalloc needs device pointers for params and stat");
+  DataStream* dsp = get_stream(ctx, sid, true);
+  if (!dsp) return SCS_ENODATA;
+  DataStream& ds = *dsp;
+  // one-time set-up on this device: device address of the static array
+  if (!g_noalloc_ptr[ctx->device]) {
+    void* ptr = nullptr;
+    CK(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+    g_noalloc_ptr[ctx->device] = ptr;
+  }
+  const int Pi = (int)P, N = ds.N;
+  const int n_chunks = (ds.K + kChunk - 1) / kChunk;
+  const int64_t bound = (int64_t)P * n_chunks;
+  const bool snr2 = ds.mode == SCS_EQUAL_SNR2;
+  const int64_t amax = (int64_t)(ds.K - 1) / kSnr2Stride + 2;
+  Carve cv{static_cast<unsigned char*>(g_noalloc_ptr[ctx->device]), 0, kNoAllocBytes};
+  Part* part = (Part*)cv.take(sizeof(Part) * P);
+  int2* crange = (int2*)cv.take(sizeof(int2) * P);
+  int64_t* nrec = (int64_t*)cv.take(sizeof(int64_t) * (P + 1));
+  int64_t* total = (int64_t*)cv.take(sizeof(int64_t) * 2);
+  int* diff = (int*)cv.take(sizeof(int) * (n_chunks + 2));
+  int* cnt = (int*)cv.take(sizeof(int) * (n_chunks + 1));
+  int* list_off = (int*)cv.take(sizeof(int) * (n_chunks + 1));
+  int* item_off = (int*)cv.take(sizeof(int) * (n_chunks + 1));
+  int* fill = (int*)cv.take(sizeof(int) * (n_chunks + 1));
+  int* list = (int*)cv.take(sizeof(int) * bound);
+  Rec* rec = (Rec*)cv.take(sizeof(Rec) * bound);
+  int* counter = (int*)cv.take(sizeof(int) * 2);
+  int* edges = nullptr;
+  double *Hs = nullptr, *Cs = nullptr;
+  if (snr2) {
+    edges = (int*)cv.take(sizeof(int) * (size_t)P * (N + 1));
+    Hs = (double*)cv.take(sizeof(double) * (size_t)P * amax);
+    Cs = (double*)cv.take(sizeof(double) * (size_t)P * amax);
+  }
+  if (cv.used > cv.cap)
+    return fail(ctx, SCS_EINVAL,
+                "scs_eval_stat_noalloc: P = %lld particles on K = %d bins (N = %d) need %zu "
+                "bytes of scratch, more than the fixed %zu",
+                (long long)P, ds.K, N, cv.used, kNoAllocBytes);
+  cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : ctx->stream;
+  const bool mixed = ctx->path == SCS_MIXED;
+  // the array keeps the previous call's contents: clear what must start at 0
+  CK(cudaMemsetAsync(diff, 0, sizeof(int) * (n_chunks + 2), s));
+  CK(cudaMemsetAsync(fill, 0, sizeof(int) * (n_chunks + 1), s));
+  CK(cudaMemsetAsync(counter, 0, sizeof(int) * 2, s));
+  k_setup<<<(Pi + 127) / 128, 128, 0, s>>>(params, Pi, ds.f_first, ds.df, ds.K, ds.T_obs,
+                                           mixed ? 1 : 0, part, crange, nrec, diff);
+  CKLAUNCH();
+  k_scan64<<<1, 1024, 0, s>>>(nrec, P, total);
+  CKLAUNCH();
+  k_chunk_table<<<1, 1024, 0, s>>>(diff, n_chunks, cnt, list_off, item_off);
+  CKLAUNCH();
+  k_fill<<<(Pi + 127) / 128, 128, 0, s>>>(crange, Pi, list_off, fill, list);
+  CKLAUNCH();
+  const int* e = ds.width_edges.as<int>();
+  int64_t stride = 0;
+  if (snr2) {
+    k_bounds<<<(Pi * 32 + 127) / 128, 128, 0, s>>>(part, Pi, ds.f_first, ds.df,
+                                                   ds.w64.as<double2>(), N, amax, Hs, Cs,
+                                                   edges);
+    CKLAUNCH();
+    e = edges;
+    stride = N + 1;
+  }
+  EvalArgs a;
+  a.f_first = ds.f_first;
+  a.df = ds.df;
+  a.T_obs = ds.T_obs;
+  a.K = ds.K;
+  a.d32 = ds.d32.as<float4>();
+  a.w32 = ds.w32.as<float2>();
+  a.dA64 = ds.dA64.as<double2>();
+  a.dE64 = ds.dE64.as<double2>();
+  a.w64 = ds.w64.as<double2>();
+  a.W0 = ds.W0;
+  a.N = N;
+  a.edges = e;
+  a.edge_stride = stride;
+  a.part = part;
+  a.P = Pi;
+  a.n_chunks = n_chunks;
+  a.cnt = cnt;
+  a.list_off = list_off;
+  a.list = list;
+  a.item_off = item_off;
+  a.rec_off = nrec;
+  a.rec = rec;
+  a.item_counter = counter;
+  a.seg_x = nullptr;
+  a.seg_hh = nullptr;
+  a.err = counter + 1;
+  if (mixed) launch_main_mixed(a, ctx->grid_mixed, s);
+  else launch_main_fp64(a, ctx->grid_fp64, s);
+  CKLAUNCH();
+  k_fixup<<<(Pi + 127) / 128, 128, 0, s>>>(part, crange, nrec, rec, Pi, N, stat, nullptr,
+                                           nullptr);
+  CKLAUNCH();
+  return SCS_OK;
+}
+
+}  // extern "C"
+

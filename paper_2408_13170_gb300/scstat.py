@@ -65,6 +65,8 @@ def lib():
         L.scs_set_profiling.restype = I
         L.scs_last_timings.argtypes = [P, P]
         L.scs_last_timings.restype = I
+        L.scs_eval_stat_noalloc.argtypes = [P, I, P, I64, P, P]
+        L.scs_eval_stat_noalloc.restype = I
         _lib = L
         return L
 
@@ -158,6 +160,13 @@ def scs_support(ctx, stream_id, params, P, k_lo, k_hi, log2_stride=None, cuda_st
 def scs_segment_edges(ctx, stream_id, params, P, edges, cuda_stream=None):
     _check(ctx, lib().scs_segment_edges(ctx, stream_id, _ptr(params), int(P), _ptr(edges),
                                         _stream(cuda_stream)))
+
+
+def scs_eval_stat_noalloc(ctx, stream_id, params, P, stat, cuda_stream=None):
+    """scs_eval_stat with scratch from the library's fixed device array (no
+    allocation); params and stat must be CUDA tensors."""
+    _check(ctx, lib().scs_eval_stat_noalloc(ctx, stream_id, _ptr(params), int(P), _ptr(stat),
+                                            _stream(cuda_stream)))
 
 
 def scs_set_profiling(ctx, enable: bool):
