@@ -144,9 +144,11 @@ __device__ inline void phase_taylor(const Part& p, double fa, double df, double 
   an.df32 = df32;
 }
 
-// Build the phase state of the span starting at k_a.
-__device__ inline void phase_anchor(const Part& p, int ka, double f_first, double df,
-                                    PhaseAnchor& an) {
+// Build the phase state of the span starting at k_a.  Out of line: it runs
+// once per span, and keeping its FP64 code out of the hot loop's footprint
+// measurably helps.
+static __device__ __noinline__ void phase_anchor(const Part& p, int ka, double f_first,
+                                                 double df, PhaseAnchor& an) {
   double fa = f_first + (double)ka * df;
   double c64[4];
   float c32[7];

@@ -20,8 +20,8 @@ constexpr double kPi = 3.141592653589793116;
 constexpr double kPiLo = 1.224646799147353207e-16;
 constexpr double kTwoPi = 6.283185307179586232;
 constexpr double kIscoV3 = 0.06804138174397717;             // 6^{-3/2}
-constexpr int kMaxLog2B = 12;                               // anchor stride <= 4096
-constexpr int kChunk = 4096;                                // bins per work chunk
+constexpr int kMaxLog2B = 11;                               // anchor stride <= 2048
+constexpr int kChunk = 2048;                                // bins per work chunk
 constexpr int kSnr2Stride = 1024;                           // equal-SNR^2 anchor grid
 
 enum : int { kOk = 0, kInvalid = 1, kEmpty = 2 };
@@ -313,6 +313,73 @@ __device__ inline void response_residual(T f, T ca, T sa, const T* Pr, const T* 
   const T is2 = (T)0.70710678118654752, is6 = (T)0.40824829046386302;
   RA = Cx<T>{(Z.re - X.re) * is2, (Z.im - X.im) * is2};
   RE = Cx<T>{(X.re - (T)2 * Y.re + Z.re) * is6, (X.im - (T)2 * Y.im + Z.im) * is6};
+}
+
+// |R_A|^2 and |R_E|^2 of the residual response in FP64 for the equal-SNR^2
+// anchors.  Same model as response_residual; the phase e^{-i pi f L} common
+// to all six links is dropped (it cancels in |.|^2), the sinc arguments
+// a (1 -+ k.n), a = pi f L, come from sin/cos of a and of a k.n by angle
+// addition (direct sin when the argument is small), and D = e^{-2 i a}.
+__device__ inline void response_power64(const Part& p, double f, double ca, double sa,
+                                        double& pA, double& pE) {
+  const double L = kArm;
+  const double eR2 = kArm / (4.0 * 1.7320508075688772);
+  const double s3 = 1.7320508075688772;
+  double c2a = ca * ca - sa * sa, s2a = 2.0 * ca * sa;
+  const double cb[3] = {1.0, -0.5, -0.5};
+  const double sbv[3] = {0.0, 0.8660254037844386, -0.8660254037844386};
+  double d[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    double c2 = c2a * cb[i] + s2a * sbv[i];
+    double s2 = s2a * cb[i] - c2a * sbv[i];
+    double c1 = ca * cb[i] + sa * sbv[i];
+    d[i][0] = eR2 * (c2 - 3.0 * cb[i]);
+    d[i][1] = eR2 * (s2 - 3.0 * sbv[i]);
+    d[i][2] = -2.0 * s3 * eR2 * c1;
+  }
+  const double a = kPi * f * L;
+  double s_a, c_a;
+  sincos(a, &s_a, &c_a);
+  Cx<double> G[3][3];
+  const int as[3] = {0, 0, 1}, ar[3] = {1, 2, 2};
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    int s = as[m], r = ar[m];
+    double n0 = (d[r][0] - d[s][0]) / L, n1 = (d[r][1] - d[s][1]) / L, n2 = (d[r][2] - d[s][2]) / L;
+    double kn = p.kx * n0 + p.ky * n1 + p.kz * n2;
+    double kd = p.kx * (d[s][0] + d[r][0]) + p.ky * (d[s][1] + d[r][1]) + p.kz * (d[s][2] + d[r][2]);
+    double q0 = n0 * n0, q1 = n1 * n1, q2 = n2 * n2, q3 = 2.0 * n0 * n1, q4 = 2.0 * n0 * n2,
+           q5 = 2.0 * n1 * n2;
+    Cx<double> nPn{p.Pr[0] * q0 + p.Pr[1] * q1 + p.Pr[2] * q2 + p.Pr[3] * q3 + p.Pr[4] * q4 + p.Pr[5] * q5,
+                   p.Pi[0] * q0 + p.Pi[1] * q1 + p.Pi[2] * q2 + p.Pi[3] * q3 + p.Pi[4] * q4 + p.Pi[5] * q5};
+    double sph, cph;
+    sincos(-kPi * f * kd, &sph, &cph);
+    Cx<double> base = cmul(Cx<double>{cph, sph}, nPn);
+    double b = a * kn, sb, cbb;
+    sincos(b, &sb, &cbb);
+    double xf = a - b, xb = a + b;
+    double sf = fabs(xf) < 0.25 ? sin(xf) : s_a * cbb - c_a * sb;
+    double sk = fabs(xb) < 0.25 ? sin(xb) : s_a * cbb + c_a * sb;
+    double sincf = xf == 0.0 ? 1.0 : sf / xf;
+    double sincb = xb == 0.0 ? 1.0 : sk / xb;
+    G[s][r] = Cx<double>{a * sincf * base.im, -a * sincf * base.re};
+    G[r][s] = Cx<double>{a * sincb * base.im, -a * sincb * base.re};
+  }
+  Cx<double> D{c_a * c_a - s_a * s_a, -2.0 * s_a * c_a};
+  Cx<double> D2 = cmul(D, D);
+  Cx<double> W{1.0 - D2.re, -D2.im};
+  auto arm = [&](int x, int y, int z) {
+    Cx<double> t1 = cadd(G[z][x], cmul(D, G[x][z]));
+    Cx<double> t2 = cadd(G[y][x], cmul(D, G[x][y]));
+    return cmul(W, csub(t1, t2));
+  };
+  Cx<double> X = arm(0, 1, 2), Y = arm(1, 2, 0), Z = arm(2, 0, 1);
+  double Ar = (Z.re - X.re) * 0.70710678118654752, Ai = (Z.im - X.im) * 0.70710678118654752;
+  double Er = (X.re - 2.0 * Y.re + Z.re) * 0.40824829046386302;
+  double Ei = (X.im - 2.0 * Y.im + Z.im) * 0.40824829046386302;
+  pA = Ar * Ar + Ai * Ai;
+  pE = Er * Er + Ei * Ei;
 }
 
 // orbital angle reduced to [-pi, pi] in FP64

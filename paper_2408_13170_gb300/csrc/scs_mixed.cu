@@ -36,7 +36,7 @@ struct Lane {
   int n_cur, e_next;
   int next_phase, next_resp, phase_k;
   int log2B, log2Br;
-  bool act, head, fresh, done;
+  bool act, head, fresh;
   const int* e;
   const Part* pp;
   Rec* rec;          // this (particle, chunk) unit's record
@@ -74,10 +74,10 @@ __device__ __forceinline__ void close_segment(Lane& L, const EvalArgs& a, double
   L.e_next = __ldg(L.e + L.n_cur + 1);
 }
 
-// nb bins from k0; MASKED: some lane is only partly inside [kb, ke).  The
+// nb bins from k0, each lane masked to its own [kb, ke) (a single loop body:
+// a second, unmasked copy measured slower through its larger code).  The
 // data of bin k+1 is loaded while bin k is computed (the FP32 arrays carry a
 // zeroed tail for the last prefetch).
-template <bool MASKED>
 __device__ __forceinline__ void run_block(Lane& L, const EvalArgs& a, double zs, int k0,
                                           int nb) {
   float4 dn = __ldg(a.d32 + k0);
@@ -88,7 +88,7 @@ __device__ __forceinline__ void run_block(Lane& L, const EvalArgs& a, double zs,
     const float2 wv = wn;
     dn = __ldg(a.d32 + k + 1);
     wn = __ldg(a.w32 + k + 1);
-    const bool m = !MASKED || (L.act && (unsigned)(k - L.kb) < (unsigned)(L.ke - L.kb));
+    const bool m = L.act && (unsigned)(k - L.kb) < (unsigned)(L.ke - L.kb);
     const bool hit = m && k == L.e_next;
     if (__any_sync(kFull, hit)) {
       if (hit) close_segment(L, a, zs, k);
@@ -105,13 +105,13 @@ __device__ __forceinline__ void run_block(Lane& L, const EvalArgs& a, double zs,
     const float qi = dv.y * G[0] - dv.x * G[1] + dv.w * G[2] - dv.z * G[3];
     const float hb = wv.x * (G[0] * G[0] + G[1] * G[1]) + wv.y * (G[2] * G[2] + G[3] * G[3]);
     float zr = qr * cp - qi * sp, zi = qr * sp + qi * cp;
-    if (MASKED && !m) {
+    if (!m) {
       zr = 0.f;
       zi = 0.f;
     }
     L.bzr += zr;
     L.bzi += zi;
-    L.bhh += (MASKED && !m) ? 0.f : hb;
+    L.bhh += m ? hb : 0.f;
 #pragma unroll
     for (int r = 0; r < kOrd; ++r) L.d[r] += L.d[r + 1];
     L.jf += 1.f;
@@ -159,7 +159,6 @@ __global__ void __launch_bounds__(128, 4) k_main_mixed(EvalArgs a) {
     L.e_next = L.act ? __ldg(L.e + L.n_cur + 1) : kNoEdge;
     L.head = true;
     L.fresh = true;
-    L.done = false;
     L.szr = L.szi = L.shh = L.ups = Kahan{0.f, 0.f};
     L.bzr = L.bzi = L.bhh = 0.f;
 #pragma unroll
@@ -202,17 +201,8 @@ __global__ void __launch_bounds__(128, 4) k_main_mixed(EvalArgs a) {
         L.jf = 0.f;
         L.next_resp += 1 << L.log2Br;
       }
-      if (L.act && !L.done && k0 >= L.ke) {
-        // past the support: contribute exact zeros from here on
-#pragma unroll
-        for (int q = 0; q < 4; ++q) L.rq.g0[q] = L.rq.g1[q] = L.rq.g2[q] = 0.f;
-        L.e_next = kNoEdge;
-        L.done = true;
-      }
       const int nb = min(BW, kw1 - k0);
-      const bool partial = L.act && !L.done && !(L.kb <= k0 && k0 + nb <= L.ke);
-      if (__any_sync(kFull, partial)) run_block<true>(L, a, zs, k0, nb);
-      else run_block<false>(L, a, zs, k0, nb);
+      run_block(L, a, zs, k0, nb);
       if (((k0 + BW) & 31) == 0) {
         kadd(L.szr, L.bzr);
         kadd(L.szi, L.bzi);

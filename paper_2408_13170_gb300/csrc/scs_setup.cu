@@ -249,20 +249,19 @@ __global__ void k_bounds(const Part* part, int P, double f_first, double df,
   int nanch = span / kSnr2Stride + 1 + (span % kSnr2Stride != 0 ? 1 : 0);
   double* H = Hs + (int64_t)gw * amax;
   double* C = Cs + (int64_t)gw * amax;
-  const double kv[3] = {p.kx, p.ky, p.kz};
   for (int a = lane; a < nanch; a += 32) {
     int ka = min(p.k_lo + a * kSnr2Stride, p.k_hi);
     double f = dd_val(grid_freq_dd(f_first, df, ka));
     double t = time_of_freq(p, f);
     double sa, ca;
     sincos(orbit_angle(t), &sa, &ca);
-    Cx<double> RA, RE;
-    response_residual<double>(f, ca, sa, p.Pr, p.Pi, kv, RA, RE);
-    double amp = pow(f, -7.0 / 6.0);
+    double pA, pE;
+    response_power64(p, f, ca, sa, pA, pE);
+    // |h|^2 = A(f)^2 |R|^2 with A(f)^2 = f^{-7/3} = u^7, u = f^{-1/3}
+    double u = rcbrt(f), u2 = u * u;
+    double amp2 = u2 * u2 * u2 * u;
     double2 w = w64[ka];
-    double hA = (amp * RA.re) * (amp * RA.re) + (amp * RA.im) * (amp * RA.im);
-    double hE = (amp * RE.re) * (amp * RE.re) + (amp * RE.im) * (amp * RE.im);
-    H[a] = __dadd_rn(__dmul_rn(w.x, hA), __dmul_rn(w.y, hE));
+    H[a] = __dadd_rn(__dmul_rn(w.x, amp2 * pA), __dmul_rn(w.y, amp2 * pE));
   }
   __syncwarp();
   if (lane == 0) {
@@ -278,30 +277,35 @@ __global__ void k_bounds(const Part* part, int P, double f_first, double df,
   }
   __syncwarp();
   double Cl = C[nanch - 1];
-  for (int n = lane; n <= N; n += 32) {
-    int en;
-    if (n == 0) {
-      en = p.k_lo;
-    } else if (n == N) {
-      en = p.k_hi + 1;
-    } else if (!(Cl > 0.0)) {
-      en = p.k_lo;
-    } else {
-      double cn = __ddiv_rn(__dmul_rn((double)n, Cl), (double)N);
-      // first a in [1, nanch-1] with C[a] >= cn (else nanch-1)
+  if (lane == 0) e[0] = p.k_lo;
+  if (lane == 31) e[N] = p.k_hi + 1;
+  // interior edges n = 1..N-1 in one contiguous range per lane: one binary
+  // search, then the anchor index only moves up with n
+  const int M = N - 1;
+  const int n0 = 1 + (int)(((int64_t)lane * M) / 32), n1 = 1 + (int)(((int64_t)(lane + 1) * M) / 32);
+  int a = 1;
+  for (int n = n0; n < n1; ++n) {
+    if (!(Cl > 0.0)) {
+      e[n] = p.k_lo;
+      continue;
+    }
+    double cn = __ddiv_rn(__dmul_rn((double)n, Cl), (double)N);
+    // first a in [1, nanch-1] with C[a] >= cn (else nanch-1)
+    if (n == n0) {
       int lo = 1, hi = nanch - 1;
       while (lo < hi) {
         int mid = (lo + hi) >> 1;
         if (C[mid] >= cn) hi = mid; else lo = mid + 1;
       }
-      int a = lo;
-      int k1 = min(p.k_lo + (a - 1) * kSnr2Stride, p.k_hi);
-      int k2 = min(p.k_lo + a * kSnr2Stride, p.k_hi);
-      double fr = __ddiv_rn(__dsub_rn(cn, C[a - 1]), __dsub_rn(C[a], C[a - 1]));
-      double kap = __dadd_rn((double)k1, __dmul_rn(fr, (double)(k2 - k1)));
-      en = (int)ceil(kap);
+      a = lo;
+    } else {
+      while (a < nanch - 1 && C[a] < cn) ++a;
     }
-    e[n] = en;
+    int k1 = min(p.k_lo + (a - 1) * kSnr2Stride, p.k_hi);
+    int k2 = min(p.k_lo + a * kSnr2Stride, p.k_hi);
+    double fr = __ddiv_rn(__dsub_rn(cn, C[a - 1]), __dsub_rn(C[a], C[a - 1]));
+    double kap = __dadd_rn((double)k1, __dmul_rn(fr, (double)(k2 - k1)));
+    e[n] = (int)ceil(kap);
   }
 }
 
