@@ -208,11 +208,12 @@ __device__ inline void g_exact64(const Part& p, double fa, double df, double x, 
   double f = fa + x * df;
   double t = time_of_freq(p, f);
   double sa, ca;
-  sincos(orbit_angle(t), &sa, &ca);
+  sincos_small(orbit_angle(t), &sa, &ca);
   const double kv[3] = {p.kx, p.ky, p.kz};
   Cx<double> RA, RE;
   response_residual<double>(f, ca, sa, p.Pr, p.Pi, kv, RA, RE);
-  double amp = pow(f, -7.0 / 6.0);
+  double u = rcbrt(f);
+  double amp = u * u * u * sqrt(u);
   out[0] = amp * RA.re;
   out[1] = amp * RA.im;
   out[2] = amp * RE.re;

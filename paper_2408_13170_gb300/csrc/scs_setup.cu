@@ -254,7 +254,7 @@ __global__ void k_bounds(const Part* part, int P, double f_first, double df,
     double f = dd_val(grid_freq_dd(f_first, df, ka));
     double t = time_of_freq(p, f);
     double sa, ca;
-    sincos(orbit_angle(t), &sa, &ca);
+    sincos_small(orbit_angle(t), &sa, &ca);
     double pA, pE;
     response_power64(p, f, ca, sa, pA, pE);
     // |h|^2 = A(f)^2 |R|^2 with A(f)^2 = f^{-7/3} = u^7, u = f^{-1/3}
