@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=48,
                     help="particles in the CPU-oracle sample")
     ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--particles", type=int, default=None,
+                    help="override the particle count (small cases for profiling)")
     return ap.parse_args()
 
 
@@ -184,6 +186,8 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     cfg, d, inj = make_workload(seed_offset=rank)
+    if args.particles:
+        cfg["P"] = args.particles
     P, N = cfg["P"], cfg["N"]
     ctx = scstat.Context(local, scstat.SCS_MIXED)
     ctx.set_data(0, d)
