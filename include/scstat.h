@@ -119,6 +119,19 @@ int scs_eval_stat(scs_ctx *ctx, int stream_id, const double *params,
                   int64_t P, double *stat, double *seg_x, double *seg_hh,
                   void *cuda_stream);
 
+/* Several data streams in one evaluation (one persistent launch): item i
+ * evaluates particles P_offsets[i] .. P_offsets[i+1]-1 of params on stream
+ * stream_ids[i] with that stream's grid, data and segmentation (streams may
+ * differ in length, band, N and mode).  Used to batch independent swarms or
+ * search tiles (Sec. IV: tiles searched independently).
+ *   stream_ids  n_items ints; P_offsets  n_items + 1 int64, P_offsets[0] = 0,
+ *               non-decreasing, P = P_offsets[n_items] in [1, 2^24].
+ *   params      P x 8 doubles; stat  P doubles (host or device).
+ * Per-particle results are identical to scs_eval_stat on the same stream.
+ * Errors: SCS_EINVAL, SCS_ENODATA, SCS_ENOMEM, SCS_ECUDA. */
+int scs_batch_eval(scs_ctx *ctx, const int *stream_ids, const int64_t *P_offsets,
+                   int n_items, const double *params, double *stat, void *cuda_stream);
+
 /* Template h_A, h_E (Sec. IV: h_alpha = T_alpha(theta, f) A(f) e^{-i Psi(f)},
  * A(f) = f^{-7/6}) of one particle on the stream's grid, FP64, complex
  * interleaved, zero outside the support.

@@ -46,7 +46,7 @@ struct DataStream {
   DevBuf wmax;          // max w as the bits of a double (FP32 scale W0)
   double W0 = 1.0;
   int N = 0, mode = -1;
-  DevBuf width_edges;   // N + 1 ints (equal-width segmentation)
+  DevBuf width_edges;   // N + 1 ints, e_n = floor(n K / N)
 };
 
 bool is_device_ptr(const void* p) {
@@ -59,6 +59,13 @@ bool is_device_ptr(const void* p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// per-call scratch pieces of the evaluation pipeline
+enum Slot {
+  kSlotStreams, kSlotPart, kSlotCrange, kSlotNrec, kSlotTotal, kSlotDiff, kSlotCnt,
+  kSlotListOff, kSlotItemOff, kSlotFill, kSlotList, kSlotRec, kSlotCounter, kSlotEdges,
+  kSlotHs, kSlotCs, kNumSlots
+};
+
 }  // namespace
 
 struct scs_ctx {
@@ -68,13 +75,12 @@ struct scs_ctx {
   int grid_mixed = 0, grid_fp64 = 0;
   cudaStream_t stream = nullptr;
   std::string err;
-  bool prof = false;               // record stage events in scs_eval_stat
+  bool prof = false;               // record stage events in the evaluation calls
   bool prof_valid = false;
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   std::map<int, DataStream> streams;
-  // per-call scratch
-  DevBuf params, part, crange, nrec, total, diff, cnt, list_off, item_off, fill, list, rec,
-      counter, edges, Hs, Cs, stat, segx, segh, tmpA, tmpE, red, misc;
+  DevBuf slot[kNumSlots];          // pipeline scratch (grow-only)
+  DevBuf params, stat, segx, segh, tmpA, tmpE, tmpS1, tmpS2, red, misc;
 };
 
 namespace {
@@ -132,43 +138,218 @@ int stage_params(scs_ctx* ctx, const double* params, int64_t P, cudaStream_t s,
   return SCS_OK;
 }
 
-// Particle setup + chunk work list for P particles on stream ds.
-int prepare(scs_ctx* ctx, DataStream& ds, const double* dparams, int P, bool want_stride,
-            cudaStream_t s, int* n_chunks_out, int64_t* max_rec) {
-  const int n_chunks = (ds.K + kChunk - 1) / kChunk;
-  CK(ctx->part.reserve(sizeof(Part) * P));
-  CK(ctx->crange.reserve(sizeof(int2) * P));
-  CK(ctx->nrec.reserve(sizeof(int64_t) * (P + 1)));
-  CK(ctx->total.reserve(sizeof(int64_t) * 2));
-  CK(ctx->diff.reserve(sizeof(int) * (n_chunks + 2)));
-  CK(ctx->cnt.reserve(sizeof(int) * (n_chunks + 1)));
-  CK(ctx->list_off.reserve(sizeof(int) * (n_chunks + 1)));
-  CK(ctx->item_off.reserve(sizeof(int) * (n_chunks + 1)));
-  CK(ctx->fill.reserve(sizeof(int) * (n_chunks + 1)));
-  CK(cudaMemsetAsync(ctx->diff.ptr, 0, sizeof(int) * (n_chunks + 2), s));
-  CK(cudaMemsetAsync(ctx->fill.ptr, 0, sizeof(int) * (n_chunks + 1), s));
-  k_setup<<<(P + 127) / 128, 128, 0, s>>>(dparams, P, ds.f_first, ds.df, ds.K, ds.T_obs,
-                                          want_stride ? 1 : 0, ctx->part.as<Part>(),
-                                          ctx->crange.as<int2>(), ctx->nrec.as<int64_t>(),
-                                          ctx->diff.as<int>());
+// Where the pipeline's scratch comes from: the context's grow-only buffers,
+// or consecutive 256-byte aligned pieces of one fixed array.
+struct ScratchSource {
+  scs_ctx* ctx = nullptr;          // context buffers when set
+  unsigned char* base = nullptr;   // else carve from [base, base + cap)
+  size_t used = 0, cap = 0;
+  cudaError_t err = cudaSuccess;
+  void* get(int slot, size_t bytes) {
+    if (ctx) {
+      cudaError_t e = ctx->slot[slot].reserve(bytes);
+      if (e != cudaSuccess) err = e;
+      return e == cudaSuccess ? ctx->slot[slot].ptr : nullptr;
+    }
+    void* p = base + used;
+    used += (bytes + 255) & ~size_t(255);
+    return used <= cap ? p : nullptr;
+  }
+  bool failed() const { return ctx ? err != cudaSuccess : used > cap; }
+};
+
+// One stream of a batch: its data and the particle range evaluated on it.
+struct BatchPart {
+  DataStream* ds;
+  int p_off, n_p;
+};
+
+// Host copy of the stream table of a batch (device pointers filled in).
+std::vector<StreamDesc> make_table(const std::vector<BatchPart>& parts, int* n_chunks_total,
+                                   int64_t* edges_total, int64_t* hc_total) {
+  std::vector<StreamDesc> t(parts.size());
+  int cb = 0;
+  int64_t eb = 0, hb = 0;
+  for (size_t i = 0; i < parts.size(); ++i) {
+    const DataStream& ds = *parts[i].ds;
+    StreamDesc& d = t[i];
+    d.f_first = ds.f_first;
+    d.df = ds.df;
+    d.T_obs = ds.T_obs;
+    d.W0 = ds.W0;
+    d.K = ds.K;
+    d.N = ds.N;
+    d.mode = ds.mode;
+    d.n_chunks = (ds.K + kChunk - 1) / kChunk;
+    d.chunk_base = cb;
+    cb += d.n_chunks;
+    d.p_off = parts[i].p_off;
+    d.n_p = parts[i].n_p;
+    d.amax = (ds.K - 1) / kSnr2Stride + 2;
+    d.edge_base = eb;
+    d.hc_base = hb;
+    if (ds.mode == SCS_EQUAL_SNR2) {
+      eb += (int64_t)d.n_p * (d.N + 1);
+      hb += (int64_t)d.n_p * d.amax;
+    }
+    d.d32 = ds.d32.as<float4>();
+    d.w32 = ds.w32.as<float2>();
+    d.dA64 = ds.dA64.as<double2>();
+    d.dE64 = ds.dE64.as<double2>();
+    d.w64 = ds.w64.as<double2>();
+    d.width_edges = ds.width_edges.as<int>();
+  }
+  *n_chunks_total = cb;
+  *edges_total = eb;
+  *hc_total = hb;
+  return t;
+}
+
+// Bytes of scratch a batch needs (the order and rounding of ScratchSource).
+size_t batch_scratch_bytes(const std::vector<BatchPart>& parts, int P) {
+  int nct = 0;
+  int64_t etot = 0, htot = 0;
+  std::vector<StreamDesc> t = make_table(parts, &nct, &etot, &htot);
+  int64_t bound = 0;
+  for (const StreamDesc& d : t) bound += (int64_t)d.n_p * d.n_chunks;
+  const size_t sizes[] = {sizeof(StreamDesc) * t.size(), sizeof(Part) * P, sizeof(int2) * P,
+                          sizeof(int64_t) * (P + 1), sizeof(int64_t) * 2,
+                          sizeof(int) * (nct + 2), sizeof(int) * (nct + 1),
+                          sizeof(int) * (nct + 1), sizeof(int) * (nct + 1),
+                          sizeof(int) * (nct + 1), sizeof(int) * bound, sizeof(int) * etot,
+                          sizeof(double) * htot, sizeof(double) * htot, sizeof(Rec) * bound,
+                          sizeof(int) * 2};
+  size_t used = 0;
+  for (size_t b : sizes) used += (b + 255) & ~size_t(255);
+  return used;
+}
+
+// Device state of a prepared batch.
+struct Prepared {
+  StreamDesc* streams = nullptr;
+  int n_streams = 0;
+  int n_chunks = 0;
+  int64_t bound = 0;        // record / list capacity
+  Part* part = nullptr;
+  int2* crange = nullptr;
+  int64_t* nrec = nullptr;
+  int* cnt = nullptr;
+  int* list_off = nullptr;
+  int* item_off = nullptr;
+  int* list = nullptr;
+  int* edges = nullptr;     // equal-SNR^2 edge tables
+  bool any_snr2 = false;
+};
+
+// Stream table upload, particle set-up, chunk work list and (if asked)
+// equal-SNR^2 edges for P particles grouped by stream.
+int prepare_batch(scs_ctx* ctx, const std::vector<BatchPart>& parts, const double* dparams,
+                  int P, bool want_stride, bool want_edges, cudaStream_t s,
+                  ScratchSource& src, Prepared& out) {
+  int nct = 0;
+  int64_t etot = 0, htot = 0;
+  std::vector<StreamDesc> table = make_table(parts, &nct, &etot, &htot);
+  const int ns = (int)table.size();
+  out.n_streams = ns;
+  out.n_chunks = nct;
+  int64_t bound = 0;
+  for (const StreamDesc& d : table) {
+    bound += (int64_t)d.n_p * d.n_chunks;
+    out.any_snr2 = out.any_snr2 || d.mode == SCS_EQUAL_SNR2;
+  }
+  out.bound = bound;
+  out.streams = (StreamDesc*)src.get(kSlotStreams, sizeof(StreamDesc) * ns);
+  out.part = (Part*)src.get(kSlotPart, sizeof(Part) * P);
+  out.crange = (int2*)src.get(kSlotCrange, sizeof(int2) * P);
+  out.nrec = (int64_t*)src.get(kSlotNrec, sizeof(int64_t) * (P + 1));
+  int64_t* total = (int64_t*)src.get(kSlotTotal, sizeof(int64_t) * 2);
+  int* diff = (int*)src.get(kSlotDiff, sizeof(int) * (nct + 2));
+  out.cnt = (int*)src.get(kSlotCnt, sizeof(int) * (nct + 1));
+  out.list_off = (int*)src.get(kSlotListOff, sizeof(int) * (nct + 1));
+  out.item_off = (int*)src.get(kSlotItemOff, sizeof(int) * (nct + 1));
+  int* fill = (int*)src.get(kSlotFill, sizeof(int) * (nct + 1));
+  out.list = (int*)src.get(kSlotList, sizeof(int) * bound);
+  double *Hs = nullptr, *Cs = nullptr;
+  if (out.any_snr2 && want_edges) {
+    out.edges = (int*)src.get(kSlotEdges, sizeof(int) * etot);
+    Hs = (double*)src.get(kSlotHs, sizeof(double) * htot);
+    Cs = (double*)src.get(kSlotCs, sizeof(double) * htot);
+  }
+  if (src.failed()) {
+    if (src.ctx) CK(src.err);
+    return SCS_ENOMEM;
+  }
+  CK(cudaMemcpyAsync(out.streams, table.data(), sizeof(StreamDesc) * ns, cudaMemcpyHostToDevice,
+                     s));
+  CK(cudaMemsetAsync(diff, 0, sizeof(int) * (nct + 2), s));
+  CK(cudaMemsetAsync(fill, 0, sizeof(int) * (nct + 1), s));
+  k_setup<<<(P + 127) / 128, 128, 0, s>>>(dparams, P, out.streams, ns, want_stride ? 1 : 0,
+                                          out.part, out.crange, out.nrec, diff);
   CKLAUNCH();
-  k_scan64<<<1, 1024, 0, s>>>(ctx->nrec.as<int64_t>(), P, ctx->total.as<int64_t>());
+  k_scan64<<<1, 1024, 0, s>>>(out.nrec, P, total);
   CKLAUNCH();
-  k_chunk_table<<<1, 1024, 0, s>>>(ctx->diff.as<int>(), n_chunks, ctx->cnt.as<int>(),
-                                   ctx->list_off.as<int>(), ctx->item_off.as<int>());
+  k_chunk_table<<<1, 1024, 0, s>>>(diff, nct, out.cnt, out.list_off, out.item_off);
   CKLAUNCH();
-  // list and records: bounded by P x (chunks a support can span)
-  int64_t bound = (int64_t)P * n_chunks;
-  CK(ctx->list.reserve(sizeof(int) * bound));
-  k_fill<<<(P + 127) / 128, 128, 0, s>>>(ctx->crange.as<int2>(), P, ctx->list_off.as<int>(),
-                                        ctx->fill.as<int>(), ctx->list.as<int>());
+  k_fill<<<(P + 127) / 128, 128, 0, s>>>(out.crange, P, out.list_off, fill, out.list);
   CKLAUNCH();
-  *n_chunks_out = n_chunks;
-  *max_rec = bound;
+  if (ctx->prof) CK(cudaEventRecord(ctx->ev[1], s));
+  if (out.any_snr2 && want_edges) {
+    k_bounds<<<(P * 32 + 127) / 128, 128, 0, s>>>(out.part, P, out.streams, out.edges, Hs, Cs);
+    CKLAUNCH();
+  }
   return SCS_OK;
 }
 
-int ensure_grids(scs_ctx* ctx);
+// The main kernel and the fix-up of a prepared batch.
+int run_batch(scs_ctx* ctx, const Prepared& pr, int P, double* dstat, double* dsx,
+              double* dsh, cudaStream_t s, ScratchSource& src) {
+  Rec* rec = (Rec*)src.get(kSlotRec, sizeof(Rec) * (size_t)pr.bound);
+  int* counter = (int*)src.get(kSlotCounter, sizeof(int) * 2);
+  if (src.failed()) {
+    if (src.ctx) CK(src.err);
+    return SCS_ENOMEM;
+  }
+  CK(cudaMemsetAsync(counter, 0, sizeof(int) * 2, s));
+  EvalArgs a;
+  a.streams = pr.streams;
+  a.n_streams = pr.n_streams;
+  a.edges_all = pr.edges;
+  a.part = pr.part;
+  a.P = P;
+  a.n_chunks = pr.n_chunks;
+  a.cnt = pr.cnt;
+  a.list_off = pr.list_off;
+  a.list = pr.list;
+  a.item_off = pr.item_off;
+  a.rec_off = pr.nrec;
+  a.rec = rec;
+  a.item_counter = counter;
+  a.seg_x = dsx;
+  a.seg_hh = dsh;
+  a.err = counter + 1;
+  if (ctx->prof) CK(cudaEventRecord(ctx->ev[2], s));
+  if (ctx->path == SCS_MIXED) launch_main_mixed(a, ctx->grid_mixed, s);
+  else launch_main_fp64(a, ctx->grid_fp64, s);
+  CKLAUNCH();
+  if (ctx->prof) CK(cudaEventRecord(ctx->ev[3], s));
+  k_fixup<<<(P + 127) / 128, 128, 0, s>>>(pr.part, pr.crange, pr.nrec, rec, P, pr.streams,
+                                          dstat, dsx, dsh);
+  CKLAUNCH();
+  if (ctx->prof) {
+    CK(cudaEventRecord(ctx->ev[4], s));
+    ctx->prof_valid = true;
+  }
+  return SCS_OK;
+}
+
+int ensure_grids(scs_ctx* ctx) {
+  int bm = 0, bf = 0;
+  if (occupancy_mixed(&bm) || occupancy_fp64(&bf))
+    return fail(ctx, SCS_ECUDA, "occupancy query failed");
+  ctx->grid_mixed = ctx->num_sms * (bm > 0 ? bm : 1);
+  ctx->grid_fp64 = ctx->num_sms * (bf > 0 ? bf : 1);
+  return SCS_OK;
+}
 
 }  // namespace
 
@@ -217,11 +398,9 @@ void scs_destroy(scs_ctx* ctx) {
     d.wmax.release();
     d.width_edges.release();
   }
-  DevBuf* bufs[] = {&ctx->params, &ctx->part, &ctx->crange, &ctx->nrec, &ctx->total,
-                    &ctx->diff, &ctx->cnt, &ctx->list_off, &ctx->item_off, &ctx->fill,
-                    &ctx->list, &ctx->rec, &ctx->counter, &ctx->edges, &ctx->Hs, &ctx->Cs,
-                    &ctx->stat, &ctx->segx, &ctx->segh, &ctx->tmpA, &ctx->tmpE, &ctx->red,
-                    &ctx->misc};
+  for (DevBuf& b : ctx->slot) b.release();
+  DevBuf* bufs[] = {&ctx->params, &ctx->stat, &ctx->segx, &ctx->segh, &ctx->tmpA,
+                    &ctx->tmpE, &ctx->tmpS1, &ctx->tmpS2, &ctx->red, &ctx->misc};
   for (DevBuf* b : bufs) b->release();
   for (cudaEvent_t& e : ctx->ev)
     if (e) cudaEventDestroy(e);
@@ -286,7 +465,7 @@ int scs_set_data(scs_ctx* ctx, int sid, const double* A, const double* E, const 
   const void* in[4] = {A, E, S_A, S_E};
   size_t sz[4] = {sizeof(double2) * Kz, sizeof(double2) * Kz, sizeof(double) * Kz,
                   sizeof(double) * Kz};
-  DevBuf* tmp[4] = {&ctx->tmpA, &ctx->tmpE, &ctx->Hs, &ctx->Cs};
+  DevBuf* tmp[4] = {&ctx->tmpA, &ctx->tmpE, &ctx->tmpS1, &ctx->tmpS2};
   const void* din[4];
   for (int i = 0; i < 4; ++i) {
     if (!in[i]) {
@@ -322,7 +501,7 @@ int scs_set_data(scs_ctx* ctx, int sid, const double* A, const double* E, const 
   ds.df = df;
   ds.T_obs = T_obs;
   if (ds.mode >= 0 && ds.N > K) ds.mode = -1;
-  bool width_stale = ds.mode == SCS_EQUAL_WIDTH && ds.K != (int)K;
+  const bool width_stale = ds.mode >= 0 && ds.K != (int)K;
   ds.K = (int)K;
   if (width_stale) {
     k_width_edges<<<64, 256, 0, s>>>(K, ds.N, ds.width_edges.as<int>());
@@ -343,54 +522,12 @@ int scs_set_segments(scs_ctx* ctx, int sid, int N, int mode) {
   if (N < 1 || N > ds->K) return fail(ctx, SCS_EINVAL, "N = %d outside [1, K = %d]", N, ds->K);
   ds->N = N;
   ds->mode = mode;
-  if (mode == SCS_EQUAL_WIDTH) {
-    CK(ds->width_edges.reserve(sizeof(int) * (N + 1)));
-    k_width_edges<<<64, 256, 0, ctx->stream>>>(ds->K, N, ds->width_edges.as<int>());
-    CKLAUNCH();
-    CK(cudaStreamSynchronize(ctx->stream));
-  }
-  return SCS_OK;
-}
-
-}  // extern "C"
-
-namespace {
-
-int ensure_grids(scs_ctx* ctx) {
-  int bm = 0, bf = 0;
-  // occupancy of the two main kernels (128 threads per block)
-  if (occupancy_mixed(&bm) || occupancy_fp64(&bf)) return fail(ctx, SCS_ECUDA, "occupancy query failed");
-  ctx->grid_mixed = ctx->num_sms * (bm > 0 ? bm : 1);
-  ctx->grid_fp64 = ctx->num_sms * (bf > 0 ? bf : 1);
-  return SCS_OK;
-}
-
-// Segment edges for the particles of the current call (device table).
-int build_edges(scs_ctx* ctx, DataStream& ds, int P, cudaStream_t s, const int** edges,
-                int64_t* stride) {
-  if (ds.mode == SCS_EQUAL_WIDTH) {
-    *edges = ds.width_edges.as<int>();
-    *stride = 0;
-    return SCS_OK;
-  }
-  const int N = ds.N;
-  int64_t amax = (int64_t)(ds.K - 1) / kSnr2Stride + 2;
-  CK(ctx->edges.reserve(sizeof(int) * (size_t)P * (N + 1)));
-  CK(ctx->Hs.reserve(sizeof(double) * (size_t)P * amax));
-  CK(ctx->Cs.reserve(sizeof(double) * (size_t)P * amax));
-  k_bounds<<<(P * 32 + 127) / 128, 128, 0, s>>>(ctx->part.as<Part>(), P, ds.f_first, ds.df,
-                                                ds.w64.as<double2>(), N, amax,
-                                                ctx->Hs.as<double>(), ctx->Cs.as<double>(),
-                                                ctx->edges.as<int>());
+  CK(ds->width_edges.reserve(sizeof(int) * (N + 1)));
+  k_width_edges<<<64, 256, 0, ctx->stream>>>(ds->K, N, ds->width_edges.as<int>());
   CKLAUNCH();
-  *edges = ctx->edges.as<int>();
-  *stride = N + 1;
+  CK(cudaStreamSynchronize(ctx->stream));
   return SCS_OK;
 }
-
-}  // namespace
-
-extern "C" {
 
 int scs_eval_stat(scs_ctx* ctx, int sid, const double* params, int64_t P, double* stat,
                   double* seg_x, double* seg_hh, void* cuda_stream) {
@@ -403,29 +540,14 @@ int scs_eval_stat(scs_ctx* ctx, int sid, const double* params, int64_t P, double
   if (rc) return rc;
   DataStream* dsp = get_stream(ctx, sid, true);
   if (!dsp) return SCS_ENODATA;
-  DataStream& ds = *dsp;
-  const int N = ds.N;
+  const int N = dsp->N;
   if ((double)P * N > 4e9 && seg_x) return fail(ctx, SCS_EINVAL, "P x N too large for segment outputs");
   cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : ctx->stream;
-  const bool mixed = ctx->path == SCS_MIXED;
   const double* dparams = nullptr;
   ctx->prof_valid = false;
   if (ctx->prof) CK(cudaEventRecord(ctx->ev[0], s));
   rc = stage_params(ctx, params, P, s, &dparams);
   if (rc) return rc;
-  int n_chunks = 0;
-  int64_t max_rec = 0;
-  rc = prepare(ctx, ds, dparams, (int)P, mixed, s, &n_chunks, &max_rec);
-  if (rc) return rc;
-  if (ctx->prof) CK(cudaEventRecord(ctx->ev[1], s));
-  const int* edges = nullptr;
-  int64_t stride = 0;
-  rc = build_edges(ctx, ds, (int)P, s, &edges, &stride);
-  if (rc) return rc;
-  CK(ctx->rec.reserve(sizeof(Rec) * (size_t)max_rec));
-  CK(ctx->counter.reserve(sizeof(int) * 2));
-  CK(cudaMemsetAsync(ctx->counter.ptr, 0, sizeof(int) * 2, s));
-  // outputs
   const bool stat_dev = is_device_ptr(stat);
   const bool seg_dev = seg_x ? (is_device_ptr(seg_x) && is_device_ptr(seg_hh)) : true;
   double* dstat = stat;
@@ -444,52 +566,63 @@ int scs_eval_stat(scs_ctx* ctx, int sid, const double* params, int64_t P, double
     CK(cudaMemsetAsync(dsx, 0, sizeof(double) * (size_t)P * N, s));
     CK(cudaMemsetAsync(dsh, 0, sizeof(double) * (size_t)P * N, s));
   }
-  EvalArgs a;
-  a.f_first = ds.f_first;
-  a.df = ds.df;
-  a.T_obs = ds.T_obs;
-  a.K = ds.K;
-  a.d32 = ds.d32.as<float4>();
-  a.w32 = ds.w32.as<float2>();
-  a.dA64 = ds.dA64.as<double2>();
-  a.dE64 = ds.dE64.as<double2>();
-  a.w64 = ds.w64.as<double2>();
-  a.W0 = ds.W0;
-  a.N = N;
-  a.edges = edges;
-  a.edge_stride = stride;
-  a.part = ctx->part.as<Part>();
-  a.P = (int)P;
-  a.n_chunks = n_chunks;
-  a.cnt = ctx->cnt.as<int>();
-  a.list_off = ctx->list_off.as<int>();
-  a.list = ctx->list.as<int>();
-  a.item_off = ctx->item_off.as<int>();
-  a.rec_off = ctx->nrec.as<int64_t>();
-  a.rec = ctx->rec.as<Rec>();
-  a.item_counter = ctx->counter.as<int>();
-  a.seg_x = dsx;
-  a.seg_hh = dsh;
-  a.err = ctx->counter.as<int>() + 1;
-  if (ctx->prof) CK(cudaEventRecord(ctx->ev[2], s));
-  if (mixed) launch_main_mixed(a, ctx->grid_mixed, s);
-  else launch_main_fp64(a, ctx->grid_fp64, s);
-  CKLAUNCH();
-  if (ctx->prof) CK(cudaEventRecord(ctx->ev[3], s));
-  k_fixup<<<(int)((P + 127) / 128), 128, 0, s>>>(ctx->part.as<Part>(), ctx->crange.as<int2>(),
-                                                 ctx->nrec.as<int64_t>(), ctx->rec.as<Rec>(),
-                                                 (int)P, N, dstat, dsx, dsh);
-  CKLAUNCH();
-  if (ctx->prof) {
-    CK(cudaEventRecord(ctx->ev[4], s));
-    ctx->prof_valid = true;
-  }
+  ScratchSource src;
+  src.ctx = ctx;
+  Prepared pr;
+  std::vector<BatchPart> parts{{dsp, 0, (int)P}};
+  rc = prepare_batch(ctx, parts, dparams, (int)P, ctx->path == SCS_MIXED, true, s, src, pr);
+  if (rc) return rc;
+  rc = run_batch(ctx, pr, (int)P, dstat, dsx, dsh, s, src);
+  if (rc) return rc;
   if (!stat_dev) CK(cudaMemcpyAsync(stat, dstat, sizeof(double) * P, cudaMemcpyDeviceToHost, s));
   if (seg_x && !seg_dev) {
     CK(cudaMemcpyAsync(seg_x, dsx, sizeof(double) * (size_t)P * N, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(seg_hh, dsh, sizeof(double) * (size_t)P * N, cudaMemcpyDeviceToHost, s));
   }
   if (!stat_dev || (seg_x && !seg_dev) || !is_device_ptr(params)) CK(cudaStreamSynchronize(s));
+  return SCS_OK;
+}
+
+int scs_batch_eval(scs_ctx* ctx, const int* stream_ids, const int64_t* P_offsets, int n_items,
+                   const double* params, double* stat, void* cuda_stream) {
+  if (!ctx) return SCS_EINVAL;
+  if (!stream_ids || !P_offsets || !params || !stat || n_items < 1 || n_items > 1024)
+    return fail(ctx, SCS_EINVAL, "bad batch arguments");
+  const int64_t P = P_offsets[n_items];
+  if (P_offsets[0] != 0 || P < 1 || P > (1 << 24))
+    return fail(ctx, SCS_EINVAL, "P_offsets must start at 0 and end in [1, 2^24]");
+  int rc = bind(ctx);
+  if (rc) return rc;
+  std::vector<BatchPart> parts;
+  for (int i = 0; i < n_items; ++i) {
+    if (P_offsets[i + 1] < P_offsets[i])
+      return fail(ctx, SCS_EINVAL, "P_offsets must be non-decreasing");
+    DataStream* d = get_stream(ctx, stream_ids[i], true);
+    if (!d) return SCS_ENODATA;
+    if (P_offsets[i + 1] > P_offsets[i])
+      parts.push_back({d, (int)P_offsets[i], (int)(P_offsets[i + 1] - P_offsets[i])});
+  }
+  cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : ctx->stream;
+  ctx->prof_valid = false;
+  if (ctx->prof) CK(cudaEventRecord(ctx->ev[0], s));
+  const double* dparams = nullptr;
+  rc = stage_params(ctx, params, P, s, &dparams);
+  if (rc) return rc;
+  const bool stat_dev = is_device_ptr(stat);
+  double* dstat = stat;
+  if (!stat_dev) {
+    CK(ctx->stat.reserve(sizeof(double) * P));
+    dstat = ctx->stat.as<double>();
+  }
+  ScratchSource src;
+  src.ctx = ctx;
+  Prepared pr;
+  rc = prepare_batch(ctx, parts, dparams, (int)P, ctx->path == SCS_MIXED, true, s, src, pr);
+  if (rc) return rc;
+  rc = run_batch(ctx, pr, (int)P, dstat, nullptr, nullptr, s, src);
+  if (rc) return rc;
+  if (!stat_dev) CK(cudaMemcpyAsync(stat, dstat, sizeof(double) * P, cudaMemcpyDeviceToHost, s));
+  if (!stat_dev || !is_device_ptr(params)) CK(cudaStreamSynchronize(s));
   return SCS_OK;
 }
 
@@ -506,15 +639,17 @@ int scs_support(scs_ctx* ctx, int sid, const double* params, int64_t P, int64_t*
   const double* dparams = nullptr;
   rc = stage_params(ctx, params, P, s, &dparams);
   if (rc) return rc;
-  int n_chunks;
-  int64_t mr;
-  rc = prepare(ctx, *ds, dparams, (int)P, log2_stride != nullptr, s, &n_chunks, &mr);
+  ScratchSource src;
+  src.ctx = ctx;
+  Prepared pr;
+  std::vector<BatchPart> parts{{ds, 0, (int)P}};
+  rc = prepare_batch(ctx, parts, dparams, (int)P, log2_stride != nullptr, false, s, src, pr);
   if (rc) return rc;
   CK(ctx->misc.reserve(sizeof(int64_t) * 2 * P + sizeof(int32_t) * P));
   int64_t* dlo = ctx->misc.as<int64_t>();
   int64_t* dhi = dlo + P;
   int32_t* dl2 = (int32_t*)(dhi + P);
-  k_support_out<<<(int)((P + 127) / 128), 128, 0, s>>>(ctx->part.as<Part>(), (int)P, dlo, dhi,
+  k_support_out<<<(int)((P + 127) / 128), 128, 0, s>>>(pr.part, (int)P, dlo, dhi,
                                                         log2_stride ? dl2 : nullptr);
   CKLAUNCH();
   CK(cudaMemcpyAsync(k_lo, dlo, sizeof(int64_t) * P, cudaMemcpyDefault, s));
@@ -537,18 +672,16 @@ int scs_segment_edges(scs_ctx* ctx, int sid, const double* params, int64_t P, in
   const double* dparams = nullptr;
   rc = stage_params(ctx, params, P, s, &dparams);
   if (rc) return rc;
-  int n_chunks;
-  int64_t mr;
-  rc = prepare(ctx, *ds, dparams, (int)P, false, s, &n_chunks, &mr);
-  if (rc) return rc;
-  const int* edges;
-  int64_t stride;
-  rc = build_edges(ctx, *ds, (int)P, s, &edges, &stride);
+  ScratchSource src;
+  src.ctx = ctx;
+  Prepared pr;
+  std::vector<BatchPart> parts{{ds, 0, (int)P}};
+  rc = prepare_batch(ctx, parts, dparams, (int)P, false, true, s, src, pr);
   if (rc) return rc;
   size_t tot = (size_t)P * (ds->N + 1);
   CK(ctx->misc.reserve(sizeof(int64_t) * tot));
-  k_edges_out<<<(int)((tot + 255) / 256), 256, 0, s>>>(ctx->part.as<Part>(), edges, stride,
-                                                        (int)P, ds->N, ctx->misc.as<int64_t>());
+  k_edges_out<<<(int)((tot + 255) / 256), 256, 0, s>>>(pr.part, pr.streams, pr.edges, (int)P,
+                                                        ds->N, ctx->misc.as<int64_t>());
   CKLAUNCH();
   CK(cudaMemcpyAsync(out, ctx->misc.ptr, sizeof(int64_t) * tot, cudaMemcpyDefault, s));
   CK(cudaStreamSynchronize(s));
@@ -560,17 +693,19 @@ static int template_to(scs_ctx* ctx, DataStream& ds, const double* theta, cudaSt
   const double* dth = nullptr;
   int rc = stage_params(ctx, theta, 1, s, &dth);
   if (rc) return rc;
-  int n_chunks;
-  int64_t mr;
-  rc = prepare(ctx, ds, dth, 1, false, s, &n_chunks, &mr);
+  ScratchSource src;
+  src.ctx = ctx;
+  Prepared pr;
+  std::vector<BatchPart> parts{{&ds, 0, 1}};
+  rc = prepare_batch(ctx, parts, dth, 1, false, false, s, src, pr);
   if (rc) return rc;
   Part hp;
-  CK(cudaMemcpyAsync(&hp, ctx->part.ptr, sizeof(Part), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&hp, pr.part, sizeof(Part), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (hp.status == kInvalid) return fail(ctx, SCS_EINVAL, "non-physical template parameters");
   CK(ctx->tmpA.reserve(sizeof(double2) * ds.K));
   CK(ctx->tmpE.reserve(sizeof(double2) * ds.K));
-  launch_waveform_fp64(ctx->part.as<Part>(), ds.f_first, ds.df, ds.K, ctx->tmpA.as<double2>(),
+  launch_waveform_fp64(pr.part, ds.f_first, ds.df, ds.K, ctx->tmpA.as<double2>(),
                        ctx->tmpE.as<double2>(), s);
   CKLAUNCH();
   *hA = ctx->tmpA.as<double2>();
@@ -671,19 +806,6 @@ constexpr int kNoAllocMaxDevices = 64;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 static void* g_noalloc_ptr[kNoAllocMaxDevices] = {nullptr};
 
-size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
-
-// carves consecutive 256-byte aligned pieces out of the static array
-struct Carve {
-  unsigned char* base;
-  size_t used, cap;
-  void* take(size_t bytes) {
-    void* p = base + used;
-    used += align256(bytes);
-    return used <= cap ? p : nullptr;
-  }
-};
-
 }  // namespace
 
 extern "C" {
@@ -701,103 +823,35 @@ int scs_eval_stat_noalloc(scs_ctx* ctx, int sid, const double* params, int64_t P
     return fail(ctx, SCS_EINVAL, "scs_eval_stat_noalloc needs device pointers for params and stat");
   DataStream* dsp = get_stream(ctx, sid, true);
   if (!dsp) return SCS_ENODATA;
-  DataStream& ds = *dsp;
+  std::vector<BatchPart> parts{{dsp, 0, (int)P}};
+  const size_t need = batch_scratch_bytes(parts, (int)P);
+  if (need > kNoAllocBytes)
+    return fail(ctx, SCS_EINVAL,
+                "scs_eval_stat_noalloc: P = %lld particles on K = %d bins (N = %d) need %zu "
+                "bytes of scratch, more than the fixed %zu",
+                (long long)P, dsp->K, dsp->N, need, kNoAllocBytes);
   // one-time set-up on this device: device address of the static array
   if (!g_noalloc_ptr[ctx->device]) {
     void* ptr = nullptr;
     CK(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
     g_noalloc_ptr[ctx->device] = ptr;
   }
-  const int Pi = (int)P, N = ds.N;
-  const int n_chunks = (ds.K + kChunk - 1) / kChunk;
-  const int64_t bound = (int64_t)P * n_chunks;
-  const bool snr2 = ds.mode == SCS_EQUAL_SNR2;
-  const int64_t amax = (int64_t)(ds.K - 1) / kSnr2Stride + 2;
-  Carve cv{static_cast<unsigned char*>(g_noalloc_ptr[ctx->device]), 0, kNoAllocBytes};
-  Part* part = (Part*)cv.take(sizeof(Part) * P);
-  int2* crange = (int2*)cv.take(sizeof(int2) * P);
-  int64_t* nrec = (int64_t*)cv.take(sizeof(int64_t) * (P + 1));
-  int64_t* total = (int64_t*)cv.take(sizeof(int64_t) * 2);
-  int* diff = (int*)cv.take(sizeof(int) * (n_chunks + 2));
-  int* cnt = (int*)cv.take(sizeof(int) * (n_chunks + 1));
-  int* list_off = (int*)cv.take(sizeof(int) * (n_chunks + 1));
-  int* item_off = (int*)cv.take(sizeof(int) * (n_chunks + 1));
-  int* fill = (int*)cv.take(sizeof(int) * (n_chunks + 1));
-  int* list = (int*)cv.take(sizeof(int) * bound);
-  Rec* rec = (Rec*)cv.take(sizeof(Rec) * bound);
-  int* counter = (int*)cv.take(sizeof(int) * 2);
-  int* edges = nullptr;
-  double *Hs = nullptr, *Cs = nullptr;
-  if (snr2) {
-    edges = (int*)cv.take(sizeof(int) * (size_t)P * (N + 1));
-    Hs = (double*)cv.take(sizeof(double) * (size_t)P * amax);
-    Cs = (double*)cv.take(sizeof(double) * (size_t)P * amax);
-  }
-  if (cv.used > cv.cap)
-    return fail(ctx, SCS_EINVAL,
-                "scs_eval_stat_noalloc: P = %lld particles on K = %d bins (N = %d) need %zu "
-                "bytes of scratch, more than the fixed %zu",
-                (long long)P, ds.K, N, cv.used, kNoAllocBytes);
   cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : ctx->stream;
-  const bool mixed = ctx->path == SCS_MIXED;
-  // the array keeps the previous call's contents: clear what must start at 0
-  CK(cudaMemsetAsync(diff, 0, sizeof(int) * (n_chunks + 2), s));
-  CK(cudaMemsetAsync(fill, 0, sizeof(int) * (n_chunks + 1), s));
-  CK(cudaMemsetAsync(counter, 0, sizeof(int) * 2, s));
-  k_setup<<<(Pi + 127) / 128, 128, 0, s>>>(params, Pi, ds.f_first, ds.df, ds.K, ds.T_obs,
-                                           mixed ? 1 : 0, part, crange, nrec, diff);
-  CKLAUNCH();
-  k_scan64<<<1, 1024, 0, s>>>(nrec, P, total);
-  CKLAUNCH();
-  k_chunk_table<<<1, 1024, 0, s>>>(diff, n_chunks, cnt, list_off, item_off);
-  CKLAUNCH();
-  k_fill<<<(Pi + 127) / 128, 128, 0, s>>>(crange, Pi, list_off, fill, list);
-  CKLAUNCH();
-  const int* e = ds.width_edges.as<int>();
-  int64_t stride = 0;
-  if (snr2) {
-    k_bounds<<<(Pi * 32 + 127) / 128, 128, 0, s>>>(part, Pi, ds.f_first, ds.df,
-                                                   ds.w64.as<double2>(), N, amax, Hs, Cs,
-                                                   edges);
-    CKLAUNCH();
-    e = edges;
-    stride = N + 1;
-  }
-  EvalArgs a;
-  a.f_first = ds.f_first;
-  a.df = ds.df;
-  a.T_obs = ds.T_obs;
-  a.K = ds.K;
-  a.d32 = ds.d32.as<float4>();
-  a.w32 = ds.w32.as<float2>();
-  a.dA64 = ds.dA64.as<double2>();
-  a.dE64 = ds.dE64.as<double2>();
-  a.w64 = ds.w64.as<double2>();
-  a.W0 = ds.W0;
-  a.N = N;
-  a.edges = e;
-  a.edge_stride = stride;
-  a.part = part;
-  a.P = Pi;
-  a.n_chunks = n_chunks;
-  a.cnt = cnt;
-  a.list_off = list_off;
-  a.list = list;
-  a.item_off = item_off;
-  a.rec_off = nrec;
-  a.rec = rec;
-  a.item_counter = counter;
-  a.seg_x = nullptr;
-  a.seg_hh = nullptr;
-  a.err = counter + 1;
-  if (mixed) launch_main_mixed(a, ctx->grid_mixed, s);
-  else launch_main_fp64(a, ctx->grid_fp64, s);
-  CKLAUNCH();
-  k_fixup<<<(Pi + 127) / 128, 128, 0, s>>>(part, crange, nrec, rec, Pi, N, stat, nullptr,
-                                           nullptr);
-  CKLAUNCH();
-  return SCS_OK;
+  // the array keeps the previous call's contents; the pipeline clears what
+  // must start at zero (chunk counters, fill cursors, the item counter)
+  ScratchSource src;
+  src.base = static_cast<unsigned char*>(g_noalloc_ptr[ctx->device]);
+  src.cap = kNoAllocBytes;
+  Prepared pr;
+  const bool prof = ctx->prof;
+  ctx->prof = false;
+  rc = prepare_batch(ctx, parts, params, (int)P, ctx->path == SCS_MIXED, true, s, src, pr);
+  if (!rc) rc = run_batch(ctx, pr, (int)P, stat, nullptr, nullptr, s, src);
+  ctx->prof = prof;
+  if (rc == SCS_ENOMEM)
+    return fail(ctx, SCS_EINVAL, "scs_eval_stat_noalloc: scratch larger than the fixed %zu bytes",
+                kNoAllocBytes);
+  return rc;
 }
 
 }  // extern "C"
-

@@ -95,6 +95,7 @@ struct Part {
   int k_lo, k_hi;   // support in grid bins (k_hi < k_lo: empty)
   int log2B;        // mixed-path phase-anchor stride
   int log2Br;       // mixed-path response sub-span (<= log2B)
+  int sid;          // index of the particle's data stream in the call's table
   double f0;
   double piMs;      // pi G M / c^3 [s]
   dd tc;            // coalescence time [s]

@@ -24,13 +24,16 @@ __global__ void __launch_bounds__(128) k_main_fp64(EvalArgs a) {
     if (lane == 0) item = atomicAdd(a.item_counter, 1);
     item = __shfl_sync(kFull, item, 0);
     if (item >= total) break;
-    const int c = find_item_chunk(a.item_off, a.n_chunks, item);
-    const int g = item - a.item_off[c];
+    const int cg = find_item_chunk(a.item_off, a.n_chunks, item);
+    const StreamDesc& sd = a.streams[stream_of_chunk(a.streams, a.n_streams, cg)];
+    const int c = cg - sd.chunk_base;   // chunk within the stream
+    const int N = sd.N;
+    const int g = item - a.item_off[cg];
     const int slot = g * 32 + lane;
-    const bool has = slot < a.cnt[c];
-    const int p = has ? a.list[a.list_off[c] + slot] : -1;
+    const bool has = slot < a.cnt[cg];
+    const int p = has ? a.list[a.list_off[cg] + slot] : -1;
     const int kc0 = c * kChunk;
-    const int kc1 = min(kc0 + kChunk, a.K);
+    const int kc1 = min(kc0 + kChunk, sd.K);
     Part pp;
     int kb = 0, ke = 0;
     if (has) {
@@ -39,8 +42,8 @@ __global__ void __launch_bounds__(128) k_main_fp64(EvalArgs a) {
       ke = min(kc1, pp.k_hi + 1);
     }
     const bool act = has && kb < ke;
-    const int* e = act ? a.edges + (int64_t)p * a.edge_stride : a.edges;
-    int n_cur = act ? segment_of(e, a.N, kb) : 0;
+    const int* e = act ? edges_of(sd, a.edges_all, p) : sd.width_edges;
+    int n_cur = act ? segment_of(e, N, kb) : 0;
     int e_next = act ? __ldg(e + n_cur + 1) : kNoEdge;
     bool head = true;
     Rec r;
@@ -64,20 +67,20 @@ __global__ void __launch_bounds__(128) k_main_fp64(EvalArgs a) {
             double x2 = s.zr * s.zr + s.zi * s.zi;
             if (s.hh > 0.0) r.ups += x2 / s.hh;
             if (a.seg_x) {
-              a.seg_x[(int64_t)p * a.N + n_cur] = sqrt(x2);
-              a.seg_hh[(int64_t)p * a.N + n_cur] = s.hh;
+              a.seg_x[(int64_t)p * N + n_cur] = sqrt(x2);
+              a.seg_hh[(int64_t)p * N + n_cur] = s.hh;
             }
           }
           s = Acc64{0.0, 0.0, 0.0};
-          n_cur = advance_segment(e, a.N, n_cur, k);
+          n_cur = advance_segment(e, N, n_cur, k);
           e_next = __ldg(e + n_cur + 1);
         }
         Cx<double> GA, GE;
         double phi;
-        bin_fp64(pp, a.f_first, a.df, k, GA, GE, phi);
+        bin_fp64(pp, sd.f_first, sd.df, k, GA, GE, phi);
         double sp, cp;
         sincospi(2.0 * phi, &sp, &cp);
-        double2 dA = a.dA64[k], dE = a.dE64[k], w = a.w64[k];
+        double2 dA = sd.dA64[k], dE = sd.dE64[k], w = sd.w64[k];
         // q = d~_A conj(G_A) + d~_E conj(G_E);  z += q e^{+2 pi i Phi}
         double qr = dA.x * GA.re + dA.y * GA.im + dE.x * GE.re + dE.y * GE.im;
         double qi = dA.y * GA.re - dA.x * GA.im + dE.y * GE.re - dE.x * GE.im;

@@ -19,26 +19,38 @@ struct Rec {
   double ups;
 };
 
-// Everything a main kernel needs; all pointers are device memory.
-struct EvalArgs {
+// One data stream of an evaluation call.  A call may batch several streams
+// (different grids, segment counts and segmentations); its particles are
+// grouped by stream (particles p_off .. p_off + n_p - 1) and its chunk table
+// is the concatenation of the streams' chunks (chunk_base .. + n_chunks - 1).
+struct StreamDesc {
   double f_first, df, T_obs;
-  int K;
+  double W0;             // FP32 copies hold d~/sqrt(W0) and w/W0
+  int K, N, mode;        // mode: 0 equal width, 1 equal SNR^2
+  int chunk_base, n_chunks;
+  int p_off, n_p;
+  int amax;              // anchor slots per particle for the equal-SNR^2 edges
+  int64_t edge_base;     // equal SNR^2: this stream's first edge table in edges_all
+  int64_t hc_base;       // equal SNR^2: its first anchor slot in the H/C scratch
   // pre-whitened data d~ = 4 df d / S and weights w = 4 df / S
-  const float4* d32;     // (A.re, A.im, E.re, E.im)
-  const float2* w32;     // (w_A, w_E)
+  const float4* d32;     // (A.re, A.im, E.re, E.im) / sqrt(W0)
+  const float2* w32;     // (w_A, w_E) / W0
   const double2* dA64;
   const double2* dE64;
   const double2* w64;
-  double W0;             // FP32 copies hold d~/sqrt(W0) and w/W0
-  // segmentation: edges[p * edge_stride + n], n = 0..N
-  int N;
-  const int* edges;
-  int64_t edge_stride;   // 0 when all particles share one edge table
+  const int* width_edges;   // equal width: the shared table e_n = floor(n K / N)
+};
+
+// Everything a main kernel needs; all pointers are device memory.
+struct EvalArgs {
+  const StreamDesc* streams;
+  int n_streams;
+  const int* edges_all;  // equal-SNR^2 edge tables of all particles
   // particles
   const Part* part;
   int P;
-  // work list: chunk c holds list[list_off[c] .. list_off[c] + cnt[c]),
-  // processed by warp items item_off[c] .. item_off[c+1]
+  // work list: global chunk g holds list[list_off[g] .. list_off[g] + cnt[g]),
+  // processed by warp items item_off[g] .. item_off[g+1]
   int n_chunks;
   const int* cnt;
   const int* list_off;
@@ -47,11 +59,18 @@ struct EvalArgs {
   const int64_t* rec_off;
   Rec* rec;
   int* item_counter;
-  // outputs (optional)
+  // per-segment outputs (single-stream calls only; NULL otherwise)
   double* seg_x;
   double* seg_hh;
   int* err;
 };
+
+// segment edge table of particle p (e_0 .. e_N, non-decreasing)
+__host__ __device__ inline const int* edges_of(const StreamDesc& d, const int* edges_all,
+                                               int p) {
+  return d.mode == 1 ? edges_all + d.edge_base + (int64_t)(p - d.p_off) * (d.N + 1)
+                     : d.width_edges;
+}
 
 void launch_main_mixed(const EvalArgs& a, int grid, cudaStream_t s);
 void launch_main_fp64(const EvalArgs& a, int grid, cudaStream_t s);
@@ -61,8 +80,28 @@ void launch_waveform_fp64(const Part* part, double f_first, double df, int K,
 int occupancy_mixed(int* blocks_per_sm);
 int occupancy_fp64(int* blocks_per_sm);
 
-// chunk index of a grid bin
+// chunk index of a grid bin within its stream
 __host__ __device__ inline int chunk_of(int k) { return k / kChunk; }
+
+// stream of global chunk g (streams ordered by chunk_base)
+__device__ inline int stream_of_chunk(const StreamDesc* s, int n, int g) {
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (s[mid].chunk_base <= g) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// stream of particle p (streams ordered by p_off)
+__device__ inline int stream_of_particle(const StreamDesc* s, int n, int p) {
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (s[mid].p_off <= p) lo = mid; else hi = mid;
+  }
+  return lo;
+}
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kNoEdge = 0x7fffffff;

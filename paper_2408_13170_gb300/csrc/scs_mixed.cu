@@ -50,7 +50,17 @@ struct Lane {
   float bzr, bzi, bhh;
 };
 
-__device__ __forceinline__ void close_segment(Lane& L, const EvalArgs& a, double zs, int k) {
+// the data stream of a work item, as the hot loop needs it
+struct ItemStream {
+  const float4* d32;
+  const float2* w32;
+  double W0, zs;          // FP32 sums -> physical units: z * zs, hh * W0
+  int N;
+  double* seg_x;
+  double* seg_hh;
+};
+
+__device__ __forceinline__ void close_segment(Lane& L, const ItemStream& a, double zs, int k) {
   float zr = kval(L.szr) + L.bzr, zi = kval(L.szi) + L.bzi, hh = kval(L.shh) + L.bhh;
   if (L.head) {
     L.rec->n_head = L.n_cur;
@@ -78,7 +88,7 @@ __device__ __forceinline__ void close_segment(Lane& L, const EvalArgs& a, double
 // a second, unmasked copy measured slower through its larger code).  The
 // data of bin k+1 is loaded while bin k is computed (the FP32 arrays carry a
 // zeroed tail for the last prefetch).
-__device__ __forceinline__ void run_block(Lane& L, const EvalArgs& a, double zs, int k0,
+__device__ __forceinline__ void run_block(Lane& L, const ItemStream& a, double zs, int k0,
                                           int nb) {
   float4 dn = __ldg(a.d32 + k0);
   float2 wn = __ldg(a.w32 + k0);
@@ -121,21 +131,32 @@ __device__ __forceinline__ void run_block(Lane& L, const EvalArgs& a, double zs,
 __global__ void __launch_bounds__(128, 4) k_main_mixed(EvalArgs a) {
   const int lane = threadIdx.x & 31;
   const int total = a.item_off[a.n_chunks];
-  const double zs = sqrt(a.W0);   // FP32 sums -> physical units
-  const float df32 = (float)a.df;
   for (;;) {
     int item = 0;
     if (lane == 0) item = atomicAdd(a.item_counter, 1);
     item = __shfl_sync(kFull, item, 0);
     if (item >= total) break;
-    const int c = find_item_chunk(a.item_off, a.n_chunks, item);
-    const int g = item - a.item_off[c];
+    const int cg = find_item_chunk(a.item_off, a.n_chunks, item);
+    const StreamDesc& sd = a.streams[stream_of_chunk(a.streams, a.n_streams, cg)];
+    ItemStream is;
+    is.d32 = sd.d32;
+    is.w32 = sd.w32;
+    is.W0 = sd.W0;
+    is.zs = sqrt(sd.W0);
+    is.N = sd.N;
+    is.seg_x = a.seg_x;
+    is.seg_hh = a.seg_hh;
+    const double zs = is.zs;
+    const double f_first = sd.f_first, df = sd.df;
+    const float df32 = (float)df;
+    const int c = cg - sd.chunk_base;   // chunk within the stream
+    const int g = item - a.item_off[cg];
     const int slot = g * 32 + lane;
-    const bool has = slot < a.cnt[c];
+    const bool has = slot < a.cnt[cg];
     const int kc0 = c * kChunk;
-    const int kc1 = min(kc0 + kChunk, a.K);
+    const int kc1 = min(kc0 + kChunk, sd.K);
     Lane L;
-    L.p = has ? a.list[a.list_off[c] + slot] : 0;
+    L.p = has ? a.list[a.list_off[cg] + slot] : 0;
     L.pp = a.part + L.p;
     L.kb = 0;
     L.ke = 0;
@@ -154,8 +175,8 @@ __global__ void __launch_bounds__(128, 4) k_main_mixed(EvalArgs a) {
     }
     L.act = has && L.kb < L.ke;
     if (!L.act) first = kNoEdge;
-    L.e = L.act ? a.edges + (int64_t)L.p * a.edge_stride : a.edges;
-    L.n_cur = L.act ? segment_of(L.e, a.N, L.kb) : 0;
+    L.e = L.act ? edges_of(sd, a.edges_all, L.p) : sd.width_edges;
+    L.n_cur = L.act ? segment_of(L.e, is.N, L.kb) : 0;
     L.e_next = L.act ? __ldg(L.e + L.n_cur + 1) : kNoEdge;
     L.head = true;
     L.fresh = true;
@@ -177,7 +198,7 @@ __global__ void __launch_bounds__(128, 4) k_main_mixed(EvalArgs a) {
     for (int k0 = kw0; k0 < kw1; k0 += BW) {
       if (L.act && k0 == L.next_phase && k0 < L.ke) {
         PhaseAnchor an;
-        phase_anchor(*L.pp, k0, a.f_first, a.df, an);
+        phase_anchor(*L.pp, k0, f_first, df, an);
 #pragma unroll
         for (int r = 0; r <= kOrd; ++r) L.d[r] = an.d[r];
         L.al0 = an.al0;
@@ -202,8 +223,12 @@ __global__ void __launch_bounds__(128, 4) k_main_mixed(EvalArgs a) {
         L.next_resp += 1 << L.log2Br;
       }
       const int nb = min(BW, kw1 - k0);
-      run_block(L, a, zs, k0, nb);
-      if (((k0 + BW) & 31) == 0) {
+      run_block(L, is, zs, k0, nb);
+      // block sums go into the Kahan accumulators at 32-aligned bins inside
+      // the lane's range and once at its end, never later: the rounding of a
+      // particle's sums does not depend on which particles share its warp
+      const int kend = k0 + nb;
+      if (k0 < L.ke && ((kend & 31) == 0 || kend >= L.ke)) {
         kadd(L.szr, L.bzr);
         kadd(L.szi, L.bzi);
         kadd(L.shh, L.bhh);
@@ -216,14 +241,14 @@ __global__ void __launch_bounds__(128, 4) k_main_mixed(EvalArgs a) {
         L.rec->n_head = L.n_cur;
         L.rec->zr_h = zr * zs;
         L.rec->zi_h = zi * zs;
-        L.rec->hh_h = hh * a.W0;
+        L.rec->hh_h = hh * is.W0;
         L.rec->n_tail = -1;
         L.rec->zr_t = L.rec->zi_t = L.rec->hh_t = 0.0;
       } else {
         L.rec->n_tail = L.n_cur;
         L.rec->zr_t = zr * zs;
         L.rec->zi_t = zi * zs;
-        L.rec->hh_t = hh * a.W0;
+        L.rec->hh_t = hh * is.W0;
       }
       L.rec->ups = (double)L.ups.s - (double)L.ups.c;
     }

@@ -118,20 +118,22 @@ __device__ void choose_strides(Part& p, double f_first, double df) {
 
 }  // namespace
 
-// One thread per particle: derive, find the support, choose the stride,
-// count the chunks the particle touches.
-__global__ void k_setup(const double* params, int P, double f_first, double df, int K,
-                        double T_obs, int want_stride, Part* part, int2* crange,
-                        int64_t* nrec, int* diff) {
+// One thread per particle: derive, find the support on its stream's grid,
+// choose the strides, count the (global) chunks the particle touches.
+__global__ void k_setup(const double* params, int P, const StreamDesc* streams, int n_streams,
+                        int want_stride, Part* part, int2* crange, int64_t* nrec, int* diff) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= P) return;
+  const int sid = stream_of_particle(streams, n_streams, i);
+  const StreamDesc& d = streams[sid];
   Part p;
   part_init(p, params + 8 * (int64_t)i);
-  part_support(p, f_first, df, K, T_obs);
+  part_support(p, d.f_first, d.df, d.K, d.T_obs);
+  p.sid = sid;
   int2 cr = make_int2(0, -1);
   if (p.status == kOk) {
-    if (want_stride) choose_strides(p, f_first, df);
-    cr = make_int2(chunk_of(p.k_lo), chunk_of(p.k_hi));
+    if (want_stride) choose_strides(p, d.f_first, d.df);
+    cr = make_int2(d.chunk_base + chunk_of(p.k_lo), d.chunk_base + chunk_of(p.k_hi));
     atomicAdd(diff + cr.x, 1);
     atomicAdd(diff + cr.y + 1, -1);
   }
@@ -233,22 +235,28 @@ __global__ void k_fill(const int2* crange, int P, const int* list_off, int* fill
 // target c_n = n C/N; kappa_n by linear inverse interpolation; segment n
 // starts at bin ceil(kappa_n).  The double operations follow that order
 // explicitly (no contraction) so that the rounding is the definition's.
-__global__ void k_bounds(const Part* part, int P, double f_first, double df,
-                         const double2* w64, int N, int64_t amax, double* Hs, double* Cs,
-                         int* edges) {
+__global__ void k_bounds(const Part* part, int P, const StreamDesc* streams, int* edges_all,
+                         double* Hs, double* Cs) {
   int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (gw >= P) return;
   const Part& p = part[gw];
-  int* e = edges + (int64_t)gw * (N + 1);
+  const StreamDesc& sd = streams[p.sid];
+  if (sd.mode != 1) return;   // equal-width streams share a fixed table
+  const int N = sd.N;
+  const double f_first = sd.f_first, df = sd.df;
+  const double2* w64 = sd.w64;
+  const int64_t amax = sd.amax;
+  const int64_t lp = gw - sd.p_off;
+  int* e = edges_all + sd.edge_base + lp * (N + 1);
   if (p.status != kOk) {
     for (int n = lane; n <= N; n += 32) e[n] = 0;
     return;
   }
   int span = p.k_hi - p.k_lo;
   int nanch = span / kSnr2Stride + 1 + (span % kSnr2Stride != 0 ? 1 : 0);
-  double* H = Hs + (int64_t)gw * amax;
-  double* C = Cs + (int64_t)gw * amax;
+  double* H = Hs + sd.hc_base + lp * amax;
+  double* C = Cs + sd.hc_base + lp * amax;
   for (int a = lane; a < nanch; a += 32) {
     int ka = min(p.k_lo + a * kSnr2Stride, p.k_hi);
     double f = dd_val(grid_freq_dd(f_first, df, ka));
@@ -311,8 +319,8 @@ __global__ void k_bounds(const Part* part, int P, double f_first, double df,
 
 // Merge the (particle, chunk) records into Upsilon_N (Sec. II.B).
 __global__ void k_fixup(const Part* part, const int2* crange, const int64_t* rec_off,
-                        const Rec* rec, int P, int N, double* stat, double* seg_x,
-                        double* seg_hh) {
+                        const Rec* rec, int P, const StreamDesc* streams, double* stat,
+                        double* seg_x, double* seg_hh) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= P) return;
   const Part& p = part[i];
@@ -324,6 +332,7 @@ __global__ void k_fixup(const Part* part, const int2* crange, const int64_t* rec
     stat[i] = 0.0;
     return;
   }
+  const int N = streams[p.sid].N;
   int2 cr = crange[i];
   double ups = 0.0;
   int n_run = -1;
@@ -456,14 +465,15 @@ __global__ void k_support_out(const Part* part, int P, int64_t* klo, int64_t* kh
   if (l2b) l2b[i] = p.log2B;
 }
 
-__global__ void k_edges_out(const Part* part, const int* edges, int64_t stride, int P, int N,
-                            int64_t* out) {
+__global__ void k_edges_out(const Part* part, const StreamDesc* streams, const int* edges_all,
+                            int P, int N, int64_t* out) {
   int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int64_t tot = (int64_t)P * (N + 1);
   if (idx >= tot) return;
-  int64_t p = idx / (N + 1);
+  int p = (int)(idx / (N + 1));
   int n = (int)(idx % (N + 1));
-  out[idx] = part[p].status == kInvalid ? -1 : edges[p * stride + n];
+  const Part& pp = part[p];
+  out[idx] = pp.status == kInvalid ? -1 : edges_of(streams[pp.sid], edges_all, p)[n];
 }
 
 }  // namespace scs

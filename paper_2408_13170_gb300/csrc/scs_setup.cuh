@@ -4,19 +4,17 @@
 
 namespace scs {
 
-__global__ void k_setup(const double* params, int P, double f_first, double df, int K,
-                        double T_obs, int want_stride, Part* part, int2* crange,
-                        int64_t* nrec, int* diff);
+__global__ void k_setup(const double* params, int P, const StreamDesc* streams, int n_streams,
+                        int want_stride, Part* part, int2* crange, int64_t* nrec, int* diff);
 __global__ void k_scan64(int64_t* v, int64_t n, int64_t* total);
 __global__ void k_chunk_table(const int* diff, int n_chunks, int* cnt, int* list_off,
                               int* item_off);
 __global__ void k_fill(const int2* crange, int P, const int* list_off, int* fill, int* list);
-__global__ void k_bounds(const Part* part, int P, double f_first, double df,
-                         const double2* w64, int N, int64_t amax, double* Hs, double* Cs,
-                         int* edges);
+__global__ void k_bounds(const Part* part, int P, const StreamDesc* streams, int* edges_all,
+                         double* Hs, double* Cs);
 __global__ void k_fixup(const Part* part, const int2* crange, const int64_t* rec_off,
-                        const Rec* rec, int P, int N, double* stat, double* seg_x,
-                        double* seg_hh);
+                        const Rec* rec, int P, const StreamDesc* streams, double* stat,
+                        double* seg_x, double* seg_hh);
 __global__ void k_prewhiten(const double2* A, const double2* E, const double* SA,
                             const double* SE, double df, int K, double2* dA64, double2* dE64,
                             double2* w64, unsigned long long* wmax);
@@ -31,7 +29,7 @@ __global__ void k_add_template(const double2* hA, const double2* hE, double s, i
 __global__ void k_width_edges(int64_t K, int N, int* e);
 __global__ void k_support_out(const Part* part, int P, int64_t* klo, int64_t* khi,
                               int32_t* l2b);
-__global__ void k_edges_out(const Part* part, const int* edges, int64_t stride, int P, int N,
-                            int64_t* out);
+__global__ void k_edges_out(const Part* part, const StreamDesc* streams, const int* edges_all,
+                            int P, int N, int64_t* out);
 
 }  // namespace scs

@@ -67,6 +67,8 @@ def lib():
         L.scs_last_timings.restype = I
         L.scs_eval_stat_noalloc.argtypes = [P, I, P, I64, P, P]
         L.scs_eval_stat_noalloc.restype = I
+        L.scs_batch_eval.argtypes = [P, P, P, I, P, P, P]
+        L.scs_batch_eval.restype = I
         _lib = L
         return L
 
@@ -139,6 +141,14 @@ def scs_set_segments(ctx, stream_id, N, mode):
 def scs_eval_stat(ctx, stream_id, params, P, stat, seg_x=None, seg_hh=None, cuda_stream=None):
     _check(ctx, lib().scs_eval_stat(ctx, stream_id, _ptr(params), int(P), _ptr(stat),
                                     _ptr(seg_x), _ptr(seg_hh), _stream(cuda_stream)))
+
+
+def scs_batch_eval(ctx, stream_ids, P_offsets, params, stat, cuda_stream=None):
+    """Items i: particles P_offsets[i]..P_offsets[i+1]-1 on stream stream_ids[i]."""
+    sids = np.ascontiguousarray(stream_ids, dtype=np.int32)
+    offs = np.ascontiguousarray(P_offsets, dtype=np.int64)
+    _check(ctx, lib().scs_batch_eval(ctx, _ptr(sids), _ptr(offs), len(sids), _ptr(params),
+                                     _ptr(stat), _stream(cuda_stream)))
 
 
 def scs_waveform(ctx, stream_id, theta, hA, hE, cuda_stream=None):
@@ -230,6 +240,16 @@ class Context:
             return stat, sx, sh
         scs_eval_stat(self.h, stream_id, params, P, stat)
         return stat
+
+    def batch_eval(self, stream_ids, params_list):
+        """One launch over several streams; returns one stat array per item."""
+        params_list = [np.ascontiguousarray(p, dtype=np.float64).reshape(-1, 8)
+                       for p in params_list]
+        offs = np.concatenate([[0], np.cumsum([len(p) for p in params_list])])
+        allp = np.ascontiguousarray(np.vstack(params_list))
+        stat = np.empty(len(allp))
+        scs_batch_eval(self.h, stream_ids, offs, allp, stat)
+        return [stat[offs[i]:offs[i + 1]] for i in range(len(params_list))]
 
     def waveform(self, stream_id, theta, K):
         hA = np.empty(K, np.complex128)

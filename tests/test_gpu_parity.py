@@ -223,3 +223,34 @@ def test_c1_full(scstat):
     assert rel_err(s64, ref) <= TOL64
     assert rel_err(s32, ref) <= TOL32
     assert np.argmax(s32) == np.argmax(ref) == 0
+
+
+def test_batch_eval_matches_single_streams(scstat):
+    """One persistent launch over three streams with different durations,
+    bands, segment counts and segmentations gives, particle by particle, the
+    single-stream results (and the oracle's)."""
+    specs = [(3e6, 0.0175, 0.0200, 31, 8, oracle.EQUAL_SNR2),
+             (2e6, 0.0150, 0.0190, 32, 5, oracle.EQUAL_WIDTH),
+             (4e6, 0.0120, 0.0220, 33, 64, oracle.EQUAL_SNR2)]
+    rng = np.random.default_rng(3)
+    with scstat.Context(0, scstat.SCS_MIXED) as ctx:
+        datas, ths = [], []
+        for i, (T, f0, f1, seed, N, mode) in enumerate(specs):
+            d, inj = stream(T=T, fmin=f0, fmax=f1, seed=seed)
+            ctx.set_data(i, d)
+            ctx.set_segments(i, N, mode)
+            th = np.vstack([inj, particles(rng, 20 + 17 * i, f_lo=f0 * 1.01, f_hi=f1 * 0.95)])
+            datas.append(d)
+            ths.append(th)
+        for path, tol in ((scstat.SCS_MIXED, TOL32), (scstat.SCS_FP64, TOL64)):
+            ctx.set_path(path)
+            single = [ctx.eval(i, th) for i, th in enumerate(ths)]
+            batched = ctx.batch_eval([0, 1, 2], ths)
+            for i in range(3):
+                np.testing.assert_array_equal(batched[i], single[i])
+                ref = oracle.evaluate(datas[i], ths[i], specs[i][4], mode=specs[i][5])
+                assert rel_err(batched[i], ref) <= tol
+        # the same stream twice, and an empty item
+        ctx.set_path(scstat.SCS_MIXED)
+        b = ctx.batch_eval([2, 0, 2], [ths[2][:5], np.zeros((0, 8)), ths[2][5:]])
+        np.testing.assert_array_equal(np.concatenate([b[0], b[2]]), ctx.eval(2, ths[2]))
