@@ -132,6 +132,82 @@ int scs_eval_stat(scs_ctx *ctx, int stream_id, const double *params,
 int scs_batch_eval(scs_ctx *ctx, const int *stream_ids, const int64_t *P_offsets,
                    int n_items, const double *params, double *stat, void *cuda_stream);
 
+/* ---- Device-side particle swarm (Sec. III.A; multi-swarm, Sec. III.B) ----
+ * One swarm state per context.  Swarm s owns particles swarm_offsets[s] ..
+ * swarm_offsets[s+1]-1 and searches data stream stream_ids[s] with that
+ * stream's segmentation.  An iteration evaluates Upsilon_N of every particle
+ * of every swarm in one batched launch (as scs_batch_eval), then on the device:
+ *   personal best  Psi_p <- theta_p where Upsilon(theta_p) > best_p (strict);
+ *   swarm best     Xi_s <- the best personal best of the swarm if it beats
+ *                  the swarm's record (strict; lowest particle index on ties);
+ *   velocity       u = Omega v + Phi_P r_P (Psi_p - theta) + Phi_G r_G (Xi_s - theta)
+ *                  per dimension (Eq. PSO_velocity_rule), evaluated as
+ *                  ((Omega v) + ((Phi_P r_P) (Psi - theta))) + ((Phi_G r_G) (Xi - theta))
+ *                  with every operation rounded once (no contraction);
+ *   clamp          v = u if |u| >= eps, else eps with the sign of u, sign(0)
+ *                  = +1 (Eq. PSO_min_velocity);
+ *   move           theta <- theta + v; lambda (dimension 3) and psi (6) wrap
+ *                  into [lo, hi); the others reflect at a bound that was
+ *                  crossed (2 bound - theta, velocity negated) and are then
+ *                  clipped to [lo, hi].  Dimension 7 (e0) stays at prior_lo[7].
+ * r_P, r_G: outputs 0 and 1 of Philox4x32-10 (Salmon et al., SC'11) with key
+ * (seed mod 2^32, seed >> 32) and counter (particle, iteration, dimension, 0),
+ * mapped to (x + 1/2) 2^-32.  The iteration counter lives on the device.
+ * Initial state: theta = lo + u0 (hi - lo), v = (u1 - 1/2) 0.2 (hi - lo) with
+ * (u0, u1) from counter (particle, 2^32 - 1, dimension, 1); best values -inf.
+ * Particles whose statistic is -inf (non-physical) never become bests. */
+
+/* Create (or replace) the swarm state and initialise it on the device.
+ *   n_swarms       1 .. 1024.
+ *   stream_ids     n_swarms data streams, each with data and segmentation set.
+ *   swarm_offsets  n_swarms + 1 int64, [0] = 0, strictly increasing, total P <= 2^24.
+ *   prior_lo/hi    8 doubles each; hi > lo in dimensions 0..6 (host memory).
+ *   seed           Philox key.
+ * Hyper-parameters default to the N = 100 row of Table III for every swarm.
+ * Synchronous.  Errors: SCS_EINVAL, SCS_ENODATA, SCS_ENOMEM, SCS_ECUDA. */
+int scs_pso_create(scs_ctx *ctx, int n_swarms, const int *stream_ids,
+                   const int64_t *swarm_offsets, const double *prior_lo,
+                   const double *prior_hi, uint64_t seed, void *cuda_stream);
+
+/* Set Omega, Phi_P, Phi_G and eps[8] (minimum speeds, parameter order of
+ * params, >= 0) of one swarm, or of every swarm if swarm = -1.  Waits for the
+ * work on cuda_stream first.  Errors: SCS_EINVAL, SCS_ENODATA (no swarm). */
+int scs_pso_set_hyper(scs_ctx *ctx, int swarm, double Omega, double PhiP, double PhiG,
+                      const double *eps, void *cuda_stream);
+
+/* Run iters (0 .. 100000) iterations, asynchronously on cuda_stream (NULL:
+ * the context's stream).  use_graph = 1 captures iters whole iterations into
+ * one CUDA graph on the first call (and again when iters, the path or a
+ * swarm's stream data or segmentation changed) and launches it; use_graph = 0
+ * launches the same kernels directly.  Both give identical states.  The
+ * swarm evaluates with its own scratch, separate from the other calls.
+ * Errors: SCS_EINVAL, SCS_ENODATA, SCS_ENOMEM, SCS_ECUDA. */
+int scs_pso_run(scs_ctx *ctx, int iters, int use_graph, void *cuda_stream);
+
+/* Copy the state out (each pointer may be NULL to skip; host or device):
+ * pos, vel, best_pos P x 8; best_val P; swarm_pos S x 8; swarm_val S;
+ * stat P (statistic of the positions evaluated last, i.e. before the last
+ * move); iteration = iterations run since create.  Synchronous. */
+int scs_pso_get(scs_ctx *ctx, double *pos, double *vel, double *best_pos, double *best_val,
+                double *swarm_pos, double *swarm_val, double *stat, int64_t *iteration,
+                void *cuda_stream);
+
+/* Overwrite parts of the state (NULL pointers keep that part; host or
+ * device) and set the iteration counter (0 .. 2^32 - 1).  Synchronous. */
+int scs_pso_set(scs_ctx *ctx, const double *pos, const double *vel, const double *best_pos,
+                const double *best_val, const double *swarm_pos, const double *swarm_val,
+                int64_t iteration, void *cuda_stream);
+
+/* Checkpoint of the whole swarm (layout, seed, prior box, hyper-parameters,
+ * state, iteration) into a caller-owned buffer: with buf = NULL, *len
+ * receives the size; otherwise *len is the buffer's size on input and the
+ * bytes written on output.  scs_pso_load recreates the swarm from such a
+ * buffer (the referenced streams must exist in this context); the run then
+ * continues bit for bit as it would have without the checkpoint.
+ * Errors: SCS_EINVAL (small buffer, not a checkpoint), as create. */
+int scs_pso_save(scs_ctx *ctx, void *buf, size_t *len, void *cuda_stream);
+int scs_pso_load(scs_ctx *ctx, const void *buf, size_t len, void *cuda_stream);
+
 /* Template h_A, h_E (Sec. IV: h_alpha = T_alpha(theta, f) A(f) e^{-i Psi(f)},
  * A(f) = f^{-7/6}) of one particle on the stream's grid, FP64, complex
  * interleaved, zero outside the support.

@@ -47,6 +47,7 @@ struct DataStream {
   double W0 = 1.0;
   int N = 0, mode = -1;
   DevBuf width_edges;   // N + 1 ints, e_n = floor(n K / N)
+  uint64_t gen = 0;     // bumped by every set_data / set_segments
 };
 
 bool is_device_ptr(const void* p) {
@@ -81,6 +82,22 @@ struct scs_ctx {
   std::map<int, DataStream> streams;
   DevBuf slot[kNumSlots];          // pipeline scratch (grow-only)
   DevBuf params, stat, segx, segh, tmpA, tmpE, tmpS1, tmpS2, red, misc;
+  // device-side particle swarm (scs_pso_*)
+  struct Pso {
+    bool made = false;
+    int P = 0, S = 0;
+    uint64_t seed = 0;
+    std::vector<int> sids;
+    std::vector<int64_t> off;
+    std::vector<double> hyper, lohi;           // S x 11; lo[8], hi[8]
+    DevBuf d_off, pos, vel, best_pos, best_val, swarm_pos, swarm_val, stat, d_hyper, d_lohi,
+        iter, table, scratch;
+    std::vector<uint64_t> gens;                // data generations the table was built from
+    int table_path = -1;
+    cudaGraphExec_t exec = nullptr;            // captured iterations
+    int graph_iters = 0;
+    cudaStream_t cap = nullptr;                // capture stream
+  } pso;
 };
 
 namespace {
@@ -245,7 +262,7 @@ struct Prepared {
 // equal-SNR^2 edges for P particles grouped by stream.
 int prepare_batch(scs_ctx* ctx, const std::vector<BatchPart>& parts, const double* dparams,
                   int P, bool want_stride, bool want_edges, cudaStream_t s,
-                  ScratchSource& src, Prepared& out) {
+                  ScratchSource& src, Prepared& out, StreamDesc* dev_table = nullptr) {
   int nct = 0;
   int64_t etot = 0, htot = 0;
   std::vector<StreamDesc> table = make_table(parts, &nct, &etot, &htot);
@@ -258,7 +275,8 @@ int prepare_batch(scs_ctx* ctx, const std::vector<BatchPart>& parts, const doubl
     out.any_snr2 = out.any_snr2 || d.mode == SCS_EQUAL_SNR2;
   }
   out.bound = bound;
-  out.streams = (StreamDesc*)src.get(kSlotStreams, sizeof(StreamDesc) * ns);
+  out.streams = dev_table ? dev_table
+                          : (StreamDesc*)src.get(kSlotStreams, sizeof(StreamDesc) * ns);
   out.part = (Part*)src.get(kSlotPart, sizeof(Part) * P);
   out.crange = (int2*)src.get(kSlotCrange, sizeof(int2) * P);
   out.nrec = (int64_t*)src.get(kSlotNrec, sizeof(int64_t) * (P + 1));
@@ -279,8 +297,9 @@ int prepare_batch(scs_ctx* ctx, const std::vector<BatchPart>& parts, const doubl
     if (src.ctx) CK(src.err);
     return SCS_ENOMEM;
   }
-  CK(cudaMemcpyAsync(out.streams, table.data(), sizeof(StreamDesc) * ns, cudaMemcpyHostToDevice,
-                     s));
+  if (!dev_table)
+    CK(cudaMemcpyAsync(out.streams, table.data(), sizeof(StreamDesc) * ns,
+                       cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(diff, 0, sizeof(int) * (nct + 2), s));
   CK(cudaMemsetAsync(fill, 0, sizeof(int) * (nct + 1), s));
   k_setup<<<(P + 127) / 128, 128, 0, s>>>(dparams, P, out.streams, ns, want_stride ? 1 : 0,
@@ -399,6 +418,15 @@ void scs_destroy(scs_ctx* ctx) {
     d.width_edges.release();
   }
   for (DevBuf& b : ctx->slot) b.release();
+  {
+    auto& q = ctx->pso;
+    if (q.exec) cudaGraphExecDestroy(q.exec);
+    if (q.cap) cudaStreamDestroy(q.cap);
+    DevBuf* pb[] = {&q.d_off, &q.pos, &q.vel, &q.best_pos, &q.best_val, &q.swarm_pos,
+                    &q.swarm_val, &q.stat, &q.d_hyper, &q.d_lohi, &q.iter, &q.table,
+                    &q.scratch};
+    for (DevBuf* b : pb) b->release();
+  }
   DevBuf* bufs[] = {&ctx->params, &ctx->stat, &ctx->segx, &ctx->segh, &ctx->tmpA,
                     &ctx->tmpE, &ctx->tmpS1, &ctx->tmpS2, &ctx->red, &ctx->misc};
   for (DevBuf* b : bufs) b->release();
@@ -508,6 +536,7 @@ int scs_set_data(scs_ctx* ctx, int sid, const double* A, const double* E, const 
     CKLAUNCH();
     CK(cudaStreamSynchronize(s));
   }
+  ds.gen++;
   return SCS_OK;
 }
 
@@ -526,6 +555,7 @@ int scs_set_segments(scs_ctx* ctx, int sid, int N, int mode) {
   k_width_edges<<<64, 256, 0, ctx->stream>>>(ds->K, N, ds->width_edges.as<int>());
   CKLAUNCH();
   CK(cudaStreamSynchronize(ctx->stream));
+  ds->gen++;
   return SCS_OK;
 }
 
@@ -852,6 +882,413 @@ int scs_eval_stat_noalloc(scs_ctx* ctx, int sid, const double* params, int64_t P
     return fail(ctx, SCS_EINVAL, "scs_eval_stat_noalloc: scratch larger than the fixed %zu bytes",
                 kNoAllocBytes);
   return rc;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Device-side particle swarm (Sec. III.A and the multi-swarm search of
+// Sec. III.B): every iteration evaluates Upsilon_N of all particles of all
+// swarms in one batched launch and moves them on the device.
+namespace {
+
+PsoArgs pso_args(scs_ctx* ctx) {
+  auto& q = ctx->pso;
+  PsoArgs a;
+  a.P = q.P;
+  a.S = q.S;
+  a.off = q.d_off.as<int64_t>();
+  a.pos = q.pos.as<double>();
+  a.vel = q.vel.as<double>();
+  a.best_pos = q.best_pos.as<double>();
+  a.best_val = q.best_val.as<double>();
+  a.swarm_pos = q.swarm_pos.as<double>();
+  a.swarm_val = q.swarm_val.as<double>();
+  a.stat = q.stat.as<double>();
+  a.hyper = q.d_hyper.as<double>();
+  a.lo = q.d_lohi.as<double>();
+  a.hi = q.d_lohi.as<double>() + 8;
+  a.iter = q.iter.as<int64_t>();
+  a.key0 = (uint32_t)(q.seed & 0xffffffffu);
+  a.key1 = (uint32_t)(q.seed >> 32);
+  return a;
+}
+
+// The swarms' batch parts; fails if a stream lost its data or segmentation.
+int pso_parts(scs_ctx* ctx, std::vector<BatchPart>& parts, std::vector<uint64_t>* gens) {
+  auto& q = ctx->pso;
+  parts.clear();
+  if (gens) gens->clear();
+  for (int s = 0; s < q.S; ++s) {
+    DataStream* d = get_stream(ctx, q.sids[s], true);
+    if (!d) return SCS_ENODATA;
+    parts.push_back({d, (int)q.off[s], (int)(q.off[s + 1] - q.off[s])});
+    if (gens) gens->push_back(d->gen);
+  }
+  return SCS_OK;
+}
+
+// (Re)builds the device stream table and the swarm's own scratch when the
+// data, the segmentation or the path changed since the last build.  Drops a
+// captured graph that refers to the old buffers.
+int pso_refresh(scs_ctx* ctx, cudaStream_t s, std::vector<BatchPart>& parts) {
+  auto& q = ctx->pso;
+  std::vector<uint64_t> gens;
+  int rc = pso_parts(ctx, parts, &gens);
+  if (rc) return rc;
+  if (gens == q.gens && q.table_path == ctx->path && q.table.ptr) return SCS_OK;
+  if (q.exec) {
+    CK(cudaStreamSynchronize(s));
+    cudaGraphExecDestroy(q.exec);
+    q.exec = nullptr;
+    q.graph_iters = 0;
+  }
+  int nct = 0;
+  int64_t etot = 0, htot = 0;
+  std::vector<StreamDesc> t = make_table(parts, &nct, &etot, &htot);
+  CK(cudaStreamSynchronize(s));   // no launch in flight uses the old buffers
+  CK(q.table.reserve(sizeof(StreamDesc) * t.size()));
+  CK(cudaMemcpy(q.table.ptr, t.data(), sizeof(StreamDesc) * t.size(), cudaMemcpyHostToDevice));
+  CK(q.scratch.reserve(batch_scratch_bytes(parts, q.P)));
+  q.gens = gens;
+  q.table_path = ctx->path;
+  return SCS_OK;
+}
+
+// One iteration: evaluate every particle, then the personal / swarm bests
+// and the move.  Only kernel launches and memsets: safe to capture.
+int pso_iteration(scs_ctx* ctx, const std::vector<BatchPart>& parts, cudaStream_t s) {
+  auto& q = ctx->pso;
+  ScratchSource src;
+  src.base = q.scratch.as<unsigned char>();
+  src.cap = q.scratch.bytes;
+  Prepared pr;
+  int rc = prepare_batch(ctx, parts, q.pos.as<double>(), q.P, ctx->path == SCS_MIXED, true, s,
+                         src, pr, q.table.as<StreamDesc>());
+  if (rc) return rc;
+  rc = run_batch(ctx, pr, q.P, q.stat.as<double>(), nullptr, nullptr, s, src);
+  if (rc) return rc;
+  launch_pso_update(pso_args(ctx), s);
+  CKLAUNCH();
+  return SCS_OK;
+}
+
+int pso_check(scs_ctx* ctx) {
+  if (!ctx) return SCS_EINVAL;
+  if (!ctx->pso.made) return fail(ctx, SCS_ENODATA, "no swarm (scs_pso_create)");
+  return bind(ctx);
+}
+
+}  // namespace
+
+extern "C" {
+
+int scs_pso_create(scs_ctx* ctx, int n_swarms, const int* stream_ids,
+                   const int64_t* swarm_offsets, const double* prior_lo,
+                   const double* prior_hi, uint64_t seed, void* cuda_stream) {
+  if (!ctx) return SCS_EINVAL;
+  if (n_swarms < 1 || n_swarms > 1024 || !stream_ids || !swarm_offsets || !prior_lo ||
+      !prior_hi)
+    return fail(ctx, SCS_EINVAL, "bad swarm arguments");
+  if (swarm_offsets[0] != 0) return fail(ctx, SCS_EINVAL, "swarm_offsets[0] must be 0");
+  for (int s = 0; s < n_swarms; ++s)
+    if (swarm_offsets[s + 1] <= swarm_offsets[s])
+      return fail(ctx, SCS_EINVAL, "swarm %d is empty or offsets decrease", s);
+  const int64_t P = swarm_offsets[n_swarms];
+  if (P > (1 << 24)) return fail(ctx, SCS_EINVAL, "P = %lld above 2^24", (long long)P);
+  for (int d = 0; d < 8; ++d) {
+    if (!std::isfinite(prior_lo[d]) || !std::isfinite(prior_hi[d]))
+      return fail(ctx, SCS_EINVAL, "prior bound %d not finite", d);
+    if (d < kPsoDims ? !(prior_hi[d] > prior_lo[d]) : !(prior_hi[d] >= prior_lo[d]))
+      return fail(ctx, SCS_EINVAL, "prior box empty in dimension %d", d);
+  }
+  int rc = bind(ctx);
+  if (rc) return rc;
+  for (int s = 0; s < n_swarms; ++s)
+    if (!get_stream(ctx, stream_ids[s], true)) return SCS_ENODATA;
+  cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : ctx->stream;
+  CK(cudaStreamSynchronize(st));
+  auto& q = ctx->pso;
+  if (q.exec) {
+    cudaGraphExecDestroy(q.exec);
+    q.exec = nullptr;
+  }
+  q.graph_iters = 0;
+  q.made = false;
+  q.P = (int)P;
+  q.S = n_swarms;
+  q.seed = seed;
+  q.sids.assign(stream_ids, stream_ids + n_swarms);
+  q.off.assign(swarm_offsets, swarm_offsets + n_swarms + 1);
+  q.lohi.assign(16, 0.0);
+  for (int d = 0; d < 8; ++d) {
+    q.lohi[d] = prior_lo[d];
+    q.lohi[8 + d] = prior_hi[d];
+  }
+  // default: the first rung of the ladder in Table III (N = 100), eps in the
+  // parameter order of this library (Mc, q, f0, lambda, beta, iota, psi, e0)
+  const double row[kPsoHyper] = {0.5, 0.2, 0.3, 0.1, 0.05, 5e-8, 0.1, 0.1, 0.2, 0.1, 0.1};
+  q.hyper.resize((size_t)kPsoHyper * n_swarms);
+  for (int s = 0; s < n_swarms; ++s)
+    for (int j = 0; j < kPsoHyper; ++j) q.hyper[(size_t)kPsoHyper * s + j] = row[j];
+  q.gens.clear();
+  q.table_path = -1;
+  CK(q.d_off.reserve(sizeof(int64_t) * (n_swarms + 1)));
+  CK(q.pos.reserve(sizeof(double) * 8 * P));
+  CK(q.vel.reserve(sizeof(double) * 8 * P));
+  CK(q.best_pos.reserve(sizeof(double) * 8 * P));
+  CK(q.best_val.reserve(sizeof(double) * P));
+  CK(q.stat.reserve(sizeof(double) * P));
+  CK(q.swarm_pos.reserve(sizeof(double) * 8 * n_swarms));
+  CK(q.swarm_val.reserve(sizeof(double) * n_swarms));
+  CK(q.d_hyper.reserve(sizeof(double) * q.hyper.size()));
+  CK(q.d_lohi.reserve(sizeof(double) * 16));
+  CK(q.iter.reserve(sizeof(int64_t)));
+  if (!q.cap) CK(cudaStreamCreateWithFlags(&q.cap, cudaStreamNonBlocking));
+  CK(cudaMemcpy(q.d_off.ptr, q.off.data(), sizeof(int64_t) * (n_swarms + 1),
+                cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(q.d_hyper.ptr, q.hyper.data(), sizeof(double) * q.hyper.size(),
+                cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(q.d_lohi.ptr, q.lohi.data(), sizeof(double) * 16, cudaMemcpyHostToDevice));
+  CK(cudaMemset(q.stat.ptr, 0, sizeof(double) * P));
+  launch_pso_init(pso_args(ctx), st);
+  CKLAUNCH();
+  CK(cudaStreamSynchronize(st));
+  q.made = true;
+  return SCS_OK;
+}
+
+int scs_pso_set_hyper(scs_ctx* ctx, int swarm, double Omega, double PhiP, double PhiG,
+                      const double* eps, void* cuda_stream) {
+  int rc = pso_check(ctx);
+  if (rc) return rc;
+  auto& q = ctx->pso;
+  if (swarm < -1 || swarm >= q.S) return fail(ctx, SCS_EINVAL, "swarm %d out of range", swarm);
+  if (!eps) return fail(ctx, SCS_EINVAL, "null eps");
+  const double h3[3] = {Omega, PhiP, PhiG};
+  for (double v : h3)
+    if (!std::isfinite(v)) return fail(ctx, SCS_EINVAL, "non-finite swarm coefficient");
+  for (int d = 0; d < 8; ++d)
+    if (!std::isfinite(eps[d]) || eps[d] < 0.0)
+      return fail(ctx, SCS_EINVAL, "eps[%d] = %g must be finite and >= 0", d, eps[d]);
+  cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : ctx->stream;
+  CK(cudaStreamSynchronize(st));   // no running iteration reads the table
+  const int s0 = swarm < 0 ? 0 : swarm, s1 = swarm < 0 ? q.S : swarm + 1;
+  for (int s = s0; s < s1; ++s) {
+    double* h = &q.hyper[(size_t)kPsoHyper * s];
+    h[0] = Omega;
+    h[1] = PhiP;
+    h[2] = PhiG;
+    for (int d = 0; d < 8; ++d) h[3 + d] = eps[d];
+  }
+  CK(cudaMemcpy(q.d_hyper.ptr, q.hyper.data(), sizeof(double) * q.hyper.size(),
+                cudaMemcpyHostToDevice));
+  return SCS_OK;
+}
+
+int scs_pso_run(scs_ctx* ctx, int iters, int use_graph, void* cuda_stream) {
+  int rc = pso_check(ctx);
+  if (rc) return rc;
+  if (iters < 0 || iters > 100000) return fail(ctx, SCS_EINVAL, "iters = %d out of range", iters);
+  if (iters == 0) return SCS_OK;
+  auto& q = ctx->pso;
+  cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : ctx->stream;
+  std::vector<BatchPart> parts;
+  rc = pso_refresh(ctx, st, parts);
+  if (rc) return rc;
+  const bool prof = ctx->prof;
+  ctx->prof = false;   // stage events are not recorded inside swarm iterations
+  ctx->prof_valid = false;
+  if (!use_graph) {
+    for (int i = 0; i < iters && !rc; ++i) rc = pso_iteration(ctx, parts, st);
+    ctx->prof = prof;
+    return rc;
+  }
+  if (q.exec && q.graph_iters != iters) {
+    CK(cudaStreamSynchronize(st));
+    cudaGraphExecDestroy(q.exec);
+    q.exec = nullptr;
+    q.graph_iters = 0;
+  }
+  if (!q.exec) {
+    // load every kernel of an iteration now: nothing is loaded under capture
+    cudaFuncAttributes fa;
+    const void* fk[] = {(const void*)k_setup, (const void*)k_scan64, (const void*)k_chunk_table,
+                        (const void*)k_fill, (const void*)k_bounds, (const void*)k_fixup};
+    for (const void* k : fk) {
+      if (cudaFuncGetAttributes(&fa, k) != cudaSuccess) {
+        ctx->prof = prof;
+        return fail(ctx, SCS_ECUDA, "loading the evaluation kernels failed");
+      }
+    }
+    if (preload_pso()) {
+      ctx->prof = prof;
+      return fail(ctx, SCS_ECUDA, "loading the swarm kernels failed");
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(q.cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      for (int i = 0; i < iters && !rc; ++i) rc = pso_iteration(ctx, parts, q.cap);
+      cudaError_t e2 = cudaStreamEndCapture(q.cap, &g);
+      if (e2 != cudaSuccess && !rc)
+        rc = fail(ctx, SCS_ECUDA, "graph capture: %s", cudaGetErrorString(e2));
+      if (!rc) {
+        e = cudaGraphInstantiate(&q.exec, g, 0);
+        if (e != cudaSuccess) rc = fail(ctx, SCS_ECUDA, "graph instantiate: %s",
+                                        cudaGetErrorString(e));
+      }
+      if (g) cudaGraphDestroy(g);
+    } else {
+      rc = fail(ctx, SCS_ECUDA, "begin capture: %s", cudaGetErrorString(e));
+    }
+    cudaGetLastError();
+    if (rc) {
+      if (q.exec) cudaGraphExecDestroy(q.exec);
+      q.exec = nullptr;
+      ctx->prof = prof;
+      return rc;
+    }
+    q.graph_iters = iters;
+  }
+  ctx->prof = prof;
+  CK(cudaGraphLaunch(q.exec, st));
+  return SCS_OK;
+}
+
+int scs_pso_get(scs_ctx* ctx, double* pos, double* vel, double* best_pos, double* best_val,
+                double* swarm_pos, double* swarm_val, double* stat, int64_t* iter,
+                void* cuda_stream) {
+  int rc = pso_check(ctx);
+  if (rc) return rc;
+  auto& q = ctx->pso;
+  cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : ctx->stream;
+  const size_t P = (size_t)q.P, S = (size_t)q.S;
+  struct { void* dst; const DevBuf* src; size_t bytes; } cp[] = {
+      {pos, &q.pos, 8 * P * sizeof(double)},         {vel, &q.vel, 8 * P * sizeof(double)},
+      {best_pos, &q.best_pos, 8 * P * sizeof(double)}, {best_val, &q.best_val, P * sizeof(double)},
+      {swarm_pos, &q.swarm_pos, 8 * S * sizeof(double)},
+      {swarm_val, &q.swarm_val, S * sizeof(double)},   {stat, &q.stat, P * sizeof(double)},
+      {iter, &q.iter, sizeof(int64_t)}};
+  for (auto& c : cp)
+    if (c.dst) CK(cudaMemcpyAsync(c.dst, c.src->ptr, c.bytes, cudaMemcpyDefault, st));
+  CK(cudaStreamSynchronize(st));
+  return SCS_OK;
+}
+
+int scs_pso_set(scs_ctx* ctx, const double* pos, const double* vel, const double* best_pos,
+                const double* best_val, const double* swarm_pos, const double* swarm_val,
+                int64_t iter, void* cuda_stream) {
+  int rc = pso_check(ctx);
+  if (rc) return rc;
+  if (iter < 0 || iter > 0xffffffffLL) return fail(ctx, SCS_EINVAL, "iteration out of range");
+  auto& q = ctx->pso;
+  cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : ctx->stream;
+  CK(cudaStreamSynchronize(st));
+  const size_t P = (size_t)q.P, S = (size_t)q.S;
+  struct { const void* src; DevBuf* dst; size_t bytes; } cp[] = {
+      {pos, &q.pos, 8 * P * sizeof(double)},         {vel, &q.vel, 8 * P * sizeof(double)},
+      {best_pos, &q.best_pos, 8 * P * sizeof(double)}, {best_val, &q.best_val, P * sizeof(double)},
+      {swarm_pos, &q.swarm_pos, 8 * S * sizeof(double)},
+      {swarm_val, &q.swarm_val, S * sizeof(double)},   {&iter, &q.iter, sizeof(int64_t)}};
+  for (auto& c : cp)
+    if (c.src) CK(cudaMemcpy(c.dst->ptr, c.src, c.bytes, cudaMemcpyDefault));
+  return SCS_OK;
+}
+
+// Checkpoint layout (native-endian): magic "SCSPSO01", int64 P, S, seed,
+// iteration; S + 1 int64 offsets; S int32 stream ids (padded to 8 bytes);
+// 16 prior bounds; S x 11 hyper-parameters; positions, velocities, personal
+// best positions (P x 8 each), personal best values (P), swarm best
+// positions (S x 8) and values (S).
+static size_t pso_blob_bytes(int64_t P, int64_t S) {
+  return 8 + 4 * 8 + 8 * (S + 1) + 8 * ((4 * S + 7) / 8) + 16 * 8 + 8 * kPsoHyper * S +
+         8 * (3 * 8 * P + P + 8 * S + S);
+}
+
+int scs_pso_save(scs_ctx* ctx, void* buf, size_t* len, void* cuda_stream) {
+  int rc = pso_check(ctx);
+  if (rc) return rc;
+  if (!len) return fail(ctx, SCS_EINVAL, "null len");
+  auto& q = ctx->pso;
+  const size_t need = pso_blob_bytes(q.P, q.S);
+  if (!buf) {
+    *len = need;
+    return SCS_OK;
+  }
+  if (*len < need) return fail(ctx, SCS_EINVAL, "buffer of %zu bytes < %zu", *len, need);
+  const size_t P = (size_t)q.P, S = (size_t)q.S;
+  unsigned char* b = (unsigned char*)buf;
+  std::memset(b, 0, need);
+  std::memcpy(b, "SCSPSO01", 8);
+  int64_t* h = (int64_t*)(b + 8);
+  h[0] = q.P;
+  h[1] = q.S;
+  std::memcpy(&h[2], &q.seed, 8);
+  unsigned char* o = b + 8 + 32;
+  std::memcpy(o, q.off.data(), 8 * (S + 1));
+  o += 8 * (S + 1);
+  std::memcpy(o, q.sids.data(), 4 * S);
+  o += 8 * ((4 * S + 7) / 8);
+  std::memcpy(o, q.lohi.data(), 16 * 8);
+  o += 16 * 8;
+  std::memcpy(o, q.hyper.data(), 8 * kPsoHyper * S);
+  o += 8 * kPsoHyper * S;
+  double* pos = (double*)o;
+  double* vel = pos + 8 * P;
+  double* bp = vel + 8 * P;
+  double* bv = bp + 8 * P;
+  double* sp = bv + P;
+  double* sv = sp + 8 * S;
+  int64_t it = 0;
+  rc = scs_pso_get(ctx, pos, vel, bp, bv, sp, sv, nullptr, &it, cuda_stream);
+  if (rc) return rc;
+  h[3] = it;
+  *len = need;
+  return SCS_OK;
+}
+
+int scs_pso_load(scs_ctx* ctx, const void* buf, size_t len, void* cuda_stream) {
+  if (!ctx) return SCS_EINVAL;
+  if (!buf || len < 40 || std::memcmp(buf, "SCSPSO01", 8) != 0)
+    return fail(ctx, SCS_EINVAL, "not a swarm checkpoint");
+  const unsigned char* b = (const unsigned char*)buf;
+  int64_t h[4];
+  std::memcpy(h, b + 8, 32);
+  const int64_t P = h[0], S = h[1];
+  if (S < 1 || S > 1024 || P < 1 || P > (1 << 24) || len != pso_blob_bytes(P, S))
+    return fail(ctx, SCS_EINVAL, "corrupt swarm checkpoint");
+  uint64_t seed;
+  std::memcpy(&seed, &h[2], 8);
+  const unsigned char* o = b + 40;
+  std::vector<int64_t> off(S + 1);
+  std::memcpy(off.data(), o, 8 * (S + 1));
+  o += 8 * (S + 1);
+  std::vector<int> sids(S);
+  std::memcpy(sids.data(), o, 4 * S);
+  o += 8 * ((4 * S + 7) / 8);
+  double lohi[16];
+  std::memcpy(lohi, o, 16 * 8);
+  o += 16 * 8;
+  std::vector<double> hyper(kPsoHyper * S);
+  std::memcpy(hyper.data(), o, 8 * kPsoHyper * S);
+  o += 8 * kPsoHyper * S;
+  if (off[S] != P) return fail(ctx, SCS_EINVAL, "corrupt swarm checkpoint");
+  int rc = scs_pso_create(ctx, (int)S, sids.data(), off.data(), lohi, lohi + 8, seed,
+                          cuda_stream);
+  if (rc) return rc;
+  auto& q = ctx->pso;
+  q.hyper = hyper;
+  CK(cudaMemcpy(q.d_hyper.ptr, q.hyper.data(), sizeof(double) * q.hyper.size(),
+                cudaMemcpyHostToDevice));
+  std::vector<double> arr((3 * 8 * P + P + 8 * S + S));
+  std::memcpy(arr.data(), o, 8 * arr.size());
+  const double* pos = arr.data();
+  const double* vel = pos + 8 * P;
+  const double* bp = vel + 8 * P;
+  const double* bv = bp + 8 * P;
+  const double* sp = bv + P;
+  const double* sv = sp + 8 * S;
+  return scs_pso_set(ctx, pos, vel, bp, bv, sp, sv, h[3], cuda_stream);
 }
 
 }  // extern "C"

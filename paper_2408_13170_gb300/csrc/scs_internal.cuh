@@ -72,6 +72,31 @@ __host__ __device__ inline const int* edges_of(const StreamDesc& d, const int* e
                      : d.width_edges;
 }
 
+// Swarm state on the device (all arrays device memory).  Particles of swarm
+// s are off[s] .. off[s+1]-1.
+constexpr int kPsoDims = 7;      // searched dimensions (e0 stays 0)
+constexpr int kPsoHyper = 11;    // Omega, Phi_P, Phi_G, eps[8] per swarm
+struct PsoArgs {
+  int P, S;
+  const int64_t* off;
+  double* pos;        // P x 8
+  double* vel;        // P x 8
+  double* best_pos;   // P x 8
+  double* best_val;   // P
+  double* swarm_pos;  // S x 8
+  double* swarm_val;  // S
+  const double* stat; // P, the last evaluation
+  const double* hyper;   // S x kPsoHyper
+  const double* lo;   // 8
+  const double* hi;   // 8
+  int64_t* iter;      // iteration counter (RNG counter word)
+  uint32_t key0, key1;
+};
+void launch_pso_init(const PsoArgs& a, cudaStream_t s);
+void launch_pso_update(const PsoArgs& a, cudaStream_t s);
+// loads the swarm kernels (so that a later stream capture loads nothing); 0 on success
+int preload_pso();
+
 void launch_main_mixed(const EvalArgs& a, int grid, cudaStream_t s);
 void launch_main_fp64(const EvalArgs& a, int grid, cudaStream_t s);
 void launch_waveform_fp64(const Part* part, double f_first, double df, int K,

@@ -69,6 +69,17 @@ def lib():
         L.scs_eval_stat_noalloc.restype = I
         L.scs_batch_eval.argtypes = [P, P, P, I, P, P, P]
         L.scs_batch_eval.restype = I
+        U64 = ctypes.c_uint64
+        L.scs_pso_create.argtypes = [P, I, P, P, P, P, U64, P]
+        L.scs_pso_set_hyper.argtypes = [P, I, D, D, D, P, P]
+        L.scs_pso_run.argtypes = [P, I, I, P]
+        L.scs_pso_get.argtypes = [P, P, P, P, P, P, P, P, P, P]
+        L.scs_pso_set.argtypes = [P, P, P, P, P, P, P, I64, P]
+        L.scs_pso_save.argtypes = [P, P, P, P]
+        L.scs_pso_load.argtypes = [P, P, ctypes.c_size_t, P]
+        for f in ("scs_pso_create", "scs_pso_set_hyper", "scs_pso_run", "scs_pso_get",
+                  "scs_pso_set", "scs_pso_save", "scs_pso_load"):
+            getattr(L, f).restype = I
         _lib = L
         return L
 
@@ -179,6 +190,73 @@ def scs_eval_stat_noalloc(ctx, stream_id, params, P, stat, cuda_stream=None):
                                             _stream(cuda_stream)))
 
 
+# Table III of the paper: (Omega, Phi_P, Phi_G) and the minimum velocities per
+# rung N of the segment ladder, with eps re-ordered to this library's parameter
+# order (Mc, q, f0, lambda, beta, iota, psi, e0); the paper's eps for eta is
+# applied to q and its eps for f_low to f0.
+TABLE3_HYPER = {
+    100: (0.5, 0.2, 0.3, (0.1, 0.05, 5e-8, 0.1, 0.1, 0.2, 0.1, 0.1)),
+    50: (0.5, 0.2, 0.4, (0.01, 0.05, 1e-8, 0.01, 0.01, 0.2, 0.1, 0.1)),
+    10: (0.3, 0.2, 0.5, (0.001, 0.05, 1e-8, 0.001, 0.001, 0.01, 0.1, 0.1)),
+    1: (0.72, 1.193, 1.193, (0.0,) * 8),
+}
+
+
+def table3_hyper(N: int):
+    """Table III row of the ladder rung closest to N (ties: the larger N)."""
+    rung = min(sorted(TABLE3_HYPER, reverse=True), key=lambda r: abs(r - N))
+    return TABLE3_HYPER[rung]
+
+
+def scs_pso_create(ctx, stream_ids, swarm_offsets, prior_lo, prior_hi, seed, cuda_stream=None):
+    sids = np.ascontiguousarray(stream_ids, dtype=np.int32)
+    offs = np.ascontiguousarray(swarm_offsets, dtype=np.int64)
+    lo = np.ascontiguousarray(prior_lo, dtype=np.float64)
+    hi = np.ascontiguousarray(prior_hi, dtype=np.float64)
+    _check(ctx, lib().scs_pso_create(ctx, len(sids), _ptr(sids), _ptr(offs), _ptr(lo),
+                                     _ptr(hi), int(seed), _stream(cuda_stream)))
+
+
+def scs_pso_set_hyper(ctx, swarm, Omega, PhiP, PhiG, eps, cuda_stream=None):
+    e = np.ascontiguousarray(eps, dtype=np.float64)
+    _check(ctx, lib().scs_pso_set_hyper(ctx, int(swarm), float(Omega), float(PhiP),
+                                        float(PhiG), _ptr(e), _stream(cuda_stream)))
+
+
+def scs_pso_run(ctx, iters, use_graph=True, cuda_stream=None):
+    _check(ctx, lib().scs_pso_run(ctx, int(iters), 1 if use_graph else 0,
+                                  _stream(cuda_stream)))
+
+
+def scs_pso_get(ctx, pos=None, vel=None, best_pos=None, best_val=None, swarm_pos=None,
+                swarm_val=None, stat=None, cuda_stream=None):
+    it = ctypes.c_int64()
+    _check(ctx, lib().scs_pso_get(ctx, _ptr(pos), _ptr(vel), _ptr(best_pos), _ptr(best_val),
+                                  _ptr(swarm_pos), _ptr(swarm_val), _ptr(stat),
+                                  ctypes.byref(it), _stream(cuda_stream)))
+    return it.value
+
+
+def scs_pso_set(ctx, pos=None, vel=None, best_pos=None, best_val=None, swarm_pos=None,
+                swarm_val=None, iteration=0, cuda_stream=None):
+    _check(ctx, lib().scs_pso_set(ctx, _ptr(pos), _ptr(vel), _ptr(best_pos), _ptr(best_val),
+                                  _ptr(swarm_pos), _ptr(swarm_val), int(iteration),
+                                  _stream(cuda_stream)))
+
+
+def scs_pso_save(ctx, cuda_stream=None) -> bytes:
+    n = ctypes.c_size_t()
+    _check(ctx, lib().scs_pso_save(ctx, None, ctypes.byref(n), _stream(cuda_stream)))
+    buf = ctypes.create_string_buffer(n.value)
+    _check(ctx, lib().scs_pso_save(ctx, buf, ctypes.byref(n), _stream(cuda_stream)))
+    return buf.raw[:n.value]
+
+
+def scs_pso_load(ctx, blob: bytes, cuda_stream=None):
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    _check(ctx, lib().scs_pso_load(ctx, buf, len(blob), _stream(cuda_stream)))
+
+
 def scs_set_profiling(ctx, enable: bool):
     _check(ctx, lib().scs_set_profiling(ctx, 1 if enable else 0))
 
@@ -276,3 +354,37 @@ class Context:
         e = np.empty((P, N + 1), np.int64)
         scs_segment_edges(self.h, stream_id, params, P, e)
         return e
+
+    # --------------------------------------------------------------- swarm
+    def pso_create(self, stream_ids, swarm_sizes, prior_lo, prior_hi, seed):
+        """Swarm s has swarm_sizes[s] particles and searches stream stream_ids[s]."""
+        offs = np.concatenate([[0], np.cumsum(swarm_sizes)]).astype(np.int64)
+        scs_pso_create(self.h, stream_ids, offs, prior_lo, prior_hi, seed)
+        self._pso_P, self._pso_S = int(offs[-1]), len(offs) - 1
+
+    def pso_set_hyper(self, Omega, PhiP, PhiG, eps, swarm=-1):
+        scs_pso_set_hyper(self.h, swarm, Omega, PhiP, PhiG, eps)
+
+    def pso_run(self, iters, use_graph=True):
+        scs_pso_run(self.h, iters, use_graph)
+
+    def pso_get(self):
+        P, S = self._pso_P, self._pso_S
+        st = dict(pos=np.empty((P, 8)), vel=np.empty((P, 8)), best_pos=np.empty((P, 8)),
+                  best_val=np.empty(P), swarm_pos=np.empty((S, 8)), swarm_val=np.empty(S),
+                  stat=np.empty(P))
+        st["iteration"] = scs_pso_get(self.h, **st)
+        return st
+
+    def pso_set(self, state):
+        keys = ("pos", "vel", "best_pos", "best_val", "swarm_pos", "swarm_val")
+        arrs = {k: np.ascontiguousarray(state[k], dtype=np.float64) for k in keys}
+        scs_pso_set(self.h, iteration=state["iteration"], **arrs)
+
+    def pso_save(self) -> bytes:
+        return scs_pso_save(self.h)
+
+    def pso_load(self, blob: bytes):
+        scs_pso_load(self.h, blob)
+        P, S = np.frombuffer(blob, np.int64, 2, 8)
+        self._pso_P, self._pso_S = int(P), int(S)
