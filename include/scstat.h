@@ -226,8 +226,9 @@ int scs_inject(scs_ctx *ctx, int stream_id, const double *theta, double snr,
                double *hh_out);
 
 /* Support and anchor stride of P particles (diagnostics): k_lo[P], k_hi[P]
- * (k_hi < k_lo: empty; both -1: non-physical) and log2 of the anchor
- * stride of the mixed path (may be NULL).  Host or device pointers. */
+ * (k_hi < k_lo: empty; both -1: non-physical) and the mixed path's
+ * strides (may be NULL): bits 0-7 log2 of the phase-anchor stride B, bits
+ * 8-15 log2 of the response sub-span Br.  Host or device pointers. */
 int scs_support(scs_ctx *ctx, int stream_id, const double *params, int64_t P,
                 int64_t *k_lo, int64_t *k_hi, int32_t *log2_stride,
                 void *cuda_stream);
@@ -260,7 +261,7 @@ int scs_last_timings(scs_ctx *ctx, double *ms);
  *   GPU that loads it until the process exits; no cudaMalloc, cudaFree or
  *   allocating library routine is called.  Calls whose scratch would exceed
  *   it are rejected with SCS_EINVAL and a message giving the bytes needed
- *   (roughly 20 + 68 C bytes per particle, C = ceil(K/4096) chunks, plus
+ *   (roughly 20 + 72 C bytes per particle, C = ceil(K/2048) chunks, plus
  *   4 (N+1) + 16 (K/1024 + 2) bytes per particle for equal-SNR^2 segments).
  *   The first call on each device looks up the array's device address
  *   (cudaGetSymbolAddress); make that first call before any stream capture.

@@ -195,11 +195,12 @@ static __device__ __noinline__ void g_node32(const Part* __restrict__ pp, float 
   float dt = x * (tq1 + x * (tq2 + x * tq3));
   float al = al0 + (float)kOmega * dt;
   float sa, ca;
-  sincosf(al, &sa, &ca);
+  sincos_small32(al, &sa, &ca);
   float f = fa32 + x * df32;
   Cx<float> RA, RE;
   response_residual<float>(f, ca, sa, p.Pr32, p.Pi32, p.k32, RA, RE);
-  float amp = powf(f, -7.0f / 6.0f);
+  const float u = rcbrtf(f);
+  const float amp = rsqrtf(f) * u * u;   // f^{-1/2} f^{-2/3}
   *out = make_float4(amp * RA.re, amp * RA.im, amp * RE.re, amp * RE.im);
 }
 

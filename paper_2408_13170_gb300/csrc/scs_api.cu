@@ -1,5 +1,6 @@
 // scs_api.cu -- the C ABI (include/scstat.h): context, data streams,
 // validation, scratch management and the per-call launch sequence.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -63,7 +64,7 @@ bool is_device_ptr(const void* p) {
 // per-call scratch pieces of the evaluation pipeline
 enum Slot {
   kSlotStreams, kSlotPart, kSlotCrange, kSlotNrec, kSlotTotal, kSlotDiff, kSlotCnt,
-  kSlotListOff, kSlotItemOff, kSlotFill, kSlotList, kSlotRec, kSlotCounter, kSlotEdges,
+  kSlotListOff, kSlotItemOff, kSlotFill, kSlotList, kSlotListTmp, kSlotRec, kSlotCounter, kSlotEdges,
   kSlotHs, kSlotCs, kNumSlots
 };
 
@@ -233,7 +234,8 @@ size_t batch_scratch_bytes(const std::vector<BatchPart>& parts, int P) {
                           sizeof(int64_t) * (P + 1), sizeof(int64_t) * 2,
                           sizeof(int) * (nct + 2), sizeof(int) * (nct + 1),
                           sizeof(int) * (nct + 1), sizeof(int) * (nct + 1),
-                          sizeof(int) * (nct + 1), sizeof(int) * bound, sizeof(int) * etot,
+                          sizeof(int) * (nct + 1), sizeof(int) * bound, sizeof(int) * bound,
+                          sizeof(int) * etot,
                           sizeof(double) * htot, sizeof(double) * htot, sizeof(Rec) * bound,
                           sizeof(int) * 2};
   size_t used = 0;
@@ -287,6 +289,7 @@ int prepare_batch(scs_ctx* ctx, const std::vector<BatchPart>& parts, const doubl
   out.item_off = (int*)src.get(kSlotItemOff, sizeof(int) * (nct + 1));
   int* fill = (int*)src.get(kSlotFill, sizeof(int) * (nct + 1));
   out.list = (int*)src.get(kSlotList, sizeof(int) * bound);
+  int* list_tmp = (int*)src.get(kSlotListTmp, sizeof(int) * bound);
   double *Hs = nullptr, *Cs = nullptr;
   if (out.any_snr2 && want_edges) {
     out.edges = (int*)src.get(kSlotEdges, sizeof(int) * etot);
@@ -302,18 +305,22 @@ int prepare_batch(scs_ctx* ctx, const std::vector<BatchPart>& parts, const doubl
                        cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(diff, 0, sizeof(int) * (nct + 2), s));
   CK(cudaMemsetAsync(fill, 0, sizeof(int) * (nct + 1), s));
-  k_setup<<<(P + 127) / 128, 128, 0, s>>>(dparams, P, out.streams, ns, want_stride ? 1 : 0,
+  k_setup<<<(P + 31) / 32, 32, 0, s>>>(dparams, P, out.streams, ns, want_stride ? 1 : 0,
                                           out.part, out.crange, out.nrec, diff);
   CKLAUNCH();
   k_scan64<<<1, 1024, 0, s>>>(out.nrec, P, total);
   CKLAUNCH();
   k_chunk_table<<<1, 1024, 0, s>>>(diff, nct, out.cnt, out.list_off, out.item_off);
   CKLAUNCH();
-  k_fill<<<(P + 127) / 128, 128, 0, s>>>(out.crange, P, out.list_off, fill, out.list);
+  k_fill<<<(P + 31) / 32, 32, 0, s>>>(out.crange, P, out.list_off, fill, list_tmp);
+  CKLAUNCH();
+  k_sort_chunks<<<nct < 1024 ? nct : 1024, 256, 0, s>>>(out.part, out.cnt, out.list_off,
+                                                          list_tmp, out.list, nct);
   CKLAUNCH();
   if (ctx->prof) CK(cudaEventRecord(ctx->ev[1], s));
   if (out.any_snr2 && want_edges) {
-    k_bounds<<<(P * 32 + 127) / 128, 128, 0, s>>>(out.part, P, out.streams, out.edges, Hs, Cs);
+    k_bounds<<<(int)(((int64_t)P * 32 + 127) / 128), 128, 0, s>>>(out.part, 0, P, out.streams,
+                                                                  out.edges, Hs, Cs);
     CKLAUNCH();
   }
   return SCS_OK;
@@ -342,16 +349,18 @@ int run_batch(scs_ctx* ctx, const Prepared& pr, int P, double* dstat, double* ds
   a.item_off = pr.item_off;
   a.rec_off = pr.nrec;
   a.rec = rec;
-  a.item_counter = counter;
   a.seg_x = dsx;
   a.seg_hh = dsh;
   a.err = counter + 1;
+  a.chunk_lo = 0;
+  a.chunk_hi = pr.n_chunks;
+  a.item_counter = counter;
   if (ctx->prof) CK(cudaEventRecord(ctx->ev[2], s));
   if (ctx->path == SCS_MIXED) launch_main_mixed(a, ctx->grid_mixed, s);
   else launch_main_fp64(a, ctx->grid_fp64, s);
   CKLAUNCH();
   if (ctx->prof) CK(cudaEventRecord(ctx->ev[3], s));
-  k_fixup<<<(P + 127) / 128, 128, 0, s>>>(pr.part, pr.crange, pr.nrec, rec, P, pr.streams,
+  k_fixup<<<(P + 31) / 32, 32, 0, s>>>(pr.part, pr.crange, pr.nrec, rec, P, pr.streams,
                                           dstat, dsx, dsh);
   CKLAUNCH();
   if (ctx->prof) {

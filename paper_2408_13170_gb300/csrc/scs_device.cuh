@@ -290,14 +290,58 @@ __device__ inline Cx<T> cadd(Cx<T> a, Cx<T> b) { return Cx<T>{a.re + b.re, a.im 
 template <typename T>
 __device__ inline Cx<T> csub(Cx<T> a, Cx<T> b) { return Cx<T>{a.re - b.re, a.im - b.im}; }
 
+// FP32 sin and cos of a moderate argument (|x| <~ 100): quadrant reduction
+// with pi/2 in two parts, then the Taylor series of sin(r) to r^9 and cos(r)
+// to r^8 on |r| <= pi/4 (truncation below 3e-8, the FP32 rounding level).
+__device__ __forceinline__ void sincos_small32(float x, float* sp, float* cp) {
+  const float kPio2Hi = 1.57079637050628662f;    // nearest float to pi/2
+  const float kPio2Lo = -4.37113900018624e-08f;  // pi/2 - kPio2Hi
+  const float k = rintf(x * 0.636619772367581343f);
+  float r = fmaf(-k, kPio2Hi, x);
+  r = fmaf(-k, kPio2Lo, r);
+  const float r2 = r * r;
+  float ps = 2.75573192239858907e-06f;          //  1/9!
+  ps = fmaf(ps, r2, -1.98412698412698413e-04f); // -1/7!
+  ps = fmaf(ps, r2, 8.33333333333333333e-03f);  //  1/5!
+  ps = fmaf(ps, r2, -1.66666666666666667e-01f); // -1/3!
+  const float s = fmaf(ps * r2, r, r);
+  float pc = 2.48015873015873016e-05f;          //  1/8!
+  pc = fmaf(pc, r2, -1.38888888888888889e-03f); // -1/6!
+  pc = fmaf(pc, r2, 4.16666666666666667e-02f);  //  1/4!
+  pc = fmaf(pc, r2, -0.5f);                     // -1/2!
+  const float c = fmaf(pc, r2, 1.0f);
+  const int q = (int)k & 3;
+  *sp = q == 0 ? s : (q == 1 ? c : (q == 2 ? -s : -c));
+  *cp = q == 0 ? c : (q == 1 ? -s : (q == 2 ? -c : s));
+}
+
 __device__ inline void sc_(double x, double* s, double* c) { sincos_small(x, s, c); }
-__device__ inline void sc_(float x, float* s, float* c) { sincosf(x, s, c); }
+__device__ inline void sc_(float x, float* s, float* c) { sincos_small32(x, s, c); }
 __device__ inline double sin_(double x) {
   double s, c;
   sincos_small(x, &s, &c);
   return s;
 }
-__device__ inline float sin_(float x) { return sinf(x); }
+// sin(x)/x; FP32: its Taylor series to x^16 for |x| < 2 (truncation below
+// 2e-10), else the quotient
+__device__ inline double sinc_(double x) { return x == 0.0 ? 1.0 : sin_(x) / x; }
+__device__ inline float sinc_(float x) {
+  const float x2 = x * x;
+  if (x2 < 4.0f) {
+    float p = 2.81145725434552076e-15f;          //  1/17!
+    p = fmaf(p, x2, -7.64716373181981648e-13f);  // -1/15!
+    p = fmaf(p, x2, 1.60590438368216146e-10f);   //  1/13!
+    p = fmaf(p, x2, -2.50521083854417188e-08f);  // -1/11!
+    p = fmaf(p, x2, 2.75573192239858907e-06f);   //  1/9!
+    p = fmaf(p, x2, -1.98412698412698413e-04f);  // -1/7!
+    p = fmaf(p, x2, 8.33333333333333333e-03f);   //  1/5!
+    p = fmaf(p, x2, -1.66666666666666667e-01f);  // -1/3!
+    return fmaf(p, x2, 1.0f);
+  }
+  float s, c;
+  sincos_small32(x, &s, &c);
+  return s / x;
+}
 
 // ca, sa: cos/sin of the orbital angle alpha = Omega t (any precision T);
 // f in Hz; P: polarisation tensor (re/im of xx,yy,zz,xy,xz,yz); k: direction.
@@ -342,8 +386,8 @@ __device__ inline void response_residual(T f, T ca, T sa, const T* Pr, const T* 
     Cx<T> ph{cph, sph};
     // s -> r uses n, r -> s uses -n
     T xf = pfl * ((T)1 - kn), xb = pfl * ((T)1 + kn);
-    T sincf = xf == (T)0 ? (T)1 : sin_(xf) / xf;
-    T sincb = xb == (T)0 ? (T)1 : sin_(xb) / xb;
+    T sincf = sinc_(xf);
+    T sincb = sinc_(xb);
     Cx<T> base = cmul(ph, nPn);
     // -i * pfl * sinc * base
     G[s][r] = Cx<T>{pfl * sincf * base.im, -pfl * sincf * base.re};

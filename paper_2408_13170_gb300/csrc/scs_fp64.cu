@@ -18,10 +18,10 @@ struct Acc64 {
 
 __global__ void __launch_bounds__(128) k_main_fp64(EvalArgs a) {
   const int lane = threadIdx.x & 31;
-  const int total = a.item_off[a.n_chunks];
+  const int first = a.item_off[a.chunk_lo], total = a.item_off[a.chunk_hi];
   for (;;) {
     int item = 0;
-    if (lane == 0) item = atomicAdd(a.item_counter, 1);
+    if (lane == 0) item = first + atomicAdd(a.item_counter, 1);
     item = __shfl_sync(kFull, item, 0);
     if (item >= total) break;
     const int cg = find_item_chunk(a.item_off, a.n_chunks, item);

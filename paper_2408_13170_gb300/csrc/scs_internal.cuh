@@ -1,5 +1,6 @@
 // scs_internal.cuh -- structures shared by the host code and the kernels.
 #pragma once
+#include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -18,6 +19,10 @@ struct Rec {
   double zr_t, zi_t, hh_t;
   double ups;
 };
+// the fix-up stages records as 8-byte words: indices in word 0, then doubles
+static_assert(sizeof(Rec) == 64 && offsetof(Rec, n_tail) == 4 && offsetof(Rec, zr_h) == 8 &&
+                  offsetof(Rec, ups) == 56,
+              "record layout");
 
 // One data stream of an evaluation call.  A call may batch several streams
 // (different grids, segment counts and segmentations); its particles are
@@ -56,9 +61,10 @@ struct EvalArgs {
   const int* list_off;
   const int* list;
   const int* item_off;   // n_chunks + 1 entries
+  int chunk_lo, chunk_hi; // this launch takes the items of chunks [chunk_lo, chunk_hi)
   const int64_t* rec_off;
   Rec* rec;
-  int* item_counter;
+  int* item_counter;      // this launch's counter (starts at 0)
   // per-segment outputs (single-stream calls only; NULL otherwise)
   double* seg_x;
   double* seg_hh;

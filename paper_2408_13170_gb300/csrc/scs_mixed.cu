@@ -33,7 +33,7 @@ __device__ __forceinline__ float kval(const Kahan& k) { return k.s - k.c; }
 // per-lane state of one work item (kept in registers)
 struct Lane {
   int kb, ke;
-  int n_cur, e_next;
+  int n_cur, e_next, e_after;   // segment, its end, the end after it (prefetched)
   int next_phase, next_resp, phase_k;
   int log2B, log2Br;
   bool act, head, fresh;
@@ -80,8 +80,18 @@ __device__ __forceinline__ void close_segment(Lane& L, const ItemStream& a, doub
   L.szi = Kahan{0.f, 0.f};
   L.shh = Kahan{0.f, 0.f};
   L.bzr = L.bzi = L.bhh = 0.f;
-  L.n_cur = advance_segment(L.e, a.N, L.n_cur, k);
-  L.e_next = __ldg(L.e + L.n_cur + 1);
+  // the next end is already in a register; only empty segments (rare) need
+  // the edge table now, and the load of the end after it is not waited for
+  // until the next close
+  int n = L.n_cur + 1;
+  int en = L.e_after;
+  if (en <= k) {
+    n = advance_segment(L.e, a.N, n, k);
+    en = __ldg(L.e + n + 1);
+  }
+  L.n_cur = n;
+  L.e_next = en;
+  L.e_after = n + 2 <= a.N ? __ldg(L.e + n + 2) : kNoEdge;
 }
 
 // nb bins from k0, each lane masked to its own [kb, ke) (a single loop body:
@@ -130,10 +140,10 @@ __device__ __forceinline__ void run_block(Lane& L, const ItemStream& a, double z
 
 __global__ void __launch_bounds__(128, 4) k_main_mixed(EvalArgs a) {
   const int lane = threadIdx.x & 31;
-  const int total = a.item_off[a.n_chunks];
+  const int first = a.item_off[a.chunk_lo], total = a.item_off[a.chunk_hi];
   for (;;) {
     int item = 0;
-    if (lane == 0) item = atomicAdd(a.item_counter, 1);
+    if (lane == 0) item = first + atomicAdd(a.item_counter, 1);
     item = __shfl_sync(kFull, item, 0);
     if (item >= total) break;
     const int cg = find_item_chunk(a.item_off, a.n_chunks, item);
@@ -178,6 +188,7 @@ __global__ void __launch_bounds__(128, 4) k_main_mixed(EvalArgs a) {
     L.e = L.act ? edges_of(sd, a.edges_all, L.p) : sd.width_edges;
     L.n_cur = L.act ? segment_of(L.e, is.N, L.kb) : 0;
     L.e_next = L.act ? __ldg(L.e + L.n_cur + 1) : kNoEdge;
+    L.e_after = L.act && L.n_cur + 2 <= is.N ? __ldg(L.e + L.n_cur + 2) : kNoEdge;
     L.head = true;
     L.fresh = true;
     L.szr = L.szi = L.shh = L.ups = Kahan{0.f, 0.f};

@@ -120,6 +120,9 @@ __device__ void choose_strides(Part& p, double f_first, double df) {
 
 // One thread per particle: derive, find the support on its stream's grid,
 // choose the strides, count the (global) chunks the particle touches.
+// Launched as one-warp blocks: the work is FP64 and a warp of particles
+// keeps one SM's FP64 units busy, so the blocks spread over as many SMs as
+// there are warps of particles.
 __global__ void k_setup(const double* params, int P, const StreamDesc* streams, int n_streams,
                         int want_stride, Part* part, int2* crange, int64_t* nrec, int* diff) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -219,13 +222,64 @@ __global__ void k_chunk_table(const int* diff, int n_chunks, int* cnt, int* list
   }
 }
 
+// Chunk lists: every particle appends itself to the list of each chunk it
+// touches.  The lanes of a warp walk the chunks together and take their
+// slots with one atomic per warp and chunk (the order within a list is
+// arbitrary; the lists are sorted afterwards).
 __global__ void k_fill(const int2* crange, int P, const int* list_off, int* fill, int* list) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= P) return;
-  int2 cr = crange[i];
-  for (int c = cr.x; c <= cr.y; ++c) {
-    int pos = atomicAdd(fill + c, 1);
-    list[list_off[c] + pos] = i;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  int2 cr = i < P ? crange[i] : make_int2(0, -1);
+  const int c0 = warp_min(cr.x <= cr.y ? cr.x : 0x7fffffff);
+  const int c1 = warp_max(cr.x <= cr.y ? cr.y : -1);
+  const unsigned lt = (1u << lane) - 1u;
+  for (int c = c0; c <= c1; ++c) {
+    const bool in = cr.x <= c && c <= cr.y;
+    const unsigned m = __ballot_sync(kFull, in);
+    if (!m) continue;
+    const int leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(fill + c, __popc(m));
+    base = __shfl_sync(kFull, base, leader);
+    if (in) list[list_off[c] + base + __popc(m & lt)] = i;
+  }
+}
+
+// Order each chunk's particle list by the mixed path's strides (response
+// sub-span first, then phase stride, both descending), so that the 32 lanes
+// of a work item share their span boundaries: a warp then runs blocks as
+// wide as its particles allow and calls the node and anchor code together
+// instead of once per lane.  Counting sort per chunk, one block per chunk;
+// the order within a key is arbitrary (results do not depend on it).
+__global__ void k_sort_chunks(const Part* part, const int* cnt, const int* list_off,
+                              const int* list_in, int* list_out, int n_chunks) {
+  constexpr int kKeys = (kMaxLog2B + 1) * (kMaxLog2B + 1);
+  __shared__ int hist[kKeys];
+  auto key_of = [&](int p) {
+    const Part& q = part[p];
+    int br = min(max(q.log2Br, 0), kMaxLog2B), b = min(max(q.log2B, 0), kMaxLog2B);
+    return (kMaxLog2B - br) * (kMaxLog2B + 1) + (kMaxLog2B - b);
+  };
+  for (int c = blockIdx.x; c < n_chunks; c += gridDim.x) {
+    const int n = cnt[c], off = list_off[c];
+    for (int i = threadIdx.x; i < kKeys; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&hist[key_of(list_in[off + i])], 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int run = 0;
+      for (int k = 0; k < kKeys; ++k) {
+        int h = hist[k];
+        hist[k] = run;
+        run += h;
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const int p = list_in[off + i];
+      list_out[off + atomicAdd(&hist[key_of(p)], 1)] = p;
+    }
+    __syncthreads();
   }
 }
 
@@ -235,11 +289,11 @@ __global__ void k_fill(const int2* crange, int P, const int* list_off, int* fill
 // target c_n = n C/N; kappa_n by linear inverse interpolation; segment n
 // starts at bin ceil(kappa_n).  The double operations follow that order
 // explicitly (no contraction) so that the rounding is the definition's.
-__global__ void k_bounds(const Part* part, int P, const StreamDesc* streams, int* edges_all,
-                         double* Hs, double* Cs) {
-  int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+__global__ void k_bounds(const Part* part, int p_lo, int p_hi, const StreamDesc* streams,
+                         int* edges_all, double* Hs, double* Cs) {
+  int gw = p_lo + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   int lane = threadIdx.x & 31;
-  if (gw >= P) return;
+  if (gw >= p_hi) return;
   const Part& p = part[gw];
   const StreamDesc& sd = streams[p.sid];
   if (sd.mode != 1) return;   // equal-width streams share a fixed table
@@ -272,15 +326,21 @@ __global__ void k_bounds(const Part* part, int P, const StreamDesc* streams, int
     H[a] = __dadd_rn(__dmul_rn(w.x, amp2 * pA), __dmul_rn(w.y, amp2 * pE));
   }
   __syncwarp();
+  // trapezoid terms (k_a - k_{a-1}) (H_{a-1} + H_a) / 2 in parallel (halving
+  // is exact, so * 0.5 rounds as / 2 does), then the running sum in order
+  for (int a = 1 + lane; a < nanch; a += 32) {
+    int ka = min(p.k_lo + a * kSnr2Stride, p.k_hi);
+    int kp = p.k_lo + (a - 1) * kSnr2Stride;
+    double s2 = __dadd_rn(H[a - 1], H[a]);
+    C[a] = __dmul_rn(__dmul_rn((double)(ka - kp), s2), 0.5);
+  }
+  __syncwarp();
   if (lane == 0) {
+    double run = 0.0;
     C[0] = 0.0;
-    int kprev = p.k_lo;
     for (int a = 1; a < nanch; ++a) {
-      int ka = min(p.k_lo + a * kSnr2Stride, p.k_hi);
-      double s2 = __dadd_rn(H[a - 1], H[a]);
-      double tr = __ddiv_rn(__dmul_rn((double)(ka - kprev), s2), 2.0);
-      C[a] = __dadd_rn(C[a - 1], tr);
-      kprev = ka;
+      run = __dadd_rn(run, C[a]);
+      C[a] = run;
     }
   }
   __syncwarp();
@@ -317,11 +377,17 @@ __global__ void k_bounds(const Part* part, int P, const StreamDesc* streams, int
   }
 }
 
-// Merge the (particle, chunk) records into Upsilon_N (Sec. II.B).
-__global__ void k_fixup(const Part* part, const int2* crange, const int64_t* rec_off,
-                        const Rec* rec, int P, const StreamDesc* streams, double* stat,
-                        double* seg_x, double* seg_hh) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+// Merge the (particle, chunk) records into Upsilon_N (Sec. II.B), one
+// thread per particle in chunk order.  Records are read kBatch at a time
+// as 16-byte vectors, all loads of a batch issued before any is used, so a
+// thread keeps several records in flight.  Launched as one-warp blocks.
+__global__ void __launch_bounds__(32) k_fixup(const Part* part, const int2* crange,
+                                              const int64_t* rec_off, const Rec* rec, int P,
+                                              const StreamDesc* streams, double* stat,
+                                              double* seg_x, double* seg_hh) {
+  constexpr int kBatch = 4;
+  constexpr int kVec = sizeof(Rec) / 16;   // 16-byte vectors per record
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= P) return;
   const Part& p = part[i];
   if (p.status == kInvalid) {
@@ -333,7 +399,8 @@ __global__ void k_fixup(const Part* part, const int2* crange, const int64_t* rec
     return;
   }
   const int N = streams[p.sid].N;
-  int2 cr = crange[i];
+  const int2 cr = crange[i];
+  const int nrec = cr.y - cr.x + 1;
   double ups = 0.0;
   int n_run = -1;
   double zr = 0.0, zi = 0.0, hh = 0.0;
@@ -346,22 +413,37 @@ __global__ void k_fixup(const Part* part, const int2* crange, const int64_t* rec
       seg_hh[(int64_t)i * N + n_run] = hh;
     }
   };
-  const Rec* r = rec + rec_off[i];
-  for (int c = cr.x; c <= cr.y; ++c, ++r) {
-    ups += r->ups;
-    if (r->n_head >= 0) {
-      if (r->n_head == n_run) {
-        zr += r->zr_h; zi += r->zi_h; hh += r->hh_h;
-      } else {
-        close();
-        n_run = r->n_head;
-        zr = r->zr_h; zi = r->zi_h; hh = r->hh_h;
+  const ulonglong2* src = reinterpret_cast<const ulonglong2*>(rec + rec_off[i]);
+  for (int c = 0; c < nrec; c += kBatch) {
+    ulonglong2 v[kBatch][kVec];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u)
+#pragma unroll
+      for (int q = 0; q < kVec; ++q)
+        v[u][q] = c + u < nrec ? __ldg(src + (int64_t)(c + u) * kVec + q) : make_ulonglong2(0, 0);
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      if (c + u >= nrec) break;
+      const int n_head = (int)(unsigned)(v[u][0].x & 0xffffffffu);
+      const int n_tail = (int)(unsigned)(v[u][0].x >> 32);
+      const double zrh = __longlong_as_double(v[u][0].y), zih = __longlong_as_double(v[u][1].x);
+      const double hhh = __longlong_as_double(v[u][1].y), zrt = __longlong_as_double(v[u][2].x);
+      const double zit = __longlong_as_double(v[u][2].y), hht = __longlong_as_double(v[u][3].x);
+      ups += __longlong_as_double(v[u][3].y);
+      if (n_head >= 0) {
+        if (n_head == n_run) {
+          zr += zrh; zi += zih; hh += hhh;
+        } else {
+          close();
+          n_run = n_head;
+          zr = zrh; zi = zih; hh = hhh;
+        }
       }
-    }
-    if (r->n_tail >= 0) {
-      close();
-      n_run = r->n_tail;
-      zr = r->zr_t; zi = r->zi_t; hh = r->hh_t;
+      if (n_tail >= 0) {
+        close();
+        n_run = n_tail;
+        zr = zrt; zi = zit; hh = hht;
+      }
     }
   }
   close();
@@ -462,7 +544,7 @@ __global__ void k_support_out(const Part* part, int P, int64_t* klo, int64_t* kh
     klo[i] = p.k_lo;
     khi[i] = p.k_hi;
   }
-  if (l2b) l2b[i] = p.log2B;
+  if (l2b) l2b[i] = p.log2B | (p.log2Br << 8);
 }
 
 __global__ void k_edges_out(const Part* part, const StreamDesc* streams, const int* edges_all,

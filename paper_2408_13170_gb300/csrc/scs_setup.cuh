@@ -10,8 +10,10 @@ __global__ void k_scan64(int64_t* v, int64_t n, int64_t* total);
 __global__ void k_chunk_table(const int* diff, int n_chunks, int* cnt, int* list_off,
                               int* item_off);
 __global__ void k_fill(const int2* crange, int P, const int* list_off, int* fill, int* list);
-__global__ void k_bounds(const Part* part, int P, const StreamDesc* streams, int* edges_all,
-                         double* Hs, double* Cs);
+__global__ void k_sort_chunks(const Part* part, const int* cnt, const int* list_off,
+                              const int* list_in, int* list_out, int n_chunks);
+__global__ void k_bounds(const Part* part, int p_lo, int p_hi, const StreamDesc* streams,
+                         int* edges_all, double* Hs, double* Cs);
 __global__ void k_fixup(const Part* part, const int2* crange, const int64_t* rec_off,
                         const Rec* rec, int P, const StreamDesc* streams, double* stat,
                         double* seg_x, double* seg_hh);

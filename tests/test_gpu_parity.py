@@ -254,3 +254,29 @@ def test_batch_eval_matches_single_streams(scstat):
         ctx.set_path(scstat.SCS_MIXED)
         b = ctx.batch_eval([2, 0, 2], [ths[2][:5], np.zeros((0, 8)), ths[2][5:]])
         np.testing.assert_array_equal(np.concatenate([b[0], b[2]]), ctx.eval(2, ths[2]))
+
+
+def test_large_call_matches_small_calls(scstat, small):
+    """A particle's result does not depend on the other particles of its
+    call (its work-item grouping, chunk-list order and batch): a large
+    equal-SNR^2 call, small calls, the no-allocation entry point and a
+    batch split all give the same bits."""
+    import torch
+    d, th, ctx = small
+    rng = np.random.default_rng(17)
+    big = np.vstack([th, particles(rng, 2600 - len(th))])
+    ctx.set_path(scstat.SCS_MIXED)
+    ctx.set_segments(0, 64, oracle.EQUAL_SNR2)
+    stat = ctx.eval(0, big)
+    pieces = np.concatenate([ctx.eval(0, big[i:i + 700]) for i in range(0, len(big), 700)])
+    np.testing.assert_array_equal(stat, pieces)
+    dev = torch.tensor(big, device="cuda")
+    out = torch.empty(len(big), dtype=torch.float64, device="cuda")
+    scstat.scs_eval_stat_noalloc(ctx.h, 0, dev, len(big), out)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out.cpu().numpy(), stat)
+    b = ctx.batch_eval([0, 0], [big[:1300], big[1300:]])
+    np.testing.assert_array_equal(np.concatenate(b), stat)
+    sample = np.arange(0, len(big), 97)
+    ref = oracle.evaluate(d, big[sample], 64, mode=oracle.EQUAL_SNR2)
+    assert rel_err(stat[sample], ref) <= TOL32
