@@ -305,7 +305,7 @@ int prepare_batch(scs_ctx* ctx, const std::vector<BatchPart>& parts, const doubl
                        cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(diff, 0, sizeof(int) * (nct + 2), s));
   CK(cudaMemsetAsync(fill, 0, sizeof(int) * (nct + 1), s));
-  k_setup<<<(P + 31) / 32, 32, 0, s>>>(dparams, P, out.streams, ns, want_stride ? 1 : 0,
+  k_setup<<<(P + 31) / 32, kSetupThreads, 0, s>>>(dparams, P, out.streams, ns, want_stride ? 1 : 0,
                                           out.part, out.crange, out.nrec, diff);
   CKLAUNCH();
   k_scan64<<<1, 1024, 0, s>>>(out.nrec, P, total);

@@ -27,56 +27,50 @@ constexpr double kTolG = 3e-7;       // relative to |G_A| + |G_E|
 
 __device__ inline int span_start(int k, int B) { return (k / B) * B; }
 
-__device__ bool phase_ok(const Part& p, int B, double f_first, double df) {
-  const int starts[3] = {span_start(p.k_lo, B), span_start((p.k_lo + p.k_hi) / 2, B),
-                         span_start(p.k_hi, B)};
-  for (int s = 0; s < 3; ++s) {
-    int ka = starts[s];
-    int jlo = max(0, p.k_lo - ka), jhi = min(B - 1, p.k_hi - ka);
-    if (jhi < jlo) continue;
-    PhaseAnchor an;
-    phase_anchor(p, ka, f_first, df, an);
-    const int js[3] = {B / 4, (3 * B) / 4, B - 1};
-    for (int t = 0; t < 3; ++t) {
-      int j = min(max(js[t], jlo), jhi);
-      double tt;
-      double exact = phase_turns_fp64(p, grid_freq_dd(f_first, df, ka + j), tt);
-      double got = (double)(int64_t)phase_anchor_at(an, j) * 5.421010862427522e-20;
-      double d = got - exact;
-      d -= rint(d);
-      if (!(fabs(d) <= kTolPhase)) return false;
-    }
-  }
-  return true;
+// Check (s, t) of stride B: span s in {first, middle, last} of the
+// support, offset t in {B/4, 3B/4, B-1} (clamped to the support).  A span
+// outside the support passes.  Phase: the kernel's own fixed-point
+// polynomial against the exact (double-double) phase.
+__device__ bool phase_check(const Part& p, int B, int s, int t, double f_first, double df) {
+  const int k = s == 0 ? p.k_lo : (s == 1 ? (p.k_lo + p.k_hi) / 2 : p.k_hi);
+  const int ka = span_start(k, B);
+  const int jlo = max(0, p.k_lo - ka), jhi = min(B - 1, p.k_hi - ka);
+  if (jhi < jlo) return true;
+  PhaseAnchor an;
+  phase_anchor(p, ka, f_first, df, an);
+  const int jt = t == 0 ? B / 4 : (t == 1 ? (3 * B) / 4 : B - 1);
+  const int j = min(max(jt, jlo), jhi);
+  double tt;
+  double exact = phase_turns_fp64(p, grid_freq_dd(f_first, df, ka + j), tt);
+  double got = (double)(int64_t)phase_anchor_at(an, j) * 5.421010862427522e-20;
+  double d = got - exact;
+  d -= rint(d);
+  return fabs(d) <= kTolPhase;
 }
 
-__device__ bool resp_ok(const Part& p, int Br, double f_first, double df) {
-  const int starts[3] = {span_start(p.k_lo, Br), span_start((p.k_lo + p.k_hi) / 2, Br),
-                         span_start(p.k_hi, Br)};
+// Response: the quadratic through the exact FP64 nodes at 0, Br/2, Br of the
+// span against the exact G at the offset.
+__device__ bool resp_check(const Part& p, int Br, int s, int t, double f_first, double df) {
+  const int k = s == 0 ? p.k_lo : (s == 1 ? (p.k_lo + p.k_hi) / 2 : p.k_hi);
+  const int ka = span_start(k, Br);
+  const int jlo = max(0, p.k_lo - ka), jhi = min(Br - 1, p.k_hi - ka);
+  if (jhi < jlo) return true;
   const double h = 0.5 * (double)Br;
-  for (int s = 0; s < 3; ++s) {
-    int ka = starts[s];
-    int jlo = max(0, p.k_lo - ka), jhi = min(Br - 1, p.k_hi - ka);
-    if (jhi < jlo) continue;
-    double fa = f_first + (double)ka * df;
-    double y0[4], y1[4], y2[4];
-    g_exact64(p, fa, df, 0.0, y0);
-    g_exact64(p, fa, df, h, y1);
-    g_exact64(p, fa, df, 2.0 * h, y2);
-    const int js[3] = {Br / 4, (3 * Br) / 4, Br - 1};
-    for (int t = 0; t < 3; ++t) {
-      double x = (double)min(max(js[t], jlo), jhi);
-      double g[4];
-      g_exact64(p, fa, df, x, g);
-      double l0 = (x - h) * (x - 2.0 * h) / (2.0 * h * h);
-      double l1 = -x * (x - 2.0 * h) / (h * h);
-      double l2 = x * (x - h) / (2.0 * h * h);
-      double err = 0.0, mag = hypot(g[0], g[1]) + hypot(g[2], g[3]);
-      for (int c = 0; c < 4; ++c) err += fabs(l0 * y0[c] + l1 * y1[c] + l2 * y2[c] - g[c]);
-      if (!(err <= kTolG * mag)) return false;
-    }
-  }
-  return true;
+  double fa = f_first + (double)ka * df;
+  double y0[4], y1[4], y2[4];
+  g_exact64(p, fa, df, 0.0, y0);
+  g_exact64(p, fa, df, h, y1);
+  g_exact64(p, fa, df, 2.0 * h, y2);
+  const int jt = t == 0 ? Br / 4 : (t == 1 ? (3 * Br) / 4 : Br - 1);
+  double x = (double)min(max(jt, jlo), jhi);
+  double g[4];
+  g_exact64(p, fa, df, x, g);
+  double l0 = (x - h) * (x - 2.0 * h) / (2.0 * h * h);
+  double l1 = -x * (x - 2.0 * h) / (h * h);
+  double l2 = x * (x - h) / (2.0 * h * h);
+  double err = 0.0, mag = hypot(g[0], g[1]) + hypot(g[2], g[3]);
+  for (int c = 0; c < 4; ++c) err += fabs(l0 * y0[c] + l1 * y1[c] + l2 * y2[c] - g[c]);
+  return err <= kTolG * mag;
 }
 
 __device__ int log2_floor_clamp(double x) {
@@ -85,12 +79,14 @@ __device__ int log2_floor_clamp(double x) {
   return l;
 }
 
-__device__ void choose_strides(Part& p, double f_first, double df) {
+// Analytic starting strides at f_lo (where the derivatives are largest):
+// the 7th bin-derivative of the PN phase and the Doppler remainder
+// f R (Omega dt/dk B)^7 / 7! bound the phase stride; the response rate
+// ~ 4 Omega dt/dk per bin (orbital harmonics of the residual response)
+// bounds the response sub-span.
+__device__ void stride_estimates(const Part& p, double f_first, double df, int* l0, int* lr_cap) {
   double flo = f_first + (double)p.k_lo * df;
   double fhi = f_first + (double)p.k_hi * df;
-  // analytic starting points at f_lo: 7th bin-derivative of the PN phase and
-  // the Doppler remainder f R (Omega dt/dk B)^7 / 7!, and the response
-  // rate ~ 4 Omega dt/dk per bin (orbital harmonics of the residual response)
   double rdf = df / flo, u = rcbrt(flo), u2 = u * u;
   double upow[4] = {u2 * u2 * u, u2 * u, u2, u};
   double d7 = 0.0, T1 = 0.0;
@@ -107,42 +103,104 @@ __device__ void choose_strides(Part& p, double f_first, double df) {
   double wdop = kOmega * fabs(T1);
   double Bdop = pow(5040.0 * 0.5 * kTolPhase / (fhi * p.Rcb + 1e-30), 1.0 / 7.0) /
                 fmax(wdop, 1e-300);
-  int l = log2_floor_clamp(fmin(fmin(Bpn, Bdop), (double)kChunk));
-  while (l > 0 && !phase_ok(p, 1 << l, f_first, df)) --l;
-  double Br = 0.033 / fmax(4.0 * wdop, 1e-12);
-  int lr = min(l, log2_floor_clamp(Br));
-  while (lr > 0 && !resp_ok(p, 1 << lr, f_first, df)) --lr;
-  p.log2B = l;
-  p.log2Br = lr;
+  *l0 = log2_floor_clamp(fmin(fmin(Bpn, Bdop), (double)kChunk));
+  *lr_cap = log2_floor_clamp(0.033 / fmax(4.0 * wdop, 1e-12));
 }
 
 }  // namespace
 
-// One thread per particle: derive, find the support on its stream's grid,
-// choose the strides, count the (global) chunks the particle touches.
-// Launched as one-warp blocks: the work is FP64 and a warp of particles
-// keeps one SM's FP64 units busy, so the blocks spread over as many SMs as
-// there are warps of particles.
-__global__ void k_setup(const double* params, int P, const StreamDesc* streams, int n_streams,
-                        int want_stride, Part* part, int2* crange, int64_t* nrec, int* diff) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= P) return;
-  const int sid = stream_of_particle(streams, n_streams, i);
-  const StreamDesc& d = streams[sid];
-  Part p;
-  part_init(p, params + 8 * (int64_t)i);
-  part_support(p, d.f_first, d.df, d.K, d.T_obs);
-  p.sid = sid;
-  int2 cr = make_int2(0, -1);
-  if (p.status == kOk) {
-    if (want_stride) choose_strides(p, d.f_first, d.df);
-    cr = make_int2(d.chunk_base + chunk_of(p.k_lo), d.chunk_base + chunk_of(p.k_hi));
-    atomicAdd(diff + cr.x, 1);
-    atomicAdd(diff + cr.y + 1, -1);
+// Particle set-up, 32 particles per block of 9 warps.  Warp 0 derives each
+// particle (one lane each), finds its support on its stream's grid and the
+// analytic stride estimates.  The strides are then searched downwards from
+// the estimates: the largest power of two B <= kChunk whose nine checks
+// (3 spans x 3 offsets) all pass, then the largest Br <= B likewise.  The
+// nine checks of a candidate run at once, one per warp (the FP64 work is
+// spread over the SM's four schedulers instead of queueing on one), and a
+// candidate is dropped for the next one below as soon as any check fails:
+// the strides are those a one-candidate-at-a-time search would choose.
+// Warp 0 then counts the (global) chunks each particle touches.
+__global__ void __launch_bounds__(kSetupThreads) k_setup(const double* params, int P,
+                                                         const StreamDesc* streams,
+                                                         int n_streams, int want_stride,
+                                                         Part* part, int2* crange,
+                                                         int64_t* nrec, int* diff) {
+  __shared__ Part sp[32];
+  __shared__ int s_l[32], s_lim[32];
+  __shared__ unsigned s_fail[32];
+  __shared__ bool s_done[32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * 32 + lane;
+  const StreamDesc* d = nullptr;
+  if (warp == 0) {
+    Part p;
+    p.status = kInvalid;
+    p.k_lo = 0;
+    p.k_hi = -1;
+    if (i < P) {
+      const int sid = stream_of_particle(streams, n_streams, i);
+      d = streams + sid;
+      part_init(p, params + 8 * (int64_t)i);
+      part_support(p, d->f_first, d->df, d->K, d->T_obs);
+      p.sid = sid;
+    }
+    int l0 = 0, lr_cap = 0;
+    if (i < P && p.status == kOk && want_stride) stride_estimates(p, d->f_first, d->df, &l0, &lr_cap);
+    sp[lane] = p;
+    s_l[lane] = l0;
+    s_lim[lane] = lr_cap;
   }
-  part[i] = p;
-  crange[i] = cr;
-  nrec[i] = cr.y - cr.x + 1;
+  __syncthreads();
+  if (want_stride) {
+    const Part& p = sp[lane];
+    const bool mine = i < P && p.status == kOk;
+    const double f_first = mine ? streams[p.sid].f_first : 0.0;
+    const double df = mine ? streams[p.sid].df : 0.0;
+    for (int pass = 0; pass < 2; ++pass) {   // 0: phase stride, 1: response sub-span
+      if (warp == 0) s_done[lane] = !(mine && s_l[lane] > 0);   // 2^0 needs no check
+      for (;;) {
+        if (warp == 0) s_fail[lane] = 0u;
+        __syncthreads();
+        const int l = s_l[lane];
+        if (!s_done[lane]) {
+          const bool ok = pass == 0 ? phase_check(p, 1 << l, warp / 3, warp % 3, f_first, df)
+                                    : resp_check(p, 1 << l, warp / 3, warp % 3, f_first, df);
+          if (!ok) atomicOr(&s_fail[lane], 1u << warp);
+        }
+        __syncthreads();
+        bool again = false;
+        if (warp == 0 && !s_done[lane]) {
+          if (s_fail[lane] == 0u) {
+            s_done[lane] = true;
+          } else {
+            s_l[lane] = l - 1;
+            s_done[lane] = l - 1 == 0;
+            again = l - 1 > 0;
+          }
+        }
+        if (!__syncthreads_or(again)) break;
+      }
+      if (warp == 0 && pass == 0) {
+        // the phase stride found; the response search starts at min(B, estimate)
+        sp[lane].log2B = s_l[lane];
+        s_l[lane] = min(s_l[lane], s_lim[lane]);
+      }
+      __syncthreads();
+    }
+    if (warp == 0) sp[lane].log2Br = s_l[lane];
+  }
+  if (warp == 0 && i < P) {
+    const Part& p = sp[lane];
+    int2 cr = make_int2(0, -1);
+    if (p.status == kOk) {
+      const StreamDesc& ds = streams[p.sid];
+      cr = make_int2(ds.chunk_base + chunk_of(p.k_lo), ds.chunk_base + chunk_of(p.k_hi));
+      atomicAdd(diff + cr.x, 1);
+      atomicAdd(diff + cr.y + 1, -1);
+    }
+    part[i] = p;
+    crange[i] = cr;
+    nrec[i] = cr.y - cr.x + 1;
+  }
 }
 
 // Single-block exclusive scan of n int64 values in place; total in *total.
@@ -223,25 +281,34 @@ __global__ void k_chunk_table(const int* diff, int n_chunks, int* cnt, int* list
 }
 
 // Chunk lists: every particle appends itself to the list of each chunk it
-// touches.  The lanes of a warp walk the chunks together and take their
-// slots with one atomic per warp and chunk (the order within a list is
-// arbitrary; the lists are sorted afterwards).
+// touches.  The lanes of a warp walk 32 chunks at a time: one ballot per
+// chunk gives the warp's members, lane j takes the slots of chunk j with
+// one atomic for the whole warp, and the 32 atomics are in flight together
+// (the order within a list is arbitrary; the lists are sorted afterwards).
 __global__ void k_fill(const int2* crange, int P, const int* list_off, int* fill, int* list) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
-  int2 cr = i < P ? crange[i] : make_int2(0, -1);
+  const int2 cr = i < P ? crange[i] : make_int2(0, -1);
   const int c0 = warp_min(cr.x <= cr.y ? cr.x : 0x7fffffff);
   const int c1 = warp_max(cr.x <= cr.y ? cr.y : -1);
   const unsigned lt = (1u << lane) - 1u;
-  for (int c = c0; c <= c1; ++c) {
-    const bool in = cr.x <= c && c <= cr.y;
-    const unsigned m = __ballot_sync(kFull, in);
-    if (!m) continue;
-    const int leader = __ffs(m) - 1;
-    int base = 0;
-    if (lane == leader) base = atomicAdd(fill + c, __popc(m));
-    base = __shfl_sync(kFull, base, leader);
-    if (in) list[list_off[c] + base + __popc(m & lt)] = i;
+  for (int base = c0; base <= c1; base += 32) {
+    unsigned mine = 0;   // members of chunk base + lane
+#pragma unroll 8
+    for (int j = 0; j < 32; ++j) {
+      const int c = base + j;
+      const unsigned m = __ballot_sync(kFull, cr.x <= c && c <= cr.y);
+      if (lane == j) mine = m;
+    }
+    int slot0 = 0;
+    if (mine) slot0 = atomicAdd(fill + base + lane, __popc(mine));
+#pragma unroll 8
+    for (int j = 0; j < 32; ++j) {
+      const int c = base + j;
+      const unsigned m = __shfl_sync(kFull, mine, j);
+      const int s0 = __shfl_sync(kFull, slot0, j);
+      if (cr.x <= c && c <= cr.y) list[list_off[c] + s0 + __popc(m & lt)] = i;
+    }
   }
 }
 
