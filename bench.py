@@ -27,10 +27,10 @@ sys.path.insert(0, ROOT)
 METRIC = "SC-stat particle-evals/s, mixed vs plain FP64 path on GB300, at rel err ≤1e-5"
 WORKLOAD = "C2"
 # Algorithmic FP32/INT32 lane-operations of the mixed path per support bin and
-# particle (itemised in the design doc): phase advance 8, phase->angle 2,
+# particle: phase advance 8, phase->angle 2,
 # G interpolation 8, channel products 8, rotate-accumulate 4, |G|^2 w 6.
 ALG_OPS_PER_BIN = 36
-LAUNCHES_PER_STEP = 7   # setup, scan, chunk table, fill, edges, main, fix-up
+LAUNCHES_PER_STEP = 8   # setup, scan, chunk table, fill, sort, edges, main, fix-up
 
 
 def parse():
@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--particles", type=int, default=None,
                     help="override the particle count (small cases for profiling)")
+    ap.add_argument("--pso-iters", type=int, default=10,
+                    help="C4: swarm iterations per captured graph (one step = one graph launch)")
     return ap.parse_args()
 
 
@@ -174,11 +176,94 @@ def run_reference(args, rank, world):
     }))
 
 
+def run_swarm(args, rank, world, local):
+    """The uneven batch (C4): eight streams of 1-4 years, one swarm each
+    (2k-32k particles, N from the search ladder, Table III coefficients),
+    whole swarm iterations on the device, captured as one CUDA graph of
+    --pso-iters iterations; one step = one graph launch."""
+    import torch
+    from paper_2408_13170_gb300 import scstat, synth
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cfgs = synth.c4_streams(seed=rank)
+    ctx = scstat.Context(local, scstat.SCS_MIXED)
+    for s, cfg in enumerate(cfgs):
+        d = synth.make_stream(cfg)
+        inj = synth.injection_params(d["rng"], *cfg["inj"])
+        ctx.set_data(s, d)
+        ctx.inject(s, inj, cfg["snr"])
+        ctx.set_segments(s, cfg["N"], scstat.SCS_EQUAL_SNR2)
+    sizes = [c["P"] for c in cfgs]
+    lo = np.min([c["lo"] for c in cfgs], axis=0)
+    hi = np.max([c["hi"] for c in cfgs], axis=0)
+    ctx.pso_create(list(range(len(cfgs))), sizes, lo, hi, 1234 + rank)
+    for s, cfg in enumerate(cfgs):
+        om, pp, pg, eps = scstat.table3_hyper(cfg["N"])
+        ctx.pso_set_hyper(om, pp, pg, eps, swarm=s)
+    G, P = args.pso_iters, int(sum(sizes))
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):        # the first launch captures the graph
+        scstat.scs_pso_run(ctx.h, G, True, stream)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    for j in range(args.steps):
+        flush.zero_()
+        ev[j][0].record(stream)
+        scstat.scs_pso_run(ctx.h, G, True, stream)
+        ev[j][1].record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ck = clocks.stop()
+    t_dev = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / 1e3, world, dev)
+    value = world * P * G * args.steps / t_dev
+    # end to end: each step also reads the swarm records back to the host
+    sv = np.empty(len(cfgs))
+    barrier(world)
+    t0 = time.perf_counter()
+    for j in range(args.steps):
+        scstat.scs_pso_run(ctx.h, G, True, None)
+        scstat.scs_pso_get(ctx.h, swarm_val=sv)
+    e2e_t = max_over_ranks(time.perf_counter() - t0, world, dev)
+    st = ctx.pso_get()
+    if rank != 0:
+        return
+    print(json.dumps({
+        "metric": METRIC, "value": value, "unit": "particle-evals/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (f64 anchors and segment totals)", "data": "synthetic",
+        "config": {"workload": "C4: uneven batch, 8 streams of 1-4 yr, swarms "
+                               f"{sizes}, N {[c['N'] for c in cfgs]}, equal-SNR^2; "
+                               f"{G} swarm iterations per CUDA-graph launch",
+                   "P": P, "K": [int(synth.grid(c['f_min'], c['f_max'], c['T_obs'])[2])
+                                 for c in cfgs],
+                   "iterations_per_step": G, "path": "mixed",
+                   "l2": "256 MB buffer written between timed steps",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": world * P * G * args.steps / e2e_t, "unit": "particle-evals/s",
+                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 8 * len(cfgs)},
+        "gpu_launches": (LAUNCHES_PER_STEP + 4) * G * args.steps,
+        "clocks": ck,
+        "swarm_best": [float(x) for x in st["swarm_val"]],
+        "iterations_run": int(st["iteration"]),
+    }))
+
+
 def main():
     args = parse()
     rank, world, local = dist_init(args)
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "C4":
+        run_swarm(args, rank, world, local)
         return
     import torch
     from paper_2408_13170_gb300 import scstat, synth

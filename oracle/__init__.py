@@ -18,7 +18,7 @@ What the oracle computes (arXiv:2408.13170):
     re-evaluated for every theta (Sec. II.B, last paragraph);
   * template h_alpha = T_alpha(theta, f) A(f) e^{-i Psi(f)} on the FFT grid
     (Sec. IV), TaylorF2 2PN circular phase and the rigid-adiabatic LISA TDI
-    A/E response (readings listed in the design doc).
+    A/E response.
 """
 from __future__ import annotations
 

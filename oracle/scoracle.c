@@ -21,7 +21,7 @@
  *                                                  (Sec. IV, TaylorF2 family)
  *   response: h_alpha = T_alpha(theta, f) h        (Sec. IV, LISA TDI A, E)
  *
- * Readings where the paper is silent (all listed in the design doc):
+ * Readings where the paper is silent:
  *   - waveform: non-spinning, circular (e0 = 0) TaylorF2 to 2PN; t(f) is
  *     defined as Psi'(f)/(2 pi); t_c fixed by t(f0) = 0; hard support cut
  *     f >= f0, t(f) <= T_obs, v <= 6^{-1/2};

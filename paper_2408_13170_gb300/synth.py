@@ -10,7 +10,7 @@ benchmark).
 Workload shapes follow Sec. IV of arXiv:2408.13170 (analytic instrumental
 PSD, stationary Gaussian noise generated directly in the frequency domain,
 one injected inspiral whose amplitude sets the SNR, uniform priors) and the
-benchmark configurations listed in the design doc.
+benchmark configurations below.
 """
 from __future__ import annotations
 
@@ -89,6 +89,32 @@ CONFIGS = {
                N=(16384, 4096, 1024, 256, 64, 16, 1), mode="equal_snr2",
                inj=(30.0, 1.5, 0.018), snr=25.0, seed=0),
 }
+
+
+YEAR = 3.15e7          # seconds (the one-year stream's duration)
+C4_YEARS = (1.0, 1.5, 2.0, 2.5, 3.0, 3.5, 4.0, 4.0)
+C4_LADDER = (100, 50, 10, 1)   # segment ladder of the search (App. B)
+
+
+def c4_streams(seed: int = 0):
+    """The uneven batch: eight independent streams (noise seeds 1-8) of
+    1-4 years, each with a band of width >= 0.01 Hz inside 0.01-0.05 Hz, one
+    injection at SNR 20, a swarm of 2048-32768 particles (log-uniform) and a
+    segment count from the search ladder.  Returns one config dict per
+    stream, with its particle prior box under "lo" / "hi"."""
+    rng = np.random.Generator(np.random.PCG64(1000 + seed))
+    out = []
+    for s, years in enumerate(C4_YEARS):
+        w = rng.uniform(0.01, 0.04)
+        f_lo = rng.uniform(0.01, 0.05 - w)
+        P = int(round(math.exp(rng.uniform(math.log(2048), math.log(32768)))))
+        lo = PRIOR_BOX["lo"].copy()
+        hi = PRIOR_BOX["hi"].copy()
+        lo[2], hi[2] = f_lo, f_lo + 0.5 * w
+        out.append(dict(T_obs=years * YEAR, f_min=f_lo, f_max=f_lo + w, P=P,
+                        N=C4_LADDER[s % len(C4_LADDER)], mode="equal_snr2",
+                        inj=(30.0, 1.5, f_lo + 0.2 * w), snr=20.0, seed=s + 1, lo=lo, hi=hi))
+    return out
 
 
 def make_stream(name_or_cfg, seed=None, noise_free=False):

@@ -1,0 +1,139 @@
+"""Parity at the workloads' full sizes, in the launch configuration the
+benchmark uses (mixed path, equal-SNR^2 segments), on sampled particles the
+oracle computes one by one.
+
+  one-year stream    K = 1 260 001, P = 4096, N = 2048 (both GPU paths)
+  four-year stream   K = 5 040 001, P = 16 384 per level, levels N = 16384,
+                     1024 and 1 of the hierarchy (mixed path; FP64 path on a
+                     subset)
+  uneven batch       eight streams of 1-4 years, swarms of 2k-32k particles,
+                     N from the search ladder, in one batched launch and as
+                     device-side swarm iterations
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2408_13170_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+TOL32 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def scstat():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_2408_13170_gb300 import scstat as m
+    return m
+
+
+def rel(got, ref):
+    ref = np.asarray(ref)
+    return np.max(np.abs(np.asarray(got) - ref) / np.maximum(np.abs(ref), 1.0))
+
+
+def _stream(cfg, seed=None):
+    d = synth.make_stream(cfg, seed=seed)
+    inj = synth.injection_params(d["rng"], *cfg["inj"])
+    oracle.inject(inj, d["f_first"], d["df"], d["K"], d["T_obs"], d["SA"], d["SE"],
+                  cfg["snr"], d["A"], d["E"])
+    return d, inj
+
+
+def test_one_year_stream_full(scstat):
+    cfg = synth.CONFIGS["C2"]
+    d, inj = _stream(cfg)
+    th = synth.draw_particles(cfg["P"], d["rng"])
+    th[0] = inj
+    sample = np.array([0, 1, 2, 517, 2048, 4095])
+    ref = oracle.evaluate(d, th[sample], cfg["N"], mode=oracle.EQUAL_SNR2)
+    with scstat.Context(0, scstat.SCS_MIXED) as ctx:
+        ctx.set_data(0, d)
+        ctx.set_segments(0, cfg["N"], scstat.SCS_EQUAL_SNR2)
+        s32 = ctx.eval(0, th)
+        edges = ctx.edges(0, th[sample], cfg["N"])
+        ctx.set_path(scstat.SCS_FP64)
+        s64 = ctx.eval(0, th)
+    assert rel(s32[sample], ref) <= TOL32
+    assert rel(s64[sample], ref) <= TOL64
+    assert rel(s32, s64) <= TOL32
+    assert np.argmax(s32) == np.argmax(s64) == 0
+    _, kap = oracle.evaluate(d, th[sample], cfg["N"], mode=oracle.EQUAL_SNR2, want_kappa=True)
+    np.testing.assert_array_equal(edges, np.ceil(kap).astype(np.int64))
+
+
+@pytest.mark.parametrize("N", [16384, 1024, 1])
+def test_four_year_stream_levels(scstat, N):
+    cfg = synth.CONFIGS["C3"]
+    d, inj = _stream(cfg)
+    lvl = cfg["N"].index(N)
+    rng = np.random.Generator(np.random.PCG64(100 + lvl))   # independent draws per level
+    th = synth.draw_particles(cfg["P"], rng)
+    th[0] = inj
+    sample = np.array([0, 1, 8191, 16383])
+    ref = oracle.evaluate(d, th[sample], N, mode=oracle.EQUAL_SNR2)
+    with scstat.Context(0, scstat.SCS_MIXED) as ctx:
+        ctx.set_data(0, d)
+        ctx.set_segments(0, N, scstat.SCS_EQUAL_SNR2)
+        s32 = ctx.eval(0, th)
+        ctx.set_path(scstat.SCS_FP64)
+        s64 = ctx.eval(0, th[:48])
+    assert rel(s32[sample], ref) <= TOL32
+    assert rel(s64[sample[:2]], ref[:2]) <= TOL64
+    assert rel(s32[:48], s64) <= TOL32
+    if N <= 1024:
+        # at N = 16384 the noise spread (sqrt(4N) = 256) hides an SNR-25 signal
+        # (rho^2 = 625) among 16384 draws; at lower N the injection stands out
+        assert np.argmax(s32) == 0
+
+
+def _c4(scstat, ctx):
+    cfgs = synth.c4_streams()
+    datas, ths = [], []
+    for s, cfg in enumerate(cfgs):
+        d, inj = _stream(cfg)
+        ctx.set_data(s, d)
+        ctx.set_segments(s, cfg["N"], scstat.SCS_EQUAL_SNR2)
+        th = synth.draw_particles(cfg["P"], d["rng"], cfg["lo"], cfg["hi"])
+        th[0] = inj
+        datas.append(d)
+        ths.append(th)
+    return cfgs, datas, ths
+
+
+def test_uneven_batch_full(scstat):
+    with scstat.Context(0, scstat.SCS_MIXED) as ctx:
+        cfgs, datas, ths = _c4(scstat, ctx)
+        out = ctx.batch_eval(list(range(len(cfgs))), ths)
+        for s, cfg in enumerate(cfgs):
+            sample = np.array([0, len(ths[s]) - 1])
+            ref = oracle.evaluate(datas[s], ths[s][sample], cfg["N"], mode=oracle.EQUAL_SNR2)
+            assert rel(out[s][sample], ref) <= TOL32
+        # the same particles stream by stream give the same bits
+        np.testing.assert_array_equal(ctx.eval(6, ths[6]), out[6])
+
+
+def test_uneven_batch_swarm_iterations(scstat):
+    with scstat.Context(0, scstat.SCS_MIXED) as a, scstat.Context(0, scstat.SCS_MIXED) as b:
+        cfgs, _, _ = _c4(scstat, a)
+        _c4(scstat, b)
+        lo = np.min([c["lo"] for c in cfgs], axis=0)
+        hi = np.max([c["hi"] for c in cfgs], axis=0)
+        sizes = [c["P"] for c in cfgs]
+        for c in (a, b):
+            c.pso_create(list(range(len(cfgs))), sizes, lo, hi, 7)
+            for s, cfg in enumerate(cfgs):
+                om, pp, pg, eps = scstat.table3_hyper(cfg["N"])
+                c.pso_set_hyper(om, pp, pg, eps, swarm=s)
+        a.pso_run(3, use_graph=True)
+        for _ in range(3):
+            b.pso_run(1, use_graph=False)
+        sa, sb = a.pso_get(), b.pso_get()
+        for k in ("pos", "vel", "best_pos", "best_val", "swarm_pos", "swarm_val", "stat"):
+            np.testing.assert_array_equal(sa[k], sb[k], err_msg=k)
+        assert sa["iteration"] == 3
+        assert np.all(np.isfinite(sa["swarm_val"]))

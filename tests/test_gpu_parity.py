@@ -2,7 +2,7 @@
 
 Tolerances (relative to max(|Upsilon_oracle|, 1), the statistic's natural
 scale: noise alone gives Upsilon ~ 2N >= 2):
-  FP64 path  1e-10   (both use double-double phases)
+  FP64 path  1e-10   (both compute the waveform phase in double-double)
   mixed path 1e-5    (FP32 split phase; the bound stated for the method)
 Integer outputs (supports, segment edges) must be identical.
 """
