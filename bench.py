@@ -31,6 +31,10 @@ WORKLOAD = "C2"
 # G interpolation 8, channel products 8, rotate-accumulate 4, |G|^2 w 6.
 ALG_OPS_PER_BIN = 36
 LAUNCHES_PER_STEP = 8   # setup, scan, chunk table, fill, sort, edges, main, fix-up
+# DRAM bytes (read + write) of one k_main_mixed launch on this workload at full
+# size, from an ncu capture of this kernel (profiles/k_main_mixed_C2.md); to be
+# re-taken whenever the kernel changes.
+MAIN_TRAFFIC_BYTES = 71.95e6 + 37.24e6
 
 
 def parse():
@@ -406,7 +410,8 @@ def main():
             ("setup_worklist", "segment_edges", "main", "fixup"), stages.mean(axis=0))},
         "roofline": {"bound": "alu", "kernel": "k_main_mixed", "achieved": achieved / 1e12,
                      "peak": peak / 1e12, "unit": "Tops/s", "frac": achieved / peak,
-                     "traffic": None,
+                     "traffic": None if args.particles else MAIN_TRAFFIC_BYTES,
+                     "traffic_unit": "bytes per launch (ncu dram read + write)",
                      "note": f"{ALG_OPS_PER_BIN} lane-ops per support bin-eval; peak = "
                              f"{props.multi_processor_count} SMs x 128 lanes x "
                              f"{sm_mhz:.0f} MHz (median SM clock under load)"},
