@@ -435,6 +435,16 @@ __device__ inline void response_power64(const Part& p, double f, double ca, doub
   const double a = kPi * f * L;
   double s_a, c_a;
   sincos_small(a, &s_a, &c_a);
+  // e_i = e^{-i pi f k.d_i}: the link phase of arm (s, r) is e_s e_r and
+  // e^{i a k.n} = e^{i pi f k.(d_r - d_s)} = e_s conj(e_r), so three sin/cos
+  // serve all six
+  Cx<double> e[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    double sn, cs;
+    sincos_small(-kPi * f * (p.kx * d[i][0] + p.ky * d[i][1] + p.kz * d[i][2]), &sn, &cs);
+    e[i] = Cx<double>{cs, sn};
+  }
   Cx<double> G[3][3];
   const int as[3] = {0, 0, 1}, ar[3] = {1, 2, 2};
 #pragma unroll
@@ -443,21 +453,26 @@ __device__ inline void response_power64(const Part& p, double f, double ca, doub
     const double iL = 1.0 / kArm;
     double n0 = (d[r][0] - d[s][0]) * iL, n1 = (d[r][1] - d[s][1]) * iL, n2 = (d[r][2] - d[s][2]) * iL;
     double kn = p.kx * n0 + p.ky * n1 + p.kz * n2;
-    double kd = p.kx * (d[s][0] + d[r][0]) + p.ky * (d[s][1] + d[r][1]) + p.kz * (d[s][2] + d[r][2]);
     double q0 = n0 * n0, q1 = n1 * n1, q2 = n2 * n2, q3 = 2.0 * n0 * n1, q4 = 2.0 * n0 * n2,
            q5 = 2.0 * n1 * n2;
     Cx<double> nPn{p.Pr[0] * q0 + p.Pr[1] * q1 + p.Pr[2] * q2 + p.Pr[3] * q3 + p.Pr[4] * q4 + p.Pr[5] * q5,
                    p.Pi[0] * q0 + p.Pi[1] * q1 + p.Pi[2] * q2 + p.Pi[3] * q3 + p.Pi[4] * q4 + p.Pi[5] * q5};
-    double sph, cph;
-    sincos_small(-kPi * f * kd, &sph, &cph);
-    Cx<double> base = cmul(Cx<double>{cph, sph}, nPn);
-    double b = a * kn, sb, cbb;
-    sincos_small(b, &sb, &cbb);
+    Cx<double> base = cmul(cmul(e[s], e[r]), nPn);
+    const Cx<double> eb = cmul(e[s], Cx<double>{e[r].re, -e[r].im});   // e^{i b}, b = a k.n
+    double b = a * kn;
     double xf = a - b, xb = a + b;
-    double sf = fabs(xf) < 0.25 ? sin_(xf) : s_a * cbb - c_a * sb;
-    double sk = fabs(xb) < 0.25 ? sin_(xb) : s_a * cbb + c_a * sb;
-    double sincf = xf == 0.0 ? 1.0 : sf / xf;
-    double sincb = xb == 0.0 ? 1.0 : sk / xb;
+    double sf = fabs(xf) < 0.25 ? sin_(xf) : s_a * eb.re - c_a * eb.im;
+    double sk = fabs(xb) < 0.25 ? sin_(xb) : s_a * eb.re + c_a * eb.im;
+    double sincf, sincb;
+    const double xx = xf * xb;
+    if (xx != 0.0) {   // one division for both reciprocals
+      const double rr = 1.0 / xx;
+      sincf = sf * (xb * rr);
+      sincb = sk * (xf * rr);
+    } else {
+      sincf = xf == 0.0 ? 1.0 : sf / xf;
+      sincb = xb == 0.0 ? 1.0 : sk / xb;
+    }
     G[s][r] = Cx<double>{a * sincf * base.im, -a * sincf * base.re};
     G[r][s] = Cx<double>{a * sincb * base.im, -a * sincb * base.re};
   }
