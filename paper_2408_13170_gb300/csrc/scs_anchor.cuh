@@ -144,10 +144,9 @@ __device__ inline void phase_taylor(const Part& p, double fa, double df, double 
   an.df32 = df32;
 }
 
-// Build the phase state of the span starting at k_a.  Out of line: it runs
-// once per span, and keeping its FP64 code out of the hot loop's footprint
-// measurably helps.
-static __device__ __noinline__ void phase_anchor(const Part& p, int ka, double f_first,
+// Build the phase state of the span starting at k_a (inlined: a call's
+// register saves cost more than the code size).
+__device__ __forceinline__ void phase_anchor(const Part& p, int ka, double f_first,
                                                  double df, PhaseAnchor& an) {
   double fa = f_first + (double)ka * df;
   double c64[4];
@@ -185,10 +184,10 @@ __device__ inline uint64_t phase_anchor_at(const PhaseAnchor& an, int j) {
   return acc;
 }
 
-// G_alpha at bin offset x from the phase anchor (FP32 node).  Not inlined:
-// called once or twice per response sub-span, so one copy of the response
-// code keeps the hot loop's instruction footprint small.
-static __device__ __noinline__ void g_node32(const Part* __restrict__ pp, float al0, float tq1,
+// G_alpha at bin offset x from the phase anchor (FP32 node).  Inlined into
+// a single loop over the span's nodes (one copy of the code, no call
+// overhead or register spills around a call).
+__device__ __forceinline__ void g_node32(const Part* __restrict__ pp, float al0, float tq1,
                                       float tq2, float tq3, float fa32, float df32, float x,
                                       float4* out) {
   const Part& p = *pp;

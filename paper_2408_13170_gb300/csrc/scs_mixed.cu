@@ -223,11 +223,17 @@ __global__ void __launch_bounds__(128, 4) k_main_mixed(EvalArgs a) {
       }
       if (L.act && k0 == L.next_resp && k0 < L.ke) {
         const float x0 = (float)(k0 - L.phase_k), h = 0.5f * (float)(1 << L.log2Br);
-        float4 y0, y1;
-        if (L.fresh) g_node32(L.pp, L.al0, L.tq1, L.tq2, L.tq3, L.fa32, df32, x0, &y0);
-        else y0 = L.yend;
-        g_node32(L.pp, L.al0, L.tq1, L.tq2, L.tq3, L.fa32, df32, x0 + h, &y1);
-        g_node32(L.pp, L.al0, L.tq1, L.tq2, L.tq3, L.fa32, df32, x0 + 2.0f * h, &L.yend);
+        // nodes at x0 + q h: q = 0 only after a new phase anchor (otherwise it
+        // is the previous sub-span's end), then q = 1, 2
+        float4 y0 = L.yend, y1 = L.yend, y2 = L.yend;
+        for (int q = L.fresh ? 0 : 1; q < 3; ++q) {
+          float4 t;
+          g_node32(L.pp, L.al0, L.tq1, L.tq2, L.tq3, L.fa32, df32, x0 + (float)q * h, &t);
+          if (q == 0) y0 = t;
+          else if (q == 1) y1 = t;
+          else y2 = t;
+        }
+        L.yend = y2;
         quad_from_nodes(y0, y1, L.yend, h, L.rq);
         L.fresh = false;
         L.jf = 0.f;
