@@ -10,8 +10,11 @@
 //   G_alpha:   quadratic in the bin offset over a response sub-span
 //   z += d~ conj(G) e^{+2 pi i Phi},  hh += w |G|^2   (Sec. II.B [a|b]_n)
 // Sums run in 32-bin FP32 blocks flushed into Kahan accumulators; when a
-// segment closes its x^2/hh (Sec. II.B, Upsilon_N) goes into a per-item
-// Kahan sum, written to the work unit's record in FP64.
+// segment ends, the lane keeps its block sums at the cut (selects, no
+// branch) and the close -- x^2/hh (Sec. II.B, Upsilon_N) into a per-item
+// Kahan sum, written to the work unit's record in FP64 -- runs once at the
+// block's end for all lanes that had a cut (blocks are shortened so that no
+// lane has two).
 #include "scs_anchor.cuh"
 #include "scs_internal.cuh"
 
@@ -33,7 +36,12 @@ __device__ __forceinline__ float kval(const Kahan& k) { return k.s - k.c; }
 // per-lane state of one work item (kept in registers)
 struct Lane {
   int kb, ke;
-  int n_cur, e_next, e_after;   // segment, its end, the end after it (prefetched)
+  int n_cur;         // current segment
+  int e_cut;         // its end if inside [kb, ke), else kNoEdge
+  int j2;            // index of the first edge after that end (N + 1: none)
+  int e_cut2;        // that edge if inside [kb, ke), else kNoEdge
+  float pzr, pzi, phh;   // block sums of the segment that ended in this block
+  bool pend;
   int next_phase, next_resp, phase_k;
   int log2B, log2Br;
   bool act, head, fresh;
@@ -60,8 +68,18 @@ struct ItemStream {
   double* seg_hh;
 };
 
-__device__ __forceinline__ void close_segment(Lane& L, const ItemStream& a, double zs, int k) {
-  float zr = kval(L.szr) + L.bzr, zi = kval(L.szi) + L.bzi, hh = kval(L.shh) + L.bhh;
+// First edge index j' >= j with e[j'] > v (N + 1 if none): skips the empty
+// segments that equal-SNR^2 edges can produce.
+__device__ __forceinline__ int next_end(const int* e, int N, int j, int v) {
+  while (j <= N && __ldg(e + j) <= v) ++j;
+  return j;
+}
+
+// The segment that ended in this block (at bin e_cut): x^2/hh (or the item's
+// head record) from its Kahan sums and the block sums kept at the cut; then
+// the next segment.  Same arithmetic as closing it at the cut.
+__device__ __forceinline__ void finish_close(Lane& L, const ItemStream& a, double zs) {
+  float zr = kval(L.szr) + L.pzr, zi = kval(L.szi) + L.pzi, hh = kval(L.shh) + L.phh;
   if (L.head) {
     L.rec->n_head = L.n_cur;
     L.rec->zr_h = zr * zs;
@@ -79,19 +97,19 @@ __device__ __forceinline__ void close_segment(Lane& L, const ItemStream& a, doub
   L.szr = Kahan{0.f, 0.f};
   L.szi = Kahan{0.f, 0.f};
   L.shh = Kahan{0.f, 0.f};
-  L.bzr = L.bzi = L.bhh = 0.f;
-  // the next end is already in a register; only empty segments (rare) need
-  // the edge table now, and the load of the end after it is not waited for
-  // until the next close
-  int n = L.n_cur + 1;
-  int en = L.e_after;
-  if (en <= k) {
-    n = advance_segment(L.e, a.N, n, k);
-    en = __ldg(L.e + n + 1);
+  L.pend = false;
+  // segment j2 - 1 runs from the cut to edge j2 (the edges in between equal
+  // the cut: empty segments)
+  L.n_cur = L.j2 - 1;
+  L.e_cut = L.e_cut2;
+  if (L.j2 <= a.N) {
+    const int v = __ldg(L.e + L.j2);
+    L.j2 = next_end(L.e, a.N, L.j2 + 1, v);
+    const int e2 = L.j2 <= a.N ? __ldg(L.e + L.j2) : kNoEdge;
+    L.e_cut2 = e2 < L.ke ? e2 : kNoEdge;
+  } else {
+    L.e_cut2 = kNoEdge;
   }
-  L.n_cur = n;
-  L.e_next = en;
-  L.e_after = n + 2 <= a.N ? __ldg(L.e + n + 2) : kNoEdge;
 }
 
 // nb bins from k0, each lane masked to its own [kb, ke) (a single loop body:
@@ -109,10 +127,16 @@ __device__ __forceinline__ void run_block(Lane& L, const ItemStream& a, double z
     dn = __ldg(a.d32 + k + 1);
     wn = __ldg(a.w32 + k + 1);
     const bool m = L.act && (unsigned)(k - L.kb) < (unsigned)(L.ke - L.kb);
-    const bool hit = m && k == L.e_next;
-    if (__any_sync(kFull, hit)) {
-      if (hit) close_segment(L, a, zs, k);
-    }
+    // a segment ends before bin k: keep its block sums, restart them (at
+    // most one end per lane and block)
+    const bool at = k == L.e_cut;
+    L.pzr = at ? L.bzr : L.pzr;
+    L.pzi = at ? L.bzi : L.pzi;
+    L.phh = at ? L.bhh : L.phh;
+    L.bzr = at ? 0.f : L.bzr;
+    L.bzi = at ? 0.f : L.bzi;
+    L.bhh = at ? 0.f : L.bhh;
+    L.pend = L.pend || at;
     // e^{+2 pi i Phi} from the top 32 bits of the fixed-point phase
     const float ang = (float)(int)(L.d[0] >> 32) * 1.4629180792671596e-09f;   // 2 pi / 2^32
     float sp, cp;
@@ -187,8 +211,18 @@ __global__ void __launch_bounds__(128, 4) k_main_mixed(EvalArgs a) {
     if (!L.act) first = kNoEdge;
     L.e = L.act ? edges_of(sd, a.edges_all, L.p) : sd.width_edges;
     L.n_cur = L.act ? segment_of(L.e, is.N, L.kb) : 0;
-    L.e_next = L.act ? __ldg(L.e + L.n_cur + 1) : kNoEdge;
-    L.e_after = L.act && L.n_cur + 2 <= is.N ? __ldg(L.e + L.n_cur + 2) : kNoEdge;
+    L.e_cut = kNoEdge;
+    L.e_cut2 = kNoEdge;
+    L.j2 = is.N + 1;
+    if (L.act) {
+      const int en = __ldg(L.e + L.n_cur + 1);   // > kb
+      L.e_cut = en < L.ke ? en : kNoEdge;
+      L.j2 = next_end(L.e, is.N, L.n_cur + 2, en);
+      const int e2 = L.j2 <= is.N ? __ldg(L.e + L.j2) : kNoEdge;
+      L.e_cut2 = e2 < L.ke ? e2 : kNoEdge;
+    }
+    L.pend = false;
+    L.pzr = L.pzi = L.phh = 0.f;
     L.head = true;
     L.fresh = true;
     L.szr = L.szi = L.shh = L.ups = Kahan{0.f, 0.f};
@@ -206,7 +240,11 @@ __global__ void __launch_bounds__(128, 4) k_main_mixed(EvalArgs a) {
     const int kw0 = warp_min(first);
     const int kw1 = warp_max(L.act ? L.ke : -1);
     const int BW = min(32, 1 << warp_min(L.act ? L.log2Br : 12));
-    for (int k0 = kw0; k0 < kw1; k0 += BW) {
+    for (int k0 = kw0, nb = 0; k0 < kw1; k0 += nb) {
+      // to the next multiple of BW, the warp's range end, and before any
+      // lane's second segment end (one end per lane and block)
+      nb = min(BW - (k0 & (BW - 1)), kw1 - k0);
+      nb = min(nb, warp_min(L.e_cut2 == kNoEdge ? kNoEdge : L.e_cut2 - k0));
       if (L.act && k0 == L.next_phase && k0 < L.ke) {
         PhaseAnchor an;
         phase_anchor(*L.pp, k0, f_first, df, an);
@@ -239,8 +277,10 @@ __global__ void __launch_bounds__(128, 4) k_main_mixed(EvalArgs a) {
         L.jf = 0.f;
         L.next_resp += 1 << L.log2Br;
       }
-      const int nb = min(BW, kw1 - k0);
       run_block(L, is, zs, k0, nb);
+      if (__any_sync(kFull, L.pend)) {
+        if (L.pend) finish_close(L, is, zs);
+      }
       // block sums go into the Kahan accumulators at 32-aligned bins inside
       // the lane's range and once at its end, never later: the rounding of a
       // particle's sums does not depend on which particles share its warp
