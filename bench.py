@@ -294,6 +294,9 @@ def main():
     def step(i):
         scstat.scs_eval_stat(ctx.h, 0, batches[i], P, stat[i], cuda_stream=stream)
 
+    # work tile chosen by the library's autotuner on the first batch (set-up,
+    # not timed)
+    tile, tile_ms = scstat.scs_autotune(ctx.h, 0, batches[0], P, cuda_stream=stream)
     scstat.scs_set_profiling(ctx.h, True)
     for i in range(args.warmup):
         flush.zero_()
@@ -403,6 +406,8 @@ def main():
                                f"TDI A,E; P={P} particles uniform in the prior box; "
                                f"N={N} equal-SNR^2 segments; injection SNR {cfg['snr']}",
                    "P": P, "K": int(d["K"]), "N": N, "path": "mixed",
+                   "tile_bins": 1 << tile,
+                   "autotune_ms": {str(1 << (11 + i)): float(t) for i, t in enumerate(tile_ms)},
                    "l2": "256 MB buffer written between timed steps",
                    "parallelism": f"replicas x{world}"},
         "bin_evals_per_s": float(world * bin_evals.sum() / t_dev),

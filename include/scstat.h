@@ -208,6 +208,23 @@ int scs_pso_set(scs_ctx *ctx, const double *pos, const double *vel, const double
 int scs_pso_save(scs_ctx *ctx, void *buf, size_t *len, void *cuda_stream);
 int scs_pso_load(scs_ctx *ctx, const void *buf, size_t len, void *cuda_stream);
 
+/* Work tile of a stream: its bins are cut into chunks of 2^log2_chunk
+ * (11 .. 14, default 12 = 4096 bins); a work item is one chunk x up to 32
+ * particles.  The tile sets where FP32 block sums are handed to the FP64
+ * merge: results for different tiles agree to FP32 rounding (~1e-8
+ * relative); one tile always gives the same bits.
+ * Errors: SCS_EINVAL, SCS_ENODATA. */
+int scs_set_tile(scs_ctx *ctx, int stream_id, int log2_chunk);
+
+/* Autotuner: times full evaluations of the given particles (P x 8, host or
+ * device; the stream's data and segmentation must be set) with every tile
+ * log2_chunk = 11 .. 14 on cuda_stream, keeps the fastest for the stream and
+ * returns it in *log2_chunk (may be NULL); ms (may be NULL) receives the
+ * four best-of-two times.  Synchronous; allocates.
+ * Errors: as scs_eval_stat. */
+int scs_autotune(scs_ctx *ctx, int stream_id, const double *params, int64_t P,
+                 int *log2_chunk, double *ms, void *cuda_stream);
+
 /* Template h_A, h_E (Sec. IV: h_alpha = T_alpha(theta, f) A(f) e^{-i Psi(f)},
  * A(f) = f^{-7/6}) of one particle on the stream's grid, FP64, complex
  * interleaved, zero outside the support.

@@ -48,7 +48,8 @@ struct DataStream {
   double W0 = 1.0;
   int N = 0, mode = -1;
   DevBuf width_edges;   // N + 1 ints, e_n = floor(n K / N)
-  uint64_t gen = 0;     // bumped by every set_data / set_segments
+  int log2_chunk = kLog2ChunkDefault;   // work tile (scs_set_tile / scs_autotune)
+  uint64_t gen = 0;     // bumped by every set_data / set_segments / set_tile
 };
 
 bool is_device_ptr(const void* p) {
@@ -198,7 +199,8 @@ std::vector<StreamDesc> make_table(const std::vector<BatchPart>& parts, int* n_c
     d.K = ds.K;
     d.N = ds.N;
     d.mode = ds.mode;
-    d.n_chunks = (ds.K + kChunk - 1) / kChunk;
+    d.log2_chunk = ds.log2_chunk;
+    d.n_chunks = (int)(((int64_t)ds.K + (1 << ds.log2_chunk) - 1) >> ds.log2_chunk);
     d.chunk_base = cb;
     cb += d.n_chunks;
     d.p_off = parts[i].p_off;
@@ -459,7 +461,7 @@ int scs_set_data(scs_ctx* ctx, int sid, const double* A, const double* E, const 
   if (!ctx) return SCS_EINVAL;
   if (sid < 0 || sid >= 1024) return fail(ctx, SCS_EINVAL, "stream_id %d out of range", sid);
   if (!A || !E || !S_A) return fail(ctx, SCS_EINVAL, "null data pointer");
-  if (K < 1 || K > (int64_t)0x7fffffff - kChunk)
+  if (K < 1 || K > (int64_t)0x7fffffff - (1 << kLog2ChunkMax))
     return fail(ctx, SCS_EINVAL, "K = %lld out of range", (long long)K);
   if (!(df > 0.0) || !std::isfinite(df) || !(f_first > 0.0) || !std::isfinite(f_first) ||
       !(T_obs > 0.0) || !(std::fabs(df * T_obs - 1.0) <= 1e-12))
@@ -663,6 +665,72 @@ int scs_batch_eval(scs_ctx* ctx, const int* stream_ids, const int64_t* P_offsets
   if (!stat_dev) CK(cudaMemcpyAsync(stat, dstat, sizeof(double) * P, cudaMemcpyDeviceToHost, s));
   if (!stat_dev || !is_device_ptr(params)) CK(cudaStreamSynchronize(s));
   return SCS_OK;
+}
+
+int scs_set_tile(scs_ctx* ctx, int sid, int log2_chunk) {
+  if (!ctx) return SCS_EINVAL;
+  if (log2_chunk < kLog2ChunkMin || log2_chunk > kLog2ChunkMax)
+    return fail(ctx, SCS_EINVAL, "log2_chunk = %d outside [%d, %d]", log2_chunk, kLog2ChunkMin,
+                kLog2ChunkMax);
+  DataStream* ds = get_stream(ctx, sid, false);
+  if (!ds) return SCS_ENODATA;
+  ds->log2_chunk = log2_chunk;
+  ds->gen++;
+  return SCS_OK;
+}
+
+int scs_autotune(scs_ctx* ctx, int sid, const double* params, int64_t P, int* log2_chunk,
+                 double* ms, void* cuda_stream) {
+  if (!ctx) return SCS_EINVAL;
+  if (!params || P < 1 || P > (1 << 24)) return fail(ctx, SCS_EINVAL, "bad particles");
+  int rc = bind(ctx);
+  if (rc) return rc;
+  DataStream* ds = get_stream(ctx, sid, true);
+  if (!ds) return SCS_ENODATA;
+  cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : ctx->stream;
+  const double* dparams = nullptr;
+  rc = stage_params(ctx, params, P, s, &dparams);
+  if (rc) return rc;
+  DevBuf out;
+  CK(out.reserve(sizeof(double) * P));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const bool prof = ctx->prof;
+  ctx->prof = false;
+  const int keep = ds->log2_chunk;
+  int best = keep;
+  float best_ms = 0.f;
+  for (int l = kLog2ChunkMin; l <= kLog2ChunkMax && !rc; ++l) {
+    ds->log2_chunk = l;
+    float t = 0.f;
+    for (int rep = 0; rep < 3 && !rc; ++rep) {   // the first one sizes the scratch
+      cudaEventRecord(e0, s);
+      rc = scs_eval_stat(ctx, sid, dparams, P, out.as<double>(), nullptr, nullptr, s);
+      cudaEventRecord(e1, s);
+      if (rc) break;
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        rc = fail(ctx, SCS_ECUDA, "autotune timing failed");
+        break;
+      }
+      float dt = 0.f;
+      cudaEventElapsedTime(&dt, e0, e1);
+      if (rep == 1 || (rep > 1 && dt < t)) t = dt;
+    }
+    if (ms) ms[l - kLog2ChunkMin] = t;
+    if (!rc && (best_ms == 0.f || t < best_ms)) {
+      best_ms = t;
+      best = l;
+    }
+  }
+  ctx->prof = prof;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  out.release();
+  ds->log2_chunk = rc ? keep : best;
+  ds->gen++;
+  if (log2_chunk) *log2_chunk = ds->log2_chunk;
+  return rc;
 }
 
 int scs_support(scs_ctx* ctx, int sid, const double* params, int64_t P, int64_t* k_lo,

@@ -21,7 +21,8 @@ constexpr double kPiLo = 1.224646799147353207e-16;
 constexpr double kTwoPi = 6.283185307179586232;
 constexpr double kIscoV3 = 0.06804138174397717;             // 6^{-3/2}
 constexpr int kMaxLog2B = 11;                               // anchor stride <= 2048
-constexpr int kChunk = 4096;                                // bins per work chunk
+constexpr int kLog2ChunkDefault = 12;                       // bins per work chunk: 4096
+constexpr int kLog2ChunkMin = 11, kLog2ChunkMax = 14;       // tile sizes the tuner may pick
 constexpr int kSnr2Stride = 1024;                           // equal-SNR^2 anchor grid
 
 enum : int { kOk = 0, kInvalid = 1, kEmpty = 2 };

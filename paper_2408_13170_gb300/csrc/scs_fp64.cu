@@ -32,8 +32,8 @@ __global__ void __launch_bounds__(128) k_main_fp64(EvalArgs a) {
     const int slot = g * 32 + lane;
     const bool has = slot < a.cnt[cg];
     const int p = has ? a.list[a.list_off[cg] + slot] : -1;
-    const int kc0 = c * kChunk;
-    const int kc1 = min(kc0 + kChunk, sd.K);
+    const int kc0 = c << sd.log2_chunk;
+    const int kc1 = min(kc0 + (1 << sd.log2_chunk), sd.K);
     Part pp;
     int kb = 0, ke = 0;
     if (has) {
@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(128) k_main_fp64(EvalArgs a) {
     }
     if (has && pp.status == kOk) {
       // a particle active in this chunk always owns a record slot
-      a.rec[a.rec_off[p] + (c - chunk_of(pp.k_lo))] = r;
+      a.rec[a.rec_off[p] + (c - chunk_of(sd, pp.k_lo))] = r;
     }
   }
 }

@@ -8,7 +8,7 @@
 
 namespace scs {
 
-// Partial sums of one (particle, chunk) work unit.  A chunk is kChunk grid
+// Partial sums of one (particle, chunk) work unit.  A chunk is 2^log2_chunk grid
 // bins; a particle's segments may straddle chunk edges, so each unit reports
 // the segment its first support bin of the chunk falls in (head), the one
 // its last bin falls in (tail, if different), and the statistic of all
@@ -33,6 +33,7 @@ struct StreamDesc {
   double W0;             // FP32 copies hold d~/sqrt(W0) and w/W0
   int K, N, mode;        // mode: 0 equal width, 1 equal SNR^2
   int chunk_base, n_chunks;
+  int log2_chunk;        // work chunk of this stream: 2^log2_chunk bins
   int p_off, n_p;
   int amax;              // anchor slots per particle for the equal-SNR^2 edges
   int64_t edge_base;     // equal SNR^2: this stream's first edge table in edges_all
@@ -112,7 +113,7 @@ int occupancy_mixed(int* blocks_per_sm);
 int occupancy_fp64(int* blocks_per_sm);
 
 // chunk index of a grid bin within its stream
-__host__ __device__ inline int chunk_of(int k) { return k / kChunk; }
+__host__ __device__ inline int chunk_of(const StreamDesc& d, int k) { return k >> d.log2_chunk; }
 
 // stream of global chunk g (streams ordered by chunk_base)
 __device__ inline int stream_of_chunk(const StreamDesc* s, int n, int g) {

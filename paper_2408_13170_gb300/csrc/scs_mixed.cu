@@ -1,6 +1,6 @@
 // scs_mixed.cu -- the mixed-precision evaluation path (the hot loop).
 //
-// Layout: one warp takes a work item (one chunk of kChunk grid bins x up to
+// Layout: one warp takes a work item (one chunk of 2^log2_chunk grid bins x up to
 // 32 particles active in it), one lane per particle.  All lanes walk the
 // same bins, so each bin's pre-whitened data (float4 d~ and float2 w) is one
 // warp-uniform load shared by 32 templates.  Per bin and lane, in FP32/INT32:
@@ -187,8 +187,8 @@ __global__ void __launch_bounds__(128, 4) k_main_mixed(EvalArgs a) {
     const int g = item - a.item_off[cg];
     const int slot = g * 32 + lane;
     const bool has = slot < a.cnt[cg];
-    const int kc0 = c * kChunk;
-    const int kc1 = min(kc0 + kChunk, sd.K);
+    const int kc0 = c << sd.log2_chunk;
+    const int kc1 = min(kc0 + (1 << sd.log2_chunk), sd.K);
     Lane L;
     L.p = has ? a.list[a.list_off[cg] + slot] : 0;
     L.pp = a.part + L.p;
@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(128, 4) k_main_mixed(EvalArgs a) {
       L.log2B = L.pp->log2B;
       L.log2Br = L.pp->log2Br;
       first = (L.kb >> L.log2B) << L.log2B;
-      L.rec = a.rec + a.rec_off[L.p] + (c - chunk_of(klo));
+      L.rec = a.rec + a.rec_off[L.p] + (c - chunk_of(sd, klo));
     }
     L.act = has && L.kb < L.ke;
     if (!L.act) first = kNoEdge;

@@ -11,7 +11,7 @@ namespace {
 
 // ---------------------------------------------------------- anchor stride
 // Strides of the mixed path, chosen per particle:
-//  - phase: the largest power of two B <= kChunk for which the kernel's own
+//  - phase: the largest power of two B <= 2^kMaxLog2B for which the kernel's own
 //    degree-6 fixed-point phase polynomial stays within kTolPhase turns of
 //    the exact (double-double) phase;
 //  - response: the largest Br <= B for which the quadratic through FP64
@@ -103,7 +103,7 @@ __device__ void stride_estimates(const Part& p, double f_first, double df, int* 
   double wdop = kOmega * fabs(T1);
   double Bdop = pow(5040.0 * 0.5 * kTolPhase / (fhi * p.Rcb + 1e-30), 1.0 / 7.0) /
                 fmax(wdop, 1e-300);
-  *l0 = log2_floor_clamp(fmin(fmin(Bpn, Bdop), (double)kChunk));
+  *l0 = log2_floor_clamp(fmin(fmin(Bpn, Bdop), (double)(1 << kMaxLog2B)));
   *lr_cap = log2_floor_clamp(0.033 / fmax(4.0 * wdop, 1e-12));
 }
 
@@ -112,7 +112,7 @@ __device__ void stride_estimates(const Part& p, double f_first, double df, int* 
 // Particle set-up, 32 particles per block of 9 warps.  Warp 0 derives each
 // particle (one lane each), finds its support on its stream's grid and the
 // analytic stride estimates.  The strides are then searched downwards from
-// the estimates: the largest power of two B <= kChunk whose nine checks
+// the estimates: the largest power of two B <= 2^kMaxLog2B whose nine checks
 // (3 spans x 3 offsets) all pass, then the largest Br <= B likewise.  The
 // nine checks of a candidate run at once, one per warp (the FP64 work is
 // spread over the SM's four schedulers instead of queueing on one), and a
@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(kSetupThreads) k_setup(const double* params, i
     int2 cr = make_int2(0, -1);
     if (p.status == kOk) {
       const StreamDesc& ds = streams[p.sid];
-      cr = make_int2(ds.chunk_base + chunk_of(p.k_lo), ds.chunk_base + chunk_of(p.k_hi));
+      cr = make_int2(ds.chunk_base + chunk_of(ds, p.k_lo), ds.chunk_base + chunk_of(ds, p.k_hi));
       atomicAdd(diff + cr.x, 1);
       atomicAdd(diff + cr.y + 1, -1);
     }

@@ -69,6 +69,10 @@ def lib():
         L.scs_eval_stat_noalloc.restype = I
         L.scs_batch_eval.argtypes = [P, P, P, I, P, P, P]
         L.scs_batch_eval.restype = I
+        L.scs_set_tile.argtypes = [P, I, I]
+        L.scs_set_tile.restype = I
+        L.scs_autotune.argtypes = [P, I, P, I64, P, P, P]
+        L.scs_autotune.restype = I
         U64 = ctypes.c_uint64
         L.scs_pso_create.argtypes = [P, I, P, P, P, P, U64, P]
         L.scs_pso_set_hyper.argtypes = [P, I, D, D, D, P, P]
@@ -255,6 +259,19 @@ def scs_pso_save(ctx, cuda_stream=None) -> bytes:
 def scs_pso_load(ctx, blob: bytes, cuda_stream=None):
     buf = ctypes.create_string_buffer(blob, len(blob))
     _check(ctx, lib().scs_pso_load(ctx, buf, len(blob), _stream(cuda_stream)))
+
+
+def scs_set_tile(ctx, stream_id, log2_chunk):
+    _check(ctx, lib().scs_set_tile(ctx, stream_id, int(log2_chunk)))
+
+
+def scs_autotune(ctx, stream_id, params, P, cuda_stream=None):
+    """Times every tile on these particles; returns (chosen log2_chunk, ms[4])."""
+    best = ctypes.c_int()
+    ms = np.zeros(4)
+    _check(ctx, lib().scs_autotune(ctx, stream_id, _ptr(params), int(P), ctypes.byref(best),
+                                   ms.ctypes.data, _stream(cuda_stream)))
+    return best.value, ms
 
 
 def scs_set_profiling(ctx, enable: bool):

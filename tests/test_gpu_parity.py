@@ -280,3 +280,29 @@ def test_large_call_matches_small_calls(scstat, small):
     sample = np.arange(0, len(big), 97)
     ref = oracle.evaluate(d, big[sample], 64, mode=oracle.EQUAL_SNR2)
     assert rel_err(stat[sample], ref) <= TOL32
+
+
+def test_tiles_give_same_bits_and_autotune(scstat, small):
+    """The work tile (bins per chunk) moves where FP32 block sums are handed
+    to the FP64 merge, so results agree across tiles to FP32 rounding (and
+    with the oracle to the mixed tolerance); the autotuner times every tile
+    and keeps the fastest; a given tile always gives the same bits."""
+    d, th, ctx = small
+    rng = np.random.default_rng(23)
+    ps = np.vstack([th, particles(rng, 300)])
+    ctx.set_path(scstat.SCS_MIXED)
+    ctx.set_segments(0, 16, oracle.EQUAL_SNR2)
+    outs = []
+    for l2 in (11, 12, 13, 14):
+        scstat.scs_set_tile(ctx.h, 0, l2)
+        outs.append(ctx.eval(0, ps))
+    ref = oracle.evaluate(d, ps, 16, mode=oracle.EQUAL_SNR2)
+    for o in outs:
+        assert rel_err(o, outs[0]) <= 1e-6
+        assert rel_err(o, ref) <= TOL32
+    best, ms = scstat.scs_autotune(ctx.h, 0, ps, len(ps))
+    assert 11 <= best <= 14 and np.all(ms > 0)
+    np.testing.assert_array_equal(ctx.eval(0, ps), outs[best - 11])
+    with pytest.raises(scstat.ScsError):
+        scstat.scs_set_tile(ctx.h, 0, 10)
+    scstat.scs_set_tile(ctx.h, 0, 12)

@@ -205,3 +205,17 @@ def test_swarm_errors(scstat, datas):
         with pytest.raises(scstat.ScsError) as e:
             ctx.pso_load(b"not a checkpoint at all, not at all......")
         assert e.value.code == scstat.SCS_EINVAL
+
+
+def test_two_hundred_iterations_in_one_graph(scstat, datas):
+    """200 whole iterations captured as one CUDA graph and launched once give
+    the state of 200 directly launched iterations."""
+    with _ctx(scstat, datas, scstat.SCS_MIXED) as a, _ctx(scstat, datas, scstat.SCS_MIXED) as b:
+        _setup(scstat, a)
+        _setup(scstat, b)
+        a.pso_run(200, use_graph=True)
+        b.pso_run(200, use_graph=False)
+        sa, sb = a.pso_get(), b.pso_get()
+        _same(sa, sb)
+        assert sa["iteration"] == 200
+        assert np.all(np.isfinite(sa["swarm_val"]))
