@@ -46,11 +46,11 @@ __device__ inline uint64_t small_turns_to_fixed(float x) {   // normally |x| << 
 // Taylor coefficients of the phase in the bin offset j about k_a:
 // c[r] = Phi^{(r)} df^r / r!  (c[0] reduced modulo one turn), orders 0-3 in
 // FP64 (c64) and 4-6 in FP32 (c32), plus the node hand-off.
-__device__ inline void phase_taylor(const Part& p, double fa, double df, double c64[4],
+__device__ inline void phase_taylor(const Part& p, double fa, double df, double idf, double c64[4],
                                     float c32[7], PhaseAnchor& an) {
-  const double rdf = df / fa;   // d/df of u^n = -(n/3) u^n / f: one bin = df
   double u = rcbrt(fa);
   double u2 = u * u;
+  const double rdf = df * (u2 * u);   // df / f (u^3 = 1/f): d/df of u^n = -(n/3) u^n / f
   double upow[4] = {u2 * u2 * u, u2 * u, u2, u};
   // PN part F_pn: bin-unit derivatives F[r] = F_pn^{(r)} df^r
   double F[5] = {0, 0, 0, 0, 0};
@@ -73,7 +73,6 @@ __device__ inline void phase_taylor(const Part& p, double fa, double df, double 
     }
   }
   // t(f) and its bin derivatives T[r] = t^{(r)} df^r (t = F'):  T[r] = F[r+1]/df
-  const double idf = 1.0 / df;
   double t0 = p.tc.hi + (p.tc.lo + F[1] * idf);
   double T1 = F[2] * idf, T2 = F[3] * idf, T3 = F[4] * idf;
   // F(f) = t_c f - 1/8 + F_pn: reduce the large terms separately
@@ -84,7 +83,7 @@ __device__ inline void phase_taylor(const Part& p, double fa, double df, double 
   double th = kOmega * t0 - p.lam;
   th -= kTwoPi * rint(th * (1.0 / kTwoPi));
   double sn, cs;
-  sincos(th, &sn, &cs);
+  sincos_small(th, &sn, &cs);   // |th| <= pi
   const double R = p.Rcb, W = kOmega;
   // q derivatives in bins (chain rule through t, orders <= 3)
   double q0 = -R * cs, q1 = R * W * sn, q2 = R * W * W * cs, q3 = -R * W * W * W * sn;
@@ -147,11 +146,11 @@ __device__ inline void phase_taylor(const Part& p, double fa, double df, double 
 // Build the phase state of the span starting at k_a (inlined: a call's
 // register saves cost more than the code size).
 __device__ __forceinline__ void phase_anchor(const Part& p, int ka, double f_first,
-                                                 double df, PhaseAnchor& an) {
+                                                 double df, double idf, PhaseAnchor& an) {
   double fa = f_first + (double)ka * df;
   double c64[4];
   float c32[7];
-  phase_taylor(p, fa, df, c64, c32, an);
+  phase_taylor(p, fa, df, idf, c64, c32, an);
   // forward differences Delta_r = sum_{s>=r} c_s r! S(s, r), with r! S(s, r)
   // (S: Stirling numbers of the second kind) the r-th forward difference at
   // 0 of j^s

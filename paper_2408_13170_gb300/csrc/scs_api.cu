@@ -194,6 +194,7 @@ std::vector<StreamDesc> make_table(const std::vector<BatchPart>& parts, int* n_c
     StreamDesc& d = t[i];
     d.f_first = ds.f_first;
     d.df = ds.df;
+    d.idf = 1.0 / ds.df;
     d.T_obs = ds.T_obs;
     d.W0 = ds.W0;
     d.K = ds.K;

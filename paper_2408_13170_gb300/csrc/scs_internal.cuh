@@ -30,6 +30,7 @@ static_assert(sizeof(Rec) == 64 && offsetof(Rec, n_tail) == 4 && offsetof(Rec, z
 // is the concatenation of the streams' chunks (chunk_base .. + n_chunks - 1).
 struct StreamDesc {
   double f_first, df, T_obs;
+  double idf;            // 1 / df
   double W0;             // FP32 copies hold d~/sqrt(W0) and w/W0
   int K, N, mode;        // mode: 0 equal width, 1 equal SNR^2
   int chunk_base, n_chunks;

@@ -37,7 +37,7 @@ __device__ bool phase_check(const Part& p, int B, int s, int t, double f_first, 
   const int jlo = max(0, p.k_lo - ka), jhi = min(B - 1, p.k_hi - ka);
   if (jhi < jlo) return true;
   PhaseAnchor an;
-  phase_anchor(p, ka, f_first, df, an);
+  phase_anchor(p, ka, f_first, df, 1.0 / df, an);
   const int jt = t == 0 ? B / 4 : (t == 1 ? (3 * B) / 4 : B - 1);
   const int j = min(max(jt, jlo), jhi);
   double tt;
