@@ -110,14 +110,14 @@ struct Part {
 __device__ constexpr int kPow[4] = {5, 3, 2, 1};
 
 // FP64 t(f) (accurate to ~1e-8 s; enough for the response and the support)
-__device__ inline double time_of_freq(const Part& p, double f) {
-  double u = rcbrt(f);
+__device__ inline double time_of_freq_u(const Part& p, double u) {
   double u2 = u * u;
   double s = u * (-(1.0 / 3.0) * p.A[3].hi +
                   u * (-(2.0 / 3.0) * p.A[2].hi +
                        u * (-p.A[1].hi + u2 * (-(5.0 / 3.0) * p.A[0].hi))));
   return p.tc.hi + (p.tc.lo + u2 * u * s);
 }
+__device__ inline double time_of_freq(const Part& p, double f) { return time_of_freq_u(p, rcbrt(f)); }
 
 // Derive a particle from theta (8 doubles).  Support is not set here.
 __device__ inline void part_init(Part& p, const double* th) {

@@ -381,13 +381,13 @@ __global__ void k_bounds(const Part* part, int p_lo, int p_hi, const StreamDesc*
   for (int a = lane; a < nanch; a += 32) {
     int ka = min(p.k_lo + a * kSnr2Stride, p.k_hi);
     double f = dd_val(grid_freq_dd(f_first, df, ka));
-    double t = time_of_freq(p, f);
+    double u = rcbrt(f), u2 = u * u;
+    double t = time_of_freq_u(p, u);
     double sa, ca;
     sincos_small(orbit_angle(t), &sa, &ca);
     double pA, pE;
     response_power64(p, f, ca, sa, pA, pE);
     // |h|^2 = A(f)^2 |R|^2 with A(f)^2 = f^{-7/3} = u^7, u = f^{-1/3}
-    double u = rcbrt(f), u2 = u * u;
     double amp2 = u2 * u2 * u2 * u;
     double2 w = w64[ka];
     H[a] = __dadd_rn(__dmul_rn(w.x, amp2 * pA), __dmul_rn(w.y, amp2 * pE));
@@ -418,13 +418,18 @@ __global__ void k_bounds(const Part* part, int p_lo, int p_hi, const StreamDesc*
   // search, then the anchor index only moves up with n
   const int M = N - 1;
   const int n0 = 1 + (int)(((int64_t)lane * M) / 32), n1 = 1 + (int)(((int64_t)(lane + 1) * M) / 32);
-  int a = 1;
+  // n C / N: for N a power of two the division is an exact scaling
+  const bool pow2 = (N & (N - 1)) == 0;
+  const double invN = 1.0 / (double)N;
+  int a = 1, a_rec = -1;
+  double rec = 0.0;   // 1 / (C[a] - C[a-1]) of the interval a_rec
   for (int n = n0; n < n1; ++n) {
     if (!(Cl > 0.0)) {
       e[n] = p.k_lo;
       continue;
     }
-    double cn = __ddiv_rn(__dmul_rn((double)n, Cl), (double)N);
+    const double q = __dmul_rn((double)n, Cl);
+    double cn = pow2 ? __dmul_rn(q, invN) : __ddiv_rn(q, (double)N);
     // first a in [1, nanch-1] with C[a] >= cn (else nanch-1)
     if (n == n0) {
       int lo = 1, hi = nanch - 1;
@@ -438,8 +443,21 @@ __global__ void k_bounds(const Part* part, int p_lo, int p_hi, const StreamDesc*
     }
     int k1 = min(p.k_lo + (a - 1) * kSnr2Stride, p.k_hi);
     int k2 = min(p.k_lo + a * kSnr2Stride, p.k_hi);
-    double fr = __ddiv_rn(__dsub_rn(cn, C[a - 1]), __dsub_rn(C[a], C[a - 1]));
-    double kap = __dadd_rn((double)k1, __dmul_rn(fr, (double)(k2 - k1)));
+    const double num = __dsub_rn(cn, C[a - 1]), den = __dsub_rn(C[a], C[a - 1]);
+    // kappa from a reciprocal kept per interval (error ~1e-10 bins); only a
+    // kappa within 1e-6 of an integer, where the ceiling could depend on the
+    // rounding, is recomputed with the definition's exact division
+    if (a != a_rec) {
+      rec = 1.0 / den;
+      a_rec = a;
+    }
+    const double dk = (double)(k2 - k1);
+    double kap = (double)k1 + (num * rec) * dk;
+    const double dist = kap - floor(kap);
+    if (!(den > 0.0) || !(dist > 1e-6 && dist < 1.0 - 1e-6)) {
+      const double fr = __ddiv_rn(num, den);
+      kap = __dadd_rn((double)k1, __dmul_rn(fr, dk));
+    }
     e[n] = (int)ceil(kap);
   }
 }
