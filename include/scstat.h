@@ -220,7 +220,7 @@ int scs_set_tile(scs_ctx *ctx, int stream_id, int log2_chunk);
  * device; the stream's data and segmentation must be set) with every tile
  * log2_chunk = 11 .. 14 on cuda_stream, keeps the fastest for the stream and
  * returns it in *log2_chunk (may be NULL); ms (may be NULL) receives the
- * four best-of-two times.  Synchronous; allocates.
+ * four best-of-three times.  Synchronous; allocates.
  * Errors: as scs_eval_stat. */
 int scs_autotune(scs_ctx *ctx, int stream_id, const double *params, int64_t P,
                  int *log2_chunk, double *ms, void *cuda_stream);

@@ -705,7 +705,7 @@ int scs_autotune(scs_ctx* ctx, int sid, const double* params, int64_t P, int* lo
   for (int l = kLog2ChunkMin; l <= kLog2ChunkMax && !rc; ++l) {
     ds->log2_chunk = l;
     float t = 0.f;
-    for (int rep = 0; rep < 3 && !rc; ++rep) {   // the first one sizes the scratch
+    for (int rep = 0; rep < 4 && !rc; ++rep) {   // the first one sizes the scratch
       cudaEventRecord(e0, s);
       rc = scs_eval_stat(ctx, sid, dparams, P, out.as<double>(), nullptr, nullptr, s);
       cudaEventRecord(e1, s);

@@ -22,7 +22,10 @@ namespace {
 // Both start from an analytic estimate of the remainder at the low end of
 // the support (where the derivatives are largest) and are verified at three
 // spans (first, middle, last) and three offsets per span, halving on failure.
-constexpr double kTolPhase = 2e-8;   // turns
+// A phase error that stays below kTolPhase turns (6e-6 rad) changes |z_n| by
+// less than 1e-10 relative: a phase offset common to a segment is maximised
+// out, and a slow drift enters |z_n| only at second order.
+constexpr double kTolPhase = 1e-6;   // turns
 constexpr double kTolG = 3e-7;       // relative to |G_A| + |G_E|
 
 __device__ inline int span_start(int k, int B) { return (k / B) * B; }
