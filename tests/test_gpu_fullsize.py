@@ -137,3 +137,34 @@ def test_uneven_batch_swarm_iterations(scstat):
             np.testing.assert_array_equal(sa[k], sb[k], err_msg=k)
         assert sa["iteration"] == 3
         assert np.all(np.isfinite(sa["swarm_val"]))
+
+
+@pytest.mark.parametrize("N", [1, 64])
+def test_false_alarm_batch_scaled(scstat, N):
+    """The false-alarm batch at reduced particle count: eight four-year
+    streams (K = 5 040 001; four noise-only, four with an injection at SNR
+    15-30), 256 particles per stream, all streams in one batched launch on
+    both paths: per-stream maximum statistic and its particle index agree."""
+    cfg = dict(synth.CONFIGS["C3"])
+    rng = np.random.Generator(np.random.PCG64(77))
+    with scstat.Context(0, scstat.SCS_MIXED) as ctx:
+        ths = []
+        for s in range(8):
+            d = synth.make_stream(cfg, seed=1 + s)
+            th = synth.draw_particles(256, d["rng"])
+            if s >= 4:
+                inj = synth.injection_params(d["rng"], *cfg["inj"])
+                oracle.inject(inj, d["f_first"], d["df"], d["K"], d["T_obs"], d["SA"], d["SE"],
+                              rng.uniform(15, 30), d["A"], d["E"])
+                th[17] = inj
+            ctx.set_data(s, d)
+            ctx.set_segments(s, N, scstat.SCS_EQUAL_SNR2)
+            ths.append(th)
+        mixed = ctx.batch_eval(list(range(8)), ths)
+        ctx.set_path(scstat.SCS_FP64)
+        plain = ctx.batch_eval(list(range(8)), ths)
+    for s in range(8):
+        assert rel(mixed[s], plain[s]) <= TOL32
+        assert np.argmax(mixed[s]) == np.argmax(plain[s])
+        if s >= 4 and N == 1:
+            assert np.argmax(mixed[s]) == 17
