@@ -120,23 +120,21 @@ __device__ __forceinline__ void run_block(Lane& L, const ItemStream& a, double z
                                           int nb) {
   float4 dn = __ldg(a.d32 + k0);
   float2 wn = __ldg(a.w32 + k0);
+  const unsigned span = L.act ? (unsigned)(L.ke - L.kb) : 0u;
   for (int i = 0; i < nb; ++i) {
     const int k = k0 + i;
     const float4 dv = dn;
     const float2 wv = wn;
     dn = __ldg(a.d32 + k + 1);
     wn = __ldg(a.w32 + k + 1);
-    const bool m = L.act && (unsigned)(k - L.kb) < (unsigned)(L.ke - L.kb);
+    const bool m = (unsigned)(k - L.kb) < span;
     // a segment ends before bin k: keep its block sums, restart them (at
-    // most one end per lane and block)
+    // most one end per lane and block); fma(b, 1, z) rounds as b + z
     const bool at = k == L.e_cut;
     L.pzr = at ? L.bzr : L.pzr;
     L.pzi = at ? L.bzi : L.pzi;
     L.phh = at ? L.bhh : L.phh;
-    L.bzr = at ? 0.f : L.bzr;
-    L.bzi = at ? 0.f : L.bzi;
-    L.bhh = at ? 0.f : L.bhh;
-    L.pend = L.pend || at;
+    const float keep = at ? 0.f : 1.f;
     // e^{+2 pi i Phi} from the top 32 bits of the fixed-point phase
     const float ang = (float)(int)(L.d[0] >> 32) * 1.4629180792671596e-09f;   // 2 pi / 2^32
     float sp, cp;
@@ -153,9 +151,9 @@ __device__ __forceinline__ void run_block(Lane& L, const ItemStream& a, double z
       zr = 0.f;
       zi = 0.f;
     }
-    L.bzr += zr;
-    L.bzi += zi;
-    L.bhh += m ? hb : 0.f;
+    L.bzr = fmaf(L.bzr, keep, zr);
+    L.bzi = fmaf(L.bzi, keep, zi);
+    L.bhh = fmaf(L.bhh, keep, m ? hb : 0.f);
 #pragma unroll
     for (int r = 0; r < kOrd; ++r) L.d[r] += L.d[r + 1];
     L.jf += 1.f;
@@ -278,6 +276,7 @@ __global__ void __launch_bounds__(128, 4) k_main_mixed(EvalArgs a) {
         L.next_resp += 1 << L.log2Br;
       }
       run_block(L, is, zs, k0, nb);
+      L.pend = (unsigned)(L.e_cut - k0) < (unsigned)nb;   // the cut fell in this block
       if (__any_sync(kFull, L.pend)) {
         if (L.pend) finish_close(L, is, zs);
       }
