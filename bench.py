@@ -34,7 +34,7 @@ LAUNCHES_PER_STEP = 8   # setup, scan, chunk table, fill, sort, edges, main, fix
 # DRAM bytes (read + write) of one k_main_mixed launch on this workload at full
 # size with the 2048-bin tile, from an ncu capture of this kernel
 # (profiles/k_main_mixed_C2.md); to be re-taken whenever the kernel changes.
-MAIN_TRAFFIC_BYTES = None
+MAIN_TRAFFIC_BYTES = 72.67e6 + 24.47e6
 
 
 def parse():
