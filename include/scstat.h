@@ -225,6 +225,58 @@ int scs_set_tile(scs_ctx *ctx, int stream_id, int log2_chunk);
 int scs_autotune(scs_ctx *ctx, int stream_id, const double *params, int64_t P,
                  int *log2_chunk, double *ms, void *cuda_stream);
 
+/* ---- The hierarchical multi-swarm search on the device (Sec. III.B, App. B) ----
+ * Convergence rule: a swarm has converged when its best value has not grown by
+ * more than delta over the last `window` evaluations (the paper: 2 over 50,
+ * the default).  The record is kept on the device by every iteration. */
+int scs_pso_set_convergence(scs_ctx *ctx, double delta, int window);
+
+/* converged[S] (may be NULL): 1 for each converged swarm; *iteration (may be
+ * NULL): iterations run.  Returns 1 when every swarm has converged, 0 when
+ * not, a negative SCS_E* code on error.  Synchronous on cuda_stream. */
+int scs_pso_status(scs_ctx *ctx, int *converged, int64_t *iteration, void *cuda_stream);
+
+/* Forget the personal and swarm bests and the convergence records (positions
+ * and velocities are kept): for a new objective, e.g. the next rung of the
+ * segment ladder.  Synchronous. */
+int scs_pso_reset_bests(scs_ctx *ctx, void *cuda_stream);
+
+/* The current swarm layout (it changes with scs_pso_regroup): *n_swarms, and
+ * if not NULL stream_ids[S] and swarm_offsets[S + 1]. */
+int scs_pso_layout(scs_ctx *ctx, int *n_swarms, int *stream_ids, int64_t *swarm_offsets);
+
+/* k-means of P positions (P x 8, host or device) in the prior box: features
+ * M_c, q, f0, beta, iota normalised to the box and lambda, psi on circles of
+ * circumference one; centroid 0 is particle 0, centroid j the particle
+ * farthest from centroids 0 .. j-1 (lowest index among equals); then `iters`
+ * Lloyd steps (nearest centroid, lowest index among equals; an empty cluster
+ * keeps its centroid).  labels[P] (host) receive the cluster of each
+ * particle, centroids (host, may be NULL) k x 9 features.  1 <= k <= P. */
+int scs_kmeans(scs_ctx *ctx, const double *pos, int64_t P, const double *prior_lo,
+               const double *prior_hi, int k, int iters, int *labels, double *centroids,
+               void *cuda_stream);
+
+/* Re-cluster the swarms (Sec. III.B): for each data stream, k-means with
+ * n_clusters centroids (seeded with that stream's swarm bests, then as
+ * scs_kmeans) over all particles of its swarms; every non-empty cluster
+ * becomes a swarm (particles renumbered: stream by stream, cluster by
+ * cluster, in their previous order), so swarms can merge, split or appear;
+ * the total number of particles is kept.  Bests are forgotten; each new
+ * swarm takes the hyper-parameters of its stream's first old swarm.
+ * Synchronous. */
+int scs_pso_regroup(scs_ctx *ctx, int n_clusters, int iters, void *cuda_stream);
+
+/* The hierarchical search (Sec. III.B): for each rung r of the ladder
+ * (n_rungs segment counts, e.g. {100, 50, 10, 1}): every swarm stream gets
+ * N = ladder[r] equal-SNR^2 segments, every swarm the hyper-parameter row
+ * hyper_rows[r] (Omega, Phi_P, Phi_G, eps[8]), the bests are reset, and
+ * iterations run in CUDA graphs of chunk_iters until all swarms have
+ * converged or max_iters have run (iters_out[r], may be NULL); between rungs
+ * the swarms are re-clustered into n_clusters per stream (0: not). */
+int scs_pso_search(scs_ctx *ctx, const int *ladder, int n_rungs, const double *hyper_rows,
+                   int n_clusters, int chunk_iters, int max_iters, int64_t *iters_out,
+                   void *cuda_stream);
+
 /* Template h_A, h_E (Sec. IV: h_alpha = T_alpha(theta, f) A(f) e^{-i Psi(f)},
  * A(f) = f^{-7/6}) of one particle on the stream's grid, FP64, complex
  * interleaved, zero outside the support.

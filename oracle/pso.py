@@ -141,3 +141,64 @@ def pso_step(pos, vel, best_pos, swarm_best_pos, swarm_of, hyper, lo, hi, seed, 
         pos[:, d] = x
         vel[:, d] = v
     return pos, vel
+
+
+def km_features(pos, lo, hi):
+    """k-means features of positions: M_c, q, f0, beta, iota normalised to the
+    prior box; lambda and psi as points on circles of circumference one."""
+    pos = np.asarray(pos, np.float64).reshape(-1, 8)
+    f = np.empty((len(pos), 9))
+    for i, d in enumerate((0, 1, 2, 4, 5)):
+        f[:, i] = (pos[:, d] - lo[d]) / (hi[d] - lo[d])
+    for j, d in enumerate((3, 6)):
+        u = (pos[:, d] - lo[d]) / (hi[d] - lo[d])
+        f[:, 5 + 2 * j] = np.cos(2 * np.pi * u) / (2 * np.pi)
+        f[:, 6 + 2 * j] = np.sin(2 * np.pi * u) / (2 * np.pi)
+    return f
+
+
+def _nearest(f, cent):
+    d2 = np.stack([np.sum((f - c) ** 2, axis=1) for c in cent], axis=1)
+    return np.argmin(d2, axis=1), np.min(d2, axis=1)
+
+
+def kmeans(pos, lo, hi, k, iters, seeds=None):
+    """Farthest-point seeded Lloyd k-means (labels, centroids): centroids from
+    `seeds` (positions) first, then particle 0 if there is none, then the
+    particle farthest from the centroids so far (first among equals); each
+    Lloyd step assigns to the nearest centroid (first among equals) and moves
+    each non-empty cluster's centroid to its members' mean."""
+    f = km_features(pos, lo, hi)
+    cent = [] if seeds is None else list(km_features(seeds, lo, hi))[:k]
+    while len(cent) < k:
+        if not cent:
+            cent.append(f[0].copy())
+        else:
+            _, d2 = _nearest(f, cent)
+            cent.append(f[int(np.argmax(d2))].copy())
+    cent = np.array(cent)
+    for _ in range(iters):
+        lab, _ = _nearest(f, cent)
+        for j in range(k):
+            m = lab == j
+            if m.any():
+                cent[j] = f[m].mean(axis=0)
+    lab, _ = _nearest(f, cent)
+    return lab, cent
+
+
+def converged_flags(history, delta, window):
+    """The convergence rule on a record of swarm best values (one row per
+    evaluation): converged after E evaluations when the best has not grown by
+    more than delta since evaluation E - 1 - window."""
+    history = np.asarray(history, np.float64)
+    E, S = history.shape
+    ref = np.full(S, -np.inf)
+    ref_it = np.zeros(S, np.int64)
+    out = []
+    for e in range(E):
+        up = history[e] > ref + delta
+        ref = np.where(up, history[e], ref)
+        ref_it = np.where(up, e, ref_it)
+        out.append(np.isfinite(ref) & (e - ref_it >= window))
+    return np.array(out)

@@ -94,6 +94,10 @@ struct scs_ctx {
     std::vector<double> hyper, lohi;           // S x 11; lo[8], hi[8]
     DevBuf d_off, pos, vel, best_pos, best_val, swarm_pos, swarm_val, stat, d_hyper, d_lohi,
         iter, table, scratch;
+    DevBuf ref_val, ref_iter;                  // convergence record per swarm
+    double conv_delta = 2.0;                   // App. B: improvement below 2 ...
+    int conv_window = 50;                      // ... over 50 iterations
+    DevBuf perm, tmp, km_cent, km_label, km_d2, km_pick;   // re-clustering scratch
     std::vector<uint64_t> gens;                // data generations the table was built from
     int table_path = -1;
     cudaGraphExec_t exec = nullptr;            // captured iterations
@@ -434,9 +438,11 @@ void scs_destroy(scs_ctx* ctx) {
     auto& q = ctx->pso;
     if (q.exec) cudaGraphExecDestroy(q.exec);
     if (q.cap) cudaStreamDestroy(q.cap);
-    DevBuf* pb[] = {&q.d_off, &q.pos, &q.vel, &q.best_pos, &q.best_val, &q.swarm_pos,
-                    &q.swarm_val, &q.stat, &q.d_hyper, &q.d_lohi, &q.iter, &q.table,
-                    &q.scratch};
+    DevBuf* pb[] = {&q.d_off,  &q.pos,      &q.vel,      &q.best_pos, &q.best_val,
+                    &q.swarm_pos, &q.swarm_val, &q.stat,   &q.d_hyper,  &q.d_lohi,
+                    &q.iter,   &q.table,    &q.scratch,  &q.ref_val,  &q.ref_iter,
+                    &q.perm,   &q.tmp,      &q.km_cent,  &q.km_label, &q.km_d2,
+                    &q.km_pick};
     for (DevBuf* b : pb) b->release();
   }
   DevBuf* bufs[] = {&ctx->params, &ctx->stat, &ctx->segx, &ctx->segh, &ctx->tmpA,
@@ -989,6 +995,9 @@ PsoArgs pso_args(scs_ctx* ctx) {
   a.iter = q.iter.as<int64_t>();
   a.key0 = (uint32_t)(q.seed & 0xffffffffu);
   a.key1 = (uint32_t)(q.seed >> 32);
+  a.ref_val = q.ref_val.as<double>();
+  a.ref_iter = q.ref_iter.as<int64_t>();
+  a.conv_delta = q.conv_delta;
   return a;
 }
 
@@ -1122,6 +1131,8 @@ int scs_pso_create(scs_ctx* ctx, int n_swarms, const int* stream_ids,
   CK(q.d_hyper.reserve(sizeof(double) * q.hyper.size()));
   CK(q.d_lohi.reserve(sizeof(double) * 16));
   CK(q.iter.reserve(sizeof(int64_t)));
+  CK(q.ref_val.reserve(sizeof(double) * n_swarms));
+  CK(q.ref_iter.reserve(sizeof(int64_t) * n_swarms));
   if (!q.cap) CK(cudaStreamCreateWithFlags(&q.cap, cudaStreamNonBlocking));
   CK(cudaMemcpy(q.d_off.ptr, q.off.data(), sizeof(int64_t) * (n_swarms + 1),
                 cudaMemcpyHostToDevice));
@@ -1273,14 +1284,16 @@ int scs_pso_set(scs_ctx* ctx, const double* pos, const double* vel, const double
   return SCS_OK;
 }
 
-// Checkpoint layout (native-endian): magic "SCSPSO01", int64 P, S, seed,
+// Checkpoint layout (native-endian): magic "SCSPSO02", int64 P, S, seed,
 // iteration; S + 1 int64 offsets; S int32 stream ids (padded to 8 bytes);
 // 16 prior bounds; S x 11 hyper-parameters; positions, velocities, personal
 // best positions (P x 8 each), personal best values (P), swarm best
-// positions (S x 8) and values (S).
+// positions (S x 8) and values (S); the convergence record: reference
+// values (S doubles), their iterations (S int64), the rule's delta (double)
+// and window (int64).
 static size_t pso_blob_bytes(int64_t P, int64_t S) {
   return 8 + 4 * 8 + 8 * (S + 1) + 8 * ((4 * S + 7) / 8) + 16 * 8 + 8 * kPsoHyper * S +
-         8 * (3 * 8 * P + P + 8 * S + S);
+         8 * (3 * 8 * P + P + 8 * S + S) + 16 * S + 16;
 }
 
 int scs_pso_save(scs_ctx* ctx, void* buf, size_t* len, void* cuda_stream) {
@@ -1297,7 +1310,7 @@ int scs_pso_save(scs_ctx* ctx, void* buf, size_t* len, void* cuda_stream) {
   const size_t P = (size_t)q.P, S = (size_t)q.S;
   unsigned char* b = (unsigned char*)buf;
   std::memset(b, 0, need);
-  std::memcpy(b, "SCSPSO01", 8);
+  std::memcpy(b, "SCSPSO02", 8);
   int64_t* h = (int64_t*)(b + 8);
   h[0] = q.P;
   h[1] = q.S;
@@ -1321,13 +1334,19 @@ int scs_pso_save(scs_ctx* ctx, void* buf, size_t* len, void* cuda_stream) {
   rc = scs_pso_get(ctx, pos, vel, bp, bv, sp, sv, nullptr, &it, cuda_stream);
   if (rc) return rc;
   h[3] = it;
+  unsigned char* r = (unsigned char*)(sv + S);
+  CK(cudaMemcpy(r, q.ref_val.ptr, 8 * S, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(r + 8 * S, q.ref_iter.ptr, 8 * S, cudaMemcpyDeviceToHost));
+  std::memcpy(r + 16 * S, &q.conv_delta, 8);
+  const int64_t win = q.conv_window;
+  std::memcpy(r + 16 * S + 8, &win, 8);
   *len = need;
   return SCS_OK;
 }
 
 int scs_pso_load(scs_ctx* ctx, const void* buf, size_t len, void* cuda_stream) {
   if (!ctx) return SCS_EINVAL;
-  if (!buf || len < 40 || std::memcmp(buf, "SCSPSO01", 8) != 0)
+  if (!buf || len < 40 || std::memcmp(buf, "SCSPSO02", 8) != 0)
     return fail(ctx, SCS_EINVAL, "not a swarm checkpoint");
   const unsigned char* b = (const unsigned char*)buf;
   int64_t h[4];
@@ -1366,7 +1385,295 @@ int scs_pso_load(scs_ctx* ctx, const void* buf, size_t len, void* cuda_stream) {
   const double* bv = bp + 8 * P;
   const double* sp = bv + P;
   const double* sv = sp + 8 * S;
-  return scs_pso_set(ctx, pos, vel, bp, bv, sp, sv, h[3], cuda_stream);
+  rc = scs_pso_set(ctx, pos, vel, bp, bv, sp, sv, h[3], cuda_stream);
+  if (rc) return rc;
+  const unsigned char* r = o + 8 * arr.size();
+  CK(cudaMemcpy(q.ref_val.ptr, r, 8 * S, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(q.ref_iter.ptr, r + 8 * S, 8 * S, cudaMemcpyHostToDevice));
+  int64_t win = 0;
+  std::memcpy(&q.conv_delta, r + 16 * S, 8);
+  std::memcpy(&win, r + 16 * S + 8, 8);
+  q.conv_window = (int)win;
+  return SCS_OK;
+}
+
+int scs_pso_set_convergence(scs_ctx* ctx, double delta, int window) {
+  int rc = pso_check(ctx);
+  if (rc) return rc;
+  if (!std::isfinite(delta) || delta < 0.0 || window < 1)
+    return fail(ctx, SCS_EINVAL, "convergence rule needs delta >= 0 and window >= 1");
+  auto& q = ctx->pso;
+  CK(cudaDeviceSynchronize());   // no captured or queued iteration reads the old delta
+  q.conv_delta = delta;
+  q.conv_window = window;
+  if (q.exec) {   // the delta is baked into the captured kernels' arguments
+    cudaGraphExecDestroy(q.exec);
+    q.exec = nullptr;
+    q.graph_iters = 0;
+  }
+  return SCS_OK;
+}
+
+int scs_pso_status(scs_ctx* ctx, int* converged, int64_t* iteration, void* cuda_stream) {
+  int rc = pso_check(ctx);
+  if (rc) return rc;
+  auto& q = ctx->pso;
+  cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : ctx->stream;
+  std::vector<double> rv(q.S);
+  std::vector<int64_t> ri(q.S);
+  int64_t it = 0;
+  CK(cudaMemcpyAsync(rv.data(), q.ref_val.ptr, 8 * q.S, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(ri.data(), q.ref_iter.ptr, 8 * q.S, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&it, q.iter.ptr, 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (iteration) *iteration = it;
+  int all = 1;
+  for (int s = 0; s < q.S; ++s) {
+    // evaluations it - 1 - ref_iter since the last improvement by > delta
+    const int c = std::isfinite(rv[s]) && it - 1 - ri[s] >= q.conv_window;
+    if (converged) converged[s] = c;
+    all &= c;
+  }
+  return all ? 1 : SCS_OK;
+}
+
+int scs_pso_reset_bests(scs_ctx* ctx, void* cuda_stream) {
+  int rc = pso_check(ctx);
+  if (rc) return rc;
+  cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : ctx->stream;
+  launch_pso_reset_bests(pso_args(ctx), st);
+  CKLAUNCH();
+  CK(cudaStreamSynchronize(st));
+  return SCS_OK;
+}
+
+int scs_pso_layout(scs_ctx* ctx, int* n_swarms, int* stream_ids, int64_t* swarm_offsets) {
+  int rc = pso_check(ctx);
+  if (rc) return rc;
+  auto& q = ctx->pso;
+  if (n_swarms) *n_swarms = q.S;
+  if (stream_ids) std::memcpy(stream_ids, q.sids.data(), sizeof(int) * q.S);
+  if (swarm_offsets) std::memcpy(swarm_offsets, q.off.data(), sizeof(int64_t) * (q.S + 1));
+  return SCS_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// k-means of particles [p0, p0 + n) of a device position array: centroids
+// 0 .. n_seed-1 from the given device positions, the rest farthest-point
+// seeded, then Lloyd iterations; labels copied to the host.
+int run_kmeans(scs_ctx* ctx, const double* pos, int p0, int n, const double* dlo,
+               const double* dhi, int k, int iters, const double* seeds, int n_seed,
+               std::vector<int>& labels, cudaStream_t st) {
+  auto& q = ctx->pso;
+  CK(q.km_cent.reserve(sizeof(double) * kKmFeat * k));
+  CK(q.km_label.reserve(sizeof(int) * n));
+  CK(q.km_d2.reserve(sizeof(double) * n));
+  CK(q.km_pick.reserve(sizeof(int)));
+  KmArgs a;
+  a.pos = pos;
+  a.p0 = p0;
+  a.n = n;
+  a.lo = dlo;
+  a.hi = dhi;
+  a.cent = q.km_cent.as<double>();
+  a.k = k;
+  a.label = q.km_label.as<int>();
+  a.d2 = q.km_d2.as<double>();
+  a.pick = q.km_pick.as<int>();
+  for (int j = 0; j < n_seed; ++j) launch_km_centroid_of(a, j, seeds + 8 * j, st);
+  launch_kmeans(a, n_seed, iters, st);
+  CKLAUNCH();
+  labels.resize(n);
+  CK(cudaMemcpyAsync(labels.data(), a.label, sizeof(int) * n, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return SCS_OK;
+}
+
+// Reorder the swarm's particles: new particle p is old perm[p].
+int pso_apply_perm(scs_ctx* ctx, const std::vector<int>& perm, cudaStream_t st) {
+  auto& q = ctx->pso;
+  CK(q.perm.reserve(sizeof(int) * q.P));
+  CK(q.tmp.reserve(sizeof(double) * 26 * (size_t)q.P));
+  CK(cudaMemcpyAsync(q.perm.ptr, perm.data(), sizeof(int) * q.P, cudaMemcpyHostToDevice, st));
+  launch_pso_permute(pso_args(ctx), q.perm.as<int>(), q.tmp.as<double>(), st);
+  CKLAUNCH();
+  CK(cudaStreamSynchronize(st));
+  return SCS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int scs_kmeans(scs_ctx* ctx, const double* pos, int64_t P, const double* prior_lo,
+               const double* prior_hi, int k, int iters, int* labels, double* centroids,
+               void* cuda_stream) {
+  if (!ctx) return SCS_EINVAL;
+  if (!pos || !prior_lo || !prior_hi || !labels || P < 1 || P > (1 << 24) || k < 1 || k > P ||
+      k > 1024 || iters < 0 || iters > 1000)
+    return fail(ctx, SCS_EINVAL, "bad k-means arguments");
+  int rc = bind(ctx);
+  if (rc) return rc;
+  cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : ctx->stream;
+  const double* dpos = nullptr;
+  rc = stage_params(ctx, pos, P, st, &dpos);
+  if (rc) return rc;
+  double lohi[16];
+  for (int d = 0; d < 8; ++d) {
+    lohi[d] = prior_lo[d];
+    lohi[8 + d] = prior_hi[d];
+  }
+  CK(ctx->misc.reserve(sizeof(double) * 16));
+  CK(cudaMemcpyAsync(ctx->misc.ptr, lohi, sizeof lohi, cudaMemcpyHostToDevice, st));
+  std::vector<int> lab;
+  rc = run_kmeans(ctx, dpos, 0, (int)P, ctx->misc.as<double>(), ctx->misc.as<double>() + 8, k,
+                  iters, nullptr, 0, lab, st);
+  if (rc) return rc;
+  std::memcpy(labels, lab.data(), sizeof(int) * P);
+  if (centroids)
+    CK(cudaMemcpy(centroids, ctx->pso.km_cent.ptr, sizeof(double) * kKmFeat * k,
+                  cudaMemcpyDeviceToHost));
+  return SCS_OK;
+}
+
+int scs_pso_regroup(scs_ctx* ctx, int n_clusters, int iters, void* cuda_stream) {
+  int rc = pso_check(ctx);
+  if (rc) return rc;
+  if (n_clusters < 1 || n_clusters > 1024 || iters < 0 || iters > 1000)
+    return fail(ctx, SCS_EINVAL, "bad regroup arguments");
+  auto& q = ctx->pso;
+  cudaStream_t st = cuda_stream ? (cudaStream_t)cuda_stream : ctx->stream;
+  CK(cudaStreamSynchronize(st));
+  // 1. particles of each stream contiguous (streams in order of first use)
+  std::vector<int> groups;
+  for (int s = 0; s < q.S; ++s)
+    if (std::find(groups.begin(), groups.end(), q.sids[s]) == groups.end())
+      groups.push_back(q.sids[s]);
+  std::vector<int> perm;
+  std::vector<int> g_begin, g_swarms_first;
+  perm.reserve(q.P);
+  std::vector<double> swarm_pos(8 * (size_t)q.S), swarm_val(q.S);
+  CK(cudaMemcpy(swarm_pos.data(), q.swarm_pos.ptr, 8 * sizeof(double) * q.S,
+                cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(swarm_val.data(), q.swarm_val.ptr, sizeof(double) * q.S,
+                cudaMemcpyDeviceToHost));
+  std::vector<std::vector<double>> seeds(groups.size());
+  std::vector<std::vector<double>> hyper_of(groups.size());
+  for (size_t g = 0; g < groups.size(); ++g) {
+    g_begin.push_back((int)perm.size());
+    for (int s = 0; s < q.S; ++s) {
+      if (q.sids[s] != groups[g]) continue;
+      for (int64_t p = q.off[s]; p < q.off[s + 1]; ++p) perm.push_back((int)p);
+      if (std::isfinite(swarm_val[s]))
+        seeds[g].insert(seeds[g].end(), &swarm_pos[8 * s], &swarm_pos[8 * s] + 8);
+      if (hyper_of[g].empty())
+        hyper_of[g].assign(&q.hyper[(size_t)kPsoHyper * s], &q.hyper[(size_t)kPsoHyper * s] + kPsoHyper);
+    }
+  }
+  g_begin.push_back((int)perm.size());
+  rc = pso_apply_perm(ctx, perm, st);
+  if (rc) return rc;
+  // 2. k-means per stream; swarms = non-empty clusters in label order
+  std::vector<int> perm2(q.P), new_sids;
+  std::vector<int64_t> new_off{0};
+  std::vector<double> new_hyper;
+  CK(q.tmp.reserve(sizeof(double) * 8 * 1024));   // seeds (also the permute scratch)
+  for (size_t g = 0; g < groups.size(); ++g) {
+    const int p0 = g_begin[g], n = g_begin[g + 1] - p0;
+    const int k = std::min(n_clusters, n);
+    const int n_seed = std::min(k, (int)(seeds[g].size() / 8));
+    if (n_seed)
+      CK(cudaMemcpy(q.tmp.ptr, seeds[g].data(), sizeof(double) * 8 * n_seed,
+                    cudaMemcpyHostToDevice));
+    std::vector<int> lab;
+    rc = run_kmeans(ctx, q.pos.as<double>(), p0, n, q.d_lohi.as<double>(),
+                    q.d_lohi.as<double>() + 8, k, iters, q.tmp.as<double>(), n_seed, lab, st);
+    if (rc) return rc;
+    std::vector<int> count(k, 0);
+    for (int v : lab) ++count[v];
+    std::vector<int> start(k, 0);
+    int run = 0;
+    for (int j = 0; j < k; ++j) {
+      start[j] = run;
+      run += count[j];
+      if (count[j]) {
+        new_sids.push_back(groups[g]);
+        new_off.push_back(new_off.back() + count[j]);
+        new_hyper.insert(new_hyper.end(), hyper_of[g].begin(), hyper_of[g].end());
+      }
+    }
+    for (int i = 0; i < n; ++i) perm2[p0 + start[lab[i]]++] = p0 + i;   // stable by label
+  }
+  rc = pso_apply_perm(ctx, perm2, st);
+  if (rc) return rc;
+  // 3. the new layout; bests forgotten (the next evaluation sets them)
+  const int S = (int)new_sids.size();
+  if (q.exec) {
+    cudaGraphExecDestroy(q.exec);
+    q.exec = nullptr;
+    q.graph_iters = 0;
+  }
+  q.S = S;
+  q.sids = new_sids;
+  q.off = new_off;
+  q.hyper = new_hyper;
+  q.gens.clear();
+  CK(q.d_off.reserve(sizeof(int64_t) * (S + 1)));
+  CK(q.swarm_pos.reserve(sizeof(double) * 8 * S));
+  CK(q.swarm_val.reserve(sizeof(double) * S));
+  CK(q.ref_val.reserve(sizeof(double) * S));
+  CK(q.ref_iter.reserve(sizeof(int64_t) * S));
+  CK(q.d_hyper.reserve(sizeof(double) * q.hyper.size()));
+  CK(cudaMemcpy(q.d_off.ptr, q.off.data(), sizeof(int64_t) * (S + 1), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(q.d_hyper.ptr, q.hyper.data(), sizeof(double) * q.hyper.size(),
+                cudaMemcpyHostToDevice));
+  launch_pso_reset_bests(pso_args(ctx), st);
+  CKLAUNCH();
+  CK(cudaStreamSynchronize(st));
+  return SCS_OK;
+}
+
+int scs_pso_search(scs_ctx* ctx, const int* ladder, int n_rungs, const double* hyper_rows,
+                   int n_clusters, int chunk_iters, int max_iters, int64_t* iters_out,
+                   void* cuda_stream) {
+  int rc = pso_check(ctx);
+  if (rc) return rc;
+  if (!ladder || !hyper_rows || n_rungs < 1 || n_rungs > 64 || chunk_iters < 1 ||
+      max_iters < chunk_iters || n_clusters < 0)
+    return fail(ctx, SCS_EINVAL, "bad search arguments");
+  auto& q = ctx->pso;
+  for (int r = 0; r < n_rungs; ++r) {
+    std::vector<int> used;
+    for (int sid : q.sids)
+      if (std::find(used.begin(), used.end(), sid) == used.end()) used.push_back(sid);
+    for (int sid : used) {
+      rc = scs_set_segments(ctx, sid, ladder[r], SCS_EQUAL_SNR2);
+      if (rc) return rc;
+    }
+    const double* h = hyper_rows + (size_t)kPsoHyper * r;
+    rc = scs_pso_set_hyper(ctx, -1, h[0], h[1], h[2], h + 3, cuda_stream);
+    if (rc) return rc;
+    rc = scs_pso_reset_bests(ctx, cuda_stream);
+    if (rc) return rc;
+    int64_t done = 0;
+    while (done < max_iters) {
+      rc = scs_pso_run(ctx, chunk_iters, 1, cuda_stream);
+      if (rc) return rc;
+      done += chunk_iters;
+      rc = scs_pso_status(ctx, nullptr, nullptr, cuda_stream);
+      if (rc < 0) return rc;
+      if (rc == 1) break;
+    }
+    if (iters_out) iters_out[r] = done;
+    if (r + 1 < n_rungs && n_clusters > 0) {
+      rc = scs_pso_regroup(ctx, n_clusters, 10, cuda_stream);
+      if (rc) return rc;
+    }
+  }
+  return SCS_OK;
 }
 
 }  // extern "C"

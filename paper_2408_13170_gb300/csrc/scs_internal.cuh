@@ -99,9 +99,42 @@ struct PsoArgs {
   const double* hi;   // 8
   int64_t* iter;      // iteration counter (RNG counter word)
   uint32_t key0, key1;
+  // convergence record per swarm: the best value at the last improvement by
+  // more than conv_delta, and the evaluation index at which it happened
+  double* ref_val;    // S
+  int64_t* ref_iter;  // S
+  double conv_delta;
 };
 void launch_pso_init(const PsoArgs& a, cudaStream_t s);
 void launch_pso_update(const PsoArgs& a, cudaStream_t s);
+// personal and swarm bests forgotten (positions and velocities kept), e.g.
+// when the objective changes to another rung of the segment ladder
+void launch_pso_reset_bests(const PsoArgs& a, cudaStream_t s);
+// gather the per-particle state into a new particle order: new p <- old perm[p]
+// (tmp: scratch of 25 doubles per particle)
+void launch_pso_permute(const PsoArgs& a, const int* perm, double* tmp, cudaStream_t s);
+
+// k-means on the particle positions (search re-clustering): 9 features per
+// particle (box-normalised M_c, q, f0, beta, iota; lambda and psi on circles)
+constexpr int kKmFeat = 9;
+struct KmArgs {
+  const double* pos;   // P x 8, particles [p0, p0 + n)
+  int p0, n;
+  const double* lo;
+  const double* hi;
+  double* cent;        // k x kKmFeat
+  int k;
+  int* label;          // n
+  double* d2;          // n: squared distance to the nearest chosen centroid
+  int* pick;           // 1: scratch for the farthest particle
+};
+// farthest-point seeding: centroids [k0, k) from the particles farthest from
+// centroids [0, j) (lowest index among equals; particle p0 when k0 = 0), then
+// `iters` Lloyd steps (nearest centroid, lowest index among equals; an empty
+// cluster keeps its centroid)
+void launch_kmeans(const KmArgs& a, int k0, int iters, cudaStream_t s);
+// centroid j from the features of position th (device, 8 doubles)
+void launch_km_centroid_of(const KmArgs& a, int j, const double* th, cudaStream_t s);
 // loads the swarm kernels (so that a later stream capture loads nothing); 0 on success
 int preload_pso();
 

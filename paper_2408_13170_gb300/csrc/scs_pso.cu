@@ -65,12 +65,160 @@ __global__ void k_pso_init(const PsoArgs a) {
   a.best_val[p] = -__longlong_as_double(0x7ff0000000000000LL);
 }
 
-__global__ void k_pso_reset_swarms(const PsoArgs a) {
+__global__ void k_pso_reset_swarms(const PsoArgs a, int keep_iter) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= a.S) return;
   a.swarm_val[s] = -__longlong_as_double(0x7ff0000000000000LL);
   for (int d = 0; d < 8; ++d) a.swarm_pos[8 * s + d] = a.lo[d];
-  if (s == 0) *a.iter = 0;
+  a.ref_val[s] = -__longlong_as_double(0x7ff0000000000000LL);
+  a.ref_iter[s] = keep_iter ? *a.iter : 0;
+  if (s == 0 && !keep_iter) *a.iter = 0;
+}
+
+__global__ void k_pso_forget(const PsoArgs a) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= a.P) return;
+  a.best_val[p] = -__longlong_as_double(0x7ff0000000000000LL);
+  for (int d = 0; d < 8; ++d) a.best_pos[8 * (int64_t)p + d] = a.pos[8 * (int64_t)p + d];
+}
+
+// per-particle state in a new order: tmp <- state[perm], then copied back
+__global__ void k_pso_gather(const PsoArgs a, const int* perm, double* tmp) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= a.P) return;
+  const int64_t q = perm[p];
+  double* t = tmp + 26 * (int64_t)p;
+  for (int d = 0; d < 8; ++d) {
+    t[d] = a.pos[8 * q + d];
+    t[8 + d] = a.vel[8 * q + d];
+    t[16 + d] = a.best_pos[8 * q + d];
+  }
+  t[24] = a.best_val[q];
+  t[25] = a.stat[q];
+}
+
+__global__ void k_pso_scatter_back(const PsoArgs a, const double* tmp) {
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= a.P) return;
+  const double* t = tmp + 26 * (int64_t)p;
+  for (int d = 0; d < 8; ++d) {
+    a.pos[8 * (int64_t)p + d] = t[d];
+    a.vel[8 * (int64_t)p + d] = t[8 + d];
+    a.best_pos[8 * (int64_t)p + d] = t[16 + d];
+  }
+  a.best_val[p] = t[24];
+  const_cast<double*>(a.stat)[p] = t[25];
+}
+
+// ------------------------------------------------------------------ k-means
+__device__ inline void km_features(const double* th, const double* lo, const double* hi,
+                                   double f[kKmFeat]) {
+  const int lin[5] = {0, 1, 2, 4, 5};
+#pragma unroll
+  for (int i = 0; i < 5; ++i) f[i] = (th[lin[i]] - lo[lin[i]]) / (hi[lin[i]] - lo[lin[i]]);
+  // lambda and psi: a full period maps to a circle of circumference 1
+  const int per[2] = {3, 6};
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const double u = (th[per[j]] - lo[per[j]]) / (hi[per[j]] - lo[per[j]]);
+    double sn, cs;
+    sincospi(2.0 * u, &sn, &cs);
+    f[5 + 2 * j] = cs * 0.15915494309189535;   // 1 / (2 pi)
+    f[6 + 2 * j] = sn * 0.15915494309189535;
+  }
+}
+
+__global__ void k_km_assign(const KmArgs a, int k) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  double f[kKmFeat];
+  km_features(a.pos + 8 * (int64_t)(a.p0 + i), a.lo, a.hi, f);
+  double best = __longlong_as_double(0x7ff0000000000000LL);
+  int bj = 0;
+  for (int j = 0; j < k; ++j) {
+    double d2 = 0.0;
+#pragma unroll
+    for (int t = 0; t < kKmFeat; ++t) {
+      const double d = f[t] - a.cent[kKmFeat * j + t];
+      d2 += d * d;
+    }
+    if (d2 < best) {
+      best = d2;
+      bj = j;
+    }
+  }
+  a.label[i] = bj;
+  a.d2[i] = best;
+}
+
+// index of the largest d2 (lowest index among equals), one block
+__global__ void k_km_argmax(const KmArgs a) {
+  __shared__ double sv[256];
+  __shared__ int si[256];
+  double bv = -1.0;
+  int bi = 0x7fffffff;
+  for (int i = threadIdx.x; i < a.n; i += blockDim.x) {
+    const double v = a.d2[i];
+    if (v > bv) {
+      bv = v;
+      bi = i;
+    }
+  }
+  sv[threadIdx.x] = bv;
+  si[threadIdx.x] = bi;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      const double v2 = sv[threadIdx.x + o];
+      const int i2 = si[threadIdx.x + o];
+      if (v2 > sv[threadIdx.x] || (v2 == sv[threadIdx.x] && i2 < si[threadIdx.x])) {
+        sv[threadIdx.x] = v2;
+        si[threadIdx.x] = i2;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *a.pick = si[0] < a.n ? si[0] : 0;
+}
+
+// centroid j from particle p0 + *pick (pick == nullptr: particle p0)
+__global__ void k_km_seed(const KmArgs a, int j, int use_pick) {
+  if (threadIdx.x != 0) return;
+  const int i = use_pick ? *a.pick : 0;
+  double f[kKmFeat];
+  km_features(a.pos + 8 * (int64_t)(a.p0 + i), a.lo, a.hi, f);
+  for (int t = 0; t < kKmFeat; ++t) a.cent[kKmFeat * j + t] = f[t];
+}
+
+__global__ void k_km_seed_pos(const KmArgs a, int j, const double* th) {
+  if (threadIdx.x != 0) return;
+  double f[kKmFeat];
+  km_features(th, a.lo, a.hi, f);
+  for (int t = 0; t < kKmFeat; ++t) a.cent[kKmFeat * j + t] = f[t];
+}
+
+// one block per cluster: the mean of its members' features (fixed order)
+__global__ void k_km_mean(const KmArgs a) {
+  const int j = blockIdx.x;
+  __shared__ double sh[256][kKmFeat + 1];
+  double acc[kKmFeat + 1];
+  for (int t = 0; t <= kKmFeat; ++t) acc[t] = 0.0;
+  for (int i = threadIdx.x; i < a.n; i += blockDim.x) {
+    if (a.label[i] != j) continue;
+    double f[kKmFeat];
+    km_features(a.pos + 8 * (int64_t)(a.p0 + i), a.lo, a.hi, f);
+    for (int t = 0; t < kKmFeat; ++t) acc[t] += f[t];
+    acc[kKmFeat] += 1.0;
+  }
+  for (int t = 0; t <= kKmFeat; ++t) sh[threadIdx.x][t] = acc[t];
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+      for (int t = 0; t <= kKmFeat; ++t) sh[threadIdx.x][t] += sh[threadIdx.x + o][t];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && sh[0][kKmFeat] > 0.0)
+    for (int t = 0; t < kKmFeat; ++t) a.cent[kKmFeat * j + t] = sh[0][t] / sh[0][kKmFeat];
 }
 
 __global__ void k_pso_personal(const PsoArgs a) {
@@ -115,9 +263,17 @@ __global__ void k_pso_swarm(const PsoArgs a) {
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0 && si[0] >= 0 && sv[0] > a.swarm_val[s]) {
-    a.swarm_val[s] = sv[0];
-    for (int d = 0; d < 8; ++d) a.swarm_pos[8 * s + d] = a.best_pos[8 * si[0] + d];
+  if (threadIdx.x == 0) {
+    if (si[0] >= 0 && sv[0] > a.swarm_val[s]) {
+      a.swarm_val[s] = sv[0];
+      for (int d = 0; d < 8; ++d) a.swarm_pos[8 * s + d] = a.best_pos[8 * si[0] + d];
+    }
+    // convergence record: the swarm has converged when its best has not
+    // grown by more than conv_delta over a window of evaluations (App. B)
+    if (a.swarm_val[s] > a.ref_val[s] + a.conv_delta) {
+      a.ref_val[s] = a.swarm_val[s];
+      a.ref_iter[s] = *a.iter;
+    }
   }
 }
 
@@ -165,6 +321,7 @@ __global__ void k_pso_tick(int64_t* iter) { *iter += 1; }
 int preload_pso() {
   cudaFuncAttributes at;
   const void* f[] = {(const void*)k_pso_init, (const void*)k_pso_reset_swarms,
+                     (const void*)k_pso_forget,
                      (const void*)k_pso_personal, (const void*)k_pso_swarm,
                      (const void*)k_pso_move, (const void*)k_pso_tick};
   for (const void* k : f)
@@ -174,7 +331,39 @@ int preload_pso() {
 
 void launch_pso_init(const PsoArgs& a, cudaStream_t s) {
   k_pso_init<<<(a.P + 127) / 128, 128, 0, s>>>(a);
-  k_pso_reset_swarms<<<(a.S + 127) / 128, 128, 0, s>>>(a);
+  k_pso_reset_swarms<<<(a.S + 127) / 128, 128, 0, s>>>(a, 0);
+}
+
+void launch_pso_reset_bests(const PsoArgs& a, cudaStream_t s) {
+  k_pso_forget<<<(a.P + 127) / 128, 128, 0, s>>>(a);
+  k_pso_reset_swarms<<<(a.S + 127) / 128, 128, 0, s>>>(a, 1);
+}
+
+void launch_pso_permute(const PsoArgs& a, const int* perm, double* tmp, cudaStream_t s) {
+  k_pso_gather<<<(a.P + 127) / 128, 128, 0, s>>>(a, perm, tmp);
+  k_pso_scatter_back<<<(a.P + 127) / 128, 128, 0, s>>>(a, tmp);
+}
+
+void launch_kmeans(const KmArgs& a, int k0, int iters, cudaStream_t s) {
+  const int nb = (a.n + 127) / 128;
+  for (int j = k0; j < a.k; ++j) {
+    if (j == 0) {
+      k_km_seed<<<1, 32, 0, s>>>(a, 0, 0);
+    } else {
+      k_km_assign<<<nb, 128, 0, s>>>(a, j);
+      k_km_argmax<<<1, 256, 0, s>>>(a);
+      k_km_seed<<<1, 32, 0, s>>>(a, j, 1);
+    }
+  }
+  for (int it = 0; it < iters; ++it) {
+    k_km_assign<<<nb, 128, 0, s>>>(a, a.k);
+    k_km_mean<<<a.k, 256, 0, s>>>(a);
+  }
+  k_km_assign<<<nb, 128, 0, s>>>(a, a.k);
+}
+
+void launch_km_centroid_of(const KmArgs& a, int j, const double* th, cudaStream_t s) {
+  k_km_seed_pos<<<1, 32, 0, s>>>(a, j, th);
 }
 
 void launch_pso_update(const PsoArgs& a, cudaStream_t s) {

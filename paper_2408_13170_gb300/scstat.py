@@ -81,8 +81,17 @@ def lib():
         L.scs_pso_set.argtypes = [P, P, P, P, P, P, P, I64, P]
         L.scs_pso_save.argtypes = [P, P, P, P]
         L.scs_pso_load.argtypes = [P, P, ctypes.c_size_t, P]
+        L.scs_pso_set_convergence.argtypes = [P, D, I]
+        L.scs_pso_status.argtypes = [P, P, P, P]
+        L.scs_pso_reset_bests.argtypes = [P, P]
+        L.scs_pso_layout.argtypes = [P, P, P, P]
+        L.scs_kmeans.argtypes = [P, P, I64, P, P, I, I, P, P, P]
+        L.scs_pso_regroup.argtypes = [P, I, I, P]
+        L.scs_pso_search.argtypes = [P, P, I, P, I, I, I, P, P]
         for f in ("scs_pso_create", "scs_pso_set_hyper", "scs_pso_run", "scs_pso_get",
-                  "scs_pso_set", "scs_pso_save", "scs_pso_load"):
+                  "scs_pso_set", "scs_pso_save", "scs_pso_load", "scs_pso_set_convergence",
+                  "scs_pso_status", "scs_pso_reset_bests", "scs_pso_layout", "scs_kmeans",
+                  "scs_pso_regroup", "scs_pso_search"):
             getattr(L, f).restype = I
         _lib = L
         return L
@@ -274,6 +283,63 @@ def scs_autotune(ctx, stream_id, params, P, cuda_stream=None):
     return best.value, ms
 
 
+def scs_pso_set_convergence(ctx, delta=2.0, window=50):
+    _check(ctx, lib().scs_pso_set_convergence(ctx, float(delta), int(window)))
+
+
+def scs_pso_layout(ctx):
+    """(stream_ids[S], swarm_offsets[S + 1]) of the current swarms."""
+    n = ctypes.c_int()
+    _check(ctx, lib().scs_pso_layout(ctx, ctypes.byref(n), None, None))
+    sids = np.empty(n.value, np.int32)
+    offs = np.empty(n.value + 1, np.int64)
+    _check(ctx, lib().scs_pso_layout(ctx, ctypes.byref(n), _ptr(sids), _ptr(offs)))
+    return sids, offs
+
+
+def scs_pso_status(ctx, cuda_stream=None):
+    """(all converged, converged[S], iteration)."""
+    S = len(scs_pso_layout(ctx)[0])
+    conv = np.zeros(S, np.int32)
+    it = ctypes.c_int64()
+    rc = lib().scs_pso_status(ctx, _ptr(conv), ctypes.byref(it), _stream(cuda_stream))
+    if rc < 0:
+        _check(ctx, rc)
+    return rc == 1, conv.astype(bool), it.value
+
+
+def scs_pso_reset_bests(ctx, cuda_stream=None):
+    _check(ctx, lib().scs_pso_reset_bests(ctx, _stream(cuda_stream)))
+
+
+def scs_kmeans(ctx, pos, prior_lo, prior_hi, k, iters, cuda_stream=None):
+    """(labels[P], centroids[k, 9]) of P x 8 positions."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 8)
+    lo = np.ascontiguousarray(prior_lo, dtype=np.float64)
+    hi = np.ascontiguousarray(prior_hi, dtype=np.float64)
+    lab = np.empty(len(pos), np.int32)
+    cen = np.empty((k, 9))
+    _check(ctx, lib().scs_kmeans(ctx, _ptr(pos), len(pos), _ptr(lo), _ptr(hi), int(k),
+                                 int(iters), _ptr(lab), _ptr(cen), _stream(cuda_stream)))
+    return lab, cen
+
+
+def scs_pso_regroup(ctx, n_clusters, iters=10, cuda_stream=None):
+    _check(ctx, lib().scs_pso_regroup(ctx, int(n_clusters), int(iters), _stream(cuda_stream)))
+
+
+def scs_pso_search(ctx, ladder, hyper_rows, n_clusters, chunk_iters, max_iters,
+                   cuda_stream=None):
+    """Runs the ladder; returns the iterations spent on each rung."""
+    lad = np.ascontiguousarray(ladder, dtype=np.int32)
+    rows = np.ascontiguousarray(hyper_rows, dtype=np.float64).reshape(len(lad), 11)
+    its = np.zeros(len(lad), np.int64)
+    _check(ctx, lib().scs_pso_search(ctx, _ptr(lad), len(lad), _ptr(rows), int(n_clusters),
+                                     int(chunk_iters), int(max_iters), _ptr(its),
+                                     _stream(cuda_stream)))
+    return its
+
+
 def scs_set_profiling(ctx, enable: bool):
     _check(ctx, lib().scs_set_profiling(ctx, 1 if enable else 0))
 
@@ -386,7 +452,8 @@ class Context:
         scs_pso_run(self.h, iters, use_graph)
 
     def pso_get(self):
-        P, S = self._pso_P, self._pso_S
+        P = self._pso_P
+        S = len(scs_pso_layout(self.h)[0])
         st = dict(pos=np.empty((P, 8)), vel=np.empty((P, 8)), best_pos=np.empty((P, 8)),
                   best_val=np.empty(P), swarm_pos=np.empty((S, 8)), swarm_val=np.empty(S),
                   stat=np.empty(P))
@@ -405,3 +472,9 @@ class Context:
         scs_pso_load(self.h, blob)
         P, S = np.frombuffer(blob, np.int64, 2, 8)
         self._pso_P, self._pso_S = int(P), int(S)
+
+    def pso_search(self, ladder, n_clusters=0, chunk_iters=10, max_iters=200):
+        """The hierarchical search with the Table III row of each rung."""
+        rows = [np.concatenate([[om, pp, pg], eps])
+                for om, pp, pg, eps in (table3_hyper(N) for N in ladder)]
+        return scs_pso_search(self.h, ladder, rows, n_clusters, chunk_iters, max_iters)

@@ -219,3 +219,82 @@ def test_two_hundred_iterations_in_one_graph(scstat, datas):
         _same(sa, sb)
         assert sa["iteration"] == 200
         assert np.all(np.isfinite(sa["swarm_val"]))
+
+
+def test_kmeans_matches_reference(scstat, datas):
+    rng = np.random.default_rng(5)
+    centers = np.array([[20, 2, 0.0178, 1.0, -0.5, 0.5, 0.3, 0],
+                        [80, 6, 0.0186, 5.5, 0.8, 2.5, 2.8, 0],
+                        [50, 4, 0.0182, 6.2, 0.0, 1.5, 0.05, 0]], float)
+    pos = np.vstack([c + rng.normal(0, 0.02, (300, 8)) * (HI - LO) for c in centers])
+    pos = np.vstack([pos, LO + rng.random((60, 8)) * (HI - LO)])   # scatter
+    pos[:, 3] %= 2 * math.pi
+    pos[:, 6] %= math.pi
+    pos[:, 7] = 0.0
+    with scstat.Context(0, scstat.SCS_MIXED) as ctx:
+        for k in (3, 5):
+            lab, cen = scstat.scs_kmeans(ctx.h, pos, LO, HI, k, 8)
+            rlab, rcen = rpso.kmeans(pos, LO, HI, k, 8)
+            np.testing.assert_array_equal(lab, rlab)
+            np.testing.assert_allclose(cen, rcen, rtol=0, atol=1e-12)
+
+
+def test_convergence_record_follows_the_rule(scstat, datas):
+    with _ctx(scstat, datas, scstat.SCS_MIXED) as ctx:
+        _setup(scstat, ctx)
+        scstat.scs_pso_set_convergence(ctx.h, 1.0, 3)
+        hist, flags = [], []
+        for _ in range(30):
+            ctx.pso_run(1, use_graph=False)
+            hist.append(ctx.pso_get()["swarm_val"].copy())
+            flags.append(scstat.scs_pso_status(ctx.h)[1])
+        ref = rpso.converged_flags(np.array(hist), 1.0, 3)
+        np.testing.assert_array_equal(np.array(flags), ref)
+        assert ref.any()
+
+
+def test_regroup_keeps_particles_and_streams(scstat, datas):
+    with _ctx(scstat, datas, scstat.SCS_MIXED) as ctx:
+        ctx.pso_create([0, 1, 0], [30, 50, 40], LO, HI, 3)
+        ctx.pso_run(5, use_graph=True)
+        before = ctx.pso_get()
+        scstat.scs_pso_regroup(ctx.h, 4, 6)
+        sids, offs = scstat.scs_pso_layout(ctx.h)
+        after = ctx.pso_get()
+        assert offs[-1] == 120 and np.all(np.diff(offs) > 0)
+        # stream 0's 70 particles first (up to 4 swarms), then stream 1's 50
+        n0 = sum(offs[i + 1] - offs[i] for i in range(len(sids)) if sids[i] == 0)
+        assert n0 == 70 and list(sids) == sorted(sids, key=lambda s: s != 0)
+        key = lambda a: a[np.lexsort(a.T[::-1])]
+        np.testing.assert_array_equal(key(after["pos"][:70]),
+                                      key(np.vstack([before["pos"][:30], before["pos"][80:]])))
+        np.testing.assert_array_equal(key(after["pos"][70:]), key(before["pos"][30:80]))
+        assert np.all(after["best_val"] == -np.inf) and np.all(after["swarm_val"] == -np.inf)
+        ctx.pso_run(3, use_graph=True)   # the new layout runs (graph re-captured)
+        assert np.all(np.isfinite(ctx.pso_get()["swarm_val"]))
+
+
+def test_search_ladder_finds_the_injection(scstat):
+    """The hierarchical search (ladder 16 -> 4 -> 1, re-clustering between
+    rungs) on a loud injection climbs to the coherent statistic of the
+    injected parameters."""
+    d = synth.make_stream(dict(T_obs=3e6, f_min=0.0175, f_max=0.0200, seed=51))
+    th = synth.injection_params(d["rng"], 30.0, 1.5, 0.018)
+    oracle.inject(th, d["f_first"], d["df"], d["K"], d["T_obs"], d["SA"], d["SE"], 30.0,
+                  d["A"], d["E"])
+    lo = th.copy()
+    hi = th.copy()
+    lo[:3] = th[:3] * np.array([0.9, 0.8, 0.999])
+    hi[:3] = th[:3] * np.array([1.1, 1.2, 1.001])
+    lo[3:7] = [0, -math.pi / 2, 0, 0]
+    hi[3:7] = [2 * math.pi, math.pi / 2, math.pi, math.pi]
+    lo[7] = hi[7] = 0.0
+    with scstat.Context(0, scstat.SCS_MIXED) as ctx:
+        ctx.set_data(0, d)
+        ctx.set_segments(0, 1, scstat.SCS_EQUAL_SNR2)
+        target = ctx.eval(0, th)[0]
+        ctx.pso_create([0, 0], [256, 256], lo, hi, 11)
+        its = ctx.pso_search([16, 4, 1], n_clusters=2, chunk_iters=10, max_iters=150)
+        assert np.all(its >= 10)
+        st = ctx.pso_get()
+        assert st["swarm_val"].max() >= 0.8 * target

@@ -180,3 +180,28 @@ def test_swarm_climbs_a_concave_objective():
         bp, bv, sp, sv = pso.pso_bests(f(pos), pos, bp, bv, sp, sv, off)
         pos, vel = pso.pso_step(pos, vel, bp, sp, swarm_of, h, lo, hi, 5, it)
     assert np.all(np.abs(sp[:, :7] - target[:7]) < 1e-4)
+
+
+def test_kmeans_reference_separates_blobs():
+    rng = np.random.default_rng(5)
+    centers = np.array([[20, 2, 0.014, 1.0, -0.5, 0.5, 0.3, 0],
+                        [80, 6, 0.025, 5.5, 0.8, 2.5, 2.8, 0],
+                        [50, 4, 0.020, 3.0, 0.0, 1.5, 1.5, 0]], float)
+    pos = np.vstack([c + rng.normal(0, 0.01, (40, 8)) * (HI - LO) for c in centers])
+    pos[:, 7] = 0
+    lab, cent = pso.kmeans(pos, LO, HI, 3, 5)
+    # each blob is one cluster
+    for b in range(3):
+        assert len(set(lab[40 * b:40 * (b + 1)])) == 1
+    assert len(set(lab)) == 3
+    # periodic dimension: lambda near 0 and near 2 pi are neighbours
+    f = pso.km_features(np.array([[50, 4, 0.02, 0.01, 0, 1, 1, 0],
+                                  [50, 4, 0.02, 2 * np.pi - 0.01, 0, 1, 1, 0]]), LO, HI)
+    assert np.sum((f[0] - f[1]) ** 2) < 2e-5   # (0.02 / 2 pi)^2, not ~1
+
+
+def test_convergence_rule_reference():
+    h = np.array([[1.0], [2.0], [3.5], [3.6], [3.7], [3.8], [6.0], [6.1], [6.2], [6.3]])
+    flags = pso.converged_flags(h, 2.0, 3)[:, 0]
+    # improvements by > 2: at 0 (-inf -> 1), 2 (1 -> 3.5), 6 (3.5 -> 6.0)
+    assert list(flags) == [False, False, False, False, False, True, False, False, False, True]
