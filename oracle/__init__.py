@@ -188,3 +188,29 @@ def evaluate(data, params, N, mode=EQUAL_WIDTH, waveform=TF2,
     if want_kappa:
         out.append(kap)
     return out[0] if len(out) == 1 else tuple(out)
+
+
+def inner_dd(data):
+    """<d|d> = sum_alpha sum_k 4 df |d_alpha(f_k)|^2 / S_alpha(f_k) (Eq. inner_prod
+    on the FFT grid)."""
+    SA = np.asarray(data["SA"], np.float64)
+    SE = SA if data.get("SE") is None else np.asarray(data["SE"], np.float64)
+    A = np.asarray(data["A"])
+    E = np.asarray(data["E"])
+    return float(np.sum(4.0 * data["df"] * np.abs(A) ** 2 / SA)
+                 + np.sum(4.0 * data["df"] * np.abs(E) ** 2 / SE))
+
+
+def loglike(data, params, N, mode=EQUAL_WIDTH, amp=None):
+    """Semi-coherent log-likelihood (Sec. II.B):
+    log L_N = -<d|d>/2 - <h|h>/2 + O_N(d, h),  O_N = sum_n x_n,
+    for the templates a * h(theta) (a: amplitude per particle, default 1).
+    Returns (logL, O_N of the unit templates, <h|h> of the unit templates)."""
+    params = np.ascontiguousarray(params, dtype=np.float64).reshape(-1, 8)
+    stat, sx, sh = evaluate(data, params, N, mode=mode, want_segments=True)
+    a = np.ones(len(params)) if amp is None else np.asarray(amp, np.float64)
+    O = sx.sum(axis=1)
+    H = sh.sum(axis=1)
+    L = -0.5 * inner_dd(data) - 0.5 * a * a * H + a * O
+    L = np.where(np.isfinite(stat), L, -np.inf)
+    return L, O, H

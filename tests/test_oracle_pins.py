@@ -505,3 +505,22 @@ def test_phase_precision_floor():
         got = oracle.phase_turns(th, f_first, df, k)
         assert abs(got - frac) < 1e-13
         assert abs(float(F)) > 1e5
+
+
+@pytest.mark.parametrize("mode", [oracle.EQUAL_WIDTH, oracle.EQUAL_SNR2])
+def test_loglike_zero_at_noise_free_truth_and_quadratic_in_amplitude(mode):
+    """log L_N = -<d|d>/2 - <h|h>/2 + O_N (Sec. II.B): for noise-free d = a h(theta)
+    every segment has x_n = a [h|h]_n, so log L_N(theta, a) = 0 for every N, and
+    log L_N(theta, a') = -(a - a')^2 <h|h> / 2 exactly."""
+    d = synth.make_stream(dict(T_obs=3e6, f_min=0.0175, f_max=0.0200, seed=3), noise_free=True)
+    th = synth.injection_params(d["rng"], 30.0, 1.5, 0.018)
+    hh0 = oracle.inject(th, d["f_first"], d["df"], d["K"], d["T_obs"], d["SA"], d["SE"], 12.0,
+                        d["A"], d["E"])
+    a = 12.0 / math.sqrt(hh0)
+    for N in (1, 7, 64):
+        L, O, H = oracle.loglike(d, th[None, :], N, mode=mode, amp=[a])
+        assert abs(L[0]) <= 1e-9 * 144.0
+        assert H[0] == pytest.approx(hh0, rel=1e-12)
+        for a2 in (0.5 * a, 1.7 * a):
+            L2, _, _ = oracle.loglike(d, th[None, :], N, mode=mode, amp=[a2])
+            assert L2[0] == pytest.approx(-0.5 * (a - a2) ** 2 * hh0, rel=1e-9, abs=1e-9)
