@@ -119,6 +119,21 @@ int scs_eval_stat(scs_ctx *ctx, int stream_id, const double *params,
                   int64_t P, double *stat, double *seg_x, double *seg_hh,
                   void *cuda_stream);
 
+/* Semi-coherent log-likelihood (Sec. II.B) of P templates a_p h(theta_p):
+ *   log L_N = -<d|d>/2 - a^2 <h|h>/2 + a O_N,  O_N = sum_n x_n,
+ *   <h|h> = sum_n [h|h]_n,
+ * on the stream's segmentation, where h(theta) is this library's template
+ * (Sec. IV form f^{-7/6} T_alpha e^{-i Psi}, the normalisation of
+ * scs_waveform) and a_p = amp[p] carries the physical amplitude (NULL: 1).
+ *   loglike P doubles (-inf for non-physical particles); overlap (O_N) and
+ *   hh (<h|h>) P doubles each of the unit templates, may be NULL.  Any array
+ *   host or device.  Uses the evaluation of scs_eval_stat with per-segment
+ *   outputs (P x N doubles of scratch).
+ * Errors: as scs_eval_stat. */
+int scs_eval_loglike(scs_ctx *ctx, int stream_id, const double *params, int64_t P,
+                     const double *amp, double *loglike, double *overlap, double *hh,
+                     void *cuda_stream);
+
 /* Several data streams in one evaluation (one persistent launch): item i
  * evaluates particles P_offsets[i] .. P_offsets[i+1]-1 of params on stream
  * stream_ids[i] with that stream's grid, data and segmentation (streams may

@@ -84,6 +84,7 @@ struct scs_ctx {
   std::map<int, DataStream> streams;
   DevBuf slot[kNumSlots];          // pipeline scratch (grow-only)
   DevBuf params, stat, segx, segh, tmpA, tmpE, tmpS1, tmpS2, red, misc;
+  DevBuf ll_x, ll_h, ll_stat, ll_amp, ll_out, ll_o, ll_hh;   // log-likelihood call
   // device-side particle swarm (scs_pso_*)
   struct Pso {
     bool made = false;
@@ -445,8 +446,10 @@ void scs_destroy(scs_ctx* ctx) {
                     &q.km_pick};
     for (DevBuf* b : pb) b->release();
   }
-  DevBuf* bufs[] = {&ctx->params, &ctx->stat, &ctx->segx, &ctx->segh, &ctx->tmpA,
-                    &ctx->tmpE, &ctx->tmpS1, &ctx->tmpS2, &ctx->red, &ctx->misc};
+  DevBuf* bufs[] = {&ctx->params, &ctx->stat,  &ctx->segx,   &ctx->segh,   &ctx->tmpA,
+                    &ctx->tmpE,   &ctx->tmpS1, &ctx->tmpS2,  &ctx->red,    &ctx->misc,
+                    &ctx->ll_x,   &ctx->ll_h,  &ctx->ll_stat, &ctx->ll_amp, &ctx->ll_out,
+                    &ctx->ll_o,   &ctx->ll_hh};
   for (DevBuf* b : bufs) b->release();
   for (cudaEvent_t& e : ctx->ev)
     if (e) cudaEventDestroy(e);
@@ -671,6 +674,68 @@ int scs_batch_eval(scs_ctx* ctx, const int* stream_ids, const int64_t* P_offsets
   if (rc) return rc;
   if (!stat_dev) CK(cudaMemcpyAsync(stat, dstat, sizeof(double) * P, cudaMemcpyDeviceToHost, s));
   if (!stat_dev || !is_device_ptr(params)) CK(cudaStreamSynchronize(s));
+  return SCS_OK;
+}
+
+int scs_eval_loglike(scs_ctx* ctx, int sid, const double* params, int64_t P, const double* amp,
+                     double* loglike, double* overlap, double* hh, void* cuda_stream) {
+  if (!ctx) return SCS_EINVAL;
+  if (!params || !loglike) return fail(ctx, SCS_EINVAL, "null params or loglike");
+  if (P < 1 || P > (1 << 24)) return fail(ctx, SCS_EINVAL, "P = %lld out of range", (long long)P);
+  int rc = bind(ctx);
+  if (rc) return rc;
+  DataStream* ds = get_stream(ctx, sid, true);
+  if (!ds) return SCS_ENODATA;
+  const int N = ds->N;
+  if ((double)P * N > 4e9) return fail(ctx, SCS_EINVAL, "P x N too large");
+  cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : ctx->stream;
+  const size_t PN = (size_t)P * N;
+  CK(ctx->ll_x.reserve(sizeof(double) * PN));
+  CK(ctx->ll_h.reserve(sizeof(double) * PN));
+  CK(ctx->ll_stat.reserve(sizeof(double) * P));
+  rc = scs_eval_stat(ctx, sid, params, P, ctx->ll_stat.as<double>(), ctx->ll_x.as<double>(),
+                     ctx->ll_h.as<double>(), s);
+  if (rc) return rc;
+  const double* damp = nullptr;
+  if (amp) {
+    if (is_device_ptr(amp)) {
+      damp = amp;
+    } else {
+      CK(ctx->ll_amp.reserve(sizeof(double) * P));
+      CK(cudaMemcpyAsync(ctx->ll_amp.ptr, amp, sizeof(double) * P, cudaMemcpyHostToDevice, s));
+      damp = ctx->ll_amp.as<double>();
+    }
+  }
+  CK(ctx->red.reserve(sizeof(double) * 1025));
+  k_dd<<<1024, 256, 0, s>>>(ds->dA64.as<double2>(), ds->dE64.as<double2>(),
+                            ds->w64.as<double2>(), ds->K, ctx->red.as<double>());
+  CKLAUNCH();
+  k_sum<<<1, 256, 0, s>>>(ctx->red.as<double>(), 1024, ctx->red.as<double>() + 1024);
+  CKLAUNCH();
+  double* outs[3] = {loglike, overlap, hh};
+  DevBuf* stage[3] = {&ctx->ll_out, &ctx->ll_o, &ctx->ll_hh};
+  double* dev[3];
+  bool host_out = false;
+  for (int i = 0; i < 3; ++i) {
+    dev[i] = nullptr;
+    if (!outs[i]) continue;
+    if (is_device_ptr(outs[i])) {
+      dev[i] = outs[i];
+    } else {
+      CK(stage[i]->reserve(sizeof(double) * P));
+      dev[i] = stage[i]->as<double>();
+      host_out = true;
+    }
+  }
+  k_loglike<<<(int)((P + 127) / 128), 128, 0, s>>>(ctx->ll_x.as<double>(), ctx->ll_h.as<double>(),
+                                                   ctx->ll_stat.as<double>(), (int)P, N, damp,
+                                                   ctx->red.as<double>() + 1024, dev[0], dev[1],
+                                                   dev[2]);
+  CKLAUNCH();
+  for (int i = 0; i < 3; ++i)
+    if (outs[i] && dev[i] != outs[i])
+      CK(cudaMemcpyAsync(outs[i], dev[i], sizeof(double) * P, cudaMemcpyDeviceToHost, s));
+  if (host_out || (amp && damp != amp) || !is_device_ptr(params)) CK(cudaStreamSynchronize(s));
   return SCS_OK;
 }
 

@@ -597,6 +597,57 @@ __global__ void k_hh(const double2* hA, const double2* hE, const double2* w64, i
   if (threadIdx.x == 0) out[blockIdx.x] = sm[0];
 }
 
+// <d|d> partial sums: sum_k |d~_A|^2 / w_A + |d~_E|^2 / w_E (d~ = w d)
+__global__ void k_dd(const double2* dA64, const double2* dE64, const double2* w64, int K,
+                     double* out) {
+  __shared__ double sm[256];
+  double s = 0.0;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
+    double2 a = dA64[k], e = dE64[k], w = w64[k];
+    s += (a.x * a.x + a.y * a.y) / w.x + (e.x * e.x + e.y * e.y) / w.y;
+  }
+  sm[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = sm[0];
+}
+
+// one block: out[0] = sum of n partial sums (fixed order)
+__global__ void k_sum(const double* in, int n, double* out) {
+  __shared__ double sm[256];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += in[i];
+  sm[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = sm[0];
+}
+
+// Semi-coherent log-likelihood (Sec. II.B) of templates a h(theta):
+// log L_N = -<d|d>/2 - a^2 <h|h>/2 + a O_N, O_N = sum_n x_n, <h|h> = sum_n [h|h]_n
+__global__ void k_loglike(const double* seg_x, const double* seg_hh, const double* stat, int P,
+                          int N, const double* amp, const double* dd, double* L, double* O,
+                          double* H) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  double o = 0.0, h = 0.0;
+  for (int n = 0; n < N; ++n) {
+    o += seg_x[(int64_t)p * N + n];
+    h += seg_hh[(int64_t)p * N + n];
+  }
+  const double a = amp ? amp[p] : 1.0;
+  const bool ok = stat[p] > -__longlong_as_double(0x7ff0000000000000LL);
+  L[p] = ok ? -0.5 * dd[0] - 0.5 * a * a * h + a * o : -__longlong_as_double(0x7ff0000000000000LL);
+  if (O) O[p] = o;
+  if (H) H[p] = h;
+}
+
 // d~ += s w h (injection) and refresh the scaled FP32 copy
 __global__ void k_add_template(const double2* hA, const double2* hE, double s, int K,
                                double2* dA64, double2* dE64, const double2* w64,

@@ -31,6 +31,12 @@ __global__ void k_hh(const double2* hA, const double2* hE, const double2* w64, i
 __global__ void k_add_template(const double2* hA, const double2* hE, double s, int K,
                                double2* dA64, double2* dE64, const double2* w64,
                                const unsigned long long* wmax, float4* d32);
+__global__ void k_dd(const double2* dA64, const double2* dE64, const double2* w64, int K,
+                     double* out);
+__global__ void k_sum(const double* in, int n, double* out);
+__global__ void k_loglike(const double* seg_x, const double* seg_hh, const double* stat, int P,
+                          int N, const double* amp, const double* dd, double* L, double* O,
+                          double* H);
 __global__ void k_width_edges(int64_t K, int N, int* e);
 __global__ void k_support_out(const Part* part, int P, int64_t* klo, int64_t* khi,
                               int32_t* l2b);

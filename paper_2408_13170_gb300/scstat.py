@@ -69,6 +69,8 @@ def lib():
         L.scs_eval_stat_noalloc.restype = I
         L.scs_batch_eval.argtypes = [P, P, P, I, P, P, P]
         L.scs_batch_eval.restype = I
+        L.scs_eval_loglike.argtypes = [P, I, P, I64, P, P, P, P, P]
+        L.scs_eval_loglike.restype = I
         L.scs_set_tile.argtypes = [P, I, I]
         L.scs_set_tile.restype = I
         L.scs_autotune.argtypes = [P, I, P, I64, P, P, P]
@@ -270,6 +272,13 @@ def scs_pso_load(ctx, blob: bytes, cuda_stream=None):
     _check(ctx, lib().scs_pso_load(ctx, buf, len(blob), _stream(cuda_stream)))
 
 
+def scs_eval_loglike(ctx, stream_id, params, P, loglike, amp=None, overlap=None, hh=None,
+                     cuda_stream=None):
+    _check(ctx, lib().scs_eval_loglike(ctx, stream_id, _ptr(params), int(P), _ptr(amp),
+                                       _ptr(loglike), _ptr(overlap), _ptr(hh),
+                                       _stream(cuda_stream)))
+
+
 def scs_set_tile(ctx, stream_id, log2_chunk):
     _check(ctx, lib().scs_set_tile(ctx, stream_id, int(log2_chunk)))
 
@@ -401,6 +410,15 @@ class Context:
             return stat, sx, sh
         scs_eval_stat(self.h, stream_id, params, P, stat)
         return stat
+
+    def loglike(self, stream_id, params, amp=None):
+        """(log L_N, O_N, <h|h>) per particle (Sec. II.B)."""
+        params = np.ascontiguousarray(params, dtype=np.float64).reshape(-1, 8)
+        P = params.shape[0]
+        L, O, H = np.empty(P), np.empty(P), np.empty(P)
+        a = None if amp is None else np.ascontiguousarray(amp, dtype=np.float64)
+        scs_eval_loglike(self.h, stream_id, params, P, L, a, O, H)
+        return L, O, H
 
     def batch_eval(self, stream_ids, params_list):
         """One launch over several streams; returns one stat array per item."""

@@ -306,3 +306,37 @@ def test_tiles_give_same_bits_and_autotune(scstat, small):
     with pytest.raises(scstat.ScsError):
         scstat.scs_set_tile(ctx.h, 0, 10)
     scstat.scs_set_tile(ctx.h, 0, 12)
+
+
+@pytest.mark.parametrize("path", ["fp64", "mixed"])
+@pytest.mark.parametrize("N", [1, 16])
+def test_loglike_parity(scstat, small, path, N):
+    """Semi-coherent log-likelihood (Sec. II.B) against the oracle; zero at the
+    noise-free truth with the injected amplitude."""
+    d, th, ctx = small
+    ctx.set_path(scstat.SCS_FP64 if path == "fp64" else scstat.SCS_MIXED)
+    ctx.set_segments(0, N, oracle.EQUAL_SNR2)
+    amp = np.linspace(0.5, 2.0, len(th)) * 1e-20
+    L, O, H = ctx.loglike(0, th, amp)
+    rL, rO, rH = oracle.loglike(d, th, N, mode=oracle.EQUAL_SNR2, amp=amp)
+    tol = TOL64 if path == "fp64" else TOL32
+    ok = np.isfinite(rL)
+    assert np.array_equal(np.isfinite(L), ok)
+    assert rel_err(O[ok], rO[ok]) <= tol * 10 and rel_err(H[ok], rH[ok]) <= tol
+    scale = 0.5 * oracle.inner_dd(d) + np.abs(amp * rO) + amp * amp * rH
+    assert np.max(np.abs(L[ok] - rL[ok]) / scale[ok]) <= tol
+
+
+def test_loglike_zero_at_noise_free_truth(scstat):
+    d = synth.make_stream(dict(T_obs=3e6, f_min=0.0175, f_max=0.0200, seed=8), noise_free=True)
+    th = synth.injection_params(d["rng"], 30.0, 1.5, 0.018)
+    hh0 = oracle.inject(th, d["f_first"], d["df"], d["K"], d["T_obs"], d["SA"], d["SE"], 12.0,
+                        d["A"], d["E"])
+    a = 12.0 / np.sqrt(hh0)
+    with scstat.Context(0, scstat.SCS_FP64) as ctx:
+        ctx.set_data(0, d)
+        for N in (1, 8):
+            ctx.set_segments(0, N, scstat.SCS_EQUAL_SNR2)
+            L, O, H = ctx.loglike(0, th[None, :], [a])
+            assert abs(L[0]) <= 1e-8 * 144.0
+            assert H[0] == pytest.approx(hh0, rel=1e-10)
