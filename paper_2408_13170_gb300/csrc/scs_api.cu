@@ -763,8 +763,12 @@ int scs_autotune(scs_ctx* ctx, int sid, const double* params, int64_t P, int* lo
   const double* dparams = nullptr;
   rc = stage_params(ctx, params, P, s, &dparams);
   if (rc) return rc;
-  DevBuf out;
+  DevBuf out, flush;
   CK(out.reserve(sizeof(double) * P));
+  // each timed evaluation starts with a cold L2 (129 MB on GB300), as a new
+  // batch of a large problem does
+  const size_t kFlushBytes = size_t(192) << 20;
+  CK(flush.reserve(kFlushBytes));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
@@ -777,6 +781,10 @@ int scs_autotune(scs_ctx* ctx, int sid, const double* params, int64_t P, int* lo
     ds->log2_chunk = l;
     float t = 0.f;
     for (int rep = 0; rep < 4 && !rc; ++rep) {   // the first one sizes the scratch
+      if (cudaMemsetAsync(flush.ptr, rep, kFlushBytes, s) != cudaSuccess) {
+        rc = fail(ctx, SCS_ECUDA, "autotune flush failed");
+        break;
+      }
       cudaEventRecord(e0, s);
       rc = scs_eval_stat(ctx, sid, dparams, P, out.as<double>(), nullptr, nullptr, s);
       cudaEventRecord(e1, s);
@@ -799,6 +807,7 @@ int scs_autotune(scs_ctx* ctx, int sid, const double* params, int64_t P, int* lo
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   out.release();
+  flush.release();
   ds->log2_chunk = rc ? keep : best;
   ds->gen++;
   if (log2_chunk) *log2_chunk = ds->log2_chunk;
