@@ -242,7 +242,8 @@ def run_swarm(args, rank, world, local):
         "metric": METRIC, "value": value, "unit": "particle-evals/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 (f64 anchors and segment totals)", "data": "synthetic",
+        "dtype": "f32", "dtype_note": "f32/int32 per bin; f64 anchors, edges and segment totals",
+        "data": "synthetic",
         "config": {"workload": "C4: uneven batch, 8 streams of 1-4 yr, swarms "
                                f"{sizes}, N {[c['N'] for c in cfgs]}, equal-SNR^2; "
                                f"{G} swarm iterations per CUDA-graph launch",
@@ -401,7 +402,8 @@ def main():
         "metric": METRIC, "value": value, "unit": "particle-evals/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 (f64 anchors and segment totals)", "data": "synthetic",
+        "dtype": "f32", "dtype_note": "f32/int32 per bin; f64 anchors, edges and segment totals",
+        "data": "synthetic",
         "config": {"workload": f"{WORKLOAD}: one-year stream T=3.15e7 s, K={d['K']} bins x "
                                f"TDI A,E; P={P} particles uniform in the prior box; "
                                f"N={N} equal-SNR^2 segments; injection SNR {cfg['snr']}",

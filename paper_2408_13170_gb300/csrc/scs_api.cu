@@ -359,7 +359,6 @@ int run_batch(scs_ctx* ctx, const Prepared& pr, int P, double* dstat, double* ds
   a.rec = rec;
   a.seg_x = dsx;
   a.seg_hh = dsh;
-  a.err = counter + 1;
   a.chunk_lo = 0;
   a.chunk_hi = pr.n_chunks;
   a.item_counter = counter;

@@ -70,7 +70,6 @@ struct EvalArgs {
   // per-segment outputs (single-stream calls only; NULL otherwise)
   double* seg_x;
   double* seg_hh;
-  int* err;
 };
 
 // segment edge table of particle p (e_0 .. e_N, non-decreasing)

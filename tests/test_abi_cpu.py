@@ -45,3 +45,23 @@ def test_create_without_device_fails_cleanly():
         assert not h.value
     assert scstat.lib().scs_create(ctypes.byref(h), 0, 7) == scstat.SCS_EINVAL
     assert scstat.lib().scs_create(None, 0, 0) == scstat.SCS_EINVAL
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch):
+    """No CPU fallback: if the library cannot be built or loaded, the
+    binding raises instead of computing anything."""
+    from paper_2408_13170_gb300 import scstat, build
+
+    def broken(*a, **k):
+        raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libscstat")
+
+    saved = scstat._lib
+    monkeypatch.setattr(build, "build", broken)
+    monkeypatch.setattr(scstat, "_lib", None)
+    try:
+        with pytest.raises(RuntimeError):
+            scstat.lib()
+        with pytest.raises(RuntimeError):
+            scstat.Context(0)
+    finally:
+        scstat._lib = saved
