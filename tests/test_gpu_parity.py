@@ -340,3 +340,19 @@ def test_loglike_zero_at_noise_free_truth(scstat):
             L, O, H = ctx.loglike(0, th[None, :], [a])
             assert abs(L[0]) <= 1e-8 * 144.0
             assert H[0] == pytest.approx(hh0, rel=1e-10)
+
+
+@pytest.mark.parametrize("N", [1500, 5000])
+def test_snr2_segments_outnumber_support_bins(scstat, small, N):
+    """Equal-SNR^2 segmentations finer than the supports: most segments hold
+    zero or one bin (coinciding edges, empty segments), on both paths, with
+    per-segment outputs."""
+    d, th, ctx = small
+    ctx.set_segments(0, N, scstat.SCS_EQUAL_SNR2)
+    ref, rx, rh = oracle.evaluate(d, th, N, mode=oracle.EQUAL_SNR2, want_segments=True)
+    for path, tol in ((scstat.SCS_FP64, TOL64), (scstat.SCS_MIXED, TOL32)):
+        ctx.set_path(path)
+        stat, sx, sh = ctx.eval(0, th, N, segments=True)
+        assert rel_err(stat, ref) <= tol
+        scale = np.maximum(rh.max(axis=1, keepdims=True), 1e-300)
+        assert np.max(np.abs(sh - rh) / scale) <= tol
