@@ -121,6 +121,7 @@ __device__ __forceinline__ void run_block(Lane& L, const ItemStream& a, double z
   float4 dn = __ldg(a.d32 + k0);
   float2 wn = __ldg(a.w32 + k0);
   const unsigned span = L.act ? (unsigned)(L.ke - L.kb) : 0u;
+#pragma unroll 2
   for (int i = 0; i < nb; ++i) {
     const int k = k0 + i;
     const float4 dv = dn;
