@@ -32,9 +32,9 @@ WORKLOAD = "C2"
 ALG_OPS_PER_BIN = 36
 LAUNCHES_PER_STEP = 8   # setup, scan, chunk table, fill, sort, edges, main, fix-up
 # DRAM bytes (read + write) of one k_main_mixed launch on this workload at full
-# size with the 2048-bin tile, from an ncu capture of this kernel
+# size, per work tile (log2 bins), from ncu captures of this kernel
 # (profiles/k_main_mixed_C2.md); to be re-taken whenever the kernel changes.
-MAIN_TRAFFIC_BYTES = 72.67e6 + 24.47e6
+MAIN_TRAFFIC_BYTES = {11: 72.53e6 + 24.34e6, 12: 68.18e6 + 7.53e6}
 
 
 def parse():
@@ -417,7 +417,7 @@ def main():
             ("setup_worklist", "segment_edges", "main", "fixup"), stages.mean(axis=0))},
         "roofline": {"bound": "alu", "kernel": "k_main_mixed", "achieved": achieved / 1e12,
                      "peak": peak / 1e12, "unit": "Tops/s", "frac": achieved / peak,
-                     "traffic": None if (args.particles or tile != 11) else MAIN_TRAFFIC_BYTES,
+                     "traffic": None if args.particles else MAIN_TRAFFIC_BYTES.get(tile),
                      "traffic_unit": "bytes per launch (ncu dram read + write)",
                      "note": f"{ALG_OPS_PER_BIN} lane-ops per support bin-eval; peak = "
                              f"{props.multi_processor_count} SMs x 128 lanes x "
