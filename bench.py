@@ -30,7 +30,7 @@ WORKLOAD = "C2"
 # particle: phase advance 8, phase->angle 2,
 # G interpolation 8, channel products 8, rotate-accumulate 4, |G|^2 w 6.
 ALG_OPS_PER_BIN = 36
-LAUNCHES_PER_STEP = 8   # setup, scan, chunk table, fill, sort, edges, main, fix-up
+LAUNCHES_PER_STEP = 9   # setup, scan, chunk table, fill, sort, edges, main, 2 x fix-up
 # DRAM bytes (read + write) of one k_main_mixed launch on this workload at full
 # size, per work tile (log2 bins), from ncu captures of this kernel
 # (profiles/k_main_mixed_C2.md); to be re-taken whenever the kernel changes.

@@ -346,7 +346,7 @@ int scs_last_timings(scs_ctx *ctx, double *ms);
  *   GPU that loads it until the process exits; no cudaMalloc, cudaFree or
  *   allocating library routine is called.  Calls whose scratch would exceed
  *   it are rejected with SCS_EINVAL and a message giving the bytes needed
- *   (roughly 20 + 72 C bytes per particle, C = ceil(K/4096) chunks, plus
+ *   (roughly 20 + 75 C bytes per particle, C = ceil(K/4096) chunks, plus
  *   4 (N+1) + 16 (K/1024 + 2) bytes per particle for equal-SNR^2 segments).
  *   The first call on each device looks up the array's device address
  *   (cudaGetSymbolAddress); make that first call before any stream capture.

@@ -65,7 +65,7 @@ bool is_device_ptr(const void* p) {
 // per-call scratch pieces of the evaluation pipeline
 enum Slot {
   kSlotStreams, kSlotPart, kSlotCrange, kSlotNrec, kSlotTotal, kSlotDiff, kSlotCnt,
-  kSlotListOff, kSlotItemOff, kSlotFill, kSlotList, kSlotListTmp, kSlotRec, kSlotCounter, kSlotEdges,
+  kSlotListOff, kSlotItemOff, kSlotFill, kSlotList, kSlotListTmp, kSlotRec, kSlotSlices, kSlotCounter, kSlotEdges,
   kSlotHs, kSlotCs, kNumSlots
 };
 
@@ -237,8 +237,13 @@ size_t batch_scratch_bytes(const std::vector<BatchPart>& parts, int P) {
   int64_t etot = 0, htot = 0;
   std::vector<StreamDesc> t = make_table(parts, &nct, &etot, &htot);
   int64_t bound = 0;
-  for (const StreamDesc& d : t) bound += (int64_t)d.n_p * d.n_chunks;
-  const size_t sizes[] = {sizeof(StreamDesc) * t.size(), sizeof(Part) * P, sizeof(int2) * P,
+  int max_chunks = 0;
+  for (const StreamDesc& d : t) {
+    bound += (int64_t)d.n_p * d.n_chunks;
+    max_chunks = std::max(max_chunks, d.n_chunks);
+  }
+  const int s_max = (max_chunks + kSlice - 1) / kSlice;
+  const size_t sizes[] = {sizeof(SliceSum) * (size_t)P * s_max,sizeof(StreamDesc) * t.size(), sizeof(Part) * P, sizeof(int2) * P,
                           sizeof(int64_t) * (P + 1), sizeof(int64_t) * 2,
                           sizeof(int) * (nct + 2), sizeof(int) * (nct + 1),
                           sizeof(int) * (nct + 1), sizeof(int) * (nct + 1),
@@ -266,6 +271,7 @@ struct Prepared {
   int* list = nullptr;
   int* edges = nullptr;     // equal-SNR^2 edge tables
   bool any_snr2 = false;
+  int s_max = 1;            // record slices per particle in the fix-up
 };
 
 // Stream table upload, particle set-up, chunk work list and (if asked)
@@ -280,10 +286,13 @@ int prepare_batch(scs_ctx* ctx, const std::vector<BatchPart>& parts, const doubl
   out.n_streams = ns;
   out.n_chunks = nct;
   int64_t bound = 0;
+  int max_chunks = 0;
   for (const StreamDesc& d : table) {
     bound += (int64_t)d.n_p * d.n_chunks;
     out.any_snr2 = out.any_snr2 || d.mode == SCS_EQUAL_SNR2;
+    max_chunks = std::max(max_chunks, d.n_chunks);
   }
+  out.s_max = std::max(1, (max_chunks + kSlice - 1) / kSlice);
   out.bound = bound;
   out.streams = dev_table ? dev_table
                           : (StreamDesc*)src.get(kSlotStreams, sizeof(StreamDesc) * ns);
@@ -367,8 +376,16 @@ int run_batch(scs_ctx* ctx, const Prepared& pr, int P, double* dstat, double* ds
   else launch_main_fp64(a, ctx->grid_fp64, s);
   CKLAUNCH();
   if (ctx->prof) CK(cudaEventRecord(ctx->ev[3], s));
-  k_fixup<<<(P + 31) / 32, 32, 0, s>>>(pr.part, pr.crange, pr.nrec, rec, P, pr.streams,
-                                          dstat, dsx, dsh);
+  SliceSum* slices = (SliceSum*)src.get(kSlotSlices, sizeof(SliceSum) * (size_t)P * pr.s_max);
+  if (src.failed()) {
+    if (src.ctx) CK(src.err);
+    return SCS_ENOMEM;
+  }
+  k_fixup_slices<<<(int)(((int64_t)P * pr.s_max + 127) / 128), 128, 0, s>>>(
+      pr.part, pr.crange, pr.nrec, rec, P, pr.s_max, pr.streams, slices, dsx, dsh);
+  CKLAUNCH();
+  k_fixup<<<(P + 31) / 32, 32, 0, s>>>(pr.part, pr.crange, P, pr.s_max, pr.streams, slices,
+                                       dstat, dsx, dsh);
   CKLAUNCH();
   if (ctx->prof) {
     CK(cudaEventRecord(ctx->ev[4], s));
@@ -1276,7 +1293,8 @@ int scs_pso_run(scs_ctx* ctx, int iters, int use_graph, void* cuda_stream) {
     // load every kernel of an iteration now: nothing is loaded under capture
     cudaFuncAttributes fa;
     const void* fk[] = {(const void*)k_setup, (const void*)k_scan64, (const void*)k_chunk_table,
-                        (const void*)k_fill, (const void*)k_bounds, (const void*)k_fixup};
+                        (const void*)k_fill, (const void*)k_bounds, (const void*)k_fixup,
+                        (const void*)k_fixup_slices};
     for (const void* k : fk) {
       if (cudaFuncGetAttributes(&fa, k) != cudaSuccess) {
         ctx->prof = prof;

@@ -19,7 +19,17 @@ struct Rec {
   double zr_t, zi_t, hh_t;
   double ups;
 };
-// the fix-up stages records as 8-byte words: indices in word 0, then doubles
+// Summary of one slice of kSlice consecutive records of a particle (the
+// fix-up merges slices in parallel, then the slices of each particle in order)
+constexpr int kSlice = 32;
+struct SliceSum {
+  double ups;          // record sums plus the runs closed inside the slice
+  double fz[3], lz[3]; // (zr, zi, hh) of the first and of the last run
+  int fn, ln;          // their segment indices
+  int single;          // the first run is also the last (open at both ends)
+  int pad;
+};
+// the fix-up reads records as 8-byte words: indices in word 0, then doubles
 static_assert(sizeof(Rec) == 64 && offsetof(Rec, n_tail) == 4 && offsetof(Rec, zr_h) == 8 &&
                   offsetof(Rec, ups) == 56,
               "record layout");

@@ -465,16 +465,113 @@ __global__ void k_bounds(const Part* part, int p_lo, int p_hi, const StreamDesc*
   }
 }
 
-// Merge the (particle, chunk) records into Upsilon_N (Sec. II.B), one
-// thread per particle in chunk order.  Records are read kBatch at a time
-// as 16-byte vectors, all loads of a batch issued before any is used, so a
-// thread keeps several records in flight.  Launched as one-warp blocks.
-__global__ void __launch_bounds__(32) k_fixup(const Part* part, const int2* crange,
-                                              const int64_t* rec_off, const Rec* rec, int P,
-                                              const StreamDesc* streams, double* stat,
-                                              double* seg_x, double* seg_hh) {
+// Merge the (particle, chunk) records into Upsilon_N (Sec. II.B).  A
+// segment's partial sums sit in consecutive records (the tail of one chunk,
+// the heads of the next ones); runs of entries with one segment index are
+// summed and closed with x^2/hh.  Two kernels: k_fixup_slices merges each
+// slice of kSlice records of each particle on its own thread (closing the
+// runs that lie inside it and keeping its first and last runs open), then
+// k_fixup joins each particle's slices in order.
+
+__device__ inline void close_run(int n, double zr, double zi, double hh, int i, int N,
+                                 double& ups, double* seg_x, double* seg_hh) {
+  if (n < 0) return;
+  const double x2 = zr * zr + zi * zi;
+  if (hh > 0.0) ups += x2 / hh;
+  if (seg_x) {
+    seg_x[(int64_t)i * N + n] = sqrt(x2);
+    seg_hh[(int64_t)i * N + n] = hh;
+  }
+}
+
+__global__ void k_fixup_slices(const Part* part, const int2* crange, const int64_t* rec_off,
+                               const Rec* rec, int P, int S_max, const StreamDesc* streams,
+                               SliceSum* out, double* seg_x, double* seg_hh) {
   constexpr int kBatch = 4;
   constexpr int kVec = sizeof(Rec) / 16;   // 16-byte vectors per record
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = (int)(t / S_max), j = (int)(t - (int64_t)i * S_max);
+  if (i >= P) return;
+  const Part& p = part[i];
+  if (p.status != kOk) return;
+  const int2 cr = crange[i];
+  const int nrec = cr.y - cr.x + 1;
+  const int c0 = j * kSlice, c1 = min(nrec, c0 + kSlice);
+  if (c0 >= c1) return;
+  const int N = streams[p.sid].N;
+  SliceSum sl;
+  sl.ups = 0.0;
+  sl.fn = -1;
+  sl.single = 1;
+  int n_run = -1;
+  double zr = 0.0, zi = 0.0, hh = 0.0;
+  // a run ends: the slice's first run is kept open (it may continue the
+  // previous slice), the later ones are complete
+  auto end_run = [&]() {
+    if (n_run < 0) return;
+    if (sl.single) {
+      sl.single = 0;
+      sl.fn = n_run;
+      sl.fz[0] = zr;
+      sl.fz[1] = zi;
+      sl.fz[2] = hh;
+    } else {
+      close_run(n_run, zr, zi, hh, i, N, sl.ups, seg_x, seg_hh);
+    }
+  };
+  const ulonglong2* src = reinterpret_cast<const ulonglong2*>(rec + rec_off[i]);
+  for (int c = c0; c < c1; c += kBatch) {
+    ulonglong2 v[kBatch][kVec];
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u)
+#pragma unroll
+      for (int q = 0; q < kVec; ++q)
+        v[u][q] = c + u < c1 ? __ldg(src + (int64_t)(c + u) * kVec + q) : make_ulonglong2(0, 0);
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) {
+      if (c + u >= c1) break;
+      const int n_head = (int)(unsigned)(v[u][0].x & 0xffffffffu);
+      const int n_tail = (int)(unsigned)(v[u][0].x >> 32);
+      const double zrh = __longlong_as_double(v[u][0].y), zih = __longlong_as_double(v[u][1].x);
+      const double hhh = __longlong_as_double(v[u][1].y), zrt = __longlong_as_double(v[u][2].x);
+      const double zit = __longlong_as_double(v[u][2].y), hht = __longlong_as_double(v[u][3].x);
+      sl.ups += __longlong_as_double(v[u][3].y);
+      if (n_head >= 0) {
+        if (n_head == n_run) {
+          zr += zrh; zi += zih; hh += hhh;
+        } else {
+          end_run();
+          n_run = n_head;
+          zr = zrh; zi = zih; hh = hhh;
+        }
+      }
+      if (n_tail >= 0) {
+        end_run();
+        n_run = n_tail;
+        zr = zrt; zi = zit; hh = hht;
+      }
+    }
+  }
+  sl.ln = n_run;
+  sl.lz[0] = zr;
+  sl.lz[1] = zi;
+  sl.lz[2] = hh;
+  if (sl.single) {
+    sl.fn = n_run;
+    sl.fz[0] = zr;
+    sl.fz[1] = zi;
+    sl.fz[2] = hh;
+  }
+  sl.pad = 0;
+  out[t] = sl;
+}
+
+// Join each particle's slices in order: a run open at a slice's end
+// continues into the next slice when the segment index matches.
+__global__ void __launch_bounds__(32) k_fixup(const Part* part, const int2* crange, int P,
+                                              int S_max, const StreamDesc* streams,
+                                              const SliceSum* sl, double* stat, double* seg_x,
+                                              double* seg_hh) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= P) return;
   const Part& p = part[i];
@@ -489,52 +586,33 @@ __global__ void __launch_bounds__(32) k_fixup(const Part* part, const int2* cran
   const int N = streams[p.sid].N;
   const int2 cr = crange[i];
   const int nrec = cr.y - cr.x + 1;
+  const int ns = (nrec + kSlice - 1) / kSlice;
   double ups = 0.0;
-  int n_run = -1;
-  double zr = 0.0, zi = 0.0, hh = 0.0;
-  auto close = [&]() {
-    if (n_run < 0) return;
-    double x2 = zr * zr + zi * zi;
-    if (hh > 0.0) ups += x2 / hh;
-    if (seg_x) {
-      seg_x[(int64_t)i * N + n_run] = sqrt(x2);
-      seg_hh[(int64_t)i * N + n_run] = hh;
+  int cn = -1;
+  double czr = 0.0, czi = 0.0, chh = 0.0;
+  for (int j = 0; j < ns; ++j) {
+    const SliceSum s = sl[(int64_t)i * S_max + j];
+    ups += s.ups;
+    if (s.fn == cn) {
+      czr += s.fz[0];
+      czi += s.fz[1];
+      chh += s.fz[2];
+    } else {
+      close_run(cn, czr, czi, chh, i, N, ups, seg_x, seg_hh);
+      cn = s.fn;
+      czr = s.fz[0];
+      czi = s.fz[1];
+      chh = s.fz[2];
     }
-  };
-  const ulonglong2* src = reinterpret_cast<const ulonglong2*>(rec + rec_off[i]);
-  for (int c = 0; c < nrec; c += kBatch) {
-    ulonglong2 v[kBatch][kVec];
-#pragma unroll
-    for (int u = 0; u < kBatch; ++u)
-#pragma unroll
-      for (int q = 0; q < kVec; ++q)
-        v[u][q] = c + u < nrec ? __ldg(src + (int64_t)(c + u) * kVec + q) : make_ulonglong2(0, 0);
-#pragma unroll
-    for (int u = 0; u < kBatch; ++u) {
-      if (c + u >= nrec) break;
-      const int n_head = (int)(unsigned)(v[u][0].x & 0xffffffffu);
-      const int n_tail = (int)(unsigned)(v[u][0].x >> 32);
-      const double zrh = __longlong_as_double(v[u][0].y), zih = __longlong_as_double(v[u][1].x);
-      const double hhh = __longlong_as_double(v[u][1].y), zrt = __longlong_as_double(v[u][2].x);
-      const double zit = __longlong_as_double(v[u][2].y), hht = __longlong_as_double(v[u][3].x);
-      ups += __longlong_as_double(v[u][3].y);
-      if (n_head >= 0) {
-        if (n_head == n_run) {
-          zr += zrh; zi += zih; hh += hhh;
-        } else {
-          close();
-          n_run = n_head;
-          zr = zrh; zi = zih; hh = hhh;
-        }
-      }
-      if (n_tail >= 0) {
-        close();
-        n_run = n_tail;
-        zr = zrt; zi = zit; hh = hht;
-      }
+    if (!s.single) {
+      close_run(cn, czr, czi, chh, i, N, ups, seg_x, seg_hh);
+      cn = s.ln;
+      czr = s.lz[0];
+      czi = s.lz[1];
+      chh = s.lz[2];
     }
   }
-  close();
+  close_run(cn, czr, czi, chh, i, N, ups, seg_x, seg_hh);
   stat[i] = ups;
 }
 

@@ -17,9 +17,13 @@ __global__ void k_sort_chunks(const Part* part, const int* cnt, const int* list_
                               const int* list_in, int* list_out, int n_chunks);
 __global__ void k_bounds(const Part* part, int p_lo, int p_hi, const StreamDesc* streams,
                          int* edges_all, double* Hs, double* Cs);
-__global__ void k_fixup(const Part* part, const int2* crange, const int64_t* rec_off,
-                        const Rec* rec, int P, const StreamDesc* streams, double* stat,
-                        double* seg_x, double* seg_hh);
+__global__ void k_fixup_slices(const Part* part, const int2* crange, const int64_t* rec_off,
+                               const Rec* rec, int P, int S_max, const StreamDesc* streams,
+                               SliceSum* out, double* seg_x, double* seg_hh);
+__global__ void __launch_bounds__(32) k_fixup(const Part* part, const int2* crange, int P,
+                                              int S_max, const StreamDesc* streams,
+                                              const SliceSum* sl, double* stat, double* seg_x,
+                                              double* seg_hh);
 __global__ void k_prewhiten(const double2* A, const double2* E, const double* SA,
                             const double* SE, double df, int K, double2* dA64, double2* dE64,
                             double2* w64, unsigned long long* wmax);
