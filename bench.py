@@ -34,7 +34,7 @@ LAUNCHES_PER_STEP = 9   # setup, scan, chunk table, fill, sort, edges, main, 2 x
 # DRAM bytes (read + write) of one k_main_mixed launch on this workload at full
 # size, per work tile (log2 bins), from ncu captures of this kernel
 # (profiles/k_main_mixed_C2.md); to be re-taken whenever the kernel changes.
-MAIN_TRAFFIC_BYTES = {11: 72.53e6 + 24.34e6, 12: 68.18e6 + 7.53e6}
+MAIN_TRAFFIC_BYTES = {11: 72.49e6 + 24.82e6, 12: 68.76e6 + 7.69e6}
 
 
 def parse():
