@@ -437,14 +437,19 @@ __device__ inline void response_power64(const Part& p, double f, double ca, doub
   double s_a, c_a;
   sincos_small(a, &s_a, &c_a);
   // e_i = e^{-i pi f k.d_i}: the link phase of arm (s, r) is e_s e_r and
-  // e^{i a k.n} = e^{i pi f k.(d_r - d_s)} = e_s conj(e_r), so three sin/cos
-  // serve all six
+  // e^{i a k.n} = e^{i pi f k.(d_r - d_s)} = e_s conj(e_r); the three craft
+  // offsets sum to zero (equally spaced beta_i), so e_2 = conj(e_0 e_1) and
+  // two sin/cos serve all six links
   Cx<double> e[3];
 #pragma unroll
-  for (int i = 0; i < 3; ++i) {
+  for (int i = 0; i < 2; ++i) {
     double sn, cs;
     sincos_small(-kPi * f * (p.kx * d[i][0] + p.ky * d[i][1] + p.kz * d[i][2]), &sn, &cs);
     e[i] = Cx<double>{cs, sn};
+  }
+  {
+    const Cx<double> e01 = cmul(e[0], e[1]);
+    e[2] = Cx<double>{e01.re, -e01.im};
   }
   Cx<double> G[3][3];
   const int as[3] = {0, 0, 1}, ar[3] = {1, 2, 2};
