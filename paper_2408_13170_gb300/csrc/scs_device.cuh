@@ -441,12 +441,15 @@ __device__ inline void response_power64(const Part& p, double f, double ca, doub
   // offsets sum to zero (equally spaced beta_i), so e_2 = conj(e_0 e_1) and
   // two sin/cos serve all six links
   Cx<double> e[3];
+  double ph[3];   // phi_i = -pi f k.d_i; a k.n of arm (s, r) = phi_s - phi_r
 #pragma unroll
   for (int i = 0; i < 2; ++i) {
     double sn, cs;
-    sincos_small(-kPi * f * (p.kx * d[i][0] + p.ky * d[i][1] + p.kz * d[i][2]), &sn, &cs);
+    ph[i] = -kPi * f * (p.kx * d[i][0] + p.ky * d[i][1] + p.kz * d[i][2]);
+    sincos_small(ph[i], &sn, &cs);
     e[i] = Cx<double>{cs, sn};
   }
+  ph[2] = -(ph[0] + ph[1]);
   {
     const Cx<double> e01 = cmul(e[0], e[1]);
     e[2] = Cx<double>{e01.re, -e01.im};
@@ -458,14 +461,13 @@ __device__ inline void response_power64(const Part& p, double f, double ca, doub
     int s = as[m], r = ar[m];
     const double iL = 1.0 / kArm;
     double n0 = (d[r][0] - d[s][0]) * iL, n1 = (d[r][1] - d[s][1]) * iL, n2 = (d[r][2] - d[s][2]) * iL;
-    double kn = p.kx * n0 + p.ky * n1 + p.kz * n2;
     double q0 = n0 * n0, q1 = n1 * n1, q2 = n2 * n2, q3 = 2.0 * n0 * n1, q4 = 2.0 * n0 * n2,
            q5 = 2.0 * n1 * n2;
     Cx<double> nPn{p.Pr[0] * q0 + p.Pr[1] * q1 + p.Pr[2] * q2 + p.Pr[3] * q3 + p.Pr[4] * q4 + p.Pr[5] * q5,
                    p.Pi[0] * q0 + p.Pi[1] * q1 + p.Pi[2] * q2 + p.Pi[3] * q3 + p.Pi[4] * q4 + p.Pi[5] * q5};
     Cx<double> base = cmul(cmul(e[s], e[r]), nPn);
     const Cx<double> eb = cmul(e[s], Cx<double>{e[r].re, -e[r].im});   // e^{i b}, b = a k.n
-    double b = a * kn;
+    double b = ph[s] - ph[r];
     double xf = a - b, xb = a + b;
     double sf = fabs(xf) < 0.25 ? sin_(xf) : s_a * eb.re - c_a * eb.im;
     double sk = fabs(xb) < 0.25 ? sin_(xb) : s_a * eb.re + c_a * eb.im;
