@@ -234,7 +234,8 @@ int scs_set_tile(scs_ctx *ctx, int stream_id, int log2_chunk);
 /* Autotuner: times full evaluations of the given particles (P x 8, host or
  * device; the stream's data and segmentation must be set) with every tile
  * log2_chunk = 11 .. 14 on cuda_stream, each started with a cold L2 (a
- * 192 MB buffer is written before it), keeps the fastest for the stream and
+ * 192 MB buffer is written before it), keeps the fastest (the smallest tile
+ * within 2% of the fastest) for the stream and
  * returns it in *log2_chunk (may be NULL); ms (may be NULL) receives the
  * four best-of-three times.  Synchronous; allocates.
  * Errors: as scs_eval_stat. */

@@ -793,6 +793,7 @@ int scs_autotune(scs_ctx* ctx, int sid, const double* params, int64_t P, int* lo
   const int keep = ds->log2_chunk;
   int best = keep;
   float best_ms = 0.f;
+  float times[kLog2ChunkMax - kLog2ChunkMin + 1] = {};
   for (int l = kLog2ChunkMin; l <= kLog2ChunkMax && !rc; ++l) {
     ds->log2_chunk = l;
     float t = 0.f;
@@ -814,11 +815,19 @@ int scs_autotune(scs_ctx* ctx, int sid, const double* params, int64_t P, int* lo
       if (rep == 1 || (rep > 1 && dt < t)) t = dt;
     }
     if (ms) ms[l - kLog2ChunkMin] = t;
+    times[l - kLog2ChunkMin] = t;
     if (!rc && (best_ms == 0.f || t < best_ms)) {
       best_ms = t;
       best = l;
     }
   }
+  // within 2% of the fastest (timing noise), the smallest tile: more work
+  // items, shorter tail
+  for (int l = kLog2ChunkMin; l < best && !rc; ++l)
+    if (times[l - kLog2ChunkMin] <= 1.02f * best_ms) {
+      best = l;
+      break;
+    }
   ctx->prof = prof;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
