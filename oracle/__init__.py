@@ -18,7 +18,8 @@ What the oracle computes (arXiv:2408.13170):
     re-evaluated for every theta (Sec. II.B, last paragraph);
   * template h_alpha = T_alpha(theta, f) A(f) e^{-i Psi(f)} on the FFT grid
     (Sec. IV), TaylorF2 2PN circular phase and the rigid-adiabatic LISA TDI
-    A/E response.
+    A/E response, optionally with the third channel T (the paper's search
+    uses all three, Sec. I).
 """
 from __future__ import annotations
 
@@ -75,12 +76,12 @@ def _load():
         lib.orc_phase_turns.restype = D
         lib.orc_response.argtypes = [P, D, D, P, P]
         lib.orc_response.restype = I
-        lib.orc_template.argtypes = [P, I, I, D, D, I64, D, D, D, P, P]
+        lib.orc_template.argtypes = [P, I, I, D, D, I64, D, D, D, P, P, P]
         lib.orc_template.restype = I
-        lib.orc_eval.argtypes = [D, D, I64, D, P, P, P, P, I, I, I, I, P, I64,
-                                 D, D, P, P, P, P, I]
+        lib.orc_eval.argtypes = [D, D, I64, D, P, P, P, P, P, P, I, I, I, I, P,
+                                 I64, D, D, P, P, P, P, I]
         lib.orc_eval.restype = I
-        lib.orc_inject.argtypes = [P, D, D, I64, D, P, P, D, P, P]
+        lib.orc_inject.argtypes = [P, D, D, I64, D, P, P, P, D, P, P, P]
         lib.orc_inject.restype = D
         _lib = lib
         return lib
@@ -124,8 +125,8 @@ def phase_turns(theta, f_first, df, k, waveform=TF2):
 
 def response(theta, f, t):
     """Links G_{1->2},G_{2->1},G_{1->3},G_{3->1},G_{2->3},G_{3->2}, X, Y, Z,
-    A, E (complex[11]) and craft positions (3x3, seconds) at (f, t)."""
-    out = np.zeros(22)
+    A, E, T (complex[12]) and craft positions (3x3, seconds) at (f, t)."""
+    out = np.zeros(24)
     pos = np.zeros(9)
     _load().orc_response(_ptr(_theta(theta)), float(f), float(t), _ptr(out),
                          _ptr(pos))
@@ -133,25 +134,33 @@ def response(theta, f, t):
 
 
 def template(theta, f_first, df, K, T_obs, waveform=TF2, response=TDI_AE,
-             amp_scale=1.0, phase0=0.0):
-    """(status, h_A[K], h_E[K]) complex128 over the whole grid."""
+             amp_scale=1.0, phase0=0.0, want_T=False):
+    """(status, h_A[K], h_E[K]) complex128 over the whole grid; with want_T
+    also h_T[K] (status, h_A, h_E, h_T)."""
     hA = np.zeros(2 * int(K))
     hE = np.zeros(2 * int(K))
+    hT = np.zeros(2 * int(K)) if want_T else None
     st = _load().orc_template(_ptr(_theta(theta)), waveform, response,
                               f_first, df, int(K), T_obs, amp_scale, phase0,
-                              _ptr(hA), _ptr(hE))
-    return st, hA.view(np.complex128), hE.view(np.complex128)
+                              _ptr(hA), _ptr(hE), _ptr(hT))
+    out = (st, hA.view(np.complex128), hE.view(np.complex128))
+    return out + (hT.view(np.complex128),) if want_T else out
 
 
-def inject(theta, f_first, df, K, T_obs, SA, SE, snr, A, E):
-    """Adds snr * h/sqrt(<h|h>) to complex128 arrays A, E in place; returns
-    <h|h> of the un-normalised template."""
+def inject(theta, f_first, df, K, T_obs, SA, SE, snr, A, E, T=None, ST=None):
+    """Adds snr * h/sqrt(<h|h>) to complex128 arrays A, E (and T, whose PSD
+    is ST, when given) in place; returns <h|h> of the un-normalised template
+    over the channels given."""
     assert A.dtype == np.complex128 and E.dtype == np.complex128
     assert A.flags.c_contiguous and E.flags.c_contiguous
+    if T is not None:
+        assert T.dtype == np.complex128 and T.flags.c_contiguous and ST is not None
+        ST = np.ascontiguousarray(ST, dtype=np.float64)
     SA = np.ascontiguousarray(SA, dtype=np.float64)
     SE = None if SE is None else np.ascontiguousarray(SE, dtype=np.float64)
     return _load().orc_inject(_ptr(_theta(theta)), f_first, df, int(K), T_obs,
-                              _ptr(SA), _ptr(SE), float(snr), _ptr(A), _ptr(E))
+                              _ptr(SA), _ptr(SE), _ptr(ST if T is not None else None),
+                              float(snr), _ptr(A), _ptr(E), _ptr(T))
 
 
 def evaluate(data, params, N, mode=EQUAL_WIDTH, waveform=TF2,
@@ -160,7 +169,8 @@ def evaluate(data, params, N, mode=EQUAL_WIDTH, waveform=TF2,
     """Upsilon_N for every particle.
 
     data: dict with f_first, df, K, T_obs, A, E (complex128[K]), SA, SE
-          (float64[K]; SE may be None).
+          (float64[K]; SE may be None); optionally the third channel T
+          (complex128[K]) with its PSD ST (float64[K]).
     params: (P, 8) float64.
     Returns stat[P] and, on request, seg_x[P, N], seg_hh[P, N],
     kappa[P, N+1].
@@ -173,13 +183,18 @@ def evaluate(data, params, N, mode=EQUAL_WIDTH, waveform=TF2,
     SA = np.ascontiguousarray(data["SA"], dtype=np.float64)
     SE = data.get("SE")
     SE = None if SE is None else np.ascontiguousarray(SE, dtype=np.float64)
+    T = data.get("T")
+    ST = None
+    if T is not None:
+        T = np.ascontiguousarray(T, dtype=np.complex128)
+        ST = np.ascontiguousarray(data["ST"], dtype=np.float64)
     stat = np.zeros(P)
     sx = np.zeros((P, N)) if want_segments else None
     sh = np.zeros((P, N)) if want_segments else None
     kap = np.zeros((P, N + 1)) if want_kappa else None
     lib.orc_eval(float(data["f_first"]), float(data["df"]), int(data["K"]),
                  float(data["T_obs"]), _ptr(A), _ptr(E), _ptr(SA), _ptr(SE),
-                 int(N), int(mode), int(waveform), int(response), _ptr(params),
+                 _ptr(T), _ptr(ST), int(N), int(mode), int(waveform), int(response), _ptr(params),
                  P, float(amp_scale), float(phase0), _ptr(stat), _ptr(sx),
                  _ptr(sh), _ptr(kap), int(nthreads))
     out = [stat]
@@ -192,13 +207,17 @@ def evaluate(data, params, N, mode=EQUAL_WIDTH, waveform=TF2,
 
 def inner_dd(data):
     """<d|d> = sum_alpha sum_k 4 df |d_alpha(f_k)|^2 / S_alpha(f_k) (Eq. inner_prod
-    on the FFT grid)."""
+    on the FFT grid), over A, E and T when the data has T."""
     SA = np.asarray(data["SA"], np.float64)
     SE = SA if data.get("SE") is None else np.asarray(data["SE"], np.float64)
     A = np.asarray(data["A"])
     E = np.asarray(data["E"])
-    return float(np.sum(4.0 * data["df"] * np.abs(A) ** 2 / SA)
-                 + np.sum(4.0 * data["df"] * np.abs(E) ** 2 / SE))
+    out = (np.sum(4.0 * data["df"] * np.abs(A) ** 2 / SA)
+           + np.sum(4.0 * data["df"] * np.abs(E) ** 2 / SE))
+    if data.get("T") is not None:
+        out += np.sum(4.0 * data["df"] * np.abs(np.asarray(data["T"])) ** 2
+                      / np.asarray(data["ST"], np.float64))
+    return float(out)
 
 
 def loglike(data, params, N, mode=EQUAL_WIDTH, amp=None):

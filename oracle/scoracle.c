@@ -19,7 +19,10 @@
  *   equal squared-SNR segment boundaries          (Sec. II.B, last paragraph)
  *   waveform: (2,2)-mode frequency-domain PN inspiral, h = A e^{-i Psi}
  *                                                  (Sec. IV, TaylorF2 family)
- *   response: h_alpha = T_alpha(theta, f) h        (Sec. IV, LISA TDI A, E)
+ *   response: h_alpha = T_alpha(theta, f) h        (Sec. IV, LISA TDI A, E
+ *                                                  and, optionally, T: the
+ *                                                  search uses all three
+ *                                                  channels, Sec. I)
  *
  * Readings where the paper is silent:
  *   - waveform: non-spinning, circular (e0 = 0) TaylorF2 to 2PN; t(f) is
@@ -27,7 +30,8 @@
  *     f >= f0, t(f) <= T_obs, v <= 6^{-1/2};
  *   - response: rigid-adiabatic single-link transfer from the two-pulse
  *     link formula, evaluated at t = t(f), first-generation TDI X,Y,Z and
- *     A = (Z-X)/sqrt2, E = (X-2Y+Z)/sqrt6, on an exactly rigid equal-arm
+ *     A = (Z-X)/sqrt2, E = (X-2Y+Z)/sqrt6, T = (X+Y+Z)/sqrt3 (the
+ *     orthonormal combinations), on an exactly rigid equal-arm
  *     orbit with the constellation centre at (R cos Omega t, R sin Omega t, 0);
  *   - equal-SNR^2 segments: trapezoid cumulative of the exact template
  *     power on an anchor grid of stride 1024 bins, linear inverse
@@ -325,9 +329,9 @@ static double complex link(const orc_particle *p, double pos[3][3], int s,
     return -I * M_PI * f * L * sinc * cexp(I * ph) * nPn;
 }
 
-/* out: G[6] (links 1->2,2->1,1->3,3->1,2->3,3->2), X, Y, Z, A, E */
+/* out: G[6] (links 1->2,2->1,1->3,3->1,2->3,3->2), X, Y, Z, A, E, T */
 static void tdi(const orc_particle *p, double f, double t,
-                double complex out[11]) {
+                double complex out[12]) {
     double pos[3][3];
     orbit(t, pos);
     double complex G12 = link(p, pos, 0, 1, f), G21 = link(p, pos, 1, 0, f);
@@ -343,12 +347,13 @@ static void tdi(const orc_particle *p, double f, double t,
     out[6] = X; out[7] = Y; out[8] = Z;
     out[9] = (Z - X) / sqrt(2.0);
     out[10] = (X - 2.0 * Y + Z) / sqrt(6.0);
+    out[11] = (X + Y + Z) / sqrt(3.0);
 }
 
-/* h_A(f_k), h_E(f_k) for one bin */
+/* h_A(f_k), h_E(f_k) and h_T(f_k) for one bin */
 static void template_bin(const orc_particle *p, dd f, double amp_scale,
                          double phase0, double complex *hA,
-                         double complex *hE) {
+                         double complex *hE, double complex *hT) {
     double fd = dd_to_d(f);
     double t = time_of_freq(p, f);
     double fr = phase_turns_reduced(p, f);
@@ -358,11 +363,13 @@ static void template_bin(const orc_particle *p, dd f, double amp_scale,
     if (p->response == ORC_IDENTITY) {
         *hA = h;
         *hE = 0.0;
+        *hT = 0.0;
     } else {
-        double complex T[11];
+        double complex T[12];
         tdi(p, fd, t, T);
         *hA = T[9] * h;
         *hE = T[10] * h;
+        *hT = T[11] * h;
     }
 }
 
@@ -440,8 +447,8 @@ double orc_phase_turns(const double *th, int waveform, double f_first,
     return phase_turns_reduced(&p, grid_freq(f_first, df, k));
 }
 
-/* response diagnostics at frequency f and time t: 11 complex values
- * (6 links, X, Y, Z, A, E) interleaved re,im -> out[22]; pos[9] positions */
+/* response diagnostics at frequency f and time t: 12 complex values
+ * (6 links, X, Y, Z, A, E, T) interleaved re,im -> out[24]; pos[9] positions */
 int orc_response(const double *th, double f, double t, double *out,
                  double *pos) {
     orc_particle p;
@@ -452,9 +459,9 @@ int orc_response(const double *th, double f, double t, double *out,
     if (!(th2[1] >= 1.0)) th2[1] = 1.0;
     if (!(th2[2] > 0.0)) th2[2] = 1e-3;
     particle_init(&p, th2, ORC_LINEAR_CHIRP, ORC_TDI_AE);
-    double complex T[11];
+    double complex T[12];
     tdi(&p, f, t, T);
-    for (int i = 0; i < 11; ++i) {
+    for (int i = 0; i < 12; ++i) {
         out[2 * i] = creal(T[i]);
         out[2 * i + 1] = cimag(T[i]);
     }
@@ -464,25 +471,32 @@ int orc_response(const double *th, double f, double t, double *out,
     return 0;
 }
 
-/* template h_A, h_E over the whole grid (complex interleaved, zero outside
- * the support).  Returns the support status. */
+/* template h_A, h_E (and h_T if hT is not NULL) over the whole grid
+ * (complex interleaved, zero outside the support).  Returns the support
+ * status. */
 int orc_template(const double *th, int waveform, int response, double f_first,
                  double df, int64_t K, double T_obs, double amp_scale,
-                 double phase0, double *hA, double *hE) {
+                 double phase0, double *hA, double *hE, double *hT) {
     memset(hA, 0, sizeof(double) * 2 * (size_t)K);
     memset(hE, 0, sizeof(double) * 2 * (size_t)K);
+    if (hT) memset(hT, 0, sizeof(double) * 2 * (size_t)K);
     int64_t lo, hi;
     int st = orc_support(th, waveform, f_first, df, K, T_obs, &lo, &hi);
     if (st != ORC_OK) return st;
     orc_particle p;
     particle_init(&p, th, waveform, response);
     for (int64_t k = lo; k <= hi; ++k) {
-        double complex a, e;
-        template_bin(&p, grid_freq(f_first, df, k), amp_scale, phase0, &a, &e);
+        double complex a, e, tt;
+        template_bin(&p, grid_freq(f_first, df, k), amp_scale, phase0, &a, &e,
+                     &tt);
         hA[2 * k] = creal(a);
         hA[2 * k + 1] = cimag(a);
         hE[2 * k] = creal(e);
         hE[2 * k + 1] = cimag(e);
+        if (hT) {
+            hT[2 * k] = creal(tt);
+            hT[2 * k + 1] = cimag(tt);
+        }
     }
     return ORC_OK;
 }
@@ -526,7 +540,8 @@ static void snr2_bounds(int64_t lo, int64_t hi, const double *hhk, int N,
 /*
  * Upsilon_N for P particles.
  *   data: A, E complex interleaved [K]; SA, SE one-sided PSD [K] (SE may be
- *         NULL -> SA);  grid f_k = f_first + k df;  T_obs.
+ *         NULL -> SA);  optional third channel T with its PSD ST (both NULL:
+ *         A and E only);  grid f_k = f_first + k df;  T_obs.
  *   params: P x 8 row-major.
  *   stat[P]; optional seg_x[P*N], seg_hh[P*N], kappa[P*(N+1)].
  *   amp_scale, phase0: template multiplied by amp_scale e^{i phase0}
@@ -535,7 +550,8 @@ static void snr2_bounds(int64_t lo, int64_t hi, const double *hhk, int N,
  */
 int orc_eval(double f_first, double df, int64_t K, double T_obs,
              const double *A, const double *E, const double *SA,
-             const double *SE, int N, int mode, int waveform, int response,
+             const double *SE, const double *T, const double *ST, int N,
+             int mode, int waveform, int response,
              const double *params, int64_t P, double amp_scale, double phase0,
              double *stat, double *seg_x, double *seg_hh, double *kappa,
              int nthreads) {
@@ -564,15 +580,21 @@ int orc_eval(double f_first, double df, int64_t K, double T_obs,
             double complex *zk = malloc(sizeof(double complex) * (size_t)S);
             double *hhk = malloc(sizeof(double) * (size_t)S);
             for (int64_t k = lo; k <= hi; ++k) {
-                double complex a, e;
+                double complex a, e, tt;
                 template_bin(&p, grid_freq(f_first, df, k), amp_scale, phase0,
-                             &a, &e);
+                             &a, &e, &tt);
                 double wA = 4.0 * df / SA[k], wE = 4.0 * df / SE[k];
                 double complex dA = A[2 * k] + I * A[2 * k + 1];
                 double complex dE = E[2 * k] + I * E[2 * k + 1];
                 zk[k - lo] = wA * dA * conj(a) + wE * dE * conj(e);
                 hhk[k - lo] = wA * (creal(a) * creal(a) + cimag(a) * cimag(a)) +
                               wE * (creal(e) * creal(e) + cimag(e) * cimag(e));
+                if (T) {   /* the third channel's terms, added last */
+                    double wT = 4.0 * df / ST[k];
+                    double complex dT = T[2 * k] + I * T[2 * k + 1];
+                    zk[k - lo] += wT * dT * conj(tt);
+                    hhk[k - lo] += wT * (creal(tt) * creal(tt) + cimag(tt) * cimag(tt));
+                }
             }
             if (mode == ORC_EQUAL_WIDTH) {
                 for (int n = 0; n <= N; ++n)
@@ -611,27 +633,35 @@ int orc_eval(double f_first, double df, int64_t K, double T_obs,
     return 0;
 }
 
-/* Adds snr * h / sqrt(<h|h>) (one particle) to the data A, E in place.
- * Returns the optimal SNR^2 <h|h> of the un-normalised template. */
+/* Adds snr * h / sqrt(<h|h>) (one particle) to the data A, E (and T, with
+ * PSD ST, if T is not NULL) in place.  Returns the optimal SNR^2 <h|h> of
+ * the un-normalised template over the channels given. */
 double orc_inject(const double *th, double f_first, double df, int64_t K,
-                  double T_obs, const double *SA, const double *SE, double snr,
-                  double *A, double *E) {
+                  double T_obs, const double *SA, const double *SE,
+                  const double *ST, double snr, double *A, double *E,
+                  double *T) {
     if (SE == NULL) SE = SA;
     double *hA = malloc(sizeof(double) * 2 * (size_t)K);
     double *hE = malloc(sizeof(double) * 2 * (size_t)K);
-    orc_template(th, ORC_TF2, ORC_TDI_AE, f_first, df, K, T_obs, 1.0, 0.0, hA, hE);
+    double *hT = T ? malloc(sizeof(double) * 2 * (size_t)K) : NULL;
+    orc_template(th, ORC_TF2, ORC_TDI_AE, f_first, df, K, T_obs, 1.0, 0.0, hA, hE,
+                 hT);
     nsum hh = {0, 0};
     for (int64_t k = 0; k < K; ++k) {
         nadd(&hh, 4.0 * df / SA[k] * (hA[2 * k] * hA[2 * k] + hA[2 * k + 1] * hA[2 * k + 1]));
         nadd(&hh, 4.0 * df / SE[k] * (hE[2 * k] * hE[2 * k] + hE[2 * k + 1] * hE[2 * k + 1]));
+        if (T)
+            nadd(&hh, 4.0 * df / ST[k] * (hT[2 * k] * hT[2 * k] + hT[2 * k + 1] * hT[2 * k + 1]));
     }
     double h2 = nval(&hh);
     double s = (h2 > 0.0) ? snr / sqrt(h2) : 0.0;
     for (int64_t i = 0; i < 2 * K; ++i) {
         A[i] += s * hA[i];
         E[i] += s * hE[i];
+        if (T) T[i] += s * hT[i];
     }
     free(hA);
     free(hE);
+    free(hT);
     return h2;
 }

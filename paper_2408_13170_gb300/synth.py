@@ -45,6 +45,20 @@ def psd_AE(f):
                                    + 2.0 * (3.0 + 2.0 * np.cos(x) + np.cos(2.0 * x)) * s_acc)
 
 
+def psd_T(f):
+    """Analytic instrumental one-sided PSD of TDI T in the same model and
+    units as psd_AE (first generation): the test-mass and optical-path
+    terms enter through 1 - cos x, so T is quiet at low frequency."""
+    f = np.asarray(f, dtype=np.float64)
+    L = ARM_M / CLIGHT
+    x = 2.0 * np.pi * f * L
+    s_oms = (15e-12) ** 2 * (1.0 + (2e-3 / f) ** 4) * (2.0 * np.pi * f / CLIGHT) ** 2
+    s_acc = ((3e-15) ** 2 * (1.0 + (4e-4 / f) ** 2) * (1.0 + (f / 8e-3) ** 4)
+             / (2.0 * np.pi * f * CLIGHT) ** 2)
+    omc = 1.0 - np.cos(x)
+    return 16.0 * np.sin(x) ** 2 * omc * (s_oms + 2.0 * omc * s_acc)
+
+
 def noise(S, T_obs, rng):
     """Stationary Gaussian FD noise: Re, Im ~ N(0, S T_obs / 4) per bin, so
     that E|n|^2 = S T_obs / 2 (one-sided PSD convention)."""
@@ -117,13 +131,17 @@ def c4_streams(seed: int = 0):
     return out
 
 
-def make_stream(name_or_cfg, seed=None, noise_free=False):
+def make_stream(name_or_cfg, seed=None, noise_free=False, channels="AE"):
     """Noise-only data stream of a configuration.
 
     Returns a dict: f_first, df, K, T_obs, A, E (complex128[K]), SA, SE
     (float64[K]), rng (the generator, positioned after the noise draws, for
-    drawing the injection and the particles), cfg.
+    drawing the injection and the particles), cfg; with channels="AET" also
+    the third TDI channel T (complex128[K]) and its PSD ST, its noise drawn
+    after that of A and E (so A and E equal those of the two-channel stream).
     """
+    if channels not in ("AE", "AET"):
+        raise ValueError("channels must be 'AE' or 'AET'")
     cfg = CONFIGS[name_or_cfg] if isinstance(name_or_cfg, str) else name_or_cfg
     seed = cfg["seed"] if seed is None else seed
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -136,5 +154,11 @@ def make_stream(name_or_cfg, seed=None, noise_free=False):
     else:
         A = noise(S, cfg["T_obs"], rng)
         E = noise(S, cfg["T_obs"], rng)
-    return dict(f_first=f_first, df=df, K=K, T_obs=cfg["T_obs"], A=A, E=E,
-                SA=S, SE=S.copy(), rng=rng, cfg=cfg)
+    out = dict(f_first=f_first, df=df, K=K, T_obs=cfg["T_obs"], A=A, E=E,
+               SA=S, SE=S.copy(), rng=rng, cfg=cfg)
+    if channels == "AET":
+        ST = psd_T(f)
+        out["ST"] = ST
+        out["T"] = (np.zeros(K, np.complex128) if noise_free
+                    else noise(ST, cfg["T_obs"], rng))
+    return out

@@ -335,8 +335,9 @@ def test_link_and_tdi_from_two_pulse_model(th, f):
     y(t) = n.[H(t - L, p_s) - H(t, p_r)].n / (2 (1 - k.n)); and first
     generation X(t) = y31 + y13(t-L) + y21(t-2L) + y12(t-3L)
     - [y21 + y12(t-L) + y31(t-2L) + y13(t-3L)], Y, Z cyclic,
-    A = (Z - X)/sqrt 2, E = (X - 2Y + Z)/sqrt 6 (static constellation,
-    delays applied to the plane-wave time dependence)."""
+    A = (Z - X)/sqrt 2, E = (X - 2Y + Z)/sqrt 6, T = (X + Y + Z)/sqrt 3
+    (static constellation, delays applied to the plane-wave time
+    dependence)."""
     t0 = 7.7e6
     T, pos = oracle.response(th, f, t0)
     lam, bet, inc, psi = th[3], th[4], th[5], th[6]
@@ -373,7 +374,8 @@ def test_link_and_tdi_from_two_pulse_model(th, f):
     scale = max(abs(X), abs(Y), abs(Z))
     for got, want in ((T[6], X), (T[7], Y), (T[8], Z),
                       (T[9], (Z - X) / np.sqrt(2)),
-                      (T[10], (X - 2 * Y + Z) / np.sqrt(6))):
+                      (T[10], (X - 2 * Y + Z) / np.sqrt(6)),
+                      (T[11], (X + Y + Z) / np.sqrt(3))):
         assert abs(got - want) <= 1e-10 * scale
 
 
