@@ -4,7 +4,9 @@ One step = one scs_eval_stat call over one batch of particles on the
 one-year stream (T = 3.15e7 s, 0.01-0.05 Hz -> K = 1 260 001 bins x TDI A, E;
 P = 4096 particles uniform in the prior box; N = 2048 equal-SNR^2 segments;
 Gaussian noise from the analytic A/E PSD plus one injection at SNR 17).
-Prints one JSON line.  `--impl reference` times the FP64 CPU oracle instead.
+Prints one JSON line.  `--impl reference` times the FP64 CPU oracle instead;
+`--channels AET` adds the third TDI channel T (its own analytic PSD) to the
+same workload.
 
 Multi-GPU: the statistic shards over independent streams/particle batches
 with no exchange, so N GPUs run N replicas (different seeds, weak scaling);
@@ -30,6 +32,8 @@ WORKLOAD = "C2"
 # particle: phase advance 8, phase->angle 2,
 # G interpolation 8, channel products 8, rotate-accumulate 4, |G|^2 w 6.
 ALG_OPS_PER_BIN = 36
+# with the third channel T: + G_T interpolation 4, products 4, |G_T|^2 w 4
+ALG_OPS_PER_BIN_AET = 48
 LAUNCHES_PER_STEP = 9   # setup, scan, chunk table, fill, sort, edges, main, 2 x fix-up
 # DRAM bytes (read + write) of one k_main_mixed launch on this workload at full
 # size, per work tile (log2 bins), from ncu captures of this kernel
@@ -49,6 +53,8 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--particles", type=int, default=None,
                     help="override the particle count (small cases for profiling)")
+    ap.add_argument("--channels", default="AE", choices=["AE", "AET"],
+                    help="TDI channels of the data stream")
     ap.add_argument("--pso-iters", type=int, default=10,
                     help="C4: swarm iterations per captured graph (one step = one graph launch)")
     return ap.parse_args()
@@ -134,11 +140,11 @@ class ClockSampler:
                 "samples": len(rows), "reasons": sorted(reasons)}
 
 
-def make_workload(seed_offset=0):
+def make_workload(seed_offset=0, channels="AE"):
     from paper_2408_13170_gb300 import synth
     cfg = dict(synth.CONFIGS[WORKLOAD])
     cfg["seed"] = cfg["seed"] + seed_offset
-    d = synth.make_stream(cfg)
+    d = synth.make_stream(cfg, channels=channels)
     inj = synth.injection_params(d["rng"], *cfg["inj"])
     return cfg, d, inj
 
@@ -150,9 +156,9 @@ def run_reference(args, rank, world):
     from paper_2408_13170_gb300 import synth
     if rank != 0:
         return
-    cfg, d, inj = make_workload()
+    cfg, d, inj = make_workload(channels=args.channels)
     oracle.inject(inj, d["f_first"], d["df"], d["K"], d["T_obs"], d["SA"], d["SE"],
-                  cfg["snr"], d["A"], d["E"])
+                  cfg["snr"], d["A"], d["E"], T=d.get("T"), ST=d.get("ST"))
     per_step = max(1, args.cpu_sample // 2)
     batches = [synth.draw_particles(per_step, d["rng"]) for _ in range(args.warmup + args.steps)]
     for b in batches[:args.warmup]:
@@ -171,7 +177,8 @@ def run_reference(args, rank, world):
         "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"{WORKLOAD}: one-year stream, {cfg['P']} particles, "
-                               f"K={d['K']} bins x 2 channels, N={cfg['N']} equal-SNR^2",
+                               f"K={d['K']} bins x TDI {','.join(args.channels)}, "
+                               f"N={cfg['N']} equal-SNR^2",
                    "sample_per_step": per_step},
         "cpu_baseline": {"value": v, "unit": "particle-evals/s", "cores": cores,
                          "kind": "oracle", "sample": sample},
@@ -275,7 +282,9 @@ def main():
     assert torch.cuda.is_available(), "bench needs a CUDA device"
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    cfg, d, inj = make_workload(seed_offset=rank)
+    cfg, d, inj = make_workload(seed_offset=rank, channels=args.channels)
+    aet = args.channels == "AET"
+    ops_per_bin = ALG_OPS_PER_BIN_AET if aet else ALG_OPS_PER_BIN
     if args.particles:
         cfg["P"] = args.particles
     P, N = cfg["P"], cfg["N"]
@@ -334,7 +343,7 @@ def main():
         bin_evals.append(float(np.sum(np.maximum(hi - lo + 1, 0))))
     bin_evals = np.array(bin_evals)
     t_main = stages[:, 2] / 1e3
-    ops = bin_evals * ALG_OPS_PER_BIN
+    ops = bin_evals * ops_per_bin
     sm_mhz = (ck or {}).get("sm_mhz") or 2070.0
     props = torch.cuda.get_device_properties(dev)
     peak = props.multi_processor_count * 128 * sm_mhz * 1e6   # lane-ops/s
@@ -382,8 +391,10 @@ def main():
         dh = dict(d)
         dh["A"] = d["A"].copy()
         dh["E"] = d["E"].copy()
+        if aet:
+            dh["T"] = d["T"].copy()
         oracle.inject(inj, d["f_first"], d["df"], d["K"], d["T_obs"], d["SA"], d["SE"],
-                      cfg["snr"], dh["A"], dh["E"])
+                      cfg["snr"], dh["A"], dh["E"], T=dh.get("T"), ST=d.get("ST"))
         sample = host_batches[args.warmup][:args.cpu_sample]
         t0 = time.perf_counter()
         ref = oracle.evaluate(dh, sample, N, mode=oracle.EQUAL_SNR2)
@@ -405,9 +416,10 @@ def main():
         "dtype": "f32", "dtype_note": "f32/int32 per bin; f64 anchors, edges and segment totals",
         "data": "synthetic",
         "config": {"workload": f"{WORKLOAD}: one-year stream T=3.15e7 s, K={d['K']} bins x "
-                               f"TDI A,E; P={P} particles uniform in the prior box; "
+                               f"TDI {','.join(args.channels)}; P={P} particles uniform in the prior box; "
                                f"N={N} equal-SNR^2 segments; injection SNR {cfg['snr']}",
                    "P": P, "K": int(d["K"]), "N": N, "path": "mixed",
+                   "channels": args.channels,
                    "tile_bins": 1 << tile,
                    "autotune_ms": {str(1 << (11 + i)): float(t) for i, t in enumerate(tile_ms)},
                    "l2": "256 MB buffer written between timed steps",
@@ -417,9 +429,9 @@ def main():
             ("setup_worklist", "segment_edges", "main", "fixup"), stages.mean(axis=0))},
         "roofline": {"bound": "alu", "kernel": "k_main_mixed", "achieved": achieved / 1e12,
                      "peak": peak / 1e12, "unit": "Tops/s", "frac": achieved / peak,
-                     "traffic": None if args.particles else MAIN_TRAFFIC_BYTES.get(tile),
+                     "traffic": None if (args.particles or aet) else MAIN_TRAFFIC_BYTES.get(tile),
                      "traffic_unit": "bytes per launch (ncu dram read + write)",
-                     "note": f"{ALG_OPS_PER_BIN} lane-ops per support bin-eval; peak = "
+                     "note": f"{ops_per_bin} lane-ops per support bin-eval; peak = "
                              f"{props.multi_processor_count} SMs x 128 lanes x "
                              f"{sm_mhz:.0f} MHz (median SM clock under load)"},
         "e2e": e2e,

@@ -97,6 +97,20 @@ int scs_set_data(scs_ctx *ctx, int stream_id, const double *A, const double *E,
                  const double *S_A, const double *S_E, double f_first,
                  double df, int64_t K, double T_obs);
 
+/* As scs_set_data, with the third TDI channel T = (X + Y + Z)/sqrt3 and its
+ * PSD S_T (the search uses all three channels, Sec. I; T's response, like
+ * A's and E's, from the rigid-adiabatic model of Sec. IV).  Every later
+ * evaluation, edge, log-likelihood and injection on the stream then sums
+ * over A, E and T: z_n gains w_T d_T conj(h_T), [h|h]_n gains w_T |h_T|^2,
+ * <d|d> gains w_T |d_T|^2.  scs_set_data on the slot drops the channel.
+ *   T    K complex values, interleaved (re, im), FP64 (host or device).
+ *   S_T  K one-sided PSD values (> 0, finite).
+ * Errors: as scs_set_data; SCS_EINVAL also for a null T or S_T. */
+int scs_set_data_aet(scs_ctx *ctx, int stream_id, const double *A, const double *E,
+                     const double *T, const double *S_A, const double *S_E,
+                     const double *S_T, double f_first, double df, int64_t K,
+                     double T_obs);
+
 /* Choose the segmentation of a stream (Sec. II.B): N segments, 1 <= N <= K,
  * mode SCS_EQUAL_WIDTH (edges floor(n K/N) shared by all particles) or
  * SCS_EQUAL_SNR2 (per particle: the cumulative template power
@@ -303,10 +317,17 @@ int scs_pso_search(scs_ctx *ctx, const int *ladder, int n_rungs, const double *h
 int scs_waveform(scs_ctx *ctx, int stream_id, const double *theta, double *hA,
                  double *hE, void *cuda_stream);
 
+/* As scs_waveform, and h_T of the third channel (T = (X + Y + Z)/sqrt3) in
+ * hT (2K doubles, host or device), on any stream's grid.
+ * Errors: as scs_waveform. */
+int scs_waveform_aet(scs_ctx *ctx, int stream_id, const double *theta, double *hA,
+                     double *hE, double *hT, void *cuda_stream);
+
 /* Add an injection to the loaded data of a stream: d += snr h/sqrt(<h|h>)
  * with h the template of theta (Sec. IV: injected signals scaled to a target
- * SNR).  *hh_out (may be NULL) receives <h|h> of the un-normalised
- * template.  Synchronous.
+ * SNR), over A, E and, on a stream loaded with scs_set_data_aet, T.
+ * *hh_out (may be NULL) receives <h|h> of the un-normalised template.
+ * Synchronous.
  * Errors: SCS_EINVAL, SCS_ENODATA, SCS_ECUDA. */
 int scs_inject(scs_ctx *ctx, int stream_id, const double *theta, double snr,
                double *hh_out);

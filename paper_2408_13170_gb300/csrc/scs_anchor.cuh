@@ -32,6 +32,9 @@ struct PhaseAnchor {
 struct RespQuad {
   float g0[4], g1[4], g2[4];   // G_A.re, G_A.im, G_E.re, G_E.im = g0 + j (g1 + j g2)
 };
+struct RespQuadT {
+  float g0[2], g1[2], g2[2];   // G_T.re, G_T.im
+};
 
 // x (turns) -> fixed point modulo one turn
 __device__ inline uint64_t turns_to_fixed(double x) {
@@ -186,40 +189,57 @@ __device__ inline uint64_t phase_anchor_at(const PhaseAnchor& an, int j) {
 // G_alpha at bin offset x from the phase anchor (FP32 node).  Inlined into
 // a single loop over the span's nodes (one copy of the code, no call
 // overhead or register spills around a call).
+// G_A, G_E (and G_T when kT) at bin offset x from the phase anchor, FP32.
+template <bool kT>
 __device__ __forceinline__ void g_node32(const Part* __restrict__ pp, float al0, float tq1,
                                       float tq2, float tq3, float fa32, float df32, float x,
-                                      float4* out) {
+                                      float4* out, float2* outT) {
   const Part& p = *pp;
   float dt = x * (tq1 + x * (tq2 + x * tq3));
   float al = al0 + (float)kOmega * dt;
   float sa, ca;
   sincos_small32(al, &sa, &ca);
   float f = fa32 + x * df32;
-  Cx<float> RA, RE;
-  response_residual<float>(f, ca, sa, p.Pr32, p.Pi32, p.k32, RA, RE);
+  Cx<float> RA, RE, RT;
+  response_residual<float>(f, ca, sa, p.Pr32, p.Pi32, p.k32, RA, RE, RT);
   const float u = rcbrtf(f);
   const float amp = rsqrtf(f) * u * u;   // f^{-1/2} f^{-2/3}
   *out = make_float4(amp * RA.re, amp * RA.im, amp * RE.re, amp * RE.im);
+  if constexpr (kT) *outT = make_float2(amp * RT.re, amp * RT.im);
 }
 
-// G_alpha at bin offset x from k_a, FP64 with the exact t(f) (stride checks).
-__device__ inline void g_exact64(const Part& p, double fa, double df, double x, double out[4]) {
+// G_alpha at bin offset x from k_a, FP64 with the exact t(f) (stride checks):
+// out[0..3] = G_A, G_E (re, im), out[4..5] = G_T.
+__device__ inline void g_exact64(const Part& p, double fa, double df, double x, double out[6]) {
   double f = fa + x * df;
   double t = time_of_freq(p, f);
   double sa, ca;
   sincos_small(orbit_angle(t), &sa, &ca);
   const double kv[3] = {p.kx, p.ky, p.kz};
-  Cx<double> RA, RE;
-  response_residual<double>(f, ca, sa, p.Pr, p.Pi, kv, RA, RE);
+  Cx<double> RA, RE, RT;
+  response_residual<double>(f, ca, sa, p.Pr, p.Pi, kv, RA, RE, RT);
   double u = rcbrt(f);
   double amp = u * u * u * sqrt(u);
   out[0] = amp * RA.re;
   out[1] = amp * RA.im;
   out[2] = amp * RE.re;
   out[3] = amp * RE.im;
+  out[4] = amp * RT.re;
+  out[5] = amp * RT.im;
 }
 
 // Quadratic through nodes (0, y0), (h, y1), (2h, y2) as g0 + j (g1 + j g2).
+__device__ inline void quad_from_nodes_t(float2 y0, float2 y1, float2 y2, float h, RespQuadT& q) {
+  const float a0[2] = {y0.x, y0.y}, a1[2] = {y1.x, y1.y}, a2[2] = {y2.x, y2.y};
+  float ih = 1.0f / h;
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    float g2 = 0.5f * (a0[c] - 2.0f * a1[c] + a2[c]) * ih * ih;
+    q.g0[c] = a0[c];
+    q.g1[c] = (a1[c] - a0[c]) * ih - g2 * h;
+    q.g2[c] = g2;
+  }
+}
 __device__ inline void quad_from_nodes(float4 y0, float4 y1, float4 y2, float h, RespQuad& q) {
   const float a0[4] = {y0.x, y0.y, y0.z, y0.w}, a1[4] = {y1.x, y1.y, y1.z, y1.w},
               a2[4] = {y2.x, y2.y, y2.z, y2.w};

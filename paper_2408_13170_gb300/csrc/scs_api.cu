@@ -44,6 +44,8 @@ struct DataStream {
   double f_first = 0, df = 0, T_obs = 0;
   int K = 0;
   DevBuf dA64, dE64, w64, d32, w32;
+  bool has_T = false;   // the third TDI channel (scs_set_data_aet)
+  DevBuf dT64, wT64, t32;
   DevBuf wmax;          // max w as the bits of a double (FP32 scale W0)
   double W0 = 1.0;
   int N = 0, mode = -1;
@@ -75,7 +77,7 @@ struct scs_ctx {
   int device = 0;
   int path = SCS_MIXED;
   int num_sms = 0;
-  int grid_mixed = 0, grid_fp64 = 0;
+  int grid_mixed = 0, grid_mixed_t = 0, grid_fp64 = 0;
   cudaStream_t stream = nullptr;
   std::string err;
   bool prof = false;               // record stage events in the evaluation calls
@@ -83,7 +85,7 @@ struct scs_ctx {
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   std::map<int, DataStream> streams;
   DevBuf slot[kNumSlots];          // pipeline scratch (grow-only)
-  DevBuf params, stat, segx, segh, tmpA, tmpE, tmpS1, tmpS2, red, misc;
+  DevBuf params, stat, segx, segh, tmpA, tmpE, tmpT, tmpS1, tmpS2, tmpS3, red, misc;
   DevBuf ll_x, ll_h, ll_stat, ll_amp, ll_out, ll_o, ll_hh;   // log-likelihood call
   // device-side particle swarm (scs_pso_*)
   struct Pso {
@@ -223,6 +225,9 @@ std::vector<StreamDesc> make_table(const std::vector<BatchPart>& parts, int* n_c
     d.dA64 = ds.dA64.as<double2>();
     d.dE64 = ds.dE64.as<double2>();
     d.w64 = ds.w64.as<double2>();
+    d.t32 = ds.has_T ? ds.t32.as<float4>() : nullptr;
+    d.dT64 = ds.has_T ? ds.dT64.as<double2>() : nullptr;
+    d.wT64 = ds.has_T ? ds.wT64.as<double>() : nullptr;
     d.width_edges = ds.width_edges.as<int>();
   }
   *n_chunks_total = cb;
@@ -271,6 +276,7 @@ struct Prepared {
   int* list = nullptr;
   int* edges = nullptr;     // equal-SNR^2 edge tables
   bool any_snr2 = false;
+  bool any_ae = false, any_t = false;   // streams without / with the third channel
   int s_max = 1;            // record slices per particle in the fix-up
 };
 
@@ -290,6 +296,10 @@ int prepare_batch(scs_ctx* ctx, const std::vector<BatchPart>& parts, const doubl
   for (const StreamDesc& d : table) {
     bound += (int64_t)d.n_p * d.n_chunks;
     out.any_snr2 = out.any_snr2 || d.mode == SCS_EQUAL_SNR2;
+    if (d.n_p > 0) {
+      out.any_ae = out.any_ae || d.t32 == nullptr;
+      out.any_t = out.any_t || d.t32 != nullptr;
+    }
     max_chunks = std::max(max_chunks, d.n_chunks);
   }
   out.s_max = std::max(1, (max_chunks + kSlice - 1) / kSlice);
@@ -372,9 +382,21 @@ int run_batch(scs_ctx* ctx, const Prepared& pr, int P, double* dstat, double* ds
   a.chunk_hi = pr.n_chunks;
   a.item_counter = counter;
   if (ctx->prof) CK(cudaEventRecord(ctx->ev[2], s));
-  if (ctx->path == SCS_MIXED) launch_main_mixed(a, ctx->grid_mixed, s);
-  else launch_main_fp64(a, ctx->grid_fp64, s);
-  CKLAUNCH();
+  if (ctx->path == SCS_MIXED) {
+    // one kernel per channel set, each with its own item counter
+    if (pr.any_ae || !pr.any_t) {
+      launch_main_mixed(a, 0, ctx->grid_mixed, s);
+      CKLAUNCH();
+    }
+    if (pr.any_t) {
+      a.item_counter = counter + 1;
+      launch_main_mixed(a, 1, ctx->grid_mixed_t, s);
+      CKLAUNCH();
+    }
+  } else {
+    launch_main_fp64(a, ctx->grid_fp64, s);
+    CKLAUNCH();
+  }
   if (ctx->prof) CK(cudaEventRecord(ctx->ev[3], s));
   SliceSum* slices = (SliceSum*)src.get(kSlotSlices, sizeof(SliceSum) * (size_t)P * pr.s_max);
   if (src.failed()) {
@@ -395,10 +417,11 @@ int run_batch(scs_ctx* ctx, const Prepared& pr, int P, double* dstat, double* ds
 }
 
 int ensure_grids(scs_ctx* ctx) {
-  int bm = 0, bf = 0;
-  if (occupancy_mixed(&bm) || occupancy_fp64(&bf))
+  int bm = 0, bt = 0, bf = 0;
+  if (occupancy_mixed(0, &bm) || occupancy_mixed(1, &bt) || occupancy_fp64(&bf))
     return fail(ctx, SCS_ECUDA, "occupancy query failed");
   ctx->grid_mixed = ctx->num_sms * (bm > 0 ? bm : 1);
+  ctx->grid_mixed_t = ctx->num_sms * (bt > 0 ? bt : 1);
   ctx->grid_fp64 = ctx->num_sms * (bf > 0 ? bf : 1);
   return SCS_OK;
 }
@@ -447,6 +470,7 @@ void scs_destroy(scs_ctx* ctx) {
   for (auto& kv : ctx->streams) {
     DataStream& d = kv.second;
     d.dA64.release(); d.dE64.release(); d.w64.release(); d.d32.release(); d.w32.release();
+    d.dT64.release(); d.wT64.release(); d.t32.release();
     d.wmax.release();
     d.width_edges.release();
   }
@@ -463,7 +487,8 @@ void scs_destroy(scs_ctx* ctx) {
     for (DevBuf* b : pb) b->release();
   }
   DevBuf* bufs[] = {&ctx->params, &ctx->stat,  &ctx->segx,   &ctx->segh,   &ctx->tmpA,
-                    &ctx->tmpE,   &ctx->tmpS1, &ctx->tmpS2,  &ctx->red,    &ctx->misc,
+                    &ctx->tmpE,   &ctx->tmpT,  &ctx->tmpS1,  &ctx->tmpS2,  &ctx->tmpS3,
+                    &ctx->red,    &ctx->misc,
                     &ctx->ll_x,   &ctx->ll_h,  &ctx->ll_stat, &ctx->ll_amp, &ctx->ll_out,
                     &ctx->ll_o,   &ctx->ll_hh};
   for (DevBuf* b : bufs) b->release();
@@ -482,11 +507,19 @@ int scs_set_path(scs_ctx* ctx, int path) {
   return SCS_OK;
 }
 
-int scs_set_data(scs_ctx* ctx, int sid, const double* A, const double* E, const double* S_A,
-                 const double* S_E, double f_first, double df, int64_t K, double T_obs) {
+}  // extern "C"
+
+namespace {
+
+// scs_set_data (T = S_T = null) and scs_set_data_aet
+int set_data_impl(scs_ctx* ctx, int sid, const double* A, const double* E, const double* T,
+                  const double* S_A, const double* S_E, const double* S_T, double f_first,
+                  double df, int64_t K, double T_obs) {
   if (!ctx) return SCS_EINVAL;
   if (sid < 0 || sid >= 1024) return fail(ctx, SCS_EINVAL, "stream_id %d out of range", sid);
   if (!A || !E || !S_A) return fail(ctx, SCS_EINVAL, "null data pointer");
+  const bool withT = T != nullptr;
+  if (withT && !S_T) return fail(ctx, SCS_EINVAL, "null T-channel PSD");
   if (K < 1 || K > (int64_t)0x7fffffff - (1 << kLog2ChunkMax))
     return fail(ctx, SCS_EINVAL, "K = %lld out of range", (long long)K);
   if (!(df > 0.0) || !std::isfinite(df) || !(f_first > 0.0) || !std::isfinite(f_first) ||
@@ -497,8 +530,8 @@ int scs_set_data(scs_ctx* ctx, int sid, const double* A, const double* E, const 
   if (rc) return rc;
   cudaStream_t s = ctx->stream;
   // PSD validation before anything is written
-  const double* S[2] = {S_A, S_E};
-  for (int c = 0; c < 2; ++c) {
+  const double* S[3] = {S_A, S_E, withT ? S_T : nullptr};
+  for (int c = 0; c < 3; ++c) {
     if (!S[c]) continue;
     if (is_device_ptr(S[c])) {
       CK(ctx->misc.reserve(sizeof(int)));
@@ -526,13 +559,24 @@ int scs_set_data(scs_ctx* ctx, int sid, const double* A, const double* E, const 
   CK(ds.w32.reserve(sizeof(float2) * (Kz + 32)));
   CK(cudaMemsetAsync(ds.d32.as<float4>() + Kz, 0, sizeof(float4) * 32, s));
   CK(cudaMemsetAsync(ds.w32.as<float2>() + Kz, 0, sizeof(float2) * 32, s));
+  ds.has_T = withT;
+  if (withT) {
+    CK(ds.dT64.reserve(sizeof(double2) * Kz));
+    CK(ds.wT64.reserve(sizeof(double) * Kz));
+    CK(ds.t32.reserve(sizeof(float4) * (Kz + 32)));
+    CK(cudaMemsetAsync(ds.t32.as<float4>() + Kz, 0, sizeof(float4) * 32, s));
+  } else {
+    ds.dT64.release();
+    ds.wT64.release();
+    ds.t32.release();
+  }
   // raw inputs on the device (reuse scratch)
-  const void* in[4] = {A, E, S_A, S_E};
-  size_t sz[4] = {sizeof(double2) * Kz, sizeof(double2) * Kz, sizeof(double) * Kz,
-                  sizeof(double) * Kz};
-  DevBuf* tmp[4] = {&ctx->tmpA, &ctx->tmpE, &ctx->tmpS1, &ctx->tmpS2};
-  const void* din[4];
-  for (int i = 0; i < 4; ++i) {
+  const void* in[6] = {A, E, S_A, S_E, withT ? T : nullptr, withT ? S_T : nullptr};
+  size_t sz[6] = {sizeof(double2) * Kz, sizeof(double2) * Kz, sizeof(double) * Kz,
+                  sizeof(double) * Kz, sizeof(double2) * Kz, sizeof(double) * Kz};
+  DevBuf* tmp[6] = {&ctx->tmpA, &ctx->tmpE, &ctx->tmpS1, &ctx->tmpS2, &ctx->tmpT, &ctx->tmpS3};
+  const void* din[6];
+  for (int i = 0; i < 6; ++i) {
     if (!in[i]) {
       din[i] = nullptr;
       continue;
@@ -547,15 +591,19 @@ int scs_set_data(scs_ctx* ctx, int sid, const double* A, const double* E, const 
   }
   CK(ds.wmax.reserve(sizeof(unsigned long long)));
   CK(cudaMemsetAsync(ds.wmax.ptr, 0, sizeof(unsigned long long), s));
+  double2* dT64 = withT ? ds.dT64.as<double2>() : nullptr;
+  double* wT64 = withT ? ds.wT64.as<double>() : nullptr;
   k_prewhiten<<<2048, 256, 0, s>>>((const double2*)din[0], (const double2*)din[1],
-                                   (const double*)din[2], (const double*)din[3], df, (int)K,
+                                   (const double2*)din[4], (const double*)din[2],
+                                   (const double*)din[3], (const double*)din[5], df, (int)K,
                                    ds.dA64.as<double2>(), ds.dE64.as<double2>(),
-                                   ds.w64.as<double2>(), ds.wmax.as<unsigned long long>());
+                                   ds.w64.as<double2>(), dT64, wT64,
+                                   ds.wmax.as<unsigned long long>());
   CKLAUNCH();
   k_to_fp32<<<2048, 256, 0, s>>>(ds.dA64.as<double2>(), ds.dE64.as<double2>(),
-                                 ds.w64.as<double2>(), (int)K,
+                                 ds.w64.as<double2>(), dT64, wT64, (int)K,
                                  ds.wmax.as<unsigned long long>(), ds.d32.as<float4>(),
-                                 ds.w32.as<float2>());
+                                 ds.w32.as<float2>(), withT ? ds.t32.as<float4>() : nullptr);
   CKLAUNCH();
   unsigned long long wbits = 0;
   CK(cudaMemcpyAsync(&wbits, ds.wmax.ptr, sizeof wbits, cudaMemcpyDeviceToHost, s));
@@ -575,6 +623,22 @@ int scs_set_data(scs_ctx* ctx, int sid, const double* A, const double* E, const 
   }
   ds.gen++;
   return SCS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int scs_set_data(scs_ctx* ctx, int sid, const double* A, const double* E, const double* S_A,
+                 const double* S_E, double f_first, double df, int64_t K, double T_obs) {
+  return set_data_impl(ctx, sid, A, E, nullptr, S_A, S_E, nullptr, f_first, df, K, T_obs);
+}
+
+int scs_set_data_aet(scs_ctx* ctx, int sid, const double* A, const double* E, const double* T,
+                     const double* S_A, const double* S_E, const double* S_T, double f_first,
+                     double df, int64_t K, double T_obs) {
+  if (ctx && (!T || !S_T)) return fail(ctx, SCS_EINVAL, "null T-channel pointer");
+  return set_data_impl(ctx, sid, A, E, T, S_A, S_E, S_T, f_first, df, K, T_obs);
 }
 
 int scs_set_segments(scs_ctx* ctx, int sid, int N, int mode) {
@@ -724,7 +788,10 @@ int scs_eval_loglike(scs_ctx* ctx, int sid, const double* params, int64_t P, con
   }
   CK(ctx->red.reserve(sizeof(double) * 1025));
   k_dd<<<1024, 256, 0, s>>>(ds->dA64.as<double2>(), ds->dE64.as<double2>(),
-                            ds->w64.as<double2>(), ds->K, ctx->red.as<double>());
+                            ds->w64.as<double2>(),
+                            ds->has_T ? ds->dT64.as<double2>() : nullptr,
+                            ds->has_T ? ds->wT64.as<double>() : nullptr, ds->K,
+                            ctx->red.as<double>());
   CKLAUNCH();
   k_sum<<<1, 256, 0, s>>>(ctx->red.as<double>(), 1024, ctx->red.as<double>() + 1024);
   CKLAUNCH();
@@ -901,8 +968,10 @@ int scs_segment_edges(scs_ctx* ctx, int sid, const double* params, int64_t P, in
   return SCS_OK;
 }
 
+// the FP64 template h_A, h_E (and h_T if hT is not null) of one particle on
+// the stream's grid, in context scratch
 static int template_to(scs_ctx* ctx, DataStream& ds, const double* theta, cudaStream_t s,
-                       double2** hA, double2** hE) {
+                       double2** hA, double2** hE, double2** hT = nullptr) {
   const double* dth = nullptr;
   int rc = stage_params(ctx, theta, 1, s, &dth);
   if (rc) return rc;
@@ -918,11 +987,13 @@ static int template_to(scs_ctx* ctx, DataStream& ds, const double* theta, cudaSt
   if (hp.status == kInvalid) return fail(ctx, SCS_EINVAL, "non-physical template parameters");
   CK(ctx->tmpA.reserve(sizeof(double2) * ds.K));
   CK(ctx->tmpE.reserve(sizeof(double2) * ds.K));
+  if (hT) CK(ctx->tmpT.reserve(sizeof(double2) * ds.K));
   launch_waveform_fp64(pr.part, ds.f_first, ds.df, ds.K, ctx->tmpA.as<double2>(),
-                       ctx->tmpE.as<double2>(), s);
+                       ctx->tmpE.as<double2>(), hT ? ctx->tmpT.as<double2>() : nullptr, s);
   CKLAUNCH();
   *hA = ctx->tmpA.as<double2>();
   *hE = ctx->tmpE.as<double2>();
+  if (hT) *hT = ctx->tmpT.as<double2>();
   return SCS_OK;
 }
 
@@ -944,6 +1015,25 @@ int scs_waveform(scs_ctx* ctx, int sid, const double* theta, double* hA, double*
   return SCS_OK;
 }
 
+int scs_waveform_aet(scs_ctx* ctx, int sid, const double* theta, double* hA, double* hE,
+                     double* hT, void* cuda_stream) {
+  if (!ctx) return SCS_EINVAL;
+  if (!theta || !hA || !hE || !hT) return fail(ctx, SCS_EINVAL, "null pointer");
+  int rc = bind(ctx);
+  if (rc) return rc;
+  DataStream* ds = get_stream(ctx, sid, false);
+  if (!ds) return SCS_ENODATA;
+  cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : ctx->stream;
+  double2 *tA, *tE, *tT;
+  rc = template_to(ctx, *ds, theta, s, &tA, &tE, &tT);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(hA, tA, sizeof(double2) * ds->K, cudaMemcpyDefault, s));
+  CK(cudaMemcpyAsync(hE, tE, sizeof(double2) * ds->K, cudaMemcpyDefault, s));
+  CK(cudaMemcpyAsync(hT, tT, sizeof(double2) * ds->K, cudaMemcpyDefault, s));
+  CK(cudaStreamSynchronize(s));
+  return SCS_OK;
+}
+
 int scs_inject(scs_ctx* ctx, int sid, const double* theta, double snr, double* hh_out) {
   if (!ctx) return SCS_EINVAL;
   if (!theta || !std::isfinite(snr)) return fail(ctx, SCS_EINVAL, "bad arguments");
@@ -952,12 +1042,14 @@ int scs_inject(scs_ctx* ctx, int sid, const double* theta, double snr, double* h
   DataStream* ds = get_stream(ctx, sid, false);
   if (!ds) return SCS_ENODATA;
   cudaStream_t s = ctx->stream;
-  double2 *tA, *tE;
-  rc = template_to(ctx, *ds, theta, s, &tA, &tE);
+  double2 *tA, *tE, *tT = nullptr;
+  rc = template_to(ctx, *ds, theta, s, &tA, &tE, ds->has_T ? &tT : nullptr);
   if (rc) return rc;
+  double* wT64 = ds->has_T ? ds->wT64.as<double>() : nullptr;
   const int nb = 1024;
   CK(ctx->red.reserve(sizeof(double) * nb));
-  k_hh<<<nb, 256, 0, s>>>(tA, tE, ds->w64.as<double2>(), ds->K, ctx->red.as<double>());
+  k_hh<<<nb, 256, 0, s>>>(tA, tE, ds->w64.as<double2>(), tT, wT64, ds->K,
+                          ctx->red.as<double>());
   CKLAUNCH();
   std::vector<double> part(nb);
   CK(cudaMemcpyAsync(part.data(), ctx->red.ptr, sizeof(double) * nb, cudaMemcpyDeviceToHost, s));
@@ -966,9 +1058,11 @@ int scs_inject(scs_ctx* ctx, int sid, const double* theta, double snr, double* h
   for (double v : part) hh += v;
   if (hh_out) *hh_out = hh;
   double scale = hh > 0.0 ? snr / std::sqrt(hh) : 0.0;
-  k_add_template<<<2048, 256, 0, s>>>(tA, tE, scale, ds->K, ds->dA64.as<double2>(),
-                                      ds->dE64.as<double2>(), ds->w64.as<double2>(),
-                                      ds->wmax.as<unsigned long long>(), ds->d32.as<float4>());
+  k_add_template<<<2048, 256, 0, s>>>(
+      tA, tE, tT, scale, ds->K, ds->dA64.as<double2>(), ds->dE64.as<double2>(),
+      ds->w64.as<double2>(), ds->has_T ? ds->dT64.as<double2>() : nullptr, wT64,
+      ds->wmax.as<unsigned long long>(), ds->d32.as<float4>(),
+      ds->has_T ? ds->t32.as<float4>() : nullptr);
   CKLAUNCH();
   CK(cudaStreamSynchronize(s));
   return SCS_OK;

@@ -346,9 +346,12 @@ __device__ inline float sinc_(float x) {
 
 // ca, sa: cos/sin of the orbital angle alpha = Omega t (any precision T);
 // f in Hz; P: polarisation tensor (re/im of xx,yy,zz,xy,xz,yz); k: direction.
+// RA, RE, RT: the orthonormal TDI combinations (Z - X)/sqrt2,
+// (X - 2Y + Z)/sqrt6 and (X + Y + Z)/sqrt3 (callers without the third
+// channel leave RT unused).
 template <typename T>
 __device__ inline void response_residual(T f, T ca, T sa, const T* Pr, const T* Pi,
-                                         const T* kv, Cx<T>& RA, Cx<T>& RE) {
+                                         const T* kv, Cx<T>& RA, Cx<T>& RE, Cx<T>& RT) {
   const T L = (T)kArm;
   const T eR2 = (T)(kArm / (4.0 * 1.7320508075688772));   // e R / 2 = L/(4 sqrt3)
   const T s3 = (T)1.7320508075688772;
@@ -408,15 +411,18 @@ __device__ inline void response_residual(T f, T ca, T sa, const T* Pr, const T* 
   const T is2 = (T)0.70710678118654752, is6 = (T)0.40824829046386302;
   RA = Cx<T>{(Z.re - X.re) * is2, (Z.im - X.im) * is2};
   RE = Cx<T>{(X.re - (T)2 * Y.re + Z.re) * is6, (X.im - (T)2 * Y.im + Z.im) * is6};
+  const T is3 = (T)0.57735026918962576;
+  RT = Cx<T>{(X.re + Y.re + Z.re) * is3, (X.im + Y.im + Z.im) * is3};
 }
 
-// |R_A|^2 and |R_E|^2 of the residual response in FP64 for the equal-SNR^2
-// anchors.  Same model as response_residual; the phase e^{-i pi f L} common
-// to all six links is dropped (it cancels in |.|^2), the sinc arguments
+// |R_A|^2 and |R_E|^2 (and |R_T|^2 if pT is not null) of the residual
+// response in FP64 for the equal-SNR^2 anchors.  Same model as
+// response_residual; the phase e^{-i pi f L} common to all six links is
+// dropped (it cancels in |.|^2), the sinc arguments
 // a (1 -+ k.n), a = pi f L, come from sin/cos of a and of a k.n by angle
 // addition (direct sin when the argument is small), and D = e^{-2 i a}.
 __device__ inline void response_power64(const Part& p, double f, double ca, double sa,
-                                        double& pA, double& pE) {
+                                        double& pA, double& pE, double* pT) {
   const double L = kArm;
   const double eR2 = kArm / (4.0 * 1.7320508075688772);
   const double s3 = 1.7320508075688772;
@@ -498,6 +504,11 @@ __device__ inline void response_power64(const Part& p, double f, double ca, doub
   double Ei = (X.im - 2.0 * Y.im + Z.im) * 0.40824829046386302;
   pA = Ar * Ar + Ai * Ai;
   pE = Er * Er + Ei * Ei;
+  if (pT) {
+    const double Tr = (X.re + Y.re + Z.re) * 0.57735026918962576;
+    const double Ti = (X.im + Y.im + Z.im) * 0.57735026918962576;
+    *pT = Tr * Tr + Ti * Ti;
+  }
 }
 
 // orbital angle reduced to [-pi, pi] in FP64
@@ -529,9 +540,10 @@ __device__ inline double phase_turns_fp64(const Part& p, dd f, double& t_out) {
 }
 
 // Full per-bin FP64 template factors: G_alpha = f^{-7/6} R_alpha (residual
-// response) and the total phase Phi, so that h_alpha = G_alpha e^{-2 pi i Phi}.
+// response, alpha = A, E, T) and the total phase Phi, so that
+// h_alpha = G_alpha e^{-2 pi i Phi}.
 __device__ inline void bin_fp64(const Part& p, double f_first, double df, int64_t k,
-                                Cx<double>& GA, Cx<double>& GE, double& phi) {
+                                Cx<double>& GA, Cx<double>& GE, Cx<double>& GT, double& phi) {
   dd f = grid_freq_dd(f_first, df, k);
   double t;
   phi = phase_turns_fp64(p, f, t);
@@ -539,13 +551,14 @@ __device__ inline void bin_fp64(const Part& p, double f_first, double df, int64_
   double sa, ca;
   sincos_small(orbit_angle(t), &sa, &ca);
   const double kv[3] = {p.kx, p.ky, p.kz};
-  Cx<double> RA, RE;
-  response_residual<double>(fd, ca, sa, p.Pr, p.Pi, kv, RA, RE);
+  Cx<double> RA, RE, RT;
+  response_residual<double>(fd, ca, sa, p.Pr, p.Pi, kv, RA, RE, RT);
   // A(f) = f^{-7/6} = u^3 sqrt(u), u = f^{-1/3}
   double u = rcbrt(fd);
   double amp = u * u * u * sqrt(u);
   GA = Cx<double>{amp * RA.re, amp * RA.im};
   GE = Cx<double>{amp * RE.re, amp * RE.im};
+  GT = Cx<double>{amp * RT.re, amp * RT.im};
 }
 
 }  // namespace scs

@@ -3,7 +3,8 @@
 // Every support bin of every particle is evaluated from scratch in FP64:
 // the waveform phase in double-double (reduced modulo one turn), t(f), the
 // residual TDI response and the guiding-centre Doppler phase, then
-// z += d~ conj(h) and hh += w |h|^2 (Sec. II.A Eq. inner_prod, Sec. II.B).
+// z += d~ conj(h) and hh += w |h|^2 over the channels A, E (and T on a
+// stream with the third channel) (Sec. II.A Eq. inner_prod, Sec. II.B).
 // This is the baseline the mixed path is measured against, and a second
 // GPU implementation for parity with the CPU oracle.
 #include "scs_internal.cuh"
@@ -75,18 +76,25 @@ __global__ void __launch_bounds__(128) k_main_fp64(EvalArgs a) {
           n_cur = advance_segment(e, N, n_cur, k);
           e_next = __ldg(e + n_cur + 1);
         }
-        Cx<double> GA, GE;
+        Cx<double> GA, GE, GT;
         double phi;
-        bin_fp64(pp, sd.f_first, sd.df, k, GA, GE, phi);
+        bin_fp64(pp, sd.f_first, sd.df, k, GA, GE, GT, phi);
         double sp, cp;
         sincospi(2.0 * phi, &sp, &cp);
         double2 dA = sd.dA64[k], dE = sd.dE64[k], w = sd.w64[k];
         // q = d~_A conj(G_A) + d~_E conj(G_E);  z += q e^{+2 pi i Phi}
         double qr = dA.x * GA.re + dA.y * GA.im + dE.x * GE.re + dE.y * GE.im;
         double qi = dA.y * GA.re - dA.x * GA.im + dE.y * GE.re - dE.x * GE.im;
+        double hb = w.x * (GA.re * GA.re + GA.im * GA.im) + w.y * (GE.re * GE.re + GE.im * GE.im);
+        if (sd.dT64) {
+          const double2 dT = sd.dT64[k];
+          qr += dT.x * GT.re + dT.y * GT.im;
+          qi += dT.y * GT.re - dT.x * GT.im;
+          hb += sd.wT64[k] * (GT.re * GT.re + GT.im * GT.im);
+        }
         s.zr += qr * cp - qi * sp;
         s.zi += qr * sp + qi * cp;
-        s.hh += w.x * (GA.re * GA.re + GA.im * GA.im) + w.y * (GE.re * GE.re + GE.im * GE.im);
+        s.hh += hb;
       }
     }
     if (act) {
@@ -106,22 +114,24 @@ __global__ void __launch_bounds__(128) k_main_fp64(EvalArgs a) {
 }
 
 __global__ void k_waveform_fp64(const Part* part, double f_first, double df, int K,
-                                double2* hA, double2* hE) {
+                                double2* hA, double2* hE, double2* hT) {
   const Part& p = *part;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
-    double2 a = make_double2(0.0, 0.0), b = make_double2(0.0, 0.0);
+    double2 a = make_double2(0.0, 0.0), b = make_double2(0.0, 0.0), c = make_double2(0.0, 0.0);
     if (p.status == kOk && k >= p.k_lo && k <= p.k_hi) {
-      Cx<double> GA, GE;
+      Cx<double> GA, GE, GT;
       double phi;
-      bin_fp64(p, f_first, df, k, GA, GE, phi);
+      bin_fp64(p, f_first, df, k, GA, GE, GT, phi);
       double sp, cp;
       sincospi(2.0 * phi, &sp, &cp);
       // h = G e^{-2 pi i Phi}
       a = make_double2(GA.re * cp + GA.im * sp, GA.im * cp - GA.re * sp);
       b = make_double2(GE.re * cp + GE.im * sp, GE.im * cp - GE.re * sp);
+      c = make_double2(GT.re * cp + GT.im * sp, GT.im * cp - GT.re * sp);
     }
     hA[k] = a;
     hE[k] = b;
+    if (hT) hT[k] = c;
   }
 }
 
@@ -132,10 +142,10 @@ void launch_main_fp64(const EvalArgs& a, int grid, cudaStream_t s) {
 }
 
 void launch_waveform_fp64(const Part* part, double f_first, double df, int K, double2* hA,
-                          double2* hE, cudaStream_t s) {
+                          double2* hE, double2* hT, cudaStream_t s) {
   int blocks = (K + 255) / 256;
   if (blocks > 4096) blocks = 4096;
-  k_waveform_fp64<<<blocks, 256, 0, s>>>(part, f_first, df, K, hA, hE);
+  k_waveform_fp64<<<blocks, 256, 0, s>>>(part, f_first, df, K, hA, hE, hT);
 }
 
 int occupancy_fp64(int* blocks_per_sm) {

@@ -55,6 +55,10 @@ struct StreamDesc {
   const double2* dA64;
   const double2* dE64;
   const double2* w64;
+  // the third TDI channel T (all null for a two-channel stream)
+  const float4* t32;     // (T.re / sqrt(W0), T.im / sqrt(W0), w_T / W0, 0)
+  const double2* dT64;
+  const double* wT64;
   const int* width_edges;   // equal width: the shared table e_n = floor(n K / N)
 };
 
@@ -147,12 +151,15 @@ void launch_km_centroid_of(const KmArgs& a, int j, const double* th, cudaStream_
 // loads the swarm kernels (so that a later stream capture loads nothing); 0 on success
 int preload_pso();
 
-void launch_main_mixed(const EvalArgs& a, int grid, cudaStream_t s);
+// The mixed path has one kernel per channel set: with_t = 0 takes the
+// items of the two-channel (A, E) streams, with_t = 1 those of the streams
+// with the third channel T; each skips the other's items.
+void launch_main_mixed(const EvalArgs& a, int with_t, int grid, cudaStream_t s);
 void launch_main_fp64(const EvalArgs& a, int grid, cudaStream_t s);
 void launch_waveform_fp64(const Part* part, double f_first, double df, int K,
-                          double2* hA, double2* hE, cudaStream_t s);
+                          double2* hA, double2* hE, double2* hT, cudaStream_t s);
 // resident 128-thread blocks per SM of the main kernels (0 on success)
-int occupancy_mixed(int* blocks_per_sm);
+int occupancy_mixed(int with_t, int* blocks_per_sm);
 int occupancy_fp64(int* blocks_per_sm);
 
 // chunk index of a grid bin within its stream

@@ -2,7 +2,8 @@
 //
 // Layout: one warp takes a work item (one chunk of 2^log2_chunk grid bins x up to
 // 32 particles active in it), one lane per particle.  All lanes walk the
-// same bins, so each bin's pre-whitened data (float4 d~ and float2 w) is one
+// same bins, so each bin's pre-whitened data (float4 d~ and float2 w, and a
+// float4 (d~_T, w_T) on a stream with the third TDI channel) is one
 // warp-uniform load shared by 32 templates.  Per bin and lane, in FP32/INT32:
 //   phase:     degree-6 forward differences in 64-bit fixed point
 //              (exact modulo one turn), re-seeded at each phase anchor
@@ -54,6 +55,8 @@ struct Lane {
   float al0, tq1, tq2, tq3, fa32;
   RespQuad rq;
   float4 yend;
+  RespQuadT rqT;     // G_T (kernels with the third channel only)
+  float2 yendT;
   Kahan szr, szi, shh, ups;
   float bzr, bzi, bhh;
 };
@@ -62,6 +65,7 @@ struct Lane {
 struct ItemStream {
   const float4* d32;
   const float2* w32;
+  const float4* t32;      // (d~_T, w_T), streams with the third channel
   double W0, zs;          // FP32 sums -> physical units: z * zs, hh * W0
   int N;
   double* seg_x;
@@ -116,10 +120,13 @@ __device__ __forceinline__ void finish_close(Lane& L, const ItemStream& a, doubl
 // a second, unmasked copy measured slower through its larger code).  The
 // data of bin k+1 is loaded while bin k is computed (the FP32 arrays carry a
 // zeroed tail for the last prefetch).
+template <bool kT>
 __device__ __forceinline__ void run_block(Lane& L, const ItemStream& a, double zs, int k0,
                                           int nb) {
   float4 dn = __ldg(a.d32 + k0);
   float2 wn = __ldg(a.w32 + k0);
+  float4 tn;
+  if constexpr (kT) tn = __ldg(a.t32 + k0);
   const unsigned span = L.act ? (unsigned)(L.ke - L.kb) : 0u;
 #pragma unroll 2
   for (int i = 0; i < nb; ++i) {
@@ -128,6 +135,11 @@ __device__ __forceinline__ void run_block(Lane& L, const ItemStream& a, double z
     const float2 wv = wn;
     dn = __ldg(a.d32 + k + 1);
     wn = __ldg(a.w32 + k + 1);
+    float4 tv;
+    if constexpr (kT) {
+      tv = tn;
+      tn = __ldg(a.t32 + k + 1);
+    }
     const bool m = (unsigned)(k - L.kb) < span;
     // a segment ends before bin k: keep its block sums, restart them (at
     // most one end per lane and block); fma(b, 1, z) rounds as b + z
@@ -143,10 +155,17 @@ __device__ __forceinline__ void run_block(Lane& L, const ItemStream& a, double z
     float G[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) G[q] = fmaf(L.jf, fmaf(L.jf, L.rq.g2[q], L.rq.g1[q]), L.rq.g0[q]);
-    // q = d~_A conj(G_A) + d~_E conj(G_E)
-    const float qr = dv.x * G[0] + dv.y * G[1] + dv.z * G[2] + dv.w * G[3];
-    const float qi = dv.y * G[0] - dv.x * G[1] + dv.w * G[2] - dv.z * G[3];
-    const float hb = wv.x * (G[0] * G[0] + G[1] * G[1]) + wv.y * (G[2] * G[2] + G[3] * G[3]);
+    // q = d~_A conj(G_A) + d~_E conj(G_E) (+ d~_T conj(G_T))
+    float qr = dv.x * G[0] + dv.y * G[1] + dv.z * G[2] + dv.w * G[3];
+    float qi = dv.y * G[0] - dv.x * G[1] + dv.w * G[2] - dv.z * G[3];
+    float hb = wv.x * (G[0] * G[0] + G[1] * G[1]) + wv.y * (G[2] * G[2] + G[3] * G[3]);
+    if constexpr (kT) {
+      const float T0 = fmaf(L.jf, fmaf(L.jf, L.rqT.g2[0], L.rqT.g1[0]), L.rqT.g0[0]);
+      const float T1 = fmaf(L.jf, fmaf(L.jf, L.rqT.g2[1], L.rqT.g1[1]), L.rqT.g0[1]);
+      qr += tv.x * T0 + tv.y * T1;
+      qi += tv.y * T0 - tv.x * T1;
+      hb += tv.z * (T0 * T0 + T1 * T1);
+    }
     float zr = qr * cp - qi * sp, zi = qr * sp + qi * cp;
     if (!m) {
       zr = 0.f;
@@ -161,7 +180,11 @@ __device__ __forceinline__ void run_block(Lane& L, const ItemStream& a, double z
   }
 }
 
-__global__ void __launch_bounds__(128, 4) k_main_mixed(EvalArgs a) {
+// kT: the kernel of the streams with the third channel (it skips the
+// two-channel streams' items, and the other kernel skips its items); its
+// extra registers take it to three resident blocks per SM.
+template <bool kT>
+__global__ void __launch_bounds__(128, kT ? 3 : 4) k_main_mixed(EvalArgs a) {
   const int lane = threadIdx.x & 31;
   const int first = a.item_off[a.chunk_lo], total = a.item_off[a.chunk_hi];
   for (;;) {
@@ -171,9 +194,11 @@ __global__ void __launch_bounds__(128, 4) k_main_mixed(EvalArgs a) {
     if (item >= total) break;
     const int cg = find_item_chunk(a.item_off, a.n_chunks, item);
     const StreamDesc& sd = a.streams[stream_of_chunk(a.streams, a.n_streams, cg)];
+    if ((sd.t32 != nullptr) != kT) continue;   // the other kernel's item
     ItemStream is;
     is.d32 = sd.d32;
     is.w32 = sd.w32;
+    is.t32 = sd.t32;
     is.W0 = sd.W0;
     is.zs = sqrt(sd.W0);
     is.N = sd.N;
@@ -231,6 +256,9 @@ __global__ void __launch_bounds__(128, 4) k_main_mixed(EvalArgs a) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) L.rq.g0[q] = L.rq.g1[q] = L.rq.g2[q] = 0.f;
     L.yend = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < 2; ++q) L.rqT.g0[q] = L.rqT.g1[q] = L.rqT.g2[q] = 0.f;
+    L.yendT = make_float2(0.f, 0.f);
     L.al0 = L.tq1 = L.tq2 = L.tq3 = L.fa32 = 0.f;
     L.jf = 0.f;
     L.next_phase = first;
@@ -263,20 +291,34 @@ __global__ void __launch_bounds__(128, 4) k_main_mixed(EvalArgs a) {
         // nodes at x0 + q h: q = 0 only after a new phase anchor (otherwise it
         // is the previous sub-span's end), then q = 1, 2
         float4 y0 = L.yend, y1 = L.yend, y2 = L.yend;
+        float2 u0 = L.yendT, u1 = L.yendT, u2 = L.yendT;
         for (int q = L.fresh ? 0 : 1; q < 3; ++q) {
           float4 t;
-          g_node32(L.pp, L.al0, L.tq1, L.tq2, L.tq3, L.fa32, df32, x0 + (float)q * h, &t);
-          if (q == 0) y0 = t;
-          else if (q == 1) y1 = t;
-          else y2 = t;
+          float2 tt;
+          g_node32<kT>(L.pp, L.al0, L.tq1, L.tq2, L.tq3, L.fa32, df32, x0 + (float)q * h, &t,
+                       &tt);
+          if (q == 0) {
+            y0 = t;
+            if constexpr (kT) u0 = tt;
+          } else if (q == 1) {
+            y1 = t;
+            if constexpr (kT) u1 = tt;
+          } else {
+            y2 = t;
+            if constexpr (kT) u2 = tt;
+          }
         }
         L.yend = y2;
         quad_from_nodes(y0, y1, L.yend, h, L.rq);
+        if constexpr (kT) {
+          L.yendT = u2;
+          quad_from_nodes_t(u0, u1, u2, h, L.rqT);
+        }
         L.fresh = false;
         L.jf = 0.f;
         L.next_resp += 1 << L.log2Br;
       }
-      run_block(L, is, zs, k0, nb);
+      run_block<kT>(L, is, zs, k0, nb);
       L.pend = (unsigned)(L.e_cut - k0) < (unsigned)nb;   // the cut fell in this block
       if (__any_sync(kFull, L.pend)) {
         if (L.pend) finish_close(L, is, zs);
@@ -314,12 +356,16 @@ __global__ void __launch_bounds__(128, 4) k_main_mixed(EvalArgs a) {
 
 }  // namespace
 
-void launch_main_mixed(const EvalArgs& a, int grid, cudaStream_t s) {
-  k_main_mixed<<<grid, 128, 0, s>>>(a);
+void launch_main_mixed(const EvalArgs& a, int with_t, int grid, cudaStream_t s) {
+  if (with_t) k_main_mixed<true><<<grid, 128, 0, s>>>(a);
+  else k_main_mixed<false><<<grid, 128, 0, s>>>(a);
 }
 
-int occupancy_mixed(int* blocks_per_sm) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_main_mixed, 128, 0) !=
+int occupancy_mixed(int with_t, int* blocks_per_sm) {
+  return (with_t ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm,
+                                                                  k_main_mixed<true>, 128, 0)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm,
+                                                                  k_main_mixed<false>, 128, 0)) !=
          cudaSuccess;
 }
 

@@ -16,7 +16,8 @@ namespace {
 //    the exact (double-double) phase;
 //  - response: the largest Br <= B for which the quadratic through FP64
 //    nodes at 0, Br/2, Br stays within kTolG of the exact G relative to
-//    |G_A| + |G_E| (so only the truncation is measured; the FP32 rounding of
+//    |G_A| + |G_E| (+ |G_T| on a stream with the third channel, whose
+//    components are then checked too; so only the truncation is measured; the FP32 rounding of
 //    the kernel's nodes does not depend on Br and is bounded by the parity
 //    tests).
 // Both start from an analytic estimate of the remainder at the low end of
@@ -26,7 +27,7 @@ namespace {
 // less than 1e-10 relative: a phase offset common to a segment is maximised
 // out, and a slow drift enters |z_n| only at second order.
 constexpr double kTolPhase = 1e-6;   // turns
-constexpr double kTolG = 3e-7;       // relative to |G_A| + |G_E|
+constexpr double kTolG = 3e-7;       // relative to |G_A| + |G_E| (+ |G_T|)
 
 __device__ inline int span_start(int k, int B) { return (k / B) * B; }
 
@@ -52,27 +53,30 @@ __device__ bool phase_check(const Part& p, int B, int s, int t, double f_first, 
 }
 
 // Response: the quadratic through the exact FP64 nodes at 0, Br/2, Br of the
-// span against the exact G at the offset.
-__device__ bool resp_check(const Part& p, int Br, int s, int t, double f_first, double df) {
+// span against the exact G at the offset (G_A, G_E, and G_T if withT).
+__device__ bool resp_check(const Part& p, int Br, int s, int t, double f_first, double df,
+                           bool withT) {
   const int k = s == 0 ? p.k_lo : (s == 1 ? (p.k_lo + p.k_hi) / 2 : p.k_hi);
   const int ka = span_start(k, Br);
   const int jlo = max(0, p.k_lo - ka), jhi = min(Br - 1, p.k_hi - ka);
   if (jhi < jlo) return true;
   const double h = 0.5 * (double)Br;
   double fa = f_first + (double)ka * df;
-  double y0[4], y1[4], y2[4];
+  double y0[6], y1[6], y2[6];
   g_exact64(p, fa, df, 0.0, y0);
   g_exact64(p, fa, df, h, y1);
   g_exact64(p, fa, df, 2.0 * h, y2);
   const int jt = t == 0 ? Br / 4 : (t == 1 ? (3 * Br) / 4 : Br - 1);
   double x = (double)min(max(jt, jlo), jhi);
-  double g[4];
+  double g[6];
   g_exact64(p, fa, df, x, g);
   double l0 = (x - h) * (x - 2.0 * h) / (2.0 * h * h);
   double l1 = -x * (x - 2.0 * h) / (h * h);
   double l2 = x * (x - h) / (2.0 * h * h);
   double err = 0.0, mag = hypot(g[0], g[1]) + hypot(g[2], g[3]);
-  for (int c = 0; c < 4; ++c) err += fabs(l0 * y0[c] + l1 * y1[c] + l2 * y2[c] - g[c]);
+  if (withT) mag += hypot(g[4], g[5]);
+  const int nc = withT ? 6 : 4;
+  for (int c = 0; c < nc; ++c) err += fabs(l0 * y0[c] + l1 * y1[c] + l2 * y2[c] - g[c]);
   return err <= kTolG * mag;
 }
 
@@ -158,6 +162,7 @@ __global__ void __launch_bounds__(kSetupThreads) k_setup(const double* params, i
     const bool mine = i < P && p.status == kOk;
     const double f_first = mine ? streams[p.sid].f_first : 0.0;
     const double df = mine ? streams[p.sid].df : 0.0;
+    const bool withT = mine && streams[p.sid].t32 != nullptr;
     for (int pass = 0; pass < 2; ++pass) {   // 0: phase stride, 1: response sub-span
       if (warp == 0) s_done[lane] = !(mine && s_l[lane] > 0);   // 2^0 needs no check
       for (;;) {
@@ -166,7 +171,8 @@ __global__ void __launch_bounds__(kSetupThreads) k_setup(const double* params, i
         const int l = s_l[lane];
         if (!s_done[lane]) {
           const bool ok = pass == 0 ? phase_check(p, 1 << l, warp / 3, warp % 3, f_first, df)
-                                    : resp_check(p, 1 << l, warp / 3, warp % 3, f_first, df);
+                                    : resp_check(p, 1 << l, warp / 3, warp % 3, f_first, df,
+                                                 withT);
           if (!ok) atomicOr(&s_fail[lane], 1u << warp);
         }
         __syncthreads();
@@ -355,7 +361,8 @@ __global__ void k_sort_chunks(const Part* part, const int* cnt, const int* list_
 
 // Equal-SNR^2 edges (one warp per particle).  The cumulative template power
 // is the trapezoid sum over the anchor bins k_lo, k_lo + 1024, ..., k_hi of
-// hh(k) = sum_alpha w_alpha(k) |h_alpha(f_k)|^2, evaluated exactly in FP64;
+// hh(k) = sum_alpha w_alpha(k) |h_alpha(f_k)|^2 (alpha = A, E, then T on a
+// stream with the third channel), evaluated exactly in FP64;
 // target c_n = n C/N; kappa_n by linear inverse interpolation; segment n
 // starts at bin ceil(kappa_n).  The double operations follow that order
 // explicitly (no contraction) so that the rounding is the definition's.
@@ -370,6 +377,7 @@ __global__ void k_bounds(const Part* part, int p_lo, int p_hi, const StreamDesc*
   const int N = sd.N;
   const double f_first = sd.f_first, df = sd.df;
   const double2* w64 = sd.w64;
+  const double* wT64 = sd.wT64;
   const int64_t amax = sd.amax;
   const int64_t lp = gw - sd.p_off;
   int* e = edges_all + sd.edge_base + lp * (N + 1);
@@ -388,12 +396,14 @@ __global__ void k_bounds(const Part* part, int p_lo, int p_hi, const StreamDesc*
     double t = time_of_freq_u(p, u);
     double sa, ca;
     sincos_small(orbit_angle(t), &sa, &ca);
-    double pA, pE;
-    response_power64(p, f, ca, sa, pA, pE);
+    double pA, pE, pT = 0.0;
+    response_power64(p, f, ca, sa, pA, pE, wT64 ? &pT : nullptr);
     // |h|^2 = A(f)^2 |R|^2 with A(f)^2 = f^{-7/3} = u^7, u = f^{-1/3}
     double amp2 = u2 * u2 * u2 * u;
     double2 w = w64[ka];
-    H[a] = __dadd_rn(__dmul_rn(w.x, amp2 * pA), __dmul_rn(w.y, amp2 * pE));
+    double hk = __dadd_rn(__dmul_rn(w.x, amp2 * pA), __dmul_rn(w.y, amp2 * pE));
+    if (wT64) hk = __dadd_rn(hk, __dmul_rn(wT64[ka], amp2 * pT));
+    H[a] = hk;
   }
   __syncwarp();
   // trapezoid terms (k_a - k_{a-1}) (H_{a-1} + H_a) / 2 in parallel (halving
@@ -616,11 +626,12 @@ __global__ void __launch_bounds__(32) k_fixup(const Part* part, const int2* cran
   stat[i] = ups;
 }
 
-// d~ = w d with w = 4 df / S (FP64); the largest w goes to *wmax (positive
-// doubles order like their bit patterns).
-__global__ void k_prewhiten(const double2* A, const double2* E, const double* SA,
-                            const double* SE, double df, int K, double2* dA64, double2* dE64,
-                            double2* w64, unsigned long long* wmax) {
+// d~ = w d with w = 4 df / S (FP64), for A, E and (if T is not null) T; the
+// largest w goes to *wmax (positive doubles order like their bit patterns).
+__global__ void k_prewhiten(const double2* A, const double2* E, const double2* T,
+                            const double* SA, const double* SE, const double* ST, double df,
+                            int K, double2* dA64, double2* dE64, double2* w64, double2* dT64,
+                            double* wT64, unsigned long long* wmax) {
   double m = 0.0;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
     double wa = 4.0 * df / SA[k];
@@ -630,6 +641,13 @@ __global__ void k_prewhiten(const double2* A, const double2* E, const double* SA
     dE64[k] = make_double2(we * e.x, we * e.y);
     w64[k] = make_double2(wa, we);
     m = fmax(m, fmax(wa, we));
+    if (T) {
+      double wt = 4.0 * df / ST[k];
+      double2 t = T[k];
+      dT64[k] = make_double2(wt * t.x, wt * t.y);
+      wT64[k] = wt;
+      m = fmax(m, wt);
+    }
   }
   atomicMax(wmax, (unsigned long long)__double_as_longlong(m));
 }
@@ -637,8 +655,10 @@ __global__ void k_prewhiten(const double2* A, const double2* E, const double* SA
 // FP32 copies for the mixed path, scaled so that FP32 sums cannot overflow:
 // w' = w / W0, d~' = d~ / sqrt(W0) with W0 = max w.  Then z' = z / sqrt(W0)
 // and hh' = hh / W0, so every x_n^2 / hh_n (hence Upsilon_N) is unchanged.
-__global__ void k_to_fp32(const double2* dA64, const double2* dE64, const double2* w64, int K,
-                          const unsigned long long* wmax, float4* d32, float2* w32) {
+__global__ void k_to_fp32(const double2* dA64, const double2* dE64, const double2* w64,
+                          const double2* dT64, const double* wT64, int K,
+                          const unsigned long long* wmax, float4* d32, float2* w32,
+                          float4* t32) {
   double W0 = __longlong_as_double((long long)*wmax);
   double iw = 1.0 / W0, isq = 1.0 / sqrt(W0);
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
@@ -646,6 +666,10 @@ __global__ void k_to_fp32(const double2* dA64, const double2* dE64, const double
     d32[k] = make_float4((float)(da.x * isq), (float)(da.y * isq), (float)(de.x * isq),
                          (float)(de.y * isq));
     w32[k] = make_float2((float)(w.x * iw), (float)(w.y * iw));
+    if (dT64) {
+      double2 dt = dT64[k];
+      t32[k] = make_float4((float)(dt.x * isq), (float)(dt.y * isq), (float)(wT64[k] * iw), 0.f);
+    }
   }
 }
 
@@ -657,14 +681,19 @@ __global__ void k_check_psd(const double* S, int K, int* bad) {
   }
 }
 
-// <h|h> partial sums of a template (block sums into out[blockIdx])
-__global__ void k_hh(const double2* hA, const double2* hE, const double2* w64, int K,
-                     double* out) {
+// <h|h> partial sums of a template (block sums into out[blockIdx]); the T
+// channel's terms when hT is not null
+__global__ void k_hh(const double2* hA, const double2* hE, const double2* w64,
+                     const double2* hT, const double* wT64, int K, double* out) {
   __shared__ double sm[256];
   double s = 0.0;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
     double2 a = hA[k], e = hE[k], w = w64[k];
     s += w.x * (a.x * a.x + a.y * a.y) + w.y * (e.x * e.x + e.y * e.y);
+    if (hT) {
+      double2 t = hT[k];
+      s += wT64[k] * (t.x * t.x + t.y * t.y);
+    }
   }
   sm[threadIdx.x] = s;
   __syncthreads();
@@ -675,14 +704,19 @@ __global__ void k_hh(const double2* hA, const double2* hE, const double2* w64, i
   if (threadIdx.x == 0) out[blockIdx.x] = sm[0];
 }
 
-// <d|d> partial sums: sum_k |d~_A|^2 / w_A + |d~_E|^2 / w_E (d~ = w d)
-__global__ void k_dd(const double2* dA64, const double2* dE64, const double2* w64, int K,
-                     double* out) {
+// <d|d> partial sums: sum_k |d~_A|^2 / w_A + |d~_E|^2 / w_E (d~ = w d), plus
+// |d~_T|^2 / w_T when dT64 is not null
+__global__ void k_dd(const double2* dA64, const double2* dE64, const double2* w64,
+                     const double2* dT64, const double* wT64, int K, double* out) {
   __shared__ double sm[256];
   double s = 0.0;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
     double2 a = dA64[k], e = dE64[k], w = w64[k];
     s += (a.x * a.x + a.y * a.y) / w.x + (e.x * e.x + e.y * e.y) / w.y;
+    if (dT64) {
+      double2 t = dT64[k];
+      s += (t.x * t.x + t.y * t.y) / wT64[k];
+    }
   }
   sm[threadIdx.x] = s;
   __syncthreads();
@@ -726,12 +760,25 @@ __global__ void k_loglike(const double* seg_x, const double* seg_hh, const doubl
   if (H) H[p] = h;
 }
 
-// d~ += s w h (injection) and refresh the scaled FP32 copy
-__global__ void k_add_template(const double2* hA, const double2* hE, double s, int K,
-                               double2* dA64, double2* dE64, const double2* w64,
-                               const unsigned long long* wmax, float4* d32) {
+// d~ += s w h (injection) and refresh the scaled FP32 copy; the T channel
+// too when hT is not null
+__global__ void k_add_template(const double2* hA, const double2* hE, const double2* hT,
+                               double s, int K, double2* dA64, double2* dE64,
+                               const double2* w64, double2* dT64, const double* wT64,
+                               const unsigned long long* wmax, float4* d32, float4* t32) {
   double isq = 1.0 / sqrt(__longlong_as_double((long long)*wmax));
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
+    if (hT) {
+      const double wt = wT64[k];
+      double2 dt = dT64[k], t = hT[k];
+      dt.x += s * wt * t.x;
+      dt.y += s * wt * t.y;
+      dT64[k] = dt;
+      float4 tv = t32[k];   // (.z = w_T / W0 stays)
+      tv.x = (float)(dt.x * isq);
+      tv.y = (float)(dt.y * isq);
+      t32[k] = tv;
+    }
     double2 w = w64[k], a = hA[k], e = hE[k];
     double2 da = dA64[k], de = dE64[k];
     da.x += s * w.x * a.x;

@@ -24,19 +24,25 @@ __global__ void __launch_bounds__(32) k_fixup(const Part* part, const int2* cran
                                               int S_max, const StreamDesc* streams,
                                               const SliceSum* sl, double* stat, double* seg_x,
                                               double* seg_hh);
-__global__ void k_prewhiten(const double2* A, const double2* E, const double* SA,
-                            const double* SE, double df, int K, double2* dA64, double2* dE64,
-                            double2* w64, unsigned long long* wmax);
-__global__ void k_to_fp32(const double2* dA64, const double2* dE64, const double2* w64, int K,
-                          const unsigned long long* wmax, float4* d32, float2* w32);
+// the T-channel arguments (T, ST, dT64, wT64, hT, t32) are null for a
+// two-channel stream
+__global__ void k_prewhiten(const double2* A, const double2* E, const double2* T,
+                            const double* SA, const double* SE, const double* ST, double df,
+                            int K, double2* dA64, double2* dE64, double2* w64, double2* dT64,
+                            double* wT64, unsigned long long* wmax);
+__global__ void k_to_fp32(const double2* dA64, const double2* dE64, const double2* w64,
+                          const double2* dT64, const double* wT64, int K,
+                          const unsigned long long* wmax, float4* d32, float2* w32,
+                          float4* t32);
 __global__ void k_check_psd(const double* S, int K, int* bad);
-__global__ void k_hh(const double2* hA, const double2* hE, const double2* w64, int K,
-                     double* out);
-__global__ void k_add_template(const double2* hA, const double2* hE, double s, int K,
-                               double2* dA64, double2* dE64, const double2* w64,
-                               const unsigned long long* wmax, float4* d32);
-__global__ void k_dd(const double2* dA64, const double2* dE64, const double2* w64, int K,
-                     double* out);
+__global__ void k_hh(const double2* hA, const double2* hE, const double2* w64,
+                     const double2* hT, const double* wT64, int K, double* out);
+__global__ void k_add_template(const double2* hA, const double2* hE, const double2* hT,
+                               double s, int K, double2* dA64, double2* dE64,
+                               const double2* w64, double2* dT64, const double* wT64,
+                               const unsigned long long* wmax, float4* d32, float4* t32);
+__global__ void k_dd(const double2* dA64, const double2* dE64, const double2* w64,
+                     const double2* dT64, const double* wT64, int K, double* out);
 __global__ void k_sum(const double* in, int n, double* out);
 __global__ void k_loglike(const double* seg_x, const double* seg_hh, const double* stat, int P,
                           int N, const double* amp, const double* dd, double* L, double* O,

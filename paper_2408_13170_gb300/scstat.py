@@ -49,12 +49,16 @@ def lib():
         L.scs_set_path.restype = I
         L.scs_set_data.argtypes = [P, I, P, P, P, P, D, D, I64, D]
         L.scs_set_data.restype = I
+        L.scs_set_data_aet.argtypes = [P, I, P, P, P, P, P, P, D, D, I64, D]
+        L.scs_set_data_aet.restype = I
         L.scs_set_segments.argtypes = [P, I, I, I]
         L.scs_set_segments.restype = I
         L.scs_eval_stat.argtypes = [P, I, P, I64, P, P, P, P]
         L.scs_eval_stat.restype = I
         L.scs_waveform.argtypes = [P, I, P, P, P, P]
         L.scs_waveform.restype = I
+        L.scs_waveform_aet.argtypes = [P, I, P, P, P, P, P]
+        L.scs_waveform_aet.restype = I
         L.scs_inject.argtypes = [P, I, P, D, P]
         L.scs_inject.restype = I
         L.scs_support.argtypes = [P, I, P, I64, P, P, P, P]
@@ -160,6 +164,12 @@ def scs_set_data(ctx, stream_id, A, E, S_A, S_E, f_first, df, K, T_obs):
                                    float(f_first), float(df), int(K), float(T_obs)))
 
 
+def scs_set_data_aet(ctx, stream_id, A, E, T, S_A, S_E, S_T, f_first, df, K, T_obs):
+    _check(ctx, lib().scs_set_data_aet(ctx, stream_id, _ptr(A), _ptr(E), _ptr(T), _ptr(S_A),
+                                       _ptr(S_E), _ptr(S_T), float(f_first), float(df), int(K),
+                                       float(T_obs)))
+
+
 def scs_set_segments(ctx, stream_id, N, mode):
     _check(ctx, lib().scs_set_segments(ctx, stream_id, int(N), int(mode)))
 
@@ -180,6 +190,11 @@ def scs_batch_eval(ctx, stream_ids, P_offsets, params, stat, cuda_stream=None):
 def scs_waveform(ctx, stream_id, theta, hA, hE, cuda_stream=None):
     _check(ctx, lib().scs_waveform(ctx, stream_id, _ptr(theta), _ptr(hA), _ptr(hE),
                                    _stream(cuda_stream)))
+
+
+def scs_waveform_aet(ctx, stream_id, theta, hA, hE, hT, cuda_stream=None):
+    _check(ctx, lib().scs_waveform_aet(ctx, stream_id, _ptr(theta), _ptr(hA), _ptr(hE),
+                                       _ptr(hT), _stream(cuda_stream)))
 
 
 def scs_inject(ctx, stream_id, theta, snr):
@@ -393,6 +408,12 @@ class Context:
         SA = np.ascontiguousarray(data["SA"], dtype=np.float64)
         SE = data.get("SE")
         SE = None if SE is None else np.ascontiguousarray(SE, dtype=np.float64)
+        if data.get("T") is not None:   # the third TDI channel with its PSD
+            T = np.ascontiguousarray(data["T"], dtype=np.complex128)
+            ST = np.ascontiguousarray(data["ST"], dtype=np.float64)
+            scs_set_data_aet(self.h, stream_id, A, E, T, SA, SE, ST, data["f_first"],
+                             data["df"], data["K"], data["T_obs"])
+            return
         scs_set_data(self.h, stream_id, A, E, SA, SE, data["f_first"], data["df"], data["K"],
                      data["T_obs"])
 
@@ -430,10 +451,14 @@ class Context:
         scs_batch_eval(self.h, stream_ids, offs, allp, stat)
         return [stat[offs[i]:offs[i + 1]] for i in range(len(params_list))]
 
-    def waveform(self, stream_id, theta, K):
+    def waveform(self, stream_id, theta, K, want_T=False):
         hA = np.empty(K, np.complex128)
         hE = np.empty(K, np.complex128)
         th = np.ascontiguousarray(theta, dtype=np.float64)
+        if want_T:
+            hT = np.empty(K, np.complex128)
+            scs_waveform_aet(self.h, stream_id, th, hA, hE, hT)
+            return hA, hE, hT
         scs_waveform(self.h, stream_id, th, hA, hE)
         return hA, hE
 

@@ -19,7 +19,8 @@ def declared_functions():
 def test_header_declares_the_boundary():
     names = declared_functions()
     for want in ("scs_create", "scs_destroy", "scs_last_error", "scs_set_data",
-                 "scs_set_segments", "scs_eval_stat", "scs_waveform", "scs_inject"):
+                 "scs_set_data_aet", "scs_set_segments", "scs_eval_stat", "scs_waveform",
+                 "scs_waveform_aet", "scs_inject"):
         assert want in names
 
 
