@@ -35,10 +35,12 @@ ALG_OPS_PER_BIN = 36
 # with the third channel T: + G_T interpolation 4, products 4, |G_T|^2 w 4
 ALG_OPS_PER_BIN_AET = 48
 LAUNCHES_PER_STEP = 9   # setup, scan, chunk table, fill, sort, edges, main, 2 x fix-up
-# DRAM bytes (read + write) of one k_main_mixed launch on this workload at full
-# size, per work tile (log2 bins), from ncu captures of this kernel
-# (profiles/k_main_mixed_C2.md); to be re-taken whenever the kernel changes.
-MAIN_TRAFFIC_BYTES = {11: 72.49e6 + 24.82e6, 12: 68.76e6 + 7.69e6}
+# DRAM bytes (read + write) of one two-channel k_main_mixed launch on this
+# workload at full size, per work tile (log2 bins), from ncu captures of the
+# kernel as it is built now; emptied whenever the kernel changes (the
+# captures in profiles/k_main_mixed_C2.md, 97.3 MB with the 2048-bin tile and
+# 76.5 MB with 4096, predate its channel-set template).
+MAIN_TRAFFIC_BYTES = {}
 
 
 def parse():
