@@ -37,10 +37,9 @@ ALG_OPS_PER_BIN_AET = 48
 LAUNCHES_PER_STEP = 9   # setup, scan, chunk table, fill, sort, edges, main, 2 x fix-up
 # DRAM bytes (read + write) of one two-channel k_main_mixed launch on this
 # workload at full size, per work tile (log2 bins), from ncu captures of the
-# kernel as it is built now; emptied whenever the kernel changes (the
-# captures in profiles/k_main_mixed_C2.md, 97.3 MB with the 2048-bin tile and
-# 76.5 MB with 4096, predate its channel-set template).
-MAIN_TRAFFIC_BYTES = {}
+# kernel as it is built now (profiles/k_main_mixed_C2.md); emptied whenever
+# the kernel changes.
+MAIN_TRAFFIC_BYTES = {11: 72.4544e6 + 24.2757e6, 12: 68.4439e6 + 7.6582e6}
 
 
 def parse():
