@@ -276,6 +276,8 @@ def main():
         run_reference(args, rank, world)
         return
     if args.workload == "C4":
+        if args.channels != "AE":
+            raise SystemExit("the uneven-batch workload is defined on TDI A and E only")
         run_swarm(args, rank, world, local)
         return
     import torch
