@@ -141,6 +141,16 @@ class ClockSampler:
                 "samples": len(rows), "reasons": sorted(reasons)}
 
 
+def oracle_threads():
+    """Threads the oracle's OpenMP loop uses: OMP_NUM_THREADS if set, else
+    every host core."""
+    try:
+        n = int(os.environ.get("OMP_NUM_THREADS", "0"))
+    except ValueError:
+        n = 0
+    return n if n > 0 else os.cpu_count()
+
+
 def make_workload(seed_offset=0, channels="AE"):
     from paper_2408_13170_gb300 import synth
     cfg = dict(synth.CONFIGS[WORKLOAD])
@@ -169,7 +179,7 @@ def run_reference(args, rank, world):
         oracle.evaluate(d, b, cfg["N"], mode=oracle.EQUAL_SNR2)
     dt = time.perf_counter() - t0
     v = per_step * args.steps / dt
-    cores = os.cpu_count()
+    cores = oracle_threads()
     sample = (f"{per_step} particles per step of the {WORKLOAD} workload "
               f"(P={cfg['P']}, K={d['K']}, N={cfg['N']} equal-SNR^2), all bins of each")
     print(json.dumps({
@@ -406,7 +416,7 @@ def main():
         acc["max_rel_err_mixed_vs_oracle_sample"] = float(
             np.max(np.abs(m - ref) / np.maximum(np.abs(ref), 1.0)))
         cpu = {"value": len(sample) / tc, "unit": "particle-evals/s",
-               "cores": os.cpu_count(), "kind": "oracle",
+               "cores": oracle_threads(), "kind": "oracle",
                "sample": f"first {len(sample)} particles of a timed batch, every support bin "
                          f"({WORKLOAD}, N={N} equal-SNR^2); {tc:.1f} s wall"}
 
