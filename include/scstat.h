@@ -7,14 +7,15 @@
  * What one evaluation computes, for every particle theta_p
  * (Sec. II.A Eq. inner_prod, Sec. II.B Eq. semi-coherent_O and Upsilon_N):
  *
- *   z_{p,n}  = sum_{k in segment n} sum_{alpha in {A,E}}
+ *   z_{p,n}  = sum_{k in segment n} sum_{alpha in {A,E} (or {A,E,T})}
  *                  4 df d_alpha(f_k) conj(h_alpha(theta_p, f_k)) / S_alpha(f_k)
  *   hh_{p,n} = sum_{k in segment n} sum_alpha 4 df |h_alpha|^2 / S_alpha
  *   x_{p,n}  = max_phi Re{z e^{-i phi}} = |z_{p,n}|
  *   Upsilon_N(p) = sum_n x_{p,n}^2 / hh_{p,n}      (terms with hh = 0 add 0)
  *
  * with h_alpha the (2,2)-mode frequency-domain inspiral (circular TaylorF2
- * to 2PN) times the LISA TDI A/E transfer function at t = t(f) (Sec. IV).
+ * to 2PN) times the LISA TDI A/E (and, on a stream loaded with
+ * scs_set_data_aet, T) transfer function at t = t(f) (Sec. IV).
  *
  * Conventions shared by all calls
  *  - Every function returns 0 (SCS_OK) or a negative SCS_E* code; the text
@@ -50,7 +51,8 @@ extern "C" {
 #define SCS_ENOMEM (-2)       /* device allocation failed */
 #define SCS_ECUDA (-3)        /* a CUDA runtime call or kernel failed */
 #define SCS_ENODATA (-4)      /* stream has no data or no segments yet */
-#define SCS_ETIMEOUT (-5)     /* a bounded device-side wait gave up */
+#define SCS_ETIMEOUT (-5)     /* a bounded device-side wait gave up (reserved:
+                                 no kernel of this library waits) */
 #define SCS_EUNSUPPORTED (-6) /* valid request the library does not do */
 
 /* evaluation paths */
