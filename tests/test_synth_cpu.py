@@ -1,0 +1,53 @@
+"""The seeded input recipes: grid sizes of the configurations, the noise
+convention, the uneven batch's stream shapes, and the three-channel stream
+keeping the two-channel stream's A and E."""
+import numpy as np
+import pytest
+
+from paper_2408_13170_gb300 import synth
+
+
+@pytest.mark.parametrize("name,K", [("C1", 45001), ("C2", 1260001), ("C3", 5040001)])
+def test_config_grids(name, K):
+    cfg = synth.CONFIGS[name]
+    f_first, df, k = synth.grid(cfg["f_min"], cfg["f_max"], cfg["T_obs"])
+    assert k == K
+    assert df * cfg["T_obs"] == pytest.approx(1.0, abs=1e-15)
+    assert f_first == pytest.approx(cfg["f_min"], abs=df)
+
+
+def test_noise_convention():
+    """One-sided PSD: Re and Im ~ N(0, S T/4), so E|n|^2 = S T/2."""
+    rng = np.random.Generator(np.random.PCG64(1))
+    S = np.full(200000, 3.0)
+    n = synth.noise(S, 8.0, rng)
+    assert np.mean(np.abs(n) ** 2) == pytest.approx(3.0 * 8.0 / 2.0, rel=0.01)
+    assert abs(np.mean(n.real * n.imag)) < 0.02 * 6.0
+
+
+def test_uneven_batch_shapes():
+    streams = synth.c4_streams()
+    assert len(streams) == 8
+    assert [s["T_obs"] / synth.YEAR for s in streams] == list(synth.C4_YEARS)
+    assert sum(s["P"] for s in streams) == 86911
+    for i, s in enumerate(streams):
+        w = s["f_max"] - s["f_min"]
+        assert 0.01 <= w <= 0.04 and 0.01 <= s["f_min"] and s["f_max"] <= 0.05
+        assert 2048 <= s["P"] <= 32768
+        assert s["N"] == synth.C4_LADDER[i % len(synth.C4_LADDER)]
+        assert s["seed"] == i + 1
+        assert s["lo"][2] == s["f_min"] and s["hi"][2] == pytest.approx(s["f_min"] + w / 2)
+
+
+def test_three_channel_stream_extends_the_two_channel_one():
+    cfg = dict(T_obs=1e6, f_min=0.0179, f_max=0.0190, seed=4)
+    d2 = synth.make_stream(cfg)
+    d3 = synth.make_stream(cfg, channels="AET")
+    np.testing.assert_array_equal(d3["A"], d2["A"])
+    np.testing.assert_array_equal(d3["E"], d2["E"])
+    assert d3["T"].shape == d2["A"].shape and np.all(d3["ST"] > 0)
+    assert "T" not in d2
+    z = synth.make_stream(cfg, channels="AET", noise_free=True)
+    assert not np.any(z["T"])
+    with pytest.raises(ValueError):
+        synth.make_stream(cfg, channels="XYZ")
