@@ -149,3 +149,20 @@ def test_aet_noise_only_sampling_law():
     mean, var = 2.0 * N, 4.0 * N
     assert abs(u.mean() - mean) < 5 * math.sqrt(var / n)
     assert abs(u.var(ddof=1) - var) < 5 * var * math.sqrt((2 + 12 / (2 * N)) / n)
+
+
+@pytest.mark.parametrize("mode", [oracle.EQUAL_WIDTH, oracle.EQUAL_SNR2])
+def test_aet_loglike_zero_at_noise_free_truth(mode):
+    """log L_N = -<d|d>/2 - a^2<h|h>/2 + a O_N (Sec. II.B) over A, E, T: zero
+    at the noise-free truth with the injected amplitude, -(a - a')^2<h|h>/2
+    at another amplitude a' (so <d|d> carries T's term too)."""
+    d = stream(noise_free=True)
+    hh0 = oracle.inject(THETA_STAR, d["f_first"], d["df"], d["K"], d["T_obs"], d["SA"],
+                        d["SE"], 11.0, d["A"], d["E"], T=d["T"], ST=d["ST"])
+    a = 11.0 / math.sqrt(hh0)
+    assert oracle.inner_dd(d) == pytest.approx(121.0, rel=1e-12)
+    for N in (1, 8):
+        L, O, H = oracle.loglike(d, THETA_STAR[None], N, mode=mode, amp=[a])
+        assert abs(L[0]) <= 1e-10 * 121.0
+        L2, _, _ = oracle.loglike(d, THETA_STAR[None], N, mode=mode, amp=[1.3 * a])
+        assert L2[0] == pytest.approx(-0.5 * (0.3 * a) ** 2 * hh0, rel=1e-9)
