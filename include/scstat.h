@@ -377,7 +377,7 @@ int scs_last_timings(scs_ctx *ctx, double *ms);
  *   Every call shares the array and it keeps the previous call's contents:
  *   calls that overlap on the GPU (different streams, or different contexts
  *   on one device) race and must be serialised by the caller.
- * The stream's data (scs_set_data) and segmentation must already be set.
+ * The stream's data (scs_set_data or scs_set_data_aet) and segmentation must already be set.
  * Errors: SCS_EINVAL (sizes, host pointers), SCS_ENODATA, SCS_ECUDA,
  * SCS_EUNSUPPORTED (device index >= 64). */
 int scs_eval_stat_noalloc(scs_ctx *ctx, int stream_id, const double *params,
