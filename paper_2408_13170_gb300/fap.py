@@ -26,12 +26,19 @@ from dataclasses import dataclass
 import numpy as np
 
 
+def _finite(background):
+    bg = np.asarray(background, dtype=np.float64).ravel()
+    if bg.size == 0:
+        raise ValueError("empty background")
+    if not np.all(np.isfinite(bg)):
+        raise ValueError("background values must be finite")
+    return bg
+
+
 def ccdf(background, x):
     """Empirical complementary CDF: the fraction of background values >= x
     (x scalar or array)."""
-    bg = np.sort(np.asarray(background, dtype=np.float64))
-    if bg.size == 0:
-        raise ValueError("empty background")
+    bg = np.sort(_finite(background))
     x = np.asarray(x, dtype=np.float64)
     return (bg.size - np.searchsorted(bg, x, side="left")) / bg.size
 
@@ -59,7 +66,7 @@ class PowerLawTail:
     def fit(cls, background, x_min=30.0):
         """Maximum likelihood (Hill): alpha = n / sum ln(x_i / x_min) over the n
         background values at or above x_min."""
-        bg = np.asarray(background, dtype=np.float64)
+        bg = _finite(background)
         tail = bg[bg >= x_min]
         n = tail.size
         if n < 2:
@@ -94,17 +101,22 @@ class Gumbel:
         """Maximum likelihood: beta solves the score equation (bracketed root),
         then mu = -beta ln mean(e^{-x/beta})."""
         from scipy.optimize import brentq
-        x = np.asarray(background, dtype=np.float64)
+        x = _finite(background)
         if x.size < 3:
             raise ValueError("too few background values to fit")
         sd = float(np.std(x))
         if not sd > 0.0:
             raise ValueError("degenerate background (all values equal)")
         b0 = sd * math.sqrt(6.0) / math.pi        # moment estimate
+        # the score rises from mean - min < 0 (beta -> 0) to +inf: bracket it
         lo, hi = b0, b0
-        while cls._score(lo, x) > 0.0:
+        for _ in range(200):
+            if cls._score(lo, x) <= 0.0:
+                break
             lo *= 0.5
-        while cls._score(hi, x) < 0.0:
+        for _ in range(200):
+            if cls._score(hi, x) >= 0.0:
+                break
             hi *= 2.0
         beta = brentq(cls._score, lo, hi, args=(x,), xtol=1e-14 * b0, rtol=1e-14)
         mu = float(x.min() - beta * math.log(np.mean(np.exp(-(x - x.min()) / beta))))

@@ -21,6 +21,9 @@ def test_ccdf_and_floor():
     assert fap.fap_floor(np.zeros(60)) == pytest.approx(1 / 60)
     with pytest.raises(ValueError):
         fap.ccdf([], 1.0)
+    for f in (fap.ccdf, lambda b, x: fap.PowerLawTail.fit(b, x), lambda b, x: fap.Gumbel.fit(b)):
+        with pytest.raises(ValueError):
+            f([40.0, np.nan, 50.0, 60.0], 30.0)
 
 
 @pytest.mark.parametrize("alpha", [3.48, 1.5])
