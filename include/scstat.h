@@ -358,10 +358,10 @@ int scs_last_timings(scs_ctx *ctx, double *ms);
 
 /* scs_eval_stat without any device allocation.  The paper has no
  * counterpart: this entry point exists for callers that cannot call
- * cudaMalloc at evaluation time -- code being captured into a CUDA graph
- * (allocation is not a capturable operation), services whose device memory
- * is entirely owned by another allocator, and loops that must not pay an
- * allocation's latency or implicit synchronisation.
+ * cudaMalloc at evaluation time -- services whose device memory is entirely
+ * owned by another allocator (a memory pool sized at start-up leaves
+ * nothing for a library to take), and loops that must not pay an
+ * allocation's latency or its implicit device synchronisation.
  *   Same evaluation as scs_eval_stat (path and segmentation of the context
  *   and stream), without per-segment outputs.  params (P x 8) and stat (P)
  *   must be device memory.  Asynchronous on cuda_stream (NULL: the
@@ -374,6 +374,8 @@ int scs_last_timings(scs_ctx *ctx, double *ms);
  *   4 (N+1) + 16 (K/1024 + 2) bytes per particle for equal-SNR^2 segments).
  *   The first call on each device looks up the array's device address
  *   (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   The stream table of the call is handed to the device as a kernel
+ *   argument, so no host buffer is read after the call returns.
  *   Every call shares the array and it keeps the previous call's contents:
  *   calls that overlap on the GPU (different streams, or different contexts
  *   on one device) race and must be serialised by the caller.

@@ -1149,10 +1149,19 @@ int scs_eval_stat_noalloc(scs_ctx* ctx, int sid, const double* params, int64_t P
   ScratchSource src;
   src.base = static_cast<unsigned char*>(g_noalloc_ptr[ctx->device]);
   src.cap = kNoAllocBytes;
+  // the one-stream table goes in as a kernel parameter (no host buffer is
+  // read after the call returns)
+  int nct = 0;
+  int64_t etot = 0, htot = 0;
+  const std::vector<StreamDesc> table = make_table(parts, &nct, &etot, &htot);
+  StreamDesc* dtable = (StreamDesc*)src.get(kSlotStreams, sizeof(StreamDesc));
+  k_put_stream<<<1, 32, 0, s>>>(table[0], dtable);
+  CKLAUNCH();
   Prepared pr;
   const bool prof = ctx->prof;
   ctx->prof = false;
-  rc = prepare_batch(ctx, parts, params, (int)P, ctx->path == SCS_MIXED, true, s, src, pr);
+  rc = prepare_batch(ctx, parts, params, (int)P, ctx->path == SCS_MIXED, true, s, src, pr,
+                     dtable);
   if (!rc) rc = run_batch(ctx, pr, (int)P, stat, nullptr, nullptr, s, src);
   ctx->prof = prof;
   if (rc == SCS_ENOMEM)

@@ -792,6 +792,13 @@ __global__ void k_add_template(const double2* hA, const double2* hE, const doubl
   }
 }
 
+// Writes one stream descriptor, passed by value as a kernel parameter, into
+// device memory: the evaluation without device allocation uploads its
+// one-stream table this way, so no host buffer has to outlive the call.
+__global__ void k_put_stream(StreamDesc d, StreamDesc* out) {
+  if (threadIdx.x == 0) *out = d;
+}
+
 __global__ void k_width_edges(int64_t K, int N, int* e) {
   for (int n = blockIdx.x * blockDim.x + threadIdx.x; n <= N; n += gridDim.x * blockDim.x)
     e[n] = (int)((int64_t)n * K / N);

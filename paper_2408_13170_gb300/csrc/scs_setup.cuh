@@ -47,6 +47,7 @@ __global__ void k_sum(const double* in, int n, double* out);
 __global__ void k_loglike(const double* seg_x, const double* seg_hh, const double* stat, int P,
                           int N, const double* amp, const double* dd, double* L, double* O,
                           double* H);
+__global__ void k_put_stream(StreamDesc d, StreamDesc* out);
 __global__ void k_width_edges(int64_t K, int N, int* e);
 __global__ void k_support_out(const Part* part, int P, int64_t* klo, int64_t* khi,
                               int32_t* l2b);

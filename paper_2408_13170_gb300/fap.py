@@ -118,6 +118,9 @@ class Gumbel:
             if cls._score(hi, x) >= 0.0:
                 break
             hi *= 2.0
+        if not (cls._score(lo, x) <= 0.0 <= cls._score(hi, x)):
+            raise ValueError("Gumbel score not bracketed: no maximum-likelihood scale "
+                             f"found in [{lo:.3g}, {hi:.3g}]")
         beta = brentq(cls._score, lo, hi, args=(x,), xtol=1e-14 * b0, rtol=1e-14)
         mu = float(x.min() - beta * math.log(np.mean(np.exp(-(x - x.min()) / beta))))
         return cls(mu, float(beta))

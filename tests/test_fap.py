@@ -71,6 +71,15 @@ def test_gumbel_recovers_its_parameters(mu, beta):
     assert g.fap(g.mu + z * g.beta) == pytest.approx(math.exp(-z), rel=1e-12)
 
 
+def test_gumbel_fit_reports_an_unbracketed_score(monkeypatch):
+    """If the bracket search cannot enclose a root of the score equation,
+    the fit says so (instead of handing the root finder a bracket without a
+    sign change)."""
+    monkeypatch.setattr(fap.Gumbel, "_score", staticmethod(lambda beta, x: -1.0))
+    with pytest.raises(ValueError, match="not bracketed"):
+        fap.Gumbel.fit(np.array([1.0, 2.0, 4.0, 8.0]))
+
+
 def test_gumbel_of_chi2_maxima():
     """Noise-only Upsilon_1 at a fixed template is chi^2_2 (Sec. II.C): the
     maximum of M independent draws has CDF (1 - e^(-x/2))^M -> Gumbel with

@@ -194,6 +194,34 @@ def test_newtonian_time_closed_form():
             assert tc - t == pytest.approx(tau, rel=1e-12)
 
 
+@pytest.mark.parametrize("theta", [
+    (10.0, 1.0, 0.0101, 0.3, -0.2, 1.0, 0.4, 0.0),   # the largest phase on the grid
+    (30.0, 1.5, 0.018, 1.1, 0.4, 1.2, 0.7, 0.0),
+    (70.0, 6.0, 0.013, 4.0, 1.0, 2.5, 2.9, 0.0),
+])
+def test_tf2_time_is_phase_derivative(theta):
+    """t(f) is defined as Psi'(f)/(2 pi) (Sec. IV reading of the SPA): over
+    one grid bin the phase in turns must advance by the integral of t, which
+    the midpoint rule gives as t(f_k + df/2) df up to t'' df^3/24 (< 1e-11
+    turns here).  The phase (pn_phase_turns, weights 1) and the time
+    (pn_time_offset, weights k - 5) come from separate series, so a wrong
+    weight, sign or power on any PN term of t(f) shows as a mismatch of order
+    1e-5 turns or more; the tolerance is 1e-9 turns."""
+    th = np.array(theta)
+    f_first, df, K = synth.grid(0.01, 0.05, 3.15e7)
+    st, lo, hi = oracle.support(th, f_first, df, K, 3.15e7)
+    assert st == oracle.OK and hi - lo > 1000
+    worst = 0.0
+    for k in np.linspace(lo, hi - 1, 7).astype(int):
+        a = oracle.phase_turns(th, f_first, df, int(k))
+        b = oracle.phase_turns(th, f_first, df, int(k) + 1)
+        t_mid = oracle.time_of_freq(th, f_first + (k + 0.5) * df)
+        d = (b - a) - t_mid * df
+        d -= round(d)
+        worst = max(worst, abs(d))
+    assert worst < 1e-9
+
+
 def test_table1_time_to_merger():
     """Table I: the GW150914-like source (Mc = 28.095555, eta = 0.2471,
     f_low = 0.018 Hz) merges 43.28 months after the start.  The circular 2PN

@@ -1,8 +1,10 @@
 """scs_eval_stat_noalloc: the evaluation entry point for callers that cannot
-allocate device memory at call time (graph capture, externally owned device
-memory, allocation-free loops).  It must give the same statistic as
-scs_eval_stat, on two calls in a row (the shared scratch array keeps the
-previous call's contents), and refuse sizes beyond its fixed scratch.
+allocate device memory at call time (device memory owned by another
+allocator, loops that must not pay an allocation's latency or
+synchronisation).  It must give the same statistic as scs_eval_stat, on two
+calls in a row (the shared scratch array keeps the previous call's
+contents), leave the device's free memory unchanged, and refuse sizes beyond
+its fixed scratch.
 
 This file is collected last on purpose; it also passes on its own."""
 import numpy as np
@@ -45,10 +47,14 @@ def test_noalloc_matches_eval_stat(env, path, tol, mode, N):
     scstat.scs_eval_stat(ctx.h, 0, dev_th, P, ref)
     torch.cuda.synchronize()
     ref = ref.cpu().numpy()
-    for _ in range(2):   # the second call starts from the first call's scratch
+    for call in range(2):   # the second call starts from the first call's scratch
         out = torch.full((P,), np.nan, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         scstat.scs_eval_stat_noalloc(ctx.h, 0, dev_th, P, out)
         torch.cuda.synchronize()
+        if call == 1:   # (the first call may load kernel code on first use)
+            assert torch.cuda.mem_get_info()[0] == free0
         got = out.cpu().numpy()
         assert np.all(np.isfinite(got))
         assert np.max(np.abs(got - ref) / np.maximum(np.abs(ref), 1.0)) <= tol
