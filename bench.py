@@ -1,12 +1,25 @@
 """Benchmark: batched evaluation of the semi-coherent statistic Upsilon_N.
 
-One step = one scs_eval_stat call over one batch of particles on the
-one-year stream (T = 3.15e7 s, 0.01-0.05 Hz -> K = 1 260 001 bins x TDI A, E;
-P = 4096 particles uniform in the prior box; N = 2048 equal-SNR^2 segments;
-Gaussian noise from the analytic A/E PSD plus one injection at SNR 17).
-Prints one JSON line.  `--impl reference` times the FP64 CPU oracle instead;
-`--channels AET` adds the third TDI channel T (its own analytic PSD) to the
-same workload.
+Workloads (`--workload`, default C2):
+  C1  T = 3.0e6 s, 0.015-0.030 Hz (K = 45 001 bins x TDI A, E), P = 256,
+      N = 8 equal-width segments, injection at SNR 20.
+  C2  the one-year stream: T = 3.15e7 s, 0.01-0.05 Hz (K = 1 260 001),
+      P = 4096, N = 2048 equal-SNR^2 segments, injection at SNR 17.
+  C3  the four-year stream: T = 1.26e8 s, 0.01-0.05 Hz (K = 5 040 001),
+      the whole hierarchy N in {16384, 4096, 1024, 256, 64, 16, 1}
+      (equal-SNR^2), 16 384 particles per level (independent draws),
+      injection at SNR 25; one step = all seven levels in one batched
+      launch.
+  C4  the uneven batch: eight streams of 1-4 years, one swarm each; one
+      step = one CUDA-graph launch of --pso-iters whole swarm iterations.
+One step (C1-C3) is one evaluation of every particle of the workload through
+the C ABI, inputs resident on the device; the JSON line also carries the
+same metric end to end (host buffers), the plain FP64 GPU path on the same
+particles (all of them on C1/C2, a seeded subset plus the certified
+best-particle candidates per level on C3), the roofline of the main kernel
+against measured pipe rates, and the FP64 CPU oracle on a bounded sample.
+`--impl reference` times the oracle alone; `--channels AET` adds the third
+TDI channel T (its own analytic PSD) to C1-C3.
 
 Multi-GPU: the statistic shards over independent streams/particle batches
 with no exchange, so N GPUs run N replicas (different seeds, weak scaling);
@@ -27,38 +40,65 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "SC-stat particle-evals/s, mixed vs plain FP64 path on GB300, at rel err ≤1e-5"
-WORKLOAD = "C2"
-# Algorithmic FP32/INT32 lane-operations of the mixed path per support bin and
-# particle: phase advance 8, phase->angle 2,
-# G interpolation 8, channel products 8, rotate-accumulate 4, |G|^2 w 6.
-ALG_OPS_PER_BIN = 36
-# with the third channel T: + G_T interpolation 4, products 4, |G_T|^2 w 4
-ALG_OPS_PER_BIN_AET = 48
+DEFAULT_WORKLOAD = "C2"
+WORKLOADS = ("C1", "C2", "C3", "C4")
+# Algorithmic work of the mixed path per support bin-evaluation (the scope
+# table's count): FP32 issue slots -- phase cubic 3, amplitude 2, response
+# interpolation 8, forming h_A, h_E 12, two complex MACs with d~ 8, norms 5,
+# Kahan updates of three accumulators 12, loads and loop 5 -- and 2 MUFU
+# (one sin/cos pair).  The third channel adds G_T interpolation 4, forming
+# h_T 6, its complex MAC 4 and norm 3.
+FP32_SLOTS_PER_BIN = 55
+FP32_SLOTS_PER_BIN_AET = 72
+MUFU_PER_BIN = 2
+# FP64 operations of one phase anchor of the mixed path as written (Taylor
+# coefficients of the PN phase to 4th order, t(f) and its derivatives, the
+# orbit angle and its sin/cos, the Doppler terms, forward differences and
+# their reduction to fixed point); one anchor per B bins of a particle.
+FP64_OPS_PER_ANCHOR = 190
+# This implementation's own reduced count (FP32/INT32 lane-operations per
+# bin-eval: phase advance 8, phase->angle 2, G interpolation 8, channel
+# products 8, rotate-accumulate 4, |G|^2 w 6), kept for comparison.
+IMPL_OPS_PER_BIN = 36
+IMPL_OPS_PER_BIN_AET = 48
+# bytes of pre-whitened FP32 data per bin read by the main kernel (float4
+# d~ + float2 w, and a float4 (d~_T, w_T) with the third channel)
+DATA_BYTES_PER_BIN = 24
+DATA_BYTES_PER_BIN_AET = 40
 LAUNCHES_PER_STEP = 9   # setup, scan, chunk table, fill, sort, edges, main, 2 x fix-up
-# DRAM bytes (read + write) of one two-channel k_main_mixed launch on this
-# workload at full size, per work tile (log2 bins), from ncu captures of the
-# kernel as it is built now (profiles/k_main_mixed_C2.md); emptied whenever
-# the kernel changes.
-MAIN_TRAFFIC_BYTES = {11: 72.4544e6 + 24.2757e6, 12: 68.4439e6 + 7.6582e6}
+# DRAM bytes (read + write) of one two-channel k_main_mixed launch on the
+# one-year workload at full size, per work tile (log2 bins), from an ncu
+# capture of the kernel as built now; emptied whenever the kernel changes.
+MAIN_TRAFFIC_BYTES: dict[int, float] = {}
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 30; 5 on C3)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison")
-    ap.add_argument("--cpu-sample", type=int, default=48,
-                    help="particles in the CPU-oracle sample")
-    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--fp64-repeats", type=int, default=3,
+                    help="timed FP64-path evaluations (after one untimed)")
+    ap.add_argument("--fp64-subset", type=int, default=64,
+                    help="C3: random particles per level in the FP64-path comparison")
+    ap.add_argument("--cpu-sample", type=int, default=None,
+                    help="particles in the CPU-oracle sample (default per workload)")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=WORKLOADS)
     ap.add_argument("--particles", type=int, default=None,
-                    help="override the particle count (small cases for profiling)")
+                    help="override the particles per level (small cases for profiling)")
     ap.add_argument("--channels", default="AE", choices=["AE", "AET"],
                     help="TDI channels of the data stream")
+    ap.add_argument("--no-peaks", action="store_true",
+                    help="skip the pipe-rate probes (roofline peaks then nominal)")
     ap.add_argument("--pso-iters", type=int, default=10,
                     help="C4: swarm iterations per captured graph (one step = one graph launch)")
-    return ap.parse_args()
+    args = ap.parse_args(argv)
+    if args.steps is None:
+        args.steps = 5 if args.workload == "C3" else 30
+    return args
 
 
 def dist_init(args):
@@ -151,48 +191,107 @@ def oracle_threads():
     return n if n > 0 else os.cpu_count()
 
 
-def make_workload(seed_offset=0, channels="AE"):
-    from paper_2408_13170_gb300 import synth
-    cfg = dict(synth.CONFIGS[WORKLOAD])
-    cfg["seed"] = cfg["seed"] + seed_offset
-    d = synth.make_stream(cfg, channels=channels)
-    inj = synth.injection_params(d["rng"], *cfg["inj"])
-    return cfg, d, inj
+# ------------------------------------------------------------- workloads
+class Workload:
+    """One data stream and its levels: levels[i] = (N, mode, params[P, 8])."""
+
+    def __init__(self, name, seed_offset=0, channels="AE", particles=None):
+        from paper_2408_13170_gb300 import synth
+        self.name = name
+        self.cfg = dict(synth.CONFIGS[name])
+        self.cfg["seed"] = self.cfg["seed"] + seed_offset
+        self.channels = channels
+        self.d = synth.make_stream(self.cfg, channels=channels)
+        self.inj = synth.injection_params(self.d["rng"], *self.cfg["inj"])
+        self.P = particles or self.cfg["P"]
+        Ns = self.cfg["N"] if isinstance(self.cfg["N"], tuple) else (self.cfg["N"],)
+        self.mode = 1 if self.cfg["mode"] == "equal_snr2" else 0
+        self.Ns = list(Ns)
+        self.K = int(self.d["K"])
+
+    def draw(self, rng):
+        """One batch: P particles per level, the injection as particle 0 of
+        every level."""
+        from paper_2408_13170_gb300 import synth
+        out = []
+        for _ in self.Ns:
+            th = synth.draw_particles(self.P, rng)
+            th[0] = self.inj
+            out.append(th)
+        return np.concatenate(out)
+
+    def describe(self):
+        c = self.cfg
+        ch = ",".join(self.channels)
+        seg = "equal-SNR^2" if self.mode else "equal-width"
+        if self.name == "C3":
+            return (f"C3: four-year stream T={c['T_obs']:.3g} s, K={self.K} bins x TDI {ch}; "
+                    f"hierarchy N={self.Ns} {seg}, {self.P} particles per level uniform in "
+                    f"the prior box (one batched launch); injection SNR {c['snr']}")
+        span = "one-year stream" if self.name == "C2" else "short stream"
+        return (f"{self.name}: {span} T={c['T_obs']:.3g} s, K={self.K} bins x TDI {ch}; "
+                f"P={self.P} particles uniform in the prior box; N={self.Ns[0]} {seg} "
+                f"segments; injection SNR {c['snr']}")
+
+    def oracle_data(self):
+        """A host copy of the stream with the injection added by the oracle."""
+        import oracle
+        d = self.d
+        dh = dict(d)
+        dh["A"] = d["A"].copy()
+        dh["E"] = d["E"].copy()
+        if d.get("T") is not None:
+            dh["T"] = d["T"].copy()
+        oracle.inject(self.inj, d["f_first"], d["df"], d["K"], d["T_obs"], d["SA"], d["SE"],
+                      self.cfg["snr"], dh["A"], dh["E"], T=dh.get("T"), ST=d.get("ST"))
+        return dh
+
+
+DEFAULT_CPU_SAMPLE = {"C1": 256, "C2": 48, "C3": 112}
 
 
 def run_reference(args, rank, world):
     """The FP64 CPU oracle, as it stands, on the host cores: each step
-    evaluates a bounded sample of the workload's particles."""
+    evaluates a bounded sample of the workload's particles (the same share
+    of every level)."""
     import oracle
-    from paper_2408_13170_gb300 import synth
     if rank != 0:
         return
-    cfg, d, inj = make_workload(channels=args.channels)
-    oracle.inject(inj, d["f_first"], d["df"], d["K"], d["T_obs"], d["SA"], d["SE"],
-                  cfg["snr"], d["A"], d["E"], T=d.get("T"), ST=d.get("ST"))
-    per_step = max(1, args.cpu_sample // 2)
-    batches = [synth.draw_particles(per_step, d["rng"]) for _ in range(args.warmup + args.steps)]
-    for b in batches[:args.warmup]:
-        oracle.evaluate(d, b, cfg["N"], mode=oracle.EQUAL_SNR2)
+    if args.workload == "C4":
+        print(json.dumps({"impl": "reference", "unavailable":
+                          "the uneven swarm batch has no oracle leg; see the C2 line"}))
+        return
+    w = Workload(args.workload, channels=args.channels, particles=args.particles)
+    dh = w.oracle_data()
+    sample = args.cpu_sample or DEFAULT_CPU_SAMPLE[w.name]
+    per_level = max(1, (sample // 2 if w.name == "C2" else sample) // len(w.Ns))
+    rng = np.random.default_rng(7)
+
+    def one_step():
+        for N in w.Ns:
+            from paper_2408_13170_gb300 import synth
+            th = synth.draw_particles(per_level, rng)
+            oracle.evaluate(dh, th, N, mode=w.mode)
+
+    for _ in range(args.warmup):
+        one_step()
     t0 = time.perf_counter()
-    for b in batches[args.warmup:]:
-        oracle.evaluate(d, b, cfg["N"], mode=oracle.EQUAL_SNR2)
+    for _ in range(args.steps):
+        one_step()
     dt = time.perf_counter() - t0
-    v = per_step * args.steps / dt
-    cores = oracle_threads()
-    sample = (f"{per_step} particles per step of the {WORKLOAD} workload "
-              f"(P={cfg['P']}, K={d['K']}, N={cfg['N']} equal-SNR^2), all bins of each")
+    n_step = per_level * len(w.Ns)
+    v = n_step * args.steps / dt
+    cores = min(oracle_threads(), per_level)   # the oracle's threads split particles
+    sample_txt = (f"{per_level} particles per level and step ({len(w.Ns)} level(s)) of the "
+                  f"{w.name} workload, all bins of each")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "particle-evals/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{WORKLOAD}: one-year stream, {cfg['P']} particles, "
-                               f"K={d['K']} bins x TDI {','.join(args.channels)}, "
-                               f"N={cfg['N']} equal-SNR^2",
-                   "sample_per_step": per_step},
+        "config": {"workload": w.describe(), "sample_per_step": n_step},
         "cpu_baseline": {"value": v, "unit": "particle-evals/s", "cores": cores,
-                         "kind": "oracle", "sample": sample},
+                         "kind": "oracle", "sample": sample_txt},
         "e2e": {"value": v, "unit": "particle-evals/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }))
@@ -279,6 +378,287 @@ def run_swarm(args, rank, world, local):
     }))
 
 
+def roofline(peaks, sms, sm_mhz, bin_evals, anchors, K, t_main, aet, hbm_gbs):
+    """Roofline of the main kernel (per launch, averaged over the timed
+    launches): the slowest of the FP32 issue, MUFU, FP64 and HBM legs at the
+    pipe rates measured on this device, scaled to the SM clock under load."""
+    slots = FP32_SLOTS_PER_BIN_AET if aet else FP32_SLOTS_PER_BIN
+    rate = {k: v["ops_per_clk_sm"] * sms * sm_mhz * 1e6 for k, v in peaks.items()}
+    legs = {
+        "fp32": float(np.mean(bin_evals * slots)) / rate["ffma"],
+        "mufu": float(np.mean(bin_evals * MUFU_PER_BIN)) / rate["mufu"],
+        "fp64": float(np.mean(anchors * FP64_OPS_PER_ANCHOR)) / rate["dfma"],
+        "hbm": K * (DATA_BYTES_PER_BIN_AET if aet else DATA_BYTES_PER_BIN) / (hbm_gbs * 1e9),
+    }
+    bound = max(legs, key=legs.get)
+    t = float(np.mean(t_main))
+    achieved = float(np.mean(bin_evals * slots / t_main))
+    impl_ops = IMPL_OPS_PER_BIN_AET if aet else IMPL_OPS_PER_BIN
+    return {
+        "bound": "alu" if bound == "fp32" else bound, "kernel": "k_main_mixed",
+        "achieved": achieved / 1e12, "peak": rate["ffma"] / 1e12, "unit": "TFP32-slots/s",
+        "frac": legs[bound] / t,
+        "legs_ms": {k: 1e3 * v for k, v in legs.items()}, "measured_ms": 1e3 * t,
+        "peaks_per_clk_sm": {k: v["ops_per_clk_sm"] for k, v in peaks.items()},
+        "peak_source": "measured on this device (scs_peak_probe), scaled to the median SM clock "
+                       "under load",
+        "impl_ops_frac": float(np.mean(bin_evals * impl_ops / t_main)) / rate["ffma"],
+        "note": f"{slots} FP32 issue slots + {MUFU_PER_BIN} MUFU per support bin-eval, "
+                f"{FP64_OPS_PER_ANCHOR} FP64 ops per phase anchor; frac = roofline time of the "
+                "slowest leg / measured kernel time",
+    }
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    from paper_2408_13170_gb300 import scstat, synth
+    assert torch.cuda.is_available(), "bench needs a CUDA device"
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    aet = args.channels == "AET"
+    w = Workload(args.workload, seed_offset=rank, channels=args.channels,
+                 particles=args.particles)
+    P_level, nl = w.P, len(w.Ns)
+    P = P_level * nl
+    sids = list(range(nl))
+    offs = np.arange(nl + 1, dtype=np.int64) * P_level
+
+    peaks = None
+    if not args.no_peaks:
+        from paper_2408_13170_gb300 import peaks as pk
+        peaks = pk.measure(local)
+
+    ctx = scstat.Context(local, scstat.SCS_MIXED)
+    for s, N in zip(sids, w.Ns):     # the levels: the same data, their own N
+        ctx.set_data(s, w.d)
+        ctx.inject(s, w.inj, w.cfg["snr"])
+        ctx.set_segments(s, N, w.mode)
+    nb = args.warmup + args.steps
+    rng = w.d["rng"]
+    host_batches = [w.draw(rng) for _ in range(nb)]
+    batches = torch.tensor(np.stack(host_batches), device=dev)
+    stat = torch.empty((nb, P), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+
+    def evaluate(params, out, cuda_stream):
+        if nl == 1:
+            scstat.scs_eval_stat(ctx.h, 0, params, P, out, cuda_stream=cuda_stream)
+        else:
+            scstat.scs_batch_eval(ctx.h, sids, offs, params, out, cuda_stream=cuda_stream)
+
+    # work tile chosen by the library's autotuner on one level of the first
+    # batch (set-up, not timed) and used for every level
+    tl = min(2, nl - 1)
+    tile, tile_ms = scstat.scs_autotune(ctx.h, tl, batches[0][tl * P_level:(tl + 1) * P_level],
+                                        P_level, cuda_stream=stream)
+    for s in sids:
+        scstat.scs_set_tile(ctx.h, s, tile)
+    scstat.scs_set_profiling(ctx.h, True)
+    for i in range(args.warmup):
+        flush.zero_()
+        evaluate(batches[i], stat[i], stream)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    stage = []
+    barrier(world)
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for j in range(args.steps):
+        flush.zero_()
+        ev[j][0].record(stream)
+        evaluate(batches[args.warmup + j], stat[args.warmup + j], stream)
+        ev[j][1].record(stream)
+        stage.append(scstat.scs_last_timings(ctx.h))
+    torch.cuda.synchronize()
+    barrier(world)
+    wall = time.perf_counter() - wall0
+    ck = clocks.stop()
+    step_ms = np.array([a.elapsed_time(b) for a, b in ev])
+    t_dev = max_over_ranks(step_ms.sum() / 1e3, world, dev)
+    value = world * P * args.steps / t_dev
+    stages = np.array(stage)            # steps x 4
+    scstat.scs_set_profiling(ctx.h, False)
+
+    # algorithmic units of the timed batches: support bin-evals and anchors
+    bin_evals, anchors = [], []
+    for j in range(args.steps):
+        hb = host_batches[args.warmup + j]
+        be = an = 0.0
+        for s in sids:
+            lo, hi, l2 = ctx.support(s, hb[s * P_level:(s + 1) * P_level])
+            ok = hi >= lo
+            be += float(np.sum(np.where(ok, hi - lo + 1, 0)))
+            lb = (l2 & 0xff).astype(np.int64)
+            an += float(np.sum(np.where(ok, (hi >> lb) - (lo >> lb) + 1, 0)))
+        bin_evals.append(be)
+        anchors.append(an)
+    bin_evals, anchors = np.array(bin_evals), np.array(anchors)
+    t_main = stages[:, 2] / 1e3
+    sm_mhz = (ck or {}).get("sm_mhz") or 2070.0
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+    if peaks is None:   # nominal: 128 FP32 / 16 MUFU lanes, FP64 at 1/64 per clock per SM
+        peaks = {"ffma": {"ops_per_clk_sm": 128.0}, "mufu": {"ops_per_clk_sm": 16.0},
+                 "dfma": {"ops_per_clk_sm": 2.0}, "iadd": {"ops_per_clk_sm": 64.0}}
+    roof = roofline(peaks, sms, sm_mhz, bin_evals, anchors, w.K, t_main, aet, hbm)
+    roof["traffic"] = (None if (args.particles or aet or w.name != "C2")
+                       else MAIN_TRAFFIC_BYTES.get(tile))
+    roof["traffic_unit"] = "bytes per launch (ncu dram read + write)"
+    roof["peak_sm_mhz"] = sm_mhz
+
+    # end to end through the public API with host buffers (pinned params in,
+    # stat out; the library copies both ways inside the call)
+    pinned = torch.from_numpy(np.stack(host_batches[:args.steps])).pin_memory()
+    host_stat = np.empty(P)
+    host_params = [pinned[j].numpy() for j in range(args.steps)]
+    barrier(world)
+    t0 = time.perf_counter()
+    for j in range(args.steps):
+        evaluate(host_params[j], host_stat, None)
+    e2e_t = max_over_ranks(time.perf_counter() - t0, world, dev)
+    e2e = {"value": world * P * args.steps / e2e_t, "unit": "particle-evals/s",
+           "h2d_bytes_per_step": P * 8 * 8, "d2h_bytes_per_step": P * 8}
+
+    fp64, acc = (None, {}) if args.no_fp64 else fp64_leg(args, ctx, w, batches, stat, stream,
+                                                         sids, P_level, value / world)
+
+    # CPU oracle on a bounded sample of the same workload (rank 0 only)
+    cpu = None
+    sample = args.cpu_sample if args.cpu_sample is not None else DEFAULT_CPU_SAMPLE[w.name]
+    if rank == 0 and world == 1 and sample > 0:
+        import oracle
+        dh = w.oracle_data()
+        per_level = max(1, sample // nl)
+        hb = host_batches[args.warmup]
+        got = stat[args.warmup].cpu().numpy()
+        t0 = time.perf_counter()
+        errs = []
+        for s, N in zip(sids, w.Ns):
+            th = hb[s * P_level: s * P_level + per_level]
+            ref = oracle.evaluate(dh, th, N, mode=w.mode)
+            m = got[s * P_level: s * P_level + per_level]
+            errs.append(np.max(np.abs(m - ref) / np.maximum(np.abs(ref), 1.0)))
+        tc = time.perf_counter() - t0
+        acc["max_rel_err_mixed_vs_oracle_sample"] = float(np.max(errs))
+        cpu = {"value": per_level * nl / tc, "unit": "particle-evals/s",
+               "cores": min(oracle_threads(), per_level), "kind": "oracle",
+               "sample": f"first {per_level} particle(s) of each of the {nl} level(s) of a "
+                         f"timed batch, every support bin ({w.name}); {tc:.1f} s wall"}
+
+    if rank != 0:
+        return
+    out = {
+        "metric": METRIC, "value": value, "unit": "particle-evals/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "dtype_note": "f32/int32 per bin; f64 anchors, edges and segment totals",
+        "data": "synthetic",
+        "config": {"workload": w.describe(), "P": P, "P_per_level": P_level, "K": w.K,
+                   "N": w.Ns if nl > 1 else w.Ns[0], "path": "mixed",
+                   "channels": args.channels, "tile_bins": 1 << tile,
+                   "autotune_ms": {str(1 << (11 + i)): float(t) for i, t in enumerate(tile_ms)},
+                   "l2": "256 MB buffer written between timed steps",
+                   "parallelism": f"replicas x{world}"},
+        "bin_evals_per_s": float(world * bin_evals.sum() / t_dev),
+        "stage_ms": {k: float(v) for k, v in zip(
+            ("setup_worklist", "segment_edges", "main", "fixup"), stages.mean(axis=0))},
+        "roofline": roof,
+        "e2e": e2e,
+        "gpu_launches": LAUNCHES_PER_STEP * args.steps,
+        "clocks": ck,
+        "fp64_path": fp64,
+        "accuracy": acc,
+        "cpu_baseline": cpu,
+        "wall_s_timed_region": wall,
+    }
+    print(json.dumps(out))
+
+
+def fp64_leg(args, ctx, w, batches, stat, stream, sids, P_level, mixed_value):
+    """The plain FP64 GPU path on the first timed batch: all particles (C1,
+    C2) or, per level, a seeded random subset plus every particle whose mixed
+    value lies within twice the error bound of the level's maximum (the
+    certified best-particle check); one untimed call, then --fp64-repeats
+    timed ones (median)."""
+    import torch
+    from paper_2408_13170_gb300 import scstat
+    dev = batches.device
+    nl = len(w.Ns)
+    b = batches[args.warmup]
+    m_all = stat[args.warmup].cpu().numpy()
+    eps = 1e-5
+    idx_levels, cand_levels = [], []
+    rng = np.random.default_rng(11)
+    for s in range(nl):
+        m = m_all[s * P_level:(s + 1) * P_level]
+        top = float(np.max(m))
+        cand = np.flatnonzero(m >= top - 2.0 * eps * max(abs(top), 1.0))
+        if nl == 1:
+            idx = np.arange(P_level)
+        else:
+            k = min(args.fp64_subset, P_level)
+            idx = np.union1d(rng.choice(P_level, size=k, replace=False), cand)
+        idx_levels.append(idx)
+        cand_levels.append(cand)
+    sub = torch.cat([b[s * P_level + torch.as_tensor(idx_levels[s], device=dev)]
+                     for s in range(nl)])
+    sub_offs = np.concatenate([[0], np.cumsum([len(i) for i in idx_levels])]).astype(np.int64)
+    n_sub = int(sub_offs[-1])
+    s64 = torch.empty(n_sub, dtype=torch.float64, device=dev)
+    ctx.set_path(scstat.SCS_FP64)
+
+    def call():
+        if nl == 1:
+            scstat.scs_eval_stat(ctx.h, 0, sub, n_sub, s64, cuda_stream=stream)
+        else:
+            scstat.scs_batch_eval(ctx.h, sids, sub_offs, sub, s64, cuda_stream=stream)
+
+    call()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(max(1, args.fp64_repeats)):
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        call()
+        e.record(stream)
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(e) / 1e3)
+    ctx.set_path(scstat.SCS_MIXED)
+    t64 = float(np.median(times))
+    r = s64.cpu().numpy()
+    errs, agree = [], []
+    for s in range(nl):
+        idx = idx_levels[s]
+        rs = r[sub_offs[s]:sub_offs[s + 1]]
+        ms = m_all[s * P_level + idx]
+        errs.append(float(np.max(np.abs(ms - rs) / np.maximum(np.abs(rs), 1.0))))
+        # best particle: the mixed argmax against the FP64 argmax over the
+        # certified candidates (lowest index among equals on both sides)
+        mix_best = int(np.argmax(m_all[s * P_level:(s + 1) * P_level]))
+        cpos = np.searchsorted(idx, cand_levels[s])
+        f64_best = int(cand_levels[s][np.argmax(rs[cpos])])
+        agree.append(mix_best == f64_best)
+    fp64 = {"value": n_sub / t64, "unit": "particle-evals/s", "ms_per_call": 1e3 * t64,
+            "repeats": len(times), "particles": n_sub,
+            "mixed_speedup": mixed_value / (n_sub / t64),
+            "subset": ("all particles" if nl == 1 else
+                       f"{args.fp64_subset} seeded random particles per level plus the "
+                       "certified best-particle candidates")}
+    acc = {"max_rel_err_mixed_vs_fp64": float(np.max(errs)),
+           "max_rel_err_mixed_vs_fp64_per_level": errs,
+           "best_particle_agrees": bool(all(agree)),
+           "best_particle_agrees_per_level": agree,
+           "best_particle_candidates_per_level": [int(len(c)) for c in cand_levels]}
+    return fp64, acc
+
+
 def main():
     args = parse()
     rank, world, local = dist_init(args)
@@ -290,172 +670,7 @@ def main():
             raise SystemExit("the uneven-batch workload is defined on TDI A and E only")
         run_swarm(args, rank, world, local)
         return
-    import torch
-    from paper_2408_13170_gb300 import scstat, synth
-    assert torch.cuda.is_available(), "bench needs a CUDA device"
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    cfg, d, inj = make_workload(seed_offset=rank, channels=args.channels)
-    aet = args.channels == "AET"
-    ops_per_bin = ALG_OPS_PER_BIN_AET if aet else ALG_OPS_PER_BIN
-    if args.particles:
-        cfg["P"] = args.particles
-    P, N = cfg["P"], cfg["N"]
-    ctx = scstat.Context(local, scstat.SCS_MIXED)
-    ctx.set_data(0, d)
-    ctx.inject(0, inj, cfg["snr"])
-    ctx.set_segments(0, N, scstat.SCS_EQUAL_SNR2)
-    nb = args.warmup + args.steps
-    host_batches = [synth.draw_particles(P, d["rng"]) for _ in range(nb)]
-    host_batches[0][0] = inj
-    batches = torch.tensor(np.stack(host_batches), device=dev)
-    stat = torch.empty((nb, P), dtype=torch.float64, device=dev)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.Stream(dev)
-    torch.cuda.set_stream(stream)
-
-    def step(i):
-        scstat.scs_eval_stat(ctx.h, 0, batches[i], P, stat[i], cuda_stream=stream)
-
-    # work tile chosen by the library's autotuner on the first batch (set-up,
-    # not timed)
-    tile, tile_ms = scstat.scs_autotune(ctx.h, 0, batches[0], P, cuda_stream=stream)
-    scstat.scs_set_profiling(ctx.h, True)
-    for i in range(args.warmup):
-        flush.zero_()
-        step(i)
-    torch.cuda.synchronize()
-    clocks = ClockSampler(local)
-    clocks.start()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    main_ms = []
-    barrier(world)
-    torch.cuda.synchronize()
-    wall0 = time.perf_counter()
-    for j in range(args.steps):
-        flush.zero_()
-        ev[j][0].record(stream)
-        step(args.warmup + j)
-        ev[j][1].record(stream)
-        main_ms.append(scstat.scs_last_timings(ctx.h))
-    torch.cuda.synchronize()
-    barrier(world)
-    wall = time.perf_counter() - wall0
-    ck = clocks.stop()
-    step_ms = np.array([a.elapsed_time(b) for a, b in ev])
-    t_dev = max_over_ranks(step_ms.sum() / 1e3, world, dev)
-    value = world * P * args.steps / t_dev
-    stages = np.array(main_ms)            # steps x 4
-    scstat.scs_set_profiling(ctx.h, False)
-
-    # supports of the timed batches: bin-evals (algorithmic units)
-    bin_evals = []
-    for j in range(args.steps):
-        lo, hi, _ = ctx.support(0, host_batches[args.warmup + j])
-        bin_evals.append(float(np.sum(np.maximum(hi - lo + 1, 0))))
-    bin_evals = np.array(bin_evals)
-    t_main = stages[:, 2] / 1e3
-    ops = bin_evals * ops_per_bin
-    sm_mhz = (ck or {}).get("sm_mhz") or 2070.0
-    props = torch.cuda.get_device_properties(dev)
-    peak = props.multi_processor_count * 128 * sm_mhz * 1e6   # lane-ops/s
-    achieved = float(np.mean(ops / t_main))
-
-    # end to end through the public API with host buffers (pinned params in,
-    # stat out; the library copies both ways inside the call)
-    pinned = torch.from_numpy(np.stack(host_batches[:args.steps])).pin_memory()
-    host_stat = np.empty(P)
-    ctx_params = [pinned[j].numpy() for j in range(args.steps)]
-    barrier(world)
-    t0 = time.perf_counter()
-    for j in range(args.steps):
-        scstat.scs_eval_stat(ctx.h, 0, ctx_params[j], P, host_stat)
-    e2e_t = max_over_ranks(time.perf_counter() - t0, world, dev)
-    e2e = {"value": world * P * args.steps / e2e_t, "unit": "particle-evals/s",
-           "h2d_bytes_per_step": P * 8 * 8, "d2h_bytes_per_step": P * 8}
-
-    # the plain FP64 path on one batch: throughput and agreement
-    fp64 = None
-    acc = {}
-    if not args.no_fp64:
-        ctx.set_path(scstat.SCS_FP64)
-        s64 = torch.empty(P, dtype=torch.float64, device=dev)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        scstat.scs_eval_stat(ctx.h, 0, batches[args.warmup], P, s64, cuda_stream=stream)
-        b.record(stream)
-        torch.cuda.synchronize()
-        t64 = a.elapsed_time(b) / 1e3
-        ctx.set_path(scstat.SCS_MIXED)
-        m = stat[args.warmup].cpu().numpy()
-        r = s64.cpu().numpy()
-        rel = np.abs(m - r) / np.maximum(np.abs(r), 1.0)
-        fp64 = {"value": P / t64, "unit": "particle-evals/s", "ms_per_step": 1e3 * t64,
-                "mixed_speedup": (P / t64) and value / world / (P / t64)}
-        acc = {"max_rel_err_mixed_vs_fp64": float(rel.max()),
-               "argmax_agrees": bool(np.argmax(m) == np.argmax(r))}
-
-    # CPU oracle on a bounded sample of the same workload (rank 0 only)
-    cpu = None
-    if rank == 0 and world == 1 and args.cpu_sample > 0:
-        import oracle
-        dh = dict(d)
-        dh["A"] = d["A"].copy()
-        dh["E"] = d["E"].copy()
-        if aet:
-            dh["T"] = d["T"].copy()
-        oracle.inject(inj, d["f_first"], d["df"], d["K"], d["T_obs"], d["SA"], d["SE"],
-                      cfg["snr"], dh["A"], dh["E"], T=dh.get("T"), ST=d.get("ST"))
-        sample = host_batches[args.warmup][:args.cpu_sample]
-        t0 = time.perf_counter()
-        ref = oracle.evaluate(dh, sample, N, mode=oracle.EQUAL_SNR2)
-        tc = time.perf_counter() - t0
-        m = stat[args.warmup, :args.cpu_sample].cpu().numpy()
-        acc["max_rel_err_mixed_vs_oracle_sample"] = float(
-            np.max(np.abs(m - ref) / np.maximum(np.abs(ref), 1.0)))
-        cpu = {"value": len(sample) / tc, "unit": "particle-evals/s",
-               "cores": oracle_threads(), "kind": "oracle",
-               "sample": f"first {len(sample)} particles of a timed batch, every support bin "
-                         f"({WORKLOAD}, N={N} equal-SNR^2); {tc:.1f} s wall"}
-
-    if rank != 0:
-        return
-    out = {
-        "metric": METRIC, "value": value, "unit": "particle-evals/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "dtype_note": "f32/int32 per bin; f64 anchors, edges and segment totals",
-        "data": "synthetic",
-        "config": {"workload": f"{WORKLOAD}: one-year stream T=3.15e7 s, K={d['K']} bins x "
-                               f"TDI {','.join(args.channels)}; P={P} particles uniform in the prior box; "
-                               f"N={N} equal-SNR^2 segments; injection SNR {cfg['snr']}",
-                   "P": P, "K": int(d["K"]), "N": N, "path": "mixed",
-                   "channels": args.channels,
-                   "tile_bins": 1 << tile,
-                   "autotune_ms": {str(1 << (11 + i)): float(t) for i, t in enumerate(tile_ms)},
-                   "l2": "256 MB buffer written between timed steps",
-                   "parallelism": f"replicas x{world}"},
-        "bin_evals_per_s": float(world * bin_evals.sum() / t_dev),
-        "stage_ms": {k: float(v) for k, v in zip(
-            ("setup_worklist", "segment_edges", "main", "fixup"), stages.mean(axis=0))},
-        "roofline": {"bound": "alu", "kernel": "k_main_mixed", "achieved": achieved / 1e12,
-                     "peak": peak / 1e12, "unit": "Tops/s", "frac": achieved / peak,
-                     "traffic": None if (args.particles or aet) else MAIN_TRAFFIC_BYTES.get(tile),
-                     "traffic_unit": "bytes per launch (ncu dram read + write)",
-                     "note": f"{ops_per_bin} lane-ops per support bin-eval; peak = "
-                             f"{props.multi_processor_count} SMs x 128 lanes x "
-                             f"{sm_mhz:.0f} MHz (median SM clock under load)"},
-        "e2e": e2e,
-        "gpu_launches": LAUNCHES_PER_STEP * args.steps,
-        "clocks": ck,
-        "fp64_path": fp64,
-        "accuracy": acc,
-        "cpu_baseline": cpu,
-        "wall_s_timed_region": wall,
-    }
-    print(json.dumps(out))
+    run_ours(args, rank, world, local)
 
 
 if __name__ == "__main__":

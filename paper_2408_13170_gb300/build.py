@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libscstat.so")
-UNITS = ["scs_api", "scs_setup", "scs_mixed", "scs_fp64", "scs_pso"]
+UNITS = ["scs_api", "scs_setup", "scs_mixed", "scs_fp64", "scs_pso", "scs_peaks"]
 HEADERS = ["scs_device.cuh", "scs_internal.cuh", "scs_anchor.cuh", "scs_setup.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
@@ -31,7 +31,8 @@ def _nvcc() -> str:
 def _newest_input() -> float:
     paths = [os.path.join(SRC, u + ".cu") for u in UNITS]
     paths += [os.path.join(SRC, h) for h in HEADERS]
-    paths.append(os.path.join(HERE, "..", "include", "scstat.h"))
+    inc = os.path.join(HERE, "..", "include")
+    paths += [os.path.join(inc, h) for h in os.listdir(inc) if h.endswith(".h")]
     paths.append(os.path.abspath(__file__))
     return max(os.path.getmtime(p) for p in paths)
 

@@ -10,14 +10,20 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def declared_functions():
-    src = open(os.path.join(ROOT, "include", "scstat.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(scs_[a-z0-9_]+)\s*\(", src)))
+def declared_functions(header=None):
+    """Functions declared by include/<header>, or by every header there."""
+    inc = os.path.join(ROOT, "include")
+    names = [header] if header else sorted(h for h in os.listdir(inc) if h.endswith(".h"))
+    out = set()
+    for h in names:
+        src = open(os.path.join(inc, h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        out.update(re.findall(r"\b(scs_[a-z0-9_]+)\s*\(", src))
+    return sorted(out)
 
 
 def test_header_declares_the_boundary():
-    names = declared_functions()
+    names = declared_functions("scstat.h")
     for want in ("scs_create", "scs_destroy", "scs_last_error", "scs_set_data",
                  "scs_set_data_aet", "scs_set_segments", "scs_eval_stat", "scs_waveform",
                  "scs_waveform_aet", "scs_inject"):
@@ -27,8 +33,19 @@ def test_header_declares_the_boundary():
 def test_library_exports_every_declared_symbol():
     from paper_2408_13170_gb300 import build
     lib = ctypes.CDLL(build.build())
-    for name in declared_functions():
+    names = declared_functions()
+    assert "scs_peak_probe" in names
+    for name in names:
         assert hasattr(lib, name), name
+
+
+def test_peak_probe_rejects_bad_arguments():
+    """The probe checks its arguments before touching a device."""
+    from paper_2408_13170_gb300 import scstat
+    fn = scstat.lib().scs_peak_probe
+    fn.argtypes = [ctypes.c_int] * 3 + [ctypes.c_void_p] * 3
+    assert fn(0, 9, 10, None, None, None) == -1
+    assert fn(0, 0, 0, None, None, None) == -1
 
 
 def test_create_without_device_fails_cleanly():

@@ -11,7 +11,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def test_reference_arm_three_channels():
     env = dict(os.environ, OMP_NUM_THREADS="2")
     cmd = [sys.executable, "bench.py", "--impl", "reference", "--channels", "AET", "--steps",
-           "1", "--warmup", "0", "--cpu-sample", "2"]
+           "1", "--warmup", "0", "--cpu-sample", "4"]
     r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
