@@ -464,7 +464,7 @@ def run_ours(args, rank, world, local):
     clocks.start()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    stage = []
+    stage, fb_counts = [], []
     barrier(world)
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
@@ -474,6 +474,7 @@ def run_ours(args, rank, world, local):
         evaluate(batches[args.warmup + j], stat[args.warmup + j], stream)
         ev[j][1].record(stream)
         stage.append(scstat.scs_last_timings(ctx.h))
+        fb_counts.append(scstat.scs_last_counters(ctx.h)[1])
     torch.cuda.synchronize()
     barrier(world)
     wall = time.perf_counter() - wall0
@@ -569,6 +570,7 @@ def run_ours(args, rank, world, local):
         "bin_evals_per_s": float(world * bin_evals.sum() / t_dev),
         "stage_ms": {k: float(v) for k, v in zip(
             ("setup_worklist", "segment_edges", "main", "fixup"), stages.mean(axis=0))},
+        "edge_fp64_fallback_particles": (float(np.mean(fb_counts)) if w.mode == 1 else None),
         "roofline": roof,
         "e2e": e2e,
         "gpu_launches": LAUNCHES_PER_STEP * args.steps,

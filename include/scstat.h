@@ -356,6 +356,15 @@ int scs_segment_edges(scs_ctx *ctx, int stream_id, const double *params,
 int scs_set_profiling(scs_ctx *ctx, int enable);
 int scs_last_timings(scs_ctx *ctx, double *ms);
 
+/* Counters of the last profiled scs_eval_stat / scs_batch_eval (profiling
+ * enabled; blocks until that call has finished): out[0] = particles
+ * evaluated, out[1] = particles whose equal-SNR^2 edges were recomputed from
+ * FP64 anchor powers because an edge lay within the double-float guard band
+ * of a bin boundary (-1 if the call computed no equal-SNR^2 edges); entries
+ * from 2 on are 0.  n >= 1 entries are written.
+ * Errors: SCS_EINVAL, SCS_ENODATA (nothing profiled yet), SCS_ECUDA. */
+int scs_last_counters(scs_ctx *ctx, int64_t *out, int n);
+
 /* scs_eval_stat without any device allocation.  The paper has no
  * counterpart: this entry point exists for callers that cannot call
  * cudaMalloc at evaluation time -- services whose device memory is entirely

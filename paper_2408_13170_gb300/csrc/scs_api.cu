@@ -44,8 +44,9 @@ struct DataStream {
   double f_first = 0, df = 0, T_obs = 0;
   int K = 0;
   DevBuf dA64, dE64, w64, d32, w32;
+  DevBuf wdf;           // double-float weights for the equal-SNR^2 edges
   bool has_T = false;   // the third TDI channel (scs_set_data_aet)
-  DevBuf dT64, wT64, t32;
+  DevBuf dT64, wT64, t32, wTdf;
   DevBuf wmax;          // max w as the bits of a double (FP32 scale W0)
   double W0 = 1.0;
   int N = 0, mode = -1;
@@ -68,7 +69,7 @@ bool is_device_ptr(const void* p) {
 enum Slot {
   kSlotStreams, kSlotPart, kSlotCrange, kSlotNrec, kSlotTotal, kSlotDiff, kSlotCnt,
   kSlotListOff, kSlotItemOff, kSlotFill, kSlotList, kSlotListTmp, kSlotRec, kSlotSlices, kSlotCounter, kSlotEdges,
-  kSlotHs, kSlotCs, kNumSlots
+  kSlotHs, kSlotCs, kSlotFb, kNumSlots
 };
 
 }  // namespace
@@ -82,6 +83,9 @@ struct scs_ctx {
   std::string err;
   bool prof = false;               // record stage events in the evaluation calls
   bool prof_valid = false;
+  int* prof_host = nullptr;        // pinned: fallback count of the last profiled call
+  int64_t prof_P = 0;              // its particles
+  bool prof_edges = false;         // it computed equal-SNR^2 edges
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   std::map<int, DataStream> streams;
   DevBuf slot[kNumSlots];          // pipeline scratch (grow-only)
@@ -229,6 +233,8 @@ std::vector<StreamDesc> make_table(const std::vector<BatchPart>& parts, int* n_c
     d.dT64 = ds.has_T ? ds.dT64.as<double2>() : nullptr;
     d.wT64 = ds.has_T ? ds.wT64.as<double>() : nullptr;
     d.width_edges = ds.width_edges.as<int>();
+    d.wdf = ds.wdf.as<float4>();
+    d.wTdf = ds.has_T ? ds.wTdf.as<float2>() : nullptr;
   }
   *n_chunks_total = cb;
   *edges_total = eb;
@@ -254,8 +260,8 @@ size_t batch_scratch_bytes(const std::vector<BatchPart>& parts, int P) {
                           sizeof(int) * (nct + 1), sizeof(int) * (nct + 1),
                           sizeof(int) * (nct + 1), sizeof(int) * bound, sizeof(int) * bound,
                           sizeof(int) * etot,
-                          sizeof(double) * htot, sizeof(double) * htot, sizeof(Rec) * bound,
-                          sizeof(int) * 2};
+                          sizeof(double) * htot, sizeof(double) * htot, sizeof(int) * (P + 1),
+                          sizeof(Rec) * bound, sizeof(int) * 2};
   size_t used = 0;
   for (size_t b : sizes) used += (b + 255) & ~size_t(255);
   return used;
@@ -318,10 +324,14 @@ int prepare_batch(scs_ctx* ctx, const std::vector<BatchPart>& parts, const doubl
   out.list = (int*)src.get(kSlotList, sizeof(int) * bound);
   int* list_tmp = (int*)src.get(kSlotListTmp, sizeof(int) * bound);
   double *Hs = nullptr, *Cs = nullptr;
+  int* fb = nullptr;   // fallback count, then the list of particles
+  int max_amax = 1;
+  for (const StreamDesc& d : table) max_amax = std::max(max_amax, d.amax);
   if (out.any_snr2 && want_edges) {
     out.edges = (int*)src.get(kSlotEdges, sizeof(int) * etot);
     Hs = (double*)src.get(kSlotHs, sizeof(double) * htot);
     Cs = (double*)src.get(kSlotCs, sizeof(double) * htot);
+    fb = (int*)src.get(kSlotFb, sizeof(int) * (P + 1));
   }
   if (src.failed()) {
     if (src.ctx) CK(src.err);
@@ -346,8 +356,19 @@ int prepare_batch(scs_ctx* ctx, const std::vector<BatchPart>& parts, const doubl
   CKLAUNCH();
   if (ctx->prof) CK(cudaEventRecord(ctx->ev[1], s));
   if (out.any_snr2 && want_edges) {
-    k_bounds<<<(int)(((int64_t)P * 32 + 127) / 128), 128, 0, s>>>(out.part, 0, P, out.streams,
-                                                                  out.edges, Hs, Cs);
+    CK(cudaMemsetAsync(fb, 0, sizeof(int), s));
+    k_bounds_df<<<(int)(((int64_t)P * 32 + 127) / 128), 128, 0, s>>>(
+        out.part, P, out.streams, out.edges, Hs, Cs, fb + 1, fb);
+    CKLAUNCH();
+    if (ctx->prof && ctx->prof_host) {
+      CK(cudaMemcpyAsync(ctx->prof_host, fb, sizeof(int), cudaMemcpyDeviceToHost, s));
+      ctx->prof_edges = true;
+    }
+    k_bounds_h64<<<ctx->num_sms * 4, 128, 0, s>>>(out.part, out.streams, fb + 1, fb,
+                                                  (max_amax + 127) / 128, Hs);
+    CKLAUNCH();
+    k_bounds_fix<<<ctx->num_sms * 2, 128, 0, s>>>(out.part, out.streams, out.edges, Hs, Cs,
+                                                  fb + 1, fb);
     CKLAUNCH();
   }
   return SCS_OK;
@@ -471,6 +492,7 @@ void scs_destroy(scs_ctx* ctx) {
     DataStream& d = kv.second;
     d.dA64.release(); d.dE64.release(); d.w64.release(); d.d32.release(); d.w32.release();
     d.dT64.release(); d.wT64.release(); d.t32.release();
+    d.wdf.release(); d.wTdf.release();
     d.wmax.release();
     d.width_edges.release();
   }
@@ -494,6 +516,7 @@ void scs_destroy(scs_ctx* ctx) {
   for (DevBuf* b : bufs) b->release();
   for (cudaEvent_t& e : ctx->ev)
     if (e) cudaEventDestroy(e);
+  if (ctx->prof_host) cudaFreeHost(ctx->prof_host);
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }
@@ -559,16 +582,19 @@ int set_data_impl(scs_ctx* ctx, int sid, const double* A, const double* E, const
   CK(ds.w32.reserve(sizeof(float2) * (Kz + 32)));
   CK(cudaMemsetAsync(ds.d32.as<float4>() + Kz, 0, sizeof(float4) * 32, s));
   CK(cudaMemsetAsync(ds.w32.as<float2>() + Kz, 0, sizeof(float2) * 32, s));
+  CK(ds.wdf.reserve(sizeof(float4) * Kz));
   ds.has_T = withT;
   if (withT) {
     CK(ds.dT64.reserve(sizeof(double2) * Kz));
     CK(ds.wT64.reserve(sizeof(double) * Kz));
     CK(ds.t32.reserve(sizeof(float4) * (Kz + 32)));
+    CK(ds.wTdf.reserve(sizeof(float2) * Kz));
     CK(cudaMemsetAsync(ds.t32.as<float4>() + Kz, 0, sizeof(float4) * 32, s));
   } else {
     ds.dT64.release();
     ds.wT64.release();
     ds.t32.release();
+    ds.wTdf.release();
   }
   // raw inputs on the device (reuse scratch)
   const void* in[6] = {A, E, S_A, S_E, withT ? T : nullptr, withT ? S_T : nullptr};
@@ -604,6 +630,10 @@ int set_data_impl(scs_ctx* ctx, int sid, const double* A, const double* E, const
                                  ds.w64.as<double2>(), dT64, wT64, (int)K,
                                  ds.wmax.as<unsigned long long>(), ds.d32.as<float4>(),
                                  ds.w32.as<float2>(), withT ? ds.t32.as<float4>() : nullptr);
+  CKLAUNCH();
+  k_to_wdf<<<2048, 256, 0, s>>>(ds.w64.as<double2>(), wT64, (int)K,
+                                ds.wmax.as<unsigned long long>(), ds.wdf.as<float4>(),
+                                withT ? ds.wTdf.as<float2>() : nullptr);
   CKLAUNCH();
   unsigned long long wbits = 0;
   CK(cudaMemcpyAsync(&wbits, ds.wmax.ptr, sizeof wbits, cudaMemcpyDeviceToHost, s));
@@ -676,6 +706,8 @@ int scs_eval_stat(scs_ctx* ctx, int sid, const double* params, int64_t P, double
   cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : ctx->stream;
   const double* dparams = nullptr;
   ctx->prof_valid = false;
+  ctx->prof_edges = false;
+  ctx->prof_P = P;
   if (ctx->prof) CK(cudaEventRecord(ctx->ev[0], s));
   rc = stage_params(ctx, params, P, s, &dparams);
   if (rc) return rc;
@@ -735,6 +767,8 @@ int scs_batch_eval(scs_ctx* ctx, const int* stream_ids, const int64_t* P_offsets
   }
   cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : ctx->stream;
   ctx->prof_valid = false;
+  ctx->prof_edges = false;
+  ctx->prof_P = P;
   if (ctx->prof) CK(cudaEventRecord(ctx->ev[0], s));
   const double* dparams = nullptr;
   rc = stage_params(ctx, params, P, s, &dparams);
@@ -1074,8 +1108,25 @@ int scs_set_profiling(scs_ctx* ctx, int enable) {
   if (rc) return rc;
   if (enable && !ctx->ev[0])
     for (cudaEvent_t& e : ctx->ev) CK(cudaEventCreate(&e));
+  if (enable && !ctx->prof_host) {
+    void* h = nullptr;
+    CK(cudaHostAlloc(&h, 64, cudaHostAllocDefault));
+    ctx->prof_host = static_cast<int*>(h);
+  }
   ctx->prof = enable != 0;
   ctx->prof_valid = false;
+  return SCS_OK;
+}
+
+int scs_last_counters(scs_ctx* ctx, int64_t* out, int n) {
+  if (!ctx || !out || n < 1) return SCS_EINVAL;
+  if (!ctx->prof_valid)
+    return fail(ctx, SCS_ENODATA, "no profiled evaluation since profiling was enabled");
+  int rc = bind(ctx);
+  if (rc) return rc;
+  CK(cudaEventSynchronize(ctx->ev[4]));
+  const int64_t c[2] = {ctx->prof_P, ctx->prof_edges ? (int64_t)*ctx->prof_host : -1};
+  for (int i = 0; i < n; ++i) out[i] = i < 2 ? c[i] : 0;
   return SCS_OK;
 }
 
@@ -1405,8 +1456,9 @@ int scs_pso_run(scs_ctx* ctx, int iters, int use_graph, void* cuda_stream) {
     // load every kernel of an iteration now: nothing is loaded under capture
     cudaFuncAttributes fa;
     const void* fk[] = {(const void*)k_setup, (const void*)k_scan64, (const void*)k_chunk_table,
-                        (const void*)k_fill, (const void*)k_bounds, (const void*)k_fixup,
-                        (const void*)k_fixup_slices};
+                        (const void*)k_fill, (const void*)k_bounds_df,
+                        (const void*)k_bounds_h64, (const void*)k_bounds_fix,
+                        (const void*)k_fixup, (const void*)k_fixup_slices};
     for (const void* k : fk) {
       if (cudaFuncGetAttributes(&fa, k) != cudaSuccess) {
         ctx->prof = prof;

@@ -105,6 +105,10 @@ struct Part {
   double Pr[6], Pi[6];          // polarisation tensor xx, yy, zz, xy, xz, yz
   double Rcb, lam;              // R cos(beta) [s], lambda
   float Pr32[6], Pi32[6], k32[3];   // FP32 copies for the mixed path
+  // the polarisation basis rotated by psi, u' = cos(psi) u + sin(psi) v and
+  // v' = -sin(psi) u + cos(psi) v, so that n.P.n = ap ((n.u')^2 - (n.v')^2)
+  // - i ax 2 (n.u')(n.v') with ap = (1 + cos^2 iota)/2, ax = cos iota
+  double up[3], vp[3], ap, ax;
 };
 
 __device__ constexpr int kPow[4] = {5, 3, 2, 1};
@@ -179,6 +183,15 @@ __device__ inline void part_init(Part& p, const double* th) {
   double v[3] = {-sb * cl, -sb * sl, cb};
   double c2p = cos(2.0 * psi), s2p = sin(2.0 * psi);
   double ap = 0.5 * (1.0 + cos(inc) * cos(inc)), ax = cos(inc);
+  {
+    const double cps = cos(psi), sps = sin(psi);
+    for (int i = 0; i < 3; ++i) {
+      p.up[i] = cps * u[i] + sps * v[i];
+      p.vp[i] = -sps * u[i] + cps * v[i];
+    }
+    p.ap = ap;
+    p.ax = ax;
+  }
   const int ii[6] = {0, 1, 2, 0, 0, 1}, jj[6] = {0, 1, 2, 1, 2, 2};
   for (int m = 0; m < 6; ++m) {
     int i = ii[m], j = jj[m];

@@ -60,6 +60,11 @@ struct StreamDesc {
   const double2* dT64;
   const double* wT64;
   const int* width_edges;   // equal width: the shared table e_n = floor(n K / N)
+  // double-float weights for the equal-SNR^2 anchor power: (w_A, w_E) / 2^e
+  // as (hi, lo) pairs, and w_T / 2^e (null for a two-channel stream), with
+  // 2^e <= W0 < 2^(e+1)
+  const float4* wdf;
+  const float2* wTdf;
 };
 
 // Everything a main kernel needs; all pointers are device memory.

@@ -2,6 +2,7 @@
 // support, the mixed path's anchor stride, equal-SNR^2 segment edges, the
 // chunk work list, the cross-chunk fix-up, and data pre-whitening.
 #include "scs_anchor.cuh"
+#include "scs_df.cuh"
 #include "scs_internal.cuh"
 #include "scs_setup.cuh"
 
@@ -359,119 +360,361 @@ __global__ void k_sort_chunks(const Part* part, const int* cnt, const int* list_
   }
 }
 
-// Equal-SNR^2 edges (one warp per particle).  The cumulative template power
-// is the trapezoid sum over the anchor bins k_lo, k_lo + 1024, ..., k_hi of
-// hh(k) = sum_alpha w_alpha(k) |h_alpha(f_k)|^2 (alpha = A, E, then T on a
-// stream with the third channel), evaluated exactly in FP64;
-// target c_n = n C/N; kappa_n by linear inverse interpolation; segment n
-// starts at bin ceil(kappa_n).  The double operations follow that order
-// explicitly (no contraction) so that the rounding is the definition's.
-__global__ void k_bounds(const Part* part, int p_lo, int p_hi, const StreamDesc* streams,
-                         int* edges_all, double* Hs, double* Cs) {
-  int gw = p_lo + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  int lane = threadIdx.x & 31;
-  if (gw >= p_hi) return;
+// ---------------------------------------------------------- equal-SNR^2 edges
+// The definition (Sec. II.B: equal squared SNR per segment): the template
+// power hh(k) = sum_alpha w_alpha(k) |h_alpha(f_k)|^2 (alpha = A, E, then T
+// on a stream with the third channel) at the anchor bins k_lo, k_lo + 1024,
+// ..., k_hi, its trapezoid cumulative C, targets c_n = n C_last / N, kappa_n
+// by linear inverse interpolation, and segment n from bin ceil(kappa_n).
+//
+// Evaluation, one warp per particle:
+//  1. k_bounds_df: the anchor powers in double-float (the response's link
+//     geometry, phases, sincs and TDI sums) with FP64 only for f, f^{-1/3},
+//     t(f) and the orbit angle; the cumulative in FP64; the interpolation in
+//     double-float.  An edge whose kappa lies so close to an integer that the
+//     double-float anchor powers (relative error ~1e-13) could move its
+//     ceiling puts the particle on a fallback list (about 1% of particles).
+//  2. k_bounds_h64 + k_bounds_fix: for the listed particles, the anchor
+//     powers in FP64 (the model's full-precision form) spread over many
+//     blocks, then the same cumulative and interpolation, where any edge
+//     within the double-float interpolation's own error band of an integer
+//     is recomputed with the definition's FP64 arithmetic.
+
+// Relative errors of the cumulative anchor power that the guard bands cover.
+// Step 1: the double-float anchor power's error, relative to the template
+// power, is bounded by its ~100 operations at 2^-47 each (7e-13; ~1e-14 for
+// random rounding), and only its variation over the support moves kappa (a
+// common relative error cancels in n C / N).  Step 2: the double-float
+// interpolation (~1e-15 of C per operation on the offset).
+constexpr float kEpsPowerDf = 5e-13f;
+constexpr float kEpsInterp = 1e-13f;
+
+// Per-particle constants of the double-float anchor power.
+struct PowDf {
+  dfl k[3], up[3], vp[3];
+  dfl A1, A2;   // ap / 48 and 2 ax / 48 (48 = (4 sqrt3)^2, see below)
+};
+
+__device__ inline void pow_consts(const Part& p, PowDf& c) {
+  c.k[0] = df_from(p.kx);
+  c.k[1] = df_from(p.ky);
+  c.k[2] = df_from(p.kz);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    c.up[i] = df_from(p.up[i]);
+    c.vp[i] = df_from(p.vp[i]);
+  }
+  c.A1 = df_from(p.ap * (1.0 / 48.0));
+  c.A2 = df_from(p.ax * (1.0 / 24.0));
+}
+
+// sin(x)/x given sin(x) (double-float)
+__device__ __forceinline__ dfl df_sinc_of(dfl x, dfl sx) {
+  return fabsf(x.hi) < 0.3f ? df_sinc_small(x) : df_div(sx, x);
+}
+
+// |R_A|^2, |R_E|^2 and |R_T|^2 of the residual response (the model of
+// response_residual) at a = pi f L and orbit angle alpha, in double-float.
+// Craft offsets from the guiding centre are d_i = (L / (4 sqrt3)) g_i with
+//   g_i = (cos(2 alpha - b_i) - 3 cos b_i, sin(2 alpha - b_i) - 3 sin b_i,
+//          -2 sqrt3 cos(alpha - b_i)),  b_i = 2 pi i / 3,  sum_i g_i = 0,
+// so arm (s, r) has n = (g_r - g_s)/(4 sqrt3), link phase factors
+// e_i = e^{i ph_i}, ph_i = -(a/(4 sqrt3)) k.g_i with e_0 e_1 e_2 = 1, and
+// n.P.n = (ap/48)(dmu^2 - dnu^2) - i (2 ax/48) dmu dnu with dmu, dnu the
+// differences of u'.g and v'.g.  With F = sinc(a - b), K = sinc(a + b),
+// b = ph_s - ph_r and base = conj(e_k) n.P.n (k the third craft), the links
+// are G_{s->r} = -i a F base, G_{r->s} = -i a K base, and with
+// U = base (K + D F), V = base (F + D K), D = e^{-2ia}:
+//   X = -i a W (U_02 - U_01), Y = -i a W (V_01 - U_12), Z = -i a W (V_12 - V_02),
+// W = 1 - D^2, |a W|^2 = 16 (a sin a cos a)^2.
+__device__ inline void response_power_df(const PowDf& c, dfl a, dfl al, dfl& qA, dfl& qE,
+                                         dfl& qT) {
+  dfl sa, ca;
+  df_sincos(al, &sa, &ca);
+  const dfl c2a = ca * ca - sa * sa;
+  const dfl s2a = df_scale2(ca * sa, 2.f);
+  constexpr dfl h3 = df_const(0.86602540378443865);    // sqrt3 / 2
+  constexpr dfl k33 = df_const(2.5980762113533160);    // 3 sqrt3 / 2
+  constexpr dfl m2s3 = df_const(-3.4641016151377546);  // -2 sqrt3
+  const dfl P = s2a * h3, Q = c2a * h3, R = sa * h3;
+  const dfl hc2 = df_scale2(c2a, 0.5f), hs2 = df_scale2(s2a, 0.5f), hca = df_scale2(ca, 0.5f);
+  dfl g[2][3];
+  g[0][0] = c2a - df_f(3.f);
+  g[0][1] = s2a;
+  g[0][2] = ca * m2s3;
+  g[1][0] = (P - hc2) + df_f(1.5f);
+  g[1][1] = -(hs2 + Q) - k33;
+  g[1][2] = (R - hca) * m2s3;
+  dfl kap[3], mu[3], nu[3];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    kap[i] = c.k[0] * g[i][0] + c.k[1] * g[i][1] + c.k[2] * g[i][2];
+    mu[i] = c.up[0] * g[i][0] + c.up[1] * g[i][1] + c.up[2] * g[i][2];
+    nu[i] = c.vp[0] * g[i][0] + c.vp[1] * g[i][1] + c.vp[2] * g[i][2];
+  }
+  kap[2] = -(kap[0] + kap[1]);
+  mu[2] = -(mu[0] + mu[1]);
+  nu[2] = -(nu[0] + nu[1]);
+  constexpr dfl i4s3 = df_const(0.14433756729740644);   // 1 / (4 sqrt3)
+  const dfl ah = a * i4s3;
+  dfl ph[3];
+  ph[0] = -(ah * kap[0]);
+  ph[1] = -(ah * kap[1]);
+  ph[2] = -(ph[0] + ph[1]);
+  cdfl e[3];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) df_sincos(ph[i], &e[i].im, &e[i].re);
+  e[2] = cdf_conj(e[0] * e[1]);
+  dfl s_a, c_a;
+  df_sincos(a, &s_a, &c_a);
+  const cdfl D{c_a * c_a - s_a * s_a, -df_scale2(s_a * c_a, 2.f)};
+  // arms (s, r) with third craft k: (0,1;2), (0,2;1), (1,2;0)
+  cdfl U[3], V[3];
+  const int as[3] = {0, 0, 1}, ar[3] = {1, 2, 2}, ak[3] = {2, 1, 0};
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    const int s = as[m], r = ar[m], k = ak[m];
+    const dfl dmu = mu[r] - mu[s], dnu = nu[r] - nu[s];
+    const cdfl nPn{c.A1 * ((dmu - dnu) * (dmu + dnu)), -(c.A2 * (dmu * dnu))};
+    const cdfl base = cdf_conj(e[k]) * nPn;
+    const cdfl eb = e[s] * cdf_conj(e[r]);    // e^{i b}
+    const dfl b = ph[s] - ph[r];
+    const dfl sc = s_a * eb.re, cs = c_a * eb.im;
+    const dfl F = df_sinc_of(a - b, sc - cs), K = df_sinc_of(a + b, sc + cs);
+    U[m] = base * cdfl{K + F * D.re, F * D.im};
+    V[m] = base * cdfl{F + K * D.re, K * D.im};
+  }
+  const cdfl X = U[1] - U[0], Y = V[0] - U[2], Z = V[2] - V[1];
+  const dfl w = (a * s_a) * c_a;
+  const dfl fac = df_scale2(w * w, 16.f);
+  constexpr dfl i6 = df_const(1.0 / 6.0), i3 = df_const(1.0 / 3.0);
+  qA = df_scale2(fac * cdf_norm2(Z - X), 0.5f);
+  const cdfl Y2{df_scale2(Y.re, 2.f), df_scale2(Y.im, 2.f)};
+  qE = (fac * cdf_norm2((X - Y2) + Z)) * i6;
+  qT = (fac * cdf_norm2((X + Y) + Z)) * i3;
+}
+
+// Cumulative anchor power and the edges of one particle (one warp) from its
+// anchor powers H[0 .. nanch) (FP64, any common scale): trapezoid terms and
+// the running sum in FP64 (each lane a contiguous run of anchors, joined by
+// a warp scan), then per lane a contiguous run of interior edges: the offset
+// c_n - C[a-1] is carried in double-float from one target to the next and
+// kappa_n - k_{a-1} = (c_n - C[a-1]) (k_a - k_{a-1}) / (C[a] - C[a-1]).
+// An edge within eps Cl / slope bins of an integer is either reported
+// (returns true; exact = false) or recomputed with the definition's FP64
+// arithmetic (exact = true).
+__device__ bool bounds_edges(const Part& p, int N, int nanch, const double* H, double* C,
+                             int* e, bool exact, float eps, int lane) {
+  const int m = nanch - 1;
+  const int per = (m + 31) / 32;
+  const int a0 = 1 + lane * per, a1 = min(nanch, a0 + per);
+  double run = 0.0;
+  for (int a = a0; a < a1; ++a) {
+    const int ka = min(p.k_lo + a * kSnr2Stride, p.k_hi);
+    const int kp = p.k_lo + (a - 1) * kSnr2Stride;
+    const double t = __dmul_rn(__dmul_rn((double)(ka - kp), __dadd_rn(H[a - 1], H[a])), 0.5);
+    C[a] = t;
+    run = __dadd_rn(run, t);
+  }
+  double incl = run;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double v = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl = __dadd_rn(incl, v);
+  }
+  double acc = __shfl_up_sync(kFull, incl, 1);
+  if (lane == 0) acc = 0.0;
+  for (int a = a0; a < a1; ++a) {
+    acc = __dadd_rn(acc, C[a]);
+    C[a] = acc;
+  }
+  if (lane == 0) C[0] = 0.0;
+  __syncwarp();
+  const double Cl = C[nanch - 1];
+  if (lane == 0) e[0] = p.k_lo;
+  if (lane == 31) e[N] = p.k_hi + 1;
+  const int M = N - 1;
+  const int n0 = 1 + (int)(((int64_t)lane * M) / 32), n1 = 1 + (int)(((int64_t)(lane + 1) * M) / 32);
+  if (!(Cl > 0.0)) {
+    for (int n = n0; n < n1; ++n) e[n] = p.k_lo;
+    return false;
+  }
+  const bool pow2 = (N & (N - 1)) == 0;
+  const double invN = 1.0 / (double)N;
+  auto target = [&](int n) {   // c_n, the definition's rounding
+    const double q = __dmul_rn((double)n, Cl);
+    return pow2 ? __dmul_rn(q, invN) : __ddiv_rn(q, (double)N);
+  };
+  auto first_at_least = [&](double c) {   // first a in [1, nanch-1] with C[a] >= c
+    int lo = 1, hi = nanch - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (C[mid] >= c) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+  };
+  bool flag = false;
+  if (n0 < n1) {
+    const double c0 = target(n0);
+    int a = first_at_least(c0);
+    dfl num = df_from(__dsub_rn(c0, C[a - 1]));
+    const dfl step = df_from(Cl * invN);
+    dfl width = df_from(__dsub_rn(C[a], C[a - 1]));
+    int a_rec = -1;
+    dfl rec{0.f, 0.f};
+    float guard = 0.f;
+    const float Clf = (float)Cl;
+    for (int n = n0; n < n1; ++n) {
+      if (n > n0) num = num + step;
+      while (a < nanch - 1 && (num.hi > width.hi || (num.hi == width.hi && num.lo > width.lo))) {
+        num = num - width;
+        ++a;
+        width = df_from(__dsub_rn(C[a], C[a - 1]));
+      }
+      const int k1 = min(p.k_lo + (a - 1) * kSnr2Stride, p.k_hi);
+      const int k2 = min(p.k_lo + a * kSnr2Stride, p.k_hi);
+      const float dk = (float)(k2 - k1);
+      if (a != a_rec) {
+        a_rec = a;
+        rec = width.hi > 0.f ? df_div(df_f(dk), width) : dfl{0.f, 0.f};
+        // kappa error of a relative error eps of the cumulative: eps Cl / slope
+        guard = width.hi > 0.f ? eps * Clf * dk / width.hi : 1e30f;
+      }
+      const dfl kap = num * rec;   // kappa_n - k1 in bins
+      const float r = rintf(kap.hi);
+      const float d = (kap.hi - r) + kap.lo;
+      int ek = k1 + (int)r + (d > 0.f ? 1 : 0);
+      if (!(fabsf(d) >= guard)) {
+        if (exact) {   // the definition's arithmetic for this edge
+          const double cn = target(n);
+          const int ae = first_at_least(cn);
+          const int e1 = min(p.k_lo + (ae - 1) * kSnr2Stride, p.k_hi);
+          const int e2 = min(p.k_lo + ae * kSnr2Stride, p.k_hi);
+          const double nm = __dsub_rn(cn, C[ae - 1]), dn = __dsub_rn(C[ae], C[ae - 1]);
+          const double fr = dn > 0.0 ? __ddiv_rn(nm, dn) : 0.0;
+          ek = (int)ceil(__dadd_rn((double)e1, __dmul_rn(fr, (double)(e2 - e1))));
+        } else {
+          flag = true;
+        }
+      }
+      e[n] = ek;
+    }
+  }
+  return __any_sync(kFull, flag);
+}
+
+// Step 1: double-float anchor powers, FP64 cumulative, edges; particles with
+// an edge in a guard band go on the fallback list (fb_list[0 .. *fb_count)).
+__global__ void __launch_bounds__(128) k_bounds_df(const Part* part, int P,
+                                                   const StreamDesc* streams, int* edges_all,
+                                                   double* Hs, double* Cs, int* fb_list,
+                                                   int* fb_count) {
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (gw >= P) return;
   const Part& p = part[gw];
   const StreamDesc& sd = streams[p.sid];
   if (sd.mode != 1) return;   // equal-width streams share a fixed table
   const int N = sd.N;
-  const double f_first = sd.f_first, df = sd.df;
-  const double2* w64 = sd.w64;
-  const double* wT64 = sd.wT64;
-  const int64_t amax = sd.amax;
   const int64_t lp = gw - sd.p_off;
   int* e = edges_all + sd.edge_base + lp * (N + 1);
   if (p.status != kOk) {
     for (int n = lane; n <= N; n += 32) e[n] = 0;
     return;
   }
-  int span = p.k_hi - p.k_lo;
-  int nanch = span / kSnr2Stride + 1 + (span % kSnr2Stride != 0 ? 1 : 0);
-  double* H = Hs + sd.hc_base + lp * amax;
-  double* C = Cs + sd.hc_base + lp * amax;
+  const int span = p.k_hi - p.k_lo;
+  const int nanch = span / kSnr2Stride + 1 + (span % kSnr2Stride != 0 ? 1 : 0);
+  double* H = Hs + sd.hc_base + lp * sd.amax;
+  double* C = Cs + sd.hc_base + lp * sd.amax;
+  PowDf pc;
+  pow_consts(p, pc);
+  const double f_first = sd.f_first, df = sd.df;
+  const bool withT = sd.wTdf != nullptr;
+  bool bad = false;
   for (int a = lane; a < nanch; a += 32) {
-    int ka = min(p.k_lo + a * kSnr2Stride, p.k_hi);
-    double f = dd_val(grid_freq_dd(f_first, df, ka));
-    double u = rcbrt(f), u2 = u * u;
-    double t = time_of_freq_u(p, u);
+    const int ka = min(p.k_lo + a * kSnr2Stride, p.k_hi);
+    const double f = fma((double)ka, df, f_first);
+    // u = f^{-1/3}: FP32 estimate and two Newton steps in FP64
+    double u = (double)rcbrtf((float)f);
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+      const double r = fma(-f, u * u * u, 1.0);
+      u = fma(u * r, 1.0 / 3.0, u);
+    }
+    const double t = time_of_freq_u(p, u);
+    const double al = orbit_angle(t);
+    const double a64 = kPi * kArm * f;
+    bad = bad || !(a64 < 3.9);   // beyond the double-float sin/cos reduction
+    dfl qA, qE, qT;
+    response_power_df(pc, df_from(a64), df_from(al), qA, qE, qT);
+    // |h|^2 = A(f)^2 |R|^2, A(f)^2 = f^{-7/3} = u^7
+    const dfl ud = df_from(u);
+    const dfl u2 = ud * ud, u4 = u2 * u2;
+    const dfl amp2 = (u4 * u2) * ud;
+    const float4 w = sd.wdf[ka];
+    dfl hk = dfl{w.x, w.y} * qA + dfl{w.z, w.w} * qE;
+    if (withT) {
+      const float2 wt = sd.wTdf[ka];
+      hk = hk + dfl{wt.x, wt.y} * qT;
+    }
+    H[a] = df_to(amp2 * hk);
+  }
+  __syncwarp();
+  const bool flag = bounds_edges(p, N, nanch, H, C, e, false, kEpsPowerDf, lane) ||
+                    __any_sync(kFull, bad);
+  if (flag && lane == 0) fb_list[atomicAdd(fb_count, 1)] = gw;
+}
+
+// Step 2a: FP64 anchor powers of the listed particles; work item = (listed
+// particle, slice of 128 anchors), one anchor per thread (the FP64 work of a
+// particle spread over many SMs).  Persistent blocks take items in turn.
+__global__ void __launch_bounds__(128) k_bounds_h64(const Part* part, const StreamDesc* streams,
+                                                    const int* fb_list, const int* fb_count,
+                                                    int slices, double* Hs) {
+  const int items = *fb_count * slices;
+  for (int it = blockIdx.x; it < items; it += gridDim.x) {
+    const int gw = fb_list[it / slices];
+    const Part& p = part[gw];
+    const StreamDesc& sd = streams[p.sid];
+    const int span = p.k_hi - p.k_lo;
+    const int nanch = span / kSnr2Stride + 1 + (span % kSnr2Stride != 0 ? 1 : 0);
+    const int a = (it % slices) * 128 + threadIdx.x;
+    if (a >= nanch) continue;
+    double* H = Hs + sd.hc_base + (int64_t)(gw - sd.p_off) * sd.amax;
+    const int ka = min(p.k_lo + a * kSnr2Stride, p.k_hi);
+    const double f = dd_val(grid_freq_dd(sd.f_first, sd.df, ka));
+    const double u = rcbrt(f), u2 = u * u;
+    const double t = time_of_freq_u(p, u);
     double sa, ca;
     sincos_small(orbit_angle(t), &sa, &ca);
     double pA, pE, pT = 0.0;
-    response_power64(p, f, ca, sa, pA, pE, wT64 ? &pT : nullptr);
-    // |h|^2 = A(f)^2 |R|^2 with A(f)^2 = f^{-7/3} = u^7, u = f^{-1/3}
-    double amp2 = u2 * u2 * u2 * u;
-    double2 w = w64[ka];
+    response_power64(p, f, ca, sa, pA, pE, sd.wT64 ? &pT : nullptr);
+    const double amp2 = u2 * u2 * u2 * u;
+    const double2 w = sd.w64[ka];
     double hk = __dadd_rn(__dmul_rn(w.x, amp2 * pA), __dmul_rn(w.y, amp2 * pE));
-    if (wT64) hk = __dadd_rn(hk, __dmul_rn(wT64[ka], amp2 * pT));
+    if (sd.wT64) hk = __dadd_rn(hk, __dmul_rn(sd.wT64[ka], amp2 * pT));
     H[a] = hk;
   }
-  __syncwarp();
-  // trapezoid terms (k_a - k_{a-1}) (H_{a-1} + H_a) / 2 in parallel (halving
-  // is exact, so * 0.5 rounds as / 2 does), then the running sum in order
-  for (int a = 1 + lane; a < nanch; a += 32) {
-    int ka = min(p.k_lo + a * kSnr2Stride, p.k_hi);
-    int kp = p.k_lo + (a - 1) * kSnr2Stride;
-    double s2 = __dadd_rn(H[a - 1], H[a]);
-    C[a] = __dmul_rn(__dmul_rn((double)(ka - kp), s2), 0.5);
-  }
-  __syncwarp();
-  if (lane == 0) {
-    double run = 0.0;
-    C[0] = 0.0;
-    for (int a = 1; a < nanch; ++a) {
-      run = __dadd_rn(run, C[a]);
-      C[a] = run;
-    }
-  }
-  __syncwarp();
-  double Cl = C[nanch - 1];
-  if (lane == 0) e[0] = p.k_lo;
-  if (lane == 31) e[N] = p.k_hi + 1;
-  // interior edges n = 1..N-1 in one contiguous range per lane: one binary
-  // search, then the anchor index only moves up with n
-  const int M = N - 1;
-  const int n0 = 1 + (int)(((int64_t)lane * M) / 32), n1 = 1 + (int)(((int64_t)(lane + 1) * M) / 32);
-  // n C / N: for N a power of two the division is an exact scaling
-  const bool pow2 = (N & (N - 1)) == 0;
-  const double invN = 1.0 / (double)N;
-  int a = 1, a_rec = -1;
-  double rec = 0.0;   // 1 / (C[a] - C[a-1]) of the interval a_rec
-  for (int n = n0; n < n1; ++n) {
-    if (!(Cl > 0.0)) {
-      e[n] = p.k_lo;
-      continue;
-    }
-    const double q = __dmul_rn((double)n, Cl);
-    double cn = pow2 ? __dmul_rn(q, invN) : __ddiv_rn(q, (double)N);
-    // first a in [1, nanch-1] with C[a] >= cn (else nanch-1)
-    if (n == n0) {
-      int lo = 1, hi = nanch - 1;
-      while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        if (C[mid] >= cn) hi = mid; else lo = mid + 1;
-      }
-      a = lo;
-    } else {
-      while (a < nanch - 1 && C[a] < cn) ++a;
-    }
-    int k1 = min(p.k_lo + (a - 1) * kSnr2Stride, p.k_hi);
-    int k2 = min(p.k_lo + a * kSnr2Stride, p.k_hi);
-    const double num = __dsub_rn(cn, C[a - 1]), den = __dsub_rn(C[a], C[a - 1]);
-    // kappa from a reciprocal kept per interval (error ~1e-10 bins); only a
-    // kappa within 1e-6 of an integer, where the ceiling could depend on the
-    // rounding, is recomputed with the definition's exact division
-    if (a != a_rec) {
-      rec = 1.0 / den;
-      a_rec = a;
-    }
-    const double dk = (double)(k2 - k1);
-    double kap = (double)k1 + (num * rec) * dk;
-    const double dist = kap - floor(kap);
-    if (!(den > 0.0) || !(dist > 1e-6 && dist < 1.0 - 1e-6)) {
-      const double fr = __ddiv_rn(num, den);
-      kap = __dadd_rn((double)k1, __dmul_rn(fr, dk));
-    }
-    e[n] = (int)ceil(kap);
+}
+
+// Step 2b: cumulative and edges of the listed particles from their FP64
+// anchor powers (one warp per particle, persistent warps).
+__global__ void __launch_bounds__(128) k_bounds_fix(const Part* part, const StreamDesc* streams,
+                                                    int* edges_all, double* Hs, double* Cs,
+                                                    const int* fb_list, const int* fb_count) {
+  const int lane = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  const int count = *fb_count;
+  for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < count; w += nw) {
+    const int gw = fb_list[w];
+    const Part& p = part[gw];
+    const StreamDesc& sd = streams[p.sid];
+    const int N = sd.N;
+    const int64_t lp = gw - sd.p_off;
+    const int span = p.k_hi - p.k_lo;
+    const int nanch = span / kSnr2Stride + 1 + (span % kSnr2Stride != 0 ? 1 : 0);
+    bounds_edges(p, N, nanch, Hs + sd.hc_base + lp * sd.amax, Cs + sd.hc_base + lp * sd.amax,
+                 edges_all + sd.edge_base + lp * (N + 1), true, kEpsInterp, lane);
   }
 }
 
@@ -669,6 +912,24 @@ __global__ void k_to_fp32(const double2* dA64, const double2* dE64, const double
     if (dT64) {
       double2 dt = dT64[k];
       t32[k] = make_float4((float)(dt.x * isq), (float)(dt.y * isq), (float)(wT64[k] * iw), 0.f);
+    }
+  }
+}
+
+// Double-float copies of the weights for the equal-SNR^2 anchor power,
+// scaled by 2^-e with 2^e <= W0 < 2^(e+1) (exact scaling; the edges do not
+// depend on a common factor of the template power).
+__global__ void k_to_wdf(const double2* w64, const double* wT64, int K,
+                         const unsigned long long* wmax, float4* wdf, float2* wTdf) {
+  const double W0 = __longlong_as_double((long long)*wmax);
+  const double sc = ldexp(1.0, -ilogb(W0));
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
+    const double2 w = w64[k];
+    const dfl a = df_from(w.x * sc), e = df_from(w.y * sc);
+    wdf[k] = make_float4(a.hi, a.lo, e.hi, e.lo);
+    if (wTdf) {
+      const dfl t = df_from(wT64[k] * sc);
+      wTdf[k] = make_float2(t.hi, t.lo);
     }
   }
 }

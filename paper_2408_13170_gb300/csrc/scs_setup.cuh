@@ -15,8 +15,21 @@ __global__ void k_chunk_table(const int* diff, int n_chunks, int* cnt, int* list
 __global__ void k_fill(const int2* crange, int P, const int* list_off, int* fill, int* list);
 __global__ void k_sort_chunks(const Part* part, const int* cnt, const int* list_off,
                               const int* list_in, int* list_out, int n_chunks);
-__global__ void k_bounds(const Part* part, int p_lo, int p_hi, const StreamDesc* streams,
-                         int* edges_all, double* Hs, double* Cs);
+// equal-SNR^2 edges: double-float pass over all particles, then the FP64
+// fallback for the particles it lists (anchor powers, then cumulative + edges)
+__global__ void __launch_bounds__(128) k_bounds_df(const Part* part, int P,
+                                                   const StreamDesc* streams, int* edges_all,
+                                                   double* Hs, double* Cs, int* fb_list,
+                                                   int* fb_count);
+__global__ void __launch_bounds__(128) k_bounds_h64(const Part* part, const StreamDesc* streams,
+                                                    const int* fb_list, const int* fb_count,
+                                                    int slices, double* Hs);
+__global__ void __launch_bounds__(128) k_bounds_fix(const Part* part, const StreamDesc* streams,
+                                                    int* edges_all, double* Hs, double* Cs,
+                                                    const int* fb_list, const int* fb_count);
+// double-float copies of the weights for the edges: w / 2^e (A, E) and w_T / 2^e
+__global__ void k_to_wdf(const double2* w64, const double* wT64, int K,
+                         const unsigned long long* wmax, float4* wdf, float2* wTdf);
 __global__ void k_fixup_slices(const Part* part, const int2* crange, const int64_t* rec_off,
                                const Rec* rec, int P, int S_max, const StreamDesc* streams,
                                SliceSum* out, double* seg_x, double* seg_hh);

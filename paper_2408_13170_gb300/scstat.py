@@ -69,6 +69,8 @@ def lib():
         L.scs_set_profiling.restype = I
         L.scs_last_timings.argtypes = [P, P]
         L.scs_last_timings.restype = I
+        L.scs_last_counters.argtypes = [P, P, I]
+        L.scs_last_counters.restype = I
         L.scs_eval_stat_noalloc.argtypes = [P, I, P, I64, P, P]
         L.scs_eval_stat_noalloc.restype = I
         L.scs_batch_eval.argtypes = [P, P, P, I, P, P, P]
@@ -366,6 +368,14 @@ def scs_pso_search(ctx, ladder, hyper_rows, n_clusters, chunk_iters, max_iters,
 
 def scs_set_profiling(ctx, enable: bool):
     _check(ctx, lib().scs_set_profiling(ctx, 1 if enable else 0))
+
+
+def scs_last_counters(ctx):
+    """(particles, particles whose equal-SNR^2 edges took the FP64 fallback
+    or -1) of the last profiled evaluation."""
+    out = np.zeros(2, np.int64)
+    _check(ctx, lib().scs_last_counters(ctx, _ptr(out), 2))
+    return int(out[0]), int(out[1])
 
 
 def scs_last_timings(ctx):
