@@ -80,6 +80,30 @@ const char *scs_last_error(const scs_ctx *ctx);
 /* Switch the evaluation path of later calls (SCS_FP64 or SCS_MIXED). */
 int scs_set_path(scs_ctx *ctx, int path);
 
+/* ---- Test-only: model switch ----
+ * Replaces, for every later call on the context (evaluation on both paths,
+ * edges, supports, templates, injection, swarm iterations), the waveform and
+ * the response by test models that have closed forms:
+ *   SCS_MODEL_TF2           the search model (default): circular TaylorF2
+ *                           to 2PN, amplitude f^{-7/6} (Sec. IV);
+ *   SCS_MODEL_NEWTONIAN     the same with the leading (Newtonian) phase term
+ *                           only: a power-law chirp;
+ *   SCS_MODEL_LINEAR_CHIRP  App. A's constant-amplitude linear chirp
+ *                           f(t) = f0 + fdot t: phase (f - f0)^2 / (2 fdot)
+ *                           - 1/8 turns, t(f) = (f - f0)/fdot, amplitude 1,
+ *                           params[0] read as fdot [Hz/s] > 0, q ignored, no
+ *                           last-stable-orbit cut;
+ *   SCS_RESPONSE_TDI        the rigid-adiabatic TDI A, E (and T) response
+ *                           (default);
+ *   SCS_RESPONSE_IDENTITY   h_A = h, h_E = h_T = 0, no Doppler modulation.
+ * Errors: SCS_EINVAL (unknown model). */
+#define SCS_MODEL_TF2 0
+#define SCS_MODEL_NEWTONIAN 1
+#define SCS_MODEL_LINEAR_CHIRP 2
+#define SCS_RESPONSE_TDI 0
+#define SCS_RESPONSE_IDENTITY 1
+int scs_debug_set_model(scs_ctx *ctx, int waveform, int response);
+
 /* Load one data stream (Sec. II.A: data d_alpha on the FFT grid with
  * one-sided PSD S_alpha; Sec. IV: grid f_k = f_first + k df, k = 0..K-1,
  * df = 1/T_obs).

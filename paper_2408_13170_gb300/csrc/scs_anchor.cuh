@@ -55,9 +55,16 @@ __device__ inline void phase_taylor(const Part& p, double fa, double df, double 
   double u2 = u * u;
   const double rdf = df * (u2 * u);   // df / f (u^3 = 1/f): d/df of u^n = -(n/3) u^n / f
   double upow[4] = {u2 * u2 * u, u2 * u, u2, u};
-  // PN part F_pn: bin-unit derivatives F[r] = F_pn^{(r)} df^r
+  // PN part F_pn: bin-unit derivatives F[r] = F_pn^{(r)} df^r (the linear
+  // chirp's phase (f - f0)^2 / (2 fdot) is exactly quadratic)
   double F[5] = {0, 0, 0, 0, 0};
   float F32[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  if (p.model == kModelLinearChirp) {
+    const double x = fa - p.lc_f0, ifd = 1.0 / p.lc_fdot;
+    F[0] = 0.5 * x * x * ifd;
+    F[1] = x * df * ifd;
+    F[2] = df * df * ifd;
+  }
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
     double n = (double)kPow[m];
@@ -201,9 +208,9 @@ __device__ __forceinline__ void g_node32(const Part* __restrict__ pp, float al0,
   sincos_small32(al, &sa, &ca);
   float f = fa32 + x * df32;
   Cx<float> RA, RE, RT;
-  response_residual<float>(f, ca, sa, p.Pr32, p.Pi32, p.k32, RA, RE, RT);
+  response_residual<float>(f, ca, sa, p.Pr32, p.Pi32, p.k32, RA, RE, RT, p.ident);
   const float u = rcbrtf(f);
-  const float amp = rsqrtf(f) * u * u;   // f^{-1/2} f^{-2/3}
+  const float amp = p.model == kModelLinearChirp ? 1.f : rsqrtf(f) * u * u;   // f^{-7/6}
   *out = make_float4(amp * RA.re, amp * RA.im, amp * RE.re, amp * RE.im);
   if constexpr (kT) *outT = make_float2(amp * RT.re, amp * RT.im);
 }
@@ -217,9 +224,9 @@ __device__ inline void g_exact64(const Part& p, double fa, double df, double x, 
   sincos_small(orbit_angle(t), &sa, &ca);
   const double kv[3] = {p.kx, p.ky, p.kz};
   Cx<double> RA, RE, RT;
-  response_residual<double>(f, ca, sa, p.Pr, p.Pi, kv, RA, RE, RT);
+  response_residual<double>(f, ca, sa, p.Pr, p.Pi, kv, RA, RE, RT, p.ident);
   double u = rcbrt(f);
-  double amp = u * u * u * sqrt(u);
+  double amp = p.model == kModelLinearChirp ? 1.0 : u * u * u * sqrt(u);
   out[0] = amp * RA.re;
   out[1] = amp * RA.im;
   out[2] = amp * RE.re;

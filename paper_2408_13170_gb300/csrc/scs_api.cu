@@ -77,6 +77,7 @@ enum Slot {
 struct scs_ctx {
   int device = 0;
   int path = SCS_MIXED;
+  int model = 0;                   // scs_debug_set_model: waveform | response << 8
   int num_sms = 0;
   int grid_mixed = 0, grid_mixed_t = 0, grid_fp64 = 0;
   cudaStream_t stream = nullptr;
@@ -107,6 +108,7 @@ struct scs_ctx {
     DevBuf perm, tmp, km_cent, km_label, km_d2, km_pick;   // re-clustering scratch
     std::vector<uint64_t> gens;                // data generations the table was built from
     int table_path = -1;
+    int table_model = -1;
     cudaGraphExec_t exec = nullptr;            // captured iterations
     int graph_iters = 0;
     cudaStream_t cap = nullptr;                // capture stream
@@ -343,6 +345,7 @@ int prepare_batch(scs_ctx* ctx, const std::vector<BatchPart>& parts, const doubl
   CK(cudaMemsetAsync(diff, 0, sizeof(int) * (nct + 2), s));
   CK(cudaMemsetAsync(fill, 0, sizeof(int) * (nct + 1), s));
   k_setup<<<(P + 31) / 32, kSetupThreads, 0, s>>>(dparams, P, out.streams, ns, want_stride ? 1 : 0,
+                                                  ctx->model,
                                           out.part, out.crange, out.nrec, diff);
   CKLAUNCH();
   k_scan64<<<1, 1024, 0, s>>>(out.nrec, P, total);
@@ -522,6 +525,16 @@ void scs_destroy(scs_ctx* ctx) {
 }
 
 const char* scs_last_error(const scs_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int scs_debug_set_model(scs_ctx* ctx, int waveform, int response) {
+  if (!ctx) return SCS_EINVAL;
+  if (waveform < SCS_MODEL_TF2 || waveform > SCS_MODEL_LINEAR_CHIRP)
+    return fail(ctx, SCS_EINVAL, "bad waveform model %d", waveform);
+  if (response != SCS_RESPONSE_TDI && response != SCS_RESPONSE_IDENTITY)
+    return fail(ctx, SCS_EINVAL, "bad response model %d", response);
+  ctx->model = waveform | (response << 8);
+  return SCS_OK;
+}
 
 int scs_set_path(scs_ctx* ctx, int path) {
   if (!ctx) return SCS_EINVAL;
@@ -1276,7 +1289,8 @@ int pso_refresh(scs_ctx* ctx, cudaStream_t s, std::vector<BatchPart>& parts) {
   std::vector<uint64_t> gens;
   int rc = pso_parts(ctx, parts, &gens);
   if (rc) return rc;
-  if (gens == q.gens && q.table_path == ctx->path && q.table.ptr) return SCS_OK;
+  if (gens == q.gens && q.table_path == ctx->path && q.table_model == ctx->model && q.table.ptr)
+    return SCS_OK;
   if (q.exec) {
     CK(cudaStreamSynchronize(s));
     cudaGraphExecDestroy(q.exec);
@@ -1292,6 +1306,7 @@ int pso_refresh(scs_ctx* ctx, cudaStream_t s, std::vector<BatchPart>& parts) {
   CK(q.scratch.reserve(batch_scratch_bytes(parts, q.P)));
   q.gens = gens;
   q.table_path = ctx->path;
+  q.table_model = ctx->model;
   return SCS_OK;
 }
 

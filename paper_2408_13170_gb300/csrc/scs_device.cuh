@@ -27,6 +27,12 @@ constexpr int kSnr2Stride = 1024;                           // equal-SNR^2 ancho
 
 enum : int { kOk = 0, kInvalid = 1, kEmpty = 2 };
 
+// Waveform and response models.  The search uses TaylorF2 with the TDI
+// response; the others are test models with closed forms (a Newtonian
+// power-law chirp, the constant-amplitude linear chirp of App. A, and an
+// identity response h_A = h, h_E = h_T = 0 without Doppler modulation).
+enum : int { kModelTF2 = 0, kModelNewtonian = 1, kModelLinearChirp = 2 };
+
 // ---------------------------------------------------------- double-double
 // Error-free transformations (Knuth two-sum, FMA two-product); explicit _rn
 // intrinsics keep nvcc from contracting them.
@@ -109,6 +115,9 @@ struct Part {
   // v' = -sin(psi) u + cos(psi) v, so that n.P.n = ap ((n.u')^2 - (n.v')^2)
   // - i ax 2 (n.u')(n.v') with ap = (1 + cos^2 iota)/2, ax = cos iota
   double up[3], vp[3], ap, ax;
+  int model;        // kModelTF2, kModelNewtonian or kModelLinearChirp
+  int ident;        // 1: identity response (A only, no Doppler)
+  double lc_f0, lc_fdot;   // linear chirp: f(t) = f0 + fdot t
 };
 
 __device__ constexpr int kPow[4] = {5, 3, 2, 1};
@@ -121,19 +130,45 @@ __device__ inline double time_of_freq_u(const Part& p, double u) {
                        u * (-p.A[1].hi + u2 * (-(5.0 / 3.0) * p.A[0].hi))));
   return p.tc.hi + (p.tc.lo + u2 * u * s);
 }
-__device__ inline double time_of_freq(const Part& p, double f) { return time_of_freq_u(p, rcbrt(f)); }
+// t(f) given f and u = f^{-1/3} (the linear chirp uses f only)
+__device__ inline double time_of_freq_fu(const Part& p, double f, double u) {
+  if (p.model == kModelLinearChirp) return (f - p.lc_f0) / p.lc_fdot;
+  return time_of_freq_u(p, u);
+}
+__device__ inline double time_of_freq(const Part& p, double f) {
+  if (p.model == kModelLinearChirp) return (f - p.lc_f0) / p.lc_fdot;
+  return time_of_freq_u(p, rcbrt(f));
+}
 
-// Derive a particle from theta (8 doubles).  Support is not set here.
-__device__ inline void part_init(Part& p, const double* th) {
+__device__ inline void part_sky(Part& p, const double* th);
+
+// Derive a particle from theta (8 doubles) under `model` (bits 0-7: the
+// waveform model, bit 8: identity response).  Support is not set here.  The
+// linear chirp reads theta[0] as fdot [Hz/s] and ignores q.
+__device__ inline void part_init(Part& p, const double* th, int model = kModelTF2) {
   p.status = kInvalid;
   p.k_lo = 0;
   p.k_hi = -1;
   p.log2B = 0;
   p.log2Br = 0;
+  p.model = model & 0xff;
+  p.ident = (model >> 8) & 1;
+  p.lc_f0 = 0.0;
+  p.lc_fdot = 0.0;
   bool fin = true;
   for (int i = 0; i < 8; ++i) fin = fin && isfinite(th[i]);
   double Mc = th[0], q = th[1], f0 = th[2];
   p.f0 = f0;
+  if (p.model == kModelLinearChirp) {
+    if (!fin || !(Mc > 0.0) || !(f0 > 0.0) || th[7] != 0.0) return;
+    p.piMs = 0.0;   // no last stable orbit
+    p.tc = mkdd(0.0);
+    for (int m = 0; m < 4; ++m) p.A[m] = mkdd(0.0);
+    p.lc_f0 = f0;
+    p.lc_fdot = Mc;
+    part_sky(p, th);
+    return;
+  }
   if (!fin || !(Mc > 0.0) || !(q >= 1.0) || !(f0 > 0.0) || th[7] != 0.0) return;
   // eta = q/(1+q)^2 ; M = Mc eta^{-3/5}
   dd onepq = dd_two_sum(1.0, q);
@@ -153,13 +188,16 @@ __device__ inline void part_init(Part& p, const double* th) {
   // c = (pi Ms)^{-1/3};  v^{k-5} = c^{5-k} u^{5-k}
   dd c = dd_rcbrt(piMs);
   dd c2 = c * c, c3 = c2 * c, c5 = c3 * c2;
-  // phi_k (TaylorF2, circular, 2PN)
+  // phi_k (TaylorF2, circular, 2PN; the Newtonian model keeps phi_0 only)
+  const bool pn = p.model == kModelTF2;
   dd phi0 = mkdd(1.0);
-  dd phi2 = dd_div(mkdd(3715.0), mkdd(756.0)) + dd_div(mkdd(55.0), mkdd(9.0)) * eta;
-  dd phi3 = mkdd(kPi, kPiLo) * -16.0;
-  dd phi4 = dd_div(mkdd(15293365.0), mkdd(508032.0)) +
-            dd_div(mkdd(27145.0), mkdd(504.0)) * eta +
-            dd_div(mkdd(3085.0), mkdd(72.0)) * (eta * eta);
+  dd phi2 = pn ? dd_div(mkdd(3715.0), mkdd(756.0)) + dd_div(mkdd(55.0), mkdd(9.0)) * eta
+               : mkdd(0.0);
+  dd phi3 = pn ? mkdd(kPi, kPiLo) * -16.0 : mkdd(0.0);
+  dd phi4 = pn ? dd_div(mkdd(15293365.0), mkdd(508032.0)) +
+                     dd_div(mkdd(27145.0), mkdd(504.0)) * eta +
+                     dd_div(mkdd(3085.0), mkdd(72.0)) * (eta * eta)
+               : mkdd(0.0);
   // 3/(256 pi eta)
   dd pre = dd_div(mkdd(3.0), mkdd(kPi, kPiLo) * 256.0 * eta);
   p.A[0] = pre * phi0 * c5;
@@ -173,7 +211,11 @@ __device__ inline void part_init(Part& p, const double* th) {
             u0 * (dd_div(p.A[2] * 2.0, mkdd(3.0)) +
                   u0 * (p.A[1] + u02 * dd_div(p.A[0] * 5.0, mkdd(3.0)))));
   p.tc = u02 * u0 * s;
-  // sky and polarisation
+  part_sky(p, th);
+}
+
+// Sky position and polarisation of a particle (theta[3..6]); marks it valid.
+__device__ inline void part_sky(Part& p, const double* th) {
   double lam = th[3], bet = th[4], inc = th[5], psi = th[6];
   double cb = cos(bet), sb = sin(bet), cl = cos(lam), sl = sin(lam);
   p.kx = -cb * cl;
@@ -200,7 +242,7 @@ __device__ inline void part_init(Part& p, const double* th) {
     p.Pr[m] = ap * (c2p * ep + s2p * ex);
     p.Pi[m] = -ax * (-s2p * ep + c2p * ex);
   }
-  p.Rcb = kAU * cb;
+  p.Rcb = p.ident ? 0.0 : kAU * cb;   // the identity response has no Doppler term
   p.lam = lam;
   for (int m = 0; m < 6; ++m) {
     p.Pr32[m] = (float)p.Pr[m];
@@ -364,7 +406,14 @@ __device__ inline float sinc_(float x) {
 // channel leave RT unused).
 template <typename T>
 __device__ inline void response_residual(T f, T ca, T sa, const T* Pr, const T* Pi,
-                                         const T* kv, Cx<T>& RA, Cx<T>& RE, Cx<T>& RT) {
+                                         const T* kv, Cx<T>& RA, Cx<T>& RE, Cx<T>& RT,
+                                         bool ident = false) {
+  if (ident) {   // identity response model: h_A = h, h_E = h_T = 0
+    RA = Cx<T>{(T)1, (T)0};
+    RE = Cx<T>{(T)0, (T)0};
+    RT = Cx<T>{(T)0, (T)0};
+    return;
+  }
   const T L = (T)kArm;
   const T eR2 = (T)(kArm / (4.0 * 1.7320508075688772));   // e R / 2 = L/(4 sqrt3)
   const T s3 = (T)1.7320508075688772;
@@ -436,6 +485,12 @@ __device__ inline void response_residual(T f, T ca, T sa, const T* Pr, const T* 
 // addition (direct sin when the argument is small), and D = e^{-2 i a}.
 __device__ inline void response_power64(const Part& p, double f, double ca, double sa,
                                         double& pA, double& pE, double* pT) {
+  if (p.ident) {
+    pA = 1.0;
+    pE = 0.0;
+    if (pT) *pT = 0.0;
+    return;
+  }
   const double L = kArm;
   const double eR2 = kArm / (4.0 * 1.7320508075688772);
   const double s3 = 1.7320508075688772;
@@ -539,10 +594,16 @@ __device__ inline double doppler_delay(const Part& p, double t) {
 // Reduced total phase (turns, in [-1/2, 1/2)) of bin f (dd) together with
 // t(f): Phi = F(f) + f k.p0(t(f)); the large F is summed in double-double.
 __device__ inline double phase_turns_fp64(const Part& p, dd f, double& t_out) {
-  dd u = dd_rcbrt(f);
-  dd u2 = u * u;
-  dd Fp = u * (p.A[3] + u * (p.A[2] + u * (p.A[1] + u2 * p.A[0])));
-  dd F = f * p.tc + Fp - mkdd(0.125);
+  dd F;
+  if (p.model == kModelLinearChirp) {   // (f - f0)^2 / (2 fdot) - 1/8
+    const dd x = f - mkdd(p.lc_f0);
+    F = dd_div(x * x, mkdd(2.0 * p.lc_fdot)) - mkdd(0.125);
+  } else {
+    dd u = dd_rcbrt(f);
+    dd u2 = u * u;
+    dd Fp = u * (p.A[3] + u * (p.A[2] + u * (p.A[1] + u2 * p.A[0])));
+    F = f * p.tc + Fp - mkdd(0.125);
+  }
   double n = rint(F.hi);
   double fr = dd_val(F - mkdd(n));
   double fd = dd_val(f);
@@ -565,10 +626,10 @@ __device__ inline void bin_fp64(const Part& p, double f_first, double df, int64_
   sincos_small(orbit_angle(t), &sa, &ca);
   const double kv[3] = {p.kx, p.ky, p.kz};
   Cx<double> RA, RE, RT;
-  response_residual<double>(fd, ca, sa, p.Pr, p.Pi, kv, RA, RE, RT);
-  // A(f) = f^{-7/6} = u^3 sqrt(u), u = f^{-1/3}
+  response_residual<double>(fd, ca, sa, p.Pr, p.Pi, kv, RA, RE, RT, p.ident);
+  // A(f) = f^{-7/6} = u^3 sqrt(u), u = f^{-1/3} (the linear chirp: 1)
   double u = rcbrt(fd);
-  double amp = u * u * u * sqrt(u);
+  double amp = p.model == kModelLinearChirp ? 1.0 : u * u * u * sqrt(u);
   GA = Cx<double>{amp * RA.re, amp * RA.im};
   GE = Cx<double>{amp * RE.re, amp * RE.im};
   GT = Cx<double>{amp * RT.re, amp * RT.im};

@@ -130,7 +130,7 @@ __device__ void stride_estimates(const Part& p, double f_first, double df, int* 
 __global__ void __launch_bounds__(kSetupThreads) k_setup(const double* params, int P,
                                                          const StreamDesc* streams,
                                                          int n_streams, int want_stride,
-                                                         Part* part, int2* crange,
+                                                         int model, Part* part, int2* crange,
                                                          int64_t* nrec, int* diff) {
   __shared__ Part sp[32];
   __shared__ int s_l[32], s_lim[32];
@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(kSetupThreads) k_setup(const double* params, i
     if (i < P) {
       const int sid = stream_of_particle(streams, n_streams, i);
       d = streams + sid;
-      part_init(p, params + 8 * (int64_t)i);
+      part_init(p, params + 8 * (int64_t)i, model);
       part_support(p, d->f_first, d->df, d->K, d->T_obs);
       p.sid = sid;
     }
@@ -641,16 +641,16 @@ __global__ void __launch_bounds__(128) k_bounds_df(const Part* part, int P,
       const double r = fma(-f, u * u * u, 1.0);
       u = fma(u * r, 1.0 / 3.0, u);
     }
-    const double t = time_of_freq_u(p, u);
+    const double t = time_of_freq_fu(p, f, u);
     const double al = orbit_angle(t);
     const double a64 = kPi * kArm * f;
     bad = bad || !(a64 < 3.9);   // beyond the double-float sin/cos reduction
-    dfl qA, qE, qT;
-    response_power_df(pc, df_from(a64), df_from(al), qA, qE, qT);
-    // |h|^2 = A(f)^2 |R|^2, A(f)^2 = f^{-7/3} = u^7
+    dfl qA{1.f, 0.f}, qE{0.f, 0.f}, qT{0.f, 0.f};   // the identity response
+    if (!p.ident) response_power_df(pc, df_from(a64), df_from(al), qA, qE, qT);
+    // |h|^2 = A(f)^2 |R|^2, A(f)^2 = f^{-7/3} = u^7 (the linear chirp: 1)
     const dfl ud = df_from(u);
     const dfl u2 = ud * ud, u4 = u2 * u2;
-    const dfl amp2 = (u4 * u2) * ud;
+    const dfl amp2 = p.model == kModelLinearChirp ? dfl{1.f, 0.f} : (u4 * u2) * ud;
     const float4 w = sd.wdf[ka];
     dfl hk = dfl{w.x, w.y} * qA + dfl{w.z, w.w} * qE;
     if (withT) {
@@ -684,12 +684,12 @@ __global__ void __launch_bounds__(128) k_bounds_h64(const Part* part, const Stre
     const int ka = min(p.k_lo + a * kSnr2Stride, p.k_hi);
     const double f = dd_val(grid_freq_dd(sd.f_first, sd.df, ka));
     const double u = rcbrt(f), u2 = u * u;
-    const double t = time_of_freq_u(p, u);
+    const double t = time_of_freq_fu(p, f, u);
     double sa, ca;
     sincos_small(orbit_angle(t), &sa, &ca);
     double pA, pE, pT = 0.0;
     response_power64(p, f, ca, sa, pA, pE, sd.wT64 ? &pT : nullptr);
-    const double amp2 = u2 * u2 * u2 * u;
+    const double amp2 = p.model == kModelLinearChirp ? 1.0 : u2 * u2 * u2 * u;
     const double2 w = sd.w64[ka];
     double hk = __dadd_rn(__dmul_rn(w.x, amp2 * pA), __dmul_rn(w.y, amp2 * pE));
     if (sd.wT64) hk = __dadd_rn(hk, __dmul_rn(sd.wT64[ka], amp2 * pT));

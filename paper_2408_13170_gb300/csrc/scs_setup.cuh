@@ -8,7 +8,7 @@ namespace scs {
 constexpr int kSetupThreads = 288;
 __global__ void __launch_bounds__(kSetupThreads)
     k_setup(const double* params, int P, const StreamDesc* streams, int n_streams,
-            int want_stride, Part* part, int2* crange, int64_t* nrec, int* diff);
+            int want_stride, int model, Part* part, int2* crange, int64_t* nrec, int* diff);
 __global__ void k_scan64(int64_t* v, int64_t n, int64_t* total);
 __global__ void k_chunk_table(const int* diff, int n_chunks, int* cnt, int* list_off,
                               int* item_off);

@@ -19,6 +19,9 @@ SCS_OK, SCS_EINVAL, SCS_ENOMEM, SCS_ECUDA, SCS_ENODATA, SCS_ETIMEOUT, SCS_EUNSUP
     0, -1, -2, -3, -4, -5, -6)
 SCS_FP64, SCS_MIXED = 0, 1
 SCS_EQUAL_WIDTH, SCS_EQUAL_SNR2 = 0, 1
+# test-only models (scs_debug_set_model)
+SCS_MODEL_TF2, SCS_MODEL_NEWTONIAN, SCS_MODEL_LINEAR_CHIRP = 0, 1, 2
+SCS_RESPONSE_TDI, SCS_RESPONSE_IDENTITY = 0, 1
 
 _lock = threading.Lock()
 _lib = None
@@ -47,6 +50,8 @@ def lib():
         L.scs_last_error.restype = ctypes.c_char_p
         L.scs_set_path.argtypes = [P, I]
         L.scs_set_path.restype = I
+        L.scs_debug_set_model.argtypes = [P, I, I]
+        L.scs_debug_set_model.restype = I
         L.scs_set_data.argtypes = [P, I, P, P, P, P, D, D, I64, D]
         L.scs_set_data.restype = I
         L.scs_set_data_aet.argtypes = [P, I, P, P, P, P, P, P, D, D, I64, D]
@@ -159,6 +164,11 @@ def scs_last_error(ctx) -> str:
 
 def scs_set_path(ctx, path: int):
     _check(ctx, lib().scs_set_path(ctx, path))
+
+
+def scs_debug_set_model(ctx, waveform: int, response: int):
+    """Test-only: switch waveform / response to a closed-form test model."""
+    _check(ctx, lib().scs_debug_set_model(ctx, waveform, response))
 
 
 def scs_set_data(ctx, stream_id, A, E, S_A, S_E, f_first, df, K, T_obs):
@@ -411,6 +421,9 @@ class Context:
 
     def set_path(self, path):
         scs_set_path(self.h, path)
+
+    def set_model(self, waveform, response):
+        scs_debug_set_model(self.h, waveform, response)
 
     def set_data(self, stream_id, data):
         A = np.ascontiguousarray(data["A"], dtype=np.complex128)
