@@ -360,7 +360,7 @@ int prepare_batch(scs_ctx* ctx, const std::vector<BatchPart>& parts, const doubl
   if (ctx->prof) CK(cudaEventRecord(ctx->ev[1], s));
   if (out.any_snr2 && want_edges) {
     CK(cudaMemsetAsync(fb, 0, sizeof(int), s));
-    k_bounds_df<<<(int)(((int64_t)P * 32 + 127) / 128), 128, 0, s>>>(
+    k_bounds_df<<<P, 128, 0, s>>>(
         out.part, P, out.streams, out.edges, Hs, Cs, fb + 1, fb);
     CKLAUNCH();
     if (ctx->prof && ctx->prof_host) {

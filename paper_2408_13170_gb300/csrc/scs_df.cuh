@@ -30,6 +30,40 @@ __device__ __forceinline__ dfl df_from(double x) {
   return dfl{h, __double2float_rn(x - (double)h)};
 }
 __device__ __forceinline__ double df_to(dfl a) { return (double)a.hi + (double)a.lo; }
+
+// The same two conversions with integer operations on the bit patterns
+// instead of FP64 conversion instructions (which GB300 issues at its FP64
+// rate).  Valid for 0 and for magnitudes whose parts are normal floats
+// (about 1e-30 .. 1e38).  df_split: hi = x rounded to 24 significant bits
+// (ties away from zero), lo = x - hi rounded to FP32.
+__device__ __forceinline__ dfl df_split(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned long long m = b & 0x7fffffffffffffffULL;
+  if (m == 0ULL) return dfl{0.f, 0.f};
+  if (m < (964ULL << 52) || m >= (1150ULL << 52)) return df_from(x);   // outside 2^-59 .. 2^127
+  const unsigned long long mr = (m + (1ULL << 28)) & ~((1ULL << 29) - 1ULL);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int eh = (int)(mr >> 52) - 1023;   // exponent of hi
+  const unsigned hb = sign | ((unsigned)(eh + 127) << 23) | (unsigned)((mr >> 29) & 0x7fffffULL);
+  // lo = (m - mr) units of 2^(ex - 52), ex the exponent of x
+  const int ex = (int)(m >> 52) - 1023;
+  const int r = (int)((long long)m - (long long)mr);
+  const float scale = __int_as_float((ex - 52 + 127) << 23);
+  const float lo = (float)r * scale;
+  return dfl{__int_as_float((int)hb), sign ? -lo : lo};
+}
+// exact FP32 -> FP64 of a normal float (or 0) by its bits
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned u = (unsigned)__float_as_int(f);
+  const unsigned mag = u & 0x7fffffffu;
+  if (mag == 0u) return 0.0;
+  if (mag < 0x00800000u || mag >= 0x7f800000u) return (double)f;   // subnormal, inf, nan
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned long long e = (unsigned long long)((mag >> 23) + 896u) << 52;
+  const unsigned long long mant = (unsigned long long)(mag & 0x7fffffu) << 29;
+  return __longlong_as_double((long long)(sign | e | mant));
+}
+__device__ __forceinline__ double df_join(dfl a) { return f2d_bits(a.hi) + f2d_bits(a.lo); }
 __device__ __forceinline__ dfl df_f(float x) { return dfl{x, 0.f}; }
 
 __device__ __forceinline__ dfl df_fast(float a, float b) {   // |a| >= |b|

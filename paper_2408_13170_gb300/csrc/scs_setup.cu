@@ -494,20 +494,24 @@ __device__ inline void response_power_df(const PowDf& c, dfl a, dfl al, dfl& qA,
   qT = (fac * cdf_norm2((X + Y) + Z)) * i3;
 }
 
-// Cumulative anchor power and the edges of one particle (one warp) from its
-// anchor powers H[0 .. nanch) (FP64, any common scale): trapezoid terms and
-// the running sum in FP64 (each lane a contiguous run of anchors, joined by
-// a warp scan), then per lane a contiguous run of interior edges: the offset
-// c_n - C[a-1] is carried in double-float from one target to the next and
+// Cumulative anchor power and the edges of one particle (one block of
+// kBT threads) from its anchor powers H[0 .. nanch) (FP64, any common
+// scale): trapezoid terms and the running sum in FP64 (each thread a
+// contiguous run of anchors, joined by a block scan), then per thread a
+// contiguous run of interior edges: the offset c_n - C[a-1] is carried in
+// double-float from one target to the next and
 // kappa_n - k_{a-1} = (c_n - C[a-1]) (k_a - k_{a-1}) / (C[a] - C[a-1]).
 // An edge within eps Cl / slope bins of an integer is either reported
-// (returns true; exact = false) or recomputed with the definition's FP64
-// arithmetic (exact = true).
+// (returns true, block-uniform; exact = false) or recomputed with the
+// definition's FP64 arithmetic (exact = true).
+constexpr int kBT = 128;
+
 __device__ bool bounds_edges(const Part& p, int N, int nanch, const double* H, double* C,
-                             int* e, bool exact, float eps, int lane) {
+                             int* e, bool exact, float eps, double* s_warp) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int m = nanch - 1;
-  const int per = (m + 31) / 32;
-  const int a0 = 1 + lane * per, a1 = min(nanch, a0 + per);
+  const int per = (m + kBT - 1) / kBT;
+  const int a0 = 1 + tid * per, a1 = min(nanch, a0 + per);
   double run = 0.0;
   for (int a = a0; a < a1; ++a) {
     const int ka = min(p.k_lo + a * kSnr2Stride, p.k_hi);
@@ -516,25 +520,30 @@ __device__ bool bounds_edges(const Part& p, int N, int nanch, const double* H, d
     C[a] = t;
     run = __dadd_rn(run, t);
   }
+  // block exclusive scan of the runs: warp scans, then the warp totals
   double incl = run;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const double v = __shfl_up_sync(kFull, incl, o);
     if (lane >= o) incl = __dadd_rn(incl, v);
   }
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  double base = 0.0;
+  for (int w = 0; w < warp; ++w) base = __dadd_rn(base, s_warp[w]);
   double acc = __shfl_up_sync(kFull, incl, 1);
-  if (lane == 0) acc = 0.0;
+  acc = lane == 0 ? base : __dadd_rn(base, acc);
   for (int a = a0; a < a1; ++a) {
     acc = __dadd_rn(acc, C[a]);
     C[a] = acc;
   }
-  if (lane == 0) C[0] = 0.0;
-  __syncwarp();
+  if (tid == 0) C[0] = 0.0;
+  __syncthreads();
   const double Cl = C[nanch - 1];
-  if (lane == 0) e[0] = p.k_lo;
-  if (lane == 31) e[N] = p.k_hi + 1;
+  if (tid == 0) e[0] = p.k_lo;
+  if (tid == kBT - 1) e[N] = p.k_hi + 1;
   const int M = N - 1;
-  const int n0 = 1 + (int)(((int64_t)lane * M) / 32), n1 = 1 + (int)(((int64_t)(lane + 1) * M) / 32);
+  const int n0 = 1 + (int)(((int64_t)tid * M) / kBT), n1 = 1 + (int)(((int64_t)(tid + 1) * M) / kBT);
   if (!(Cl > 0.0)) {
     for (int n = n0; n < n1; ++n) e[n] = p.k_lo;
     return false;
@@ -557,9 +566,9 @@ __device__ bool bounds_edges(const Part& p, int N, int nanch, const double* H, d
   if (n0 < n1) {
     const double c0 = target(n0);
     int a = first_at_least(c0);
-    dfl num = df_from(__dsub_rn(c0, C[a - 1]));
-    const dfl step = df_from(Cl * invN);
-    dfl width = df_from(__dsub_rn(C[a], C[a - 1]));
+    dfl num = df_split(__dsub_rn(c0, C[a - 1]));
+    const dfl step = df_split(Cl * invN);
+    dfl width = df_split(__dsub_rn(C[a], C[a - 1]));
     int a_rec = -1;
     dfl rec{0.f, 0.f};
     float guard = 0.f;
@@ -569,7 +578,7 @@ __device__ bool bounds_edges(const Part& p, int N, int nanch, const double* H, d
       while (a < nanch - 1 && (num.hi > width.hi || (num.hi == width.hi && num.lo > width.lo))) {
         num = num - width;
         ++a;
-        width = df_from(__dsub_rn(C[a], C[a - 1]));
+        width = df_split(__dsub_rn(C[a], C[a - 1]));
       }
       const int k1 = min(p.k_lo + (a - 1) * kSnr2Stride, p.k_hi);
       const int k2 = min(p.k_lo + a * kSnr2Stride, p.k_hi);
@@ -600,26 +609,29 @@ __device__ bool bounds_edges(const Part& p, int N, int nanch, const double* H, d
       e[n] = ek;
     }
   }
-  return __any_sync(kFull, flag);
+  return __syncthreads_or(flag) != 0;
 }
 
 // Step 1: double-float anchor powers, FP64 cumulative, edges; particles with
 // an edge in a guard band go on the fallback list (fb_list[0 .. *fb_count)).
-__global__ void __launch_bounds__(128) k_bounds_df(const Part* part, int P,
+// One block of kBT threads per particle; the anchors are spread over the
+// block, FP64 only for f, f^{-1/3}, t(f), the orbit angle and the sums.
+__global__ void __launch_bounds__(kBT) k_bounds_df(const Part* part, int P,
                                                    const StreamDesc* streams, int* edges_all,
                                                    double* Hs, double* Cs, int* fb_list,
                                                    int* fb_count) {
-  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (gw >= P) return;
-  const Part& p = part[gw];
+  __shared__ double s_warp[kBT / 32];
+  const int gp = blockIdx.x;
+  const int tid = threadIdx.x;
+  if (gp >= P) return;
+  const Part& p = part[gp];
   const StreamDesc& sd = streams[p.sid];
   if (sd.mode != 1) return;   // equal-width streams share a fixed table
   const int N = sd.N;
-  const int64_t lp = gw - sd.p_off;
+  const int64_t lp = gp - sd.p_off;
   int* e = edges_all + sd.edge_base + lp * (N + 1);
   if (p.status != kOk) {
-    for (int n = lane; n <= N; n += 32) e[n] = 0;
+    for (int n = tid; n <= N; n += kBT) e[n] = 0;
     return;
   }
   const int span = p.k_hi - p.k_lo;
@@ -630,39 +642,41 @@ __global__ void __launch_bounds__(128) k_bounds_df(const Part* part, int P,
   pow_consts(p, pc);
   const double f_first = sd.f_first, df = sd.df;
   const bool withT = sd.wTdf != nullptr;
+  const bool lin = p.model == kModelLinearChirp;
   bool bad = false;
-  for (int a = lane; a < nanch; a += 32) {
+  for (int a = tid; a < nanch; a += kBT) {
     const int ka = min(p.k_lo + a * kSnr2Stride, p.k_hi);
     const double f = fma((double)ka, df, f_first);
-    // u = f^{-1/3}: FP32 estimate and two Newton steps in FP64
-    double u = (double)rcbrtf((float)f);
-#pragma unroll
-    for (int it = 0; it < 2; ++it) {
-      const double r = fma(-f, u * u * u, 1.0);
-      u = fma(u * r, 1.0 / 3.0, u);
-    }
+    // u = f^{-1/3}: FP32 estimate, one Newton step in double-float, one in FP64
+    const dfl fd = df_split(f);
+    const float u0 = rcbrtf(fd.hi);
+    const dfl u03 = (df_f(u0) * df_f(u0)) * u0;
+    const dfl r0 = df_f(1.f) - fd * u03;
+    const dfl u1 = df_f(u0) + (r0 * df_f(u0)) * df_const(1.0 / 3.0);
+    double u = df_join(u1);
+    u = fma(u * fma(-f, u * u * u, 1.0), 1.0 / 3.0, u);
     const double t = time_of_freq_fu(p, f, u);
     const double al = orbit_angle(t);
-    const double a64 = kPi * kArm * f;
+    const double a64 = (kPi * kArm) * f;
     bad = bad || !(a64 < 3.9);   // beyond the double-float sin/cos reduction
     dfl qA{1.f, 0.f}, qE{0.f, 0.f}, qT{0.f, 0.f};   // the identity response
-    if (!p.ident) response_power_df(pc, df_from(a64), df_from(al), qA, qE, qT);
+    if (!p.ident) response_power_df(pc, df_split(a64), df_split(al), qA, qE, qT);
     // |h|^2 = A(f)^2 |R|^2, A(f)^2 = f^{-7/3} = u^7 (the linear chirp: 1)
-    const dfl ud = df_from(u);
+    const dfl ud = df_split(u);
     const dfl u2 = ud * ud, u4 = u2 * u2;
-    const dfl amp2 = p.model == kModelLinearChirp ? dfl{1.f, 0.f} : (u4 * u2) * ud;
+    const dfl amp2 = lin ? dfl{1.f, 0.f} : (u4 * u2) * ud;
     const float4 w = sd.wdf[ka];
     dfl hk = dfl{w.x, w.y} * qA + dfl{w.z, w.w} * qE;
     if (withT) {
       const float2 wt = sd.wTdf[ka];
       hk = hk + dfl{wt.x, wt.y} * qT;
     }
-    H[a] = df_to(amp2 * hk);
+    H[a] = df_join(amp2 * hk);
   }
-  __syncwarp();
-  const bool flag = bounds_edges(p, N, nanch, H, C, e, false, kEpsPowerDf, lane) ||
-                    __any_sync(kFull, bad);
-  if (flag && lane == 0) fb_list[atomicAdd(fb_count, 1)] = gw;
+  __syncthreads();
+  const bool flag = bounds_edges(p, N, nanch, H, C, e, false, kEpsPowerDf, s_warp) ||
+                    __syncthreads_or(bad);
+  if (flag && tid == 0) fb_list[atomicAdd(fb_count, 1)] = gp;
 }
 
 // Step 2a: FP64 anchor powers of the listed particles; work item = (listed
@@ -698,14 +712,13 @@ __global__ void __launch_bounds__(128) k_bounds_h64(const Part* part, const Stre
 }
 
 // Step 2b: cumulative and edges of the listed particles from their FP64
-// anchor powers (one warp per particle, persistent warps).
-__global__ void __launch_bounds__(128) k_bounds_fix(const Part* part, const StreamDesc* streams,
+// anchor powers (one block per particle, persistent blocks).
+__global__ void __launch_bounds__(kBT) k_bounds_fix(const Part* part, const StreamDesc* streams,
                                                     int* edges_all, double* Hs, double* Cs,
                                                     const int* fb_list, const int* fb_count) {
-  const int lane = threadIdx.x & 31;
-  const int nw = (gridDim.x * blockDim.x) >> 5;
+  __shared__ double s_warp[kBT / 32];
   const int count = *fb_count;
-  for (int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < count; w += nw) {
+  for (int w = blockIdx.x; w < count; w += gridDim.x) {
     const int gw = fb_list[w];
     const Part& p = part[gw];
     const StreamDesc& sd = streams[p.sid];
@@ -714,7 +727,8 @@ __global__ void __launch_bounds__(128) k_bounds_fix(const Part* part, const Stre
     const int span = p.k_hi - p.k_lo;
     const int nanch = span / kSnr2Stride + 1 + (span % kSnr2Stride != 0 ? 1 : 0);
     bounds_edges(p, N, nanch, Hs + sd.hc_base + lp * sd.amax, Cs + sd.hc_base + lp * sd.amax,
-                 edges_all + sd.edge_base + lp * (N + 1), true, kEpsInterp, lane);
+                 edges_all + sd.edge_base + lp * (N + 1), true, kEpsInterp, s_warp);
+    __syncthreads();   // s_warp is reused by the next particle
   }
 }
 
