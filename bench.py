@@ -80,6 +80,8 @@ def parse(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison")
+    ap.add_argument("--no-spline", action="store_true",
+                    help="skip the sparse-grid spline path (the paper's design) comparison")
     ap.add_argument("--fp64-repeats", type=int, default=3,
                     help="timed FP64-path evaluations (after one untimed)")
     ap.add_argument("--fp64-subset", type=int, default=64,
@@ -529,6 +531,8 @@ def run_ours(args, rank, world, local):
 
     fp64, acc = (None, {}) if args.no_fp64 else fp64_leg(args, ctx, w, batches, stat, stream,
                                                          sids, P_level, value / world)
+    spline = None if (args.no_spline or nl > 1) else spline_leg(
+        args, ctx, w, batches, stat, stream, P, value / world, acc)
 
     # CPU oracle on a bounded sample of the same workload (rank 0 only)
     cpu = None
@@ -576,6 +580,7 @@ def run_ours(args, rank, world, local):
         "gpu_launches": LAUNCHES_PER_STEP * args.steps,
         "clocks": ck,
         "fp64_path": fp64,
+        "spline_path": spline,
         "accuracy": acc,
         "cpu_baseline": cpu,
         "wall_s_timed_region": wall,
@@ -659,6 +664,39 @@ def fp64_leg(args, ctx, w, batches, stat, stream, sids, P_level, mixed_value):
            "best_particle_agrees_per_level": agree,
            "best_particle_candidates_per_level": [int(len(c)) for c in cand_levels]}
     return fp64, acc
+
+
+def spline_leg(args, ctx, w, batches, stat, stream, P, mixed_value, acc):
+    """The sparse-grid spline path (the paper's GPU design: waveform and
+    response exact on nodes <= 1024 bins apart, cubic splines onto the FFT
+    grid) on the first timed batch: one untimed call, then --fp64-repeats
+    timed ones (median); its error against the mixed path's statistic (and
+    the FP64 path's, when that ran)."""
+    import torch
+    from paper_2408_13170_gb300 import scstat
+    b = batches[args.warmup]
+    out = torch.empty(P, dtype=torch.float64, device=b.device)
+    ctx.set_path(scstat.SCS_SPLINE)
+    scstat.scs_eval_stat(ctx.h, 0, b, P, out, cuda_stream=stream)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(max(1, args.fp64_repeats)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        scstat.scs_eval_stat(ctx.h, 0, b, P, out, cuda_stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    ctx.set_path(scstat.SCS_MIXED)
+    t = float(np.median(times))
+    s = out.cpu().numpy()
+    m = stat[args.warmup].cpu().numpy()
+    acc["max_rel_err_spline_vs_mixed"] = float(np.max(np.abs(s - m) / np.maximum(np.abs(m), 1.0)))
+    return {"value": P / t, "unit": "particle-evals/s", "ms_per_call": 1e3 * t,
+            "repeats": len(times), "mixed_speedup": mixed_value / (P / t),
+            "design": "nodes every <= 1024 bins (x1000 sparse grid, halved where the phase "
+                      "spline would exceed 1e-6 turns), not-a-knot cubic splines of the phase "
+                      "(FP64) and of G (FP32), FP32 products, Kahan sums"}
 
 
 def main():

@@ -58,6 +58,10 @@ extern "C" {
 /* evaluation paths */
 #define SCS_FP64 0   /* every bin in FP64, double-double phase */
 #define SCS_MIXED 1  /* FP64 anchors + FP32 split-phase bins, Kahan sums */
+#define SCS_SPLINE 2 /* comparison path built like the paper's GPU design (Sec. IV):
+                        phase and amplitude x transfer functions exact on a sparse
+                        node grid, cubic splines onto the FFT grid (FP64 phase
+                        spline, FP32 products, Kahan sums); see scs_set_spline */
 
 /* segmentations */
 #define SCS_EQUAL_WIDTH 0 /* n-th edge floor(n K / N) over the whole grid */
@@ -67,6 +71,7 @@ typedef struct scs_ctx scs_ctx; /* opaque, owned by the library */
 
 /* Create a context on CUDA device `device` using evaluation path `path`
  * (SCS_FP64 or SCS_MIXED).  *out receives the context (NULL on failure).
+ * SCS_SPLINE is accepted too.
  * Errors: SCS_EINVAL (bad device/path/out), SCS_ECUDA, SCS_ENOMEM. */
 int scs_create(scs_ctx **out, int device, int path);
 
@@ -77,8 +82,24 @@ void scs_destroy(scs_ctx *ctx);
  * context, valid until the next call on it). */
 const char *scs_last_error(const scs_ctx *ctx);
 
-/* Switch the evaluation path of later calls (SCS_FP64 or SCS_MIXED). */
+/* Switch the evaluation path of later calls (SCS_FP64, SCS_MIXED or
+ * SCS_SPLINE; the swarm calls refuse SCS_SPLINE with SCS_EUNSUPPORTED). */
 int scs_set_path(scs_ctx *ctx, int path);
+
+/* Node grid of the SCS_SPLINE path.  Sec. IV evaluates the waveform and the
+ * response on a grid about 1000 times coarser than the FFT grid and
+ * spline-interpolates them onto it; here each particle's nodes are
+ * k_lo, k_lo + S, ..., k_hi with S the largest power of two
+ * <= 2^max_log2_spacing (default 10: 1024 bins) for which twice the cubic
+ * spline's phase error bound (5/384) S^4 max|d^4 Phi/dk^4| stays below 1e-6
+ * turns, the phase tolerance of the mixed path's anchors.  The splines are
+ * not-a-knot cubic splines of the unwrapped total phase Phi (turns, FP64
+ * coefficients) and of the real and imaginary parts of G_A, G_E (and G_T),
+ * G = A(f) R(f) (FP32 coefficients).  An evaluation on this path
+ * synchronises with the host once (to size the node scratch) and allocates.
+ *   max_log2_spacing  3 .. 14.
+ * Errors: SCS_EINVAL. */
+int scs_set_spline(scs_ctx *ctx, int max_log2_spacing);
 
 /* ---- Test-only: model switch ----
  * Replaces, for every later call on the context (evaluation on both paths,

@@ -15,8 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libscstat.so")
-UNITS = ["scs_api", "scs_setup", "scs_mixed", "scs_fp64", "scs_pso", "scs_peaks"]
-HEADERS = ["scs_device.cuh", "scs_internal.cuh", "scs_anchor.cuh", "scs_setup.cuh"]
+UNITS = ["scs_api", "scs_setup", "scs_mixed", "scs_fp64", "scs_pso", "scs_peaks", "scs_spline"]
+HEADERS = ["scs_device.cuh", "scs_internal.cuh", "scs_anchor.cuh", "scs_setup.cuh", "scs_df.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -69,7 +69,8 @@ bool is_device_ptr(const void* p) {
 enum Slot {
   kSlotStreams, kSlotPart, kSlotCrange, kSlotNrec, kSlotTotal, kSlotDiff, kSlotCnt,
   kSlotListOff, kSlotItemOff, kSlotFill, kSlotList, kSlotListTmp, kSlotRec, kSlotSlices, kSlotCounter, kSlotEdges,
-  kSlotHs, kSlotCs, kSlotFb, kNumSlots
+  kSlotHs, kSlotCs, kSlotFb, kSlotSplL2, kSlotSplCnt, kSlotSplPhi, kSlotSplG, kSlotSplWork,
+  kSlotSplPc, kSlotSplGc, kNumSlots
 };
 
 }  // namespace
@@ -77,9 +78,10 @@ enum Slot {
 struct scs_ctx {
   int device = 0;
   int path = SCS_MIXED;
+  int spline_log2 = 10;            // largest node spacing of the spline path: 1024 bins
   int model = 0;                   // scs_debug_set_model: waveform | response << 8
   int num_sms = 0;
-  int grid_mixed = 0, grid_mixed_t = 0, grid_fp64 = 0;
+  int grid_mixed = 0, grid_mixed_t = 0, grid_fp64 = 0, grid_spline = 0;
   cudaStream_t stream = nullptr;
   std::string err;
   bool prof = false;               // record stage events in the evaluation calls
@@ -417,6 +419,31 @@ int run_batch(scs_ctx* ctx, const Prepared& pr, int P, double* dstat, double* ds
       launch_main_mixed(a, 1, ctx->grid_mixed_t, s);
       CKLAUNCH();
     }
+  } else if (ctx->path == SCS_SPLINE) {
+    // the sparse-grid spline path: node counts, their offsets (needed on
+    // the host to size the node scratch), node values, coefficients
+    if (!src.ctx) return fail(ctx, SCS_EUNSUPPORTED, "the spline path allocates its scratch");
+    int* l2s = (int*)src.get(kSlotSplL2, sizeof(int) * P);
+    int64_t* cnt = (int64_t*)src.get(kSlotSplCnt, sizeof(int64_t) * (P + 2));
+    if (src.failed()) CK(src.err);
+    if (spline_prepare(pr.part, P, pr.streams, ctx->spline_log2, l2s, cnt, s))
+      return fail(ctx, SCS_ECUDA, "spline set-up launch failed");
+    k_scan64<<<1, 1024, 0, s>>>(cnt, P, cnt + P + 1);
+    CKLAUNCH();
+    int64_t nodes = 0;
+    CK(cudaMemcpyAsync(&nodes, cnt + P + 1, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const size_t T = (size_t)std::max<int64_t>(nodes, 1);
+    double* phi = (double*)src.get(kSlotSplPhi, sizeof(double) * T);
+    double* G = (double*)src.get(kSlotSplG, sizeof(double) * 6 * T);
+    double* work = (double*)src.get(kSlotSplWork, sizeof(double) * 14 * T);
+    double* pc = (double*)src.get(kSlotSplPc, sizeof(double) * 4 * T);
+    float* gc = (float*)src.get(kSlotSplGc, sizeof(float) * 24 * T);
+    if (src.failed()) CK(src.err);
+    if (spline_build(pr.part, P, pr.streams, l2s, cnt, phi, G, work, pc, gc, s))
+      return fail(ctx, SCS_ECUDA, "spline build launch failed");
+    launch_main_spline(a, l2s, cnt, pc, gc, ctx->grid_spline, s);
+    CKLAUNCH();
   } else {
     launch_main_fp64(a, ctx->grid_fp64, s);
     CKLAUNCH();
@@ -441,9 +468,11 @@ int run_batch(scs_ctx* ctx, const Prepared& pr, int P, double* dstat, double* ds
 }
 
 int ensure_grids(scs_ctx* ctx) {
-  int bm = 0, bt = 0, bf = 0;
-  if (occupancy_mixed(0, &bm) || occupancy_mixed(1, &bt) || occupancy_fp64(&bf))
+  int bm = 0, bt = 0, bf = 0, bs = 0;
+  if (occupancy_mixed(0, &bm) || occupancy_mixed(1, &bt) || occupancy_fp64(&bf) ||
+      occupancy_spline(&bs))
     return fail(ctx, SCS_ECUDA, "occupancy query failed");
+  ctx->grid_spline = ctx->num_sms * (bs > 0 ? bs : 1);
   ctx->grid_mixed = ctx->num_sms * (bm > 0 ? bm : 1);
   ctx->grid_mixed_t = ctx->num_sms * (bt > 0 ? bt : 1);
   ctx->grid_fp64 = ctx->num_sms * (bf > 0 ? bf : 1);
@@ -457,7 +486,7 @@ extern "C" {
 int scs_create(scs_ctx** out, int device, int path) {
   if (!out) return SCS_EINVAL;
   *out = nullptr;
-  if (path != SCS_FP64 && path != SCS_MIXED) return SCS_EINVAL;
+  if (path != SCS_FP64 && path != SCS_MIXED && path != SCS_SPLINE) return SCS_EINVAL;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
     cudaGetLastError();
@@ -538,8 +567,17 @@ int scs_debug_set_model(scs_ctx* ctx, int waveform, int response) {
 
 int scs_set_path(scs_ctx* ctx, int path) {
   if (!ctx) return SCS_EINVAL;
-  if (path != SCS_FP64 && path != SCS_MIXED) return fail(ctx, SCS_EINVAL, "bad path %d", path);
+  if (path != SCS_FP64 && path != SCS_MIXED && path != SCS_SPLINE)
+    return fail(ctx, SCS_EINVAL, "bad path %d", path);
   ctx->path = path;
+  return SCS_OK;
+}
+
+int scs_set_spline(scs_ctx* ctx, int max_log2_spacing) {
+  if (!ctx) return SCS_EINVAL;
+  if (max_log2_spacing < 3 || max_log2_spacing > 14)
+    return fail(ctx, SCS_EINVAL, "spline spacing 2^%d outside 2^3 .. 2^14", max_log2_spacing);
+  ctx->spline_log2 = max_log2_spacing;
   return SCS_OK;
 }
 
@@ -1331,6 +1369,8 @@ int pso_iteration(scs_ctx* ctx, const std::vector<BatchPart>& parts, cudaStream_
 int pso_check(scs_ctx* ctx) {
   if (!ctx) return SCS_EINVAL;
   if (!ctx->pso.made) return fail(ctx, SCS_ENODATA, "no swarm (scs_pso_create)");
+  if (ctx->path == SCS_SPLINE)
+    return fail(ctx, SCS_EUNSUPPORTED, "the swarm runs on the FP64 or the mixed path");
   return bind(ctx);
 }
 

@@ -167,6 +167,21 @@ void launch_waveform_fp64(const Part* part, double f_first, double df, int K,
 int occupancy_mixed(int with_t, int* blocks_per_sm);
 int occupancy_fp64(int* blocks_per_sm);
 
+// The sparse-grid spline path (scs_spline.cu).  spline_prepare: node spacing
+// (log2, l2s[P]) and node count (count[P]) of every particle; after an
+// exclusive scan of count into node offsets, spline_build: node values and
+// spline coefficients (phi, G: 1 and 6 doubles per node; work: 14 doubles
+// per node; pc: 4 doubles, gc: 24 floats per node); launch_main_spline: the
+// evaluation.  The prepare/build calls return nonzero on a launch error.
+int spline_prepare(const Part* part, int P, const StreamDesc* streams, int max_log2, int* l2s,
+                   int64_t* count, cudaStream_t s);
+int spline_build(const Part* part, int P, const StreamDesc* streams, const int* l2s,
+                 const int64_t* off, double* phi, double* G, double* work, double* pc,
+                 float* gc, cudaStream_t s);
+void launch_main_spline(const EvalArgs& a, const int* l2s, const int64_t* off, const double* pc,
+                        const float* gc, int grid, cudaStream_t s);
+int occupancy_spline(int* blocks_per_sm);
+
 // chunk index of a grid bin within its stream
 __host__ __device__ inline int chunk_of(const StreamDesc& d, int k) { return k >> d.log2_chunk; }
 

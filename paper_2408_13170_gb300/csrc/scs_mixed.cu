@@ -12,8 +12,8 @@
 //   z += d~ conj(G) e^{+2 pi i Phi},  hh += w |G|^2   (Sec. II.B [a|b]_n)
 // Sums run in 32-bin FP32 blocks flushed into Kahan accumulators; when a
 // segment ends, the lane keeps its block sums at the cut (selects, no
-// branch) and the close -- x^2/hh (Sec. II.B, Upsilon_N) into a per-item
-// Kahan sum, written to the work unit's record in FP64 -- runs once at the
+// branch) and the close -- x^2/hh (Sec. II.B, Upsilon_N) added to the item's
+// FP64 sum, which goes to the work unit's record -- runs once at the
 // block's end for all lanes that had a cut (blocks are shortened so that no
 // lane has two).
 #include "scs_anchor.cuh"
@@ -46,6 +46,7 @@ struct Lane {
   int next_phase, next_resp, phase_k;
   int log2B, log2Br;
   bool act, head, fresh;
+  bool done;         // past its range end: G zeroed, contributes nothing
   const int* e;
   const Part* pp;
   Rec* rec;          // this (particle, chunk) unit's record
@@ -57,7 +58,8 @@ struct Lane {
   float4 yend;
   RespQuadT rqT;     // G_T (kernels with the third channel only)
   float2 yendT;
-  Kahan szr, szi, shh, ups;
+  Kahan szr, szi, shh;
+  double ups;        // the item's sum of x_n^2 / [h|h]_n, in FP64
   float bzr, bzi, bhh;
 };
 
@@ -92,7 +94,7 @@ __device__ __forceinline__ void finish_close(Lane& L, const ItemStream& a, doubl
     L.head = false;
   } else {
     float x2 = zr * zr + zi * zi;
-    if (hh > 0.f) kadd(L.ups, __fdividef(x2, hh));
+    if (hh > 0.f) L.ups += (double)__fdividef(x2, hh);
     if (a.seg_x) {
       a.seg_x[(int64_t)L.p * a.N + L.n_cur] = (double)sqrtf(x2) * zs;
       a.seg_hh[(int64_t)L.p * a.N + L.n_cur] = (double)hh * a.W0;
@@ -116,18 +118,19 @@ __device__ __forceinline__ void finish_close(Lane& L, const ItemStream& a, doubl
   }
 }
 
-// nb bins from k0, each lane masked to its own [kb, ke) (a single loop body:
-// a second, unmasked copy measured slower through its larger code).  The
-// data of bin k+1 is loaded while bin k is computed (the FP32 arrays carry a
-// zeroed tail for the last prefetch).
-template <bool kT>
+// nb bins from k0.  kMask: each lane masked to its own [kb, ke); without it
+// (blocks that every contributing lane covers in full, the common case away
+// from the supports' ends) the range test and the three selects per bin are
+// left out.  The data of bin k+1 is loaded while bin k is computed (the FP32
+// arrays carry a zeroed tail for the last prefetch).
+template <bool kT, bool kMask>
 __device__ __forceinline__ void run_block(Lane& L, const ItemStream& a, double zs, int k0,
                                           int nb) {
   float4 dn = __ldg(a.d32 + k0);
   float2 wn = __ldg(a.w32 + k0);
   float4 tn;
   if constexpr (kT) tn = __ldg(a.t32 + k0);
-  const unsigned span = L.act ? (unsigned)(L.ke - L.kb) : 0u;
+  const unsigned span = kMask && L.act ? (unsigned)(L.ke - L.kb) : 0u;
 #pragma unroll 2
   for (int i = 0; i < nb; ++i) {
     const int k = k0 + i;
@@ -140,7 +143,7 @@ __device__ __forceinline__ void run_block(Lane& L, const ItemStream& a, double z
       tv = tn;
       tn = __ldg(a.t32 + k + 1);
     }
-    const bool m = (unsigned)(k - L.kb) < span;
+    const bool m = kMask ? (unsigned)(k - L.kb) < span : true;
     // a segment ends before bin k: keep its block sums, restart them (at
     // most one end per lane and block); fma(b, 1, z) rounds as b + z
     const bool at = k == L.e_cut;
@@ -167,13 +170,14 @@ __device__ __forceinline__ void run_block(Lane& L, const ItemStream& a, double z
       hb += tv.z * (T0 * T0 + T1 * T1);
     }
     float zr = qr * cp - qi * sp, zi = qr * sp + qi * cp;
-    if (!m) {
+    if (kMask && !m) {
       zr = 0.f;
       zi = 0.f;
+      hb = 0.f;
     }
     L.bzr = fmaf(L.bzr, keep, zr);
     L.bzi = fmaf(L.bzi, keep, zi);
-    L.bhh = fmaf(L.bhh, keep, m ? hb : 0.f);
+    L.bhh = fmaf(L.bhh, keep, hb);
 #pragma unroll
     for (int r = 0; r < kOrd; ++r) L.d[r] += L.d[r + 1];
     L.jf += 1.f;
@@ -249,7 +253,9 @@ __global__ void __launch_bounds__(128, kT ? 3 : 4) k_main_mixed(EvalArgs a) {
     L.pzr = L.pzi = L.phh = 0.f;
     L.head = true;
     L.fresh = true;
-    L.szr = L.szi = L.shh = L.ups = Kahan{0.f, 0.f};
+    L.done = false;
+    L.szr = L.szi = L.shh = Kahan{0.f, 0.f};
+    L.ups = 0.0;
     L.bzr = L.bzi = L.bhh = 0.f;
 #pragma unroll
     for (int r = 0; r <= kOrd; ++r) L.d[r] = 0;
@@ -318,7 +324,11 @@ __global__ void __launch_bounds__(128, kT ? 3 : 4) k_main_mixed(EvalArgs a) {
         L.jf = 0.f;
         L.next_resp += 1 << L.log2Br;
       }
-      run_block<kT>(L, is, zs, k0, nb);
+      // a lane contributes in full to this block, or not at all (inactive,
+      // or past its range end with G zeroed)
+      const bool full = !L.act || L.done || (L.kb <= k0 && k0 + nb <= L.ke);
+      if (__all_sync(kFull, full)) run_block<kT, false>(L, is, zs, k0, nb);
+      else run_block<kT, true>(L, is, zs, k0, nb);
       L.pend = (unsigned)(L.e_cut - k0) < (unsigned)nb;   // the cut fell in this block
       if (__any_sync(kFull, L.pend)) {
         if (L.pend) finish_close(L, is, zs);
@@ -332,6 +342,15 @@ __global__ void __launch_bounds__(128, kT ? 3 : 4) k_main_mixed(EvalArgs a) {
         kadd(L.szi, L.bzi);
         kadd(L.shh, L.bhh);
         L.bzr = L.bzi = L.bhh = 0.f;
+      }
+      if (L.act && !L.done && kend >= L.ke) {   // the lane's range has ended
+        L.done = true;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) L.rq.g0[q] = L.rq.g1[q] = L.rq.g2[q] = 0.f;
+        if constexpr (kT) {
+#pragma unroll
+          for (int q = 0; q < 2; ++q) L.rqT.g0[q] = L.rqT.g1[q] = L.rqT.g2[q] = 0.f;
+        }
       }
     }
     if (L.act) {
@@ -349,7 +368,7 @@ __global__ void __launch_bounds__(128, kT ? 3 : 4) k_main_mixed(EvalArgs a) {
         L.rec->zi_t = zi * zs;
         L.rec->hh_t = hh * is.W0;
       }
-      L.rec->ups = (double)L.ups.s - (double)L.ups.c;
+      L.rec->ups = L.ups;
     }
   }
 }

@@ -17,7 +17,7 @@ from . import build as _build
 
 SCS_OK, SCS_EINVAL, SCS_ENOMEM, SCS_ECUDA, SCS_ENODATA, SCS_ETIMEOUT, SCS_EUNSUPPORTED = (
     0, -1, -2, -3, -4, -5, -6)
-SCS_FP64, SCS_MIXED = 0, 1
+SCS_FP64, SCS_MIXED, SCS_SPLINE = 0, 1, 2
 SCS_EQUAL_WIDTH, SCS_EQUAL_SNR2 = 0, 1
 # test-only models (scs_debug_set_model)
 SCS_MODEL_TF2, SCS_MODEL_NEWTONIAN, SCS_MODEL_LINEAR_CHIRP = 0, 1, 2
@@ -52,6 +52,8 @@ def lib():
         L.scs_set_path.restype = I
         L.scs_debug_set_model.argtypes = [P, I, I]
         L.scs_debug_set_model.restype = I
+        L.scs_set_spline.argtypes = [P, I]
+        L.scs_set_spline.restype = I
         L.scs_set_data.argtypes = [P, I, P, P, P, P, D, D, I64, D]
         L.scs_set_data.restype = I
         L.scs_set_data_aet.argtypes = [P, I, P, P, P, P, P, P, D, D, I64, D]
@@ -164,6 +166,11 @@ def scs_last_error(ctx) -> str:
 
 def scs_set_path(ctx, path: int):
     _check(ctx, lib().scs_set_path(ctx, path))
+
+
+def scs_set_spline(ctx, max_log2_spacing: int):
+    """Largest node spacing (log2 bins) of the SCS_SPLINE path."""
+    _check(ctx, lib().scs_set_spline(ctx, max_log2_spacing))
 
 
 def scs_debug_set_model(ctx, waveform: int, response: int):
