@@ -9,6 +9,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/scstat.h"
 #include "scs_internal.cuh"
 #include "scs_setup.cuh"
@@ -16,6 +18,17 @@
 using namespace scs;
 
 namespace {
+
+// NVTX range over an entry point or a stage (host side: it brackets the
+// launches a call enqueues).  NVTX v3 is header-only and does nothing unless
+// a profiler injects itself.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define SCS_TRACE(name) NvtxRange scs_nvtx_range_(name)
 
 struct DevBuf {
   void* ptr = nullptr;
@@ -346,6 +359,7 @@ int prepare_batch(scs_ctx* ctx, const std::vector<BatchPart>& parts, const doubl
                        cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(diff, 0, sizeof(int) * (nct + 2), s));
   CK(cudaMemsetAsync(fill, 0, sizeof(int) * (nct + 1), s));
+  SCS_TRACE("setup+worklist+edges");
   k_setup<<<(P + 31) / 32, kSetupThreads, 0, s>>>(dparams, P, out.streams, ns, want_stride ? 1 : 0,
                                                   ctx->model,
                                           out.part, out.crange, out.nrec, diff);
@@ -388,6 +402,7 @@ int run_batch(scs_ctx* ctx, const Prepared& pr, int P, double* dstat, double* ds
     if (src.ctx) CK(src.err);
     return SCS_ENOMEM;
   }
+  SCS_TRACE("main+fixup");
   CK(cudaMemsetAsync(counter, 0, sizeof(int) * 2, s));
   EvalArgs a;
   a.streams = pr.streams;
@@ -712,12 +727,14 @@ extern "C" {
 
 int scs_set_data(scs_ctx* ctx, int sid, const double* A, const double* E, const double* S_A,
                  const double* S_E, double f_first, double df, int64_t K, double T_obs) {
+  SCS_TRACE("scs_set_data");
   return set_data_impl(ctx, sid, A, E, nullptr, S_A, S_E, nullptr, f_first, df, K, T_obs);
 }
 
 int scs_set_data_aet(scs_ctx* ctx, int sid, const double* A, const double* E, const double* T,
                      const double* S_A, const double* S_E, const double* S_T, double f_first,
                      double df, int64_t K, double T_obs) {
+  SCS_TRACE("scs_set_data_aet");
   if (ctx && (!T || !S_T)) return fail(ctx, SCS_EINVAL, "null T-channel pointer");
   return set_data_impl(ctx, sid, A, E, T, S_A, S_E, S_T, f_first, df, K, T_obs);
 }
@@ -743,6 +760,7 @@ int scs_set_segments(scs_ctx* ctx, int sid, int N, int mode) {
 
 int scs_eval_stat(scs_ctx* ctx, int sid, const double* params, int64_t P, double* stat,
                   double* seg_x, double* seg_hh, void* cuda_stream) {
+  SCS_TRACE("scs_eval_stat");
   if (!ctx) return SCS_EINVAL;
   if (!params || !stat) return fail(ctx, SCS_EINVAL, "null params or stat");
   if (P < 1 || P > (1 << 24)) return fail(ctx, SCS_EINVAL, "P = %lld out of range", (long long)P);
@@ -799,6 +817,7 @@ int scs_eval_stat(scs_ctx* ctx, int sid, const double* params, int64_t P, double
 
 int scs_batch_eval(scs_ctx* ctx, const int* stream_ids, const int64_t* P_offsets, int n_items,
                    const double* params, double* stat, void* cuda_stream) {
+  SCS_TRACE("scs_batch_eval");
   if (!ctx) return SCS_EINVAL;
   if (!stream_ids || !P_offsets || !params || !stat || n_items < 1 || n_items > 1024)
     return fail(ctx, SCS_EINVAL, "bad batch arguments");
@@ -844,6 +863,7 @@ int scs_batch_eval(scs_ctx* ctx, const int* stream_ids, const int64_t* P_offsets
 
 int scs_eval_loglike(scs_ctx* ctx, int sid, const double* params, int64_t P, const double* amp,
                      double* loglike, double* overlap, double* hh, void* cuda_stream) {
+  SCS_TRACE("scs_eval_loglike");
   if (!ctx) return SCS_EINVAL;
   if (!params || !loglike) return fail(ctx, SCS_EINVAL, "null params or loglike");
   if (P < 1 || P > (1 << 24)) return fail(ctx, SCS_EINVAL, "P = %lld out of range", (long long)P);
@@ -921,6 +941,7 @@ int scs_set_tile(scs_ctx* ctx, int sid, int log2_chunk) {
 
 int scs_autotune(scs_ctx* ctx, int sid, const double* params, int64_t P, int* log2_chunk,
                  double* ms, void* cuda_stream) {
+  SCS_TRACE("scs_autotune");
   if (!ctx) return SCS_EINVAL;
   if (!params || P < 1 || P > (1 << 24)) return fail(ctx, SCS_EINVAL, "bad particles");
   int rc = bind(ctx);
@@ -993,6 +1014,7 @@ int scs_autotune(scs_ctx* ctx, int sid, const double* params, int64_t P, int* lo
 
 int scs_support(scs_ctx* ctx, int sid, const double* params, int64_t P, int64_t* k_lo,
                 int64_t* k_hi, int32_t* log2_stride, void* cuda_stream) {
+  SCS_TRACE("scs_support");
   if (!ctx) return SCS_EINVAL;
   if (!params || !k_lo || !k_hi || P < 1 || P > (1 << 24))
     return fail(ctx, SCS_EINVAL, "bad arguments");
@@ -1027,6 +1049,7 @@ int scs_support(scs_ctx* ctx, int sid, const double* params, int64_t P, int64_t*
 
 int scs_segment_edges(scs_ctx* ctx, int sid, const double* params, int64_t P, int64_t* out,
                       void* cuda_stream) {
+  SCS_TRACE("scs_segment_edges");
   if (!ctx) return SCS_EINVAL;
   if (!params || !out || P < 1 || P > (1 << 24)) return fail(ctx, SCS_EINVAL, "bad arguments");
   int rc = bind(ctx);
@@ -1084,6 +1107,7 @@ static int template_to(scs_ctx* ctx, DataStream& ds, const double* theta, cudaSt
 
 int scs_waveform(scs_ctx* ctx, int sid, const double* theta, double* hA, double* hE,
                  void* cuda_stream) {
+  SCS_TRACE("scs_waveform");
   if (!ctx) return SCS_EINVAL;
   if (!theta || !hA || !hE) return fail(ctx, SCS_EINVAL, "null pointer");
   int rc = bind(ctx);
@@ -1102,6 +1126,7 @@ int scs_waveform(scs_ctx* ctx, int sid, const double* theta, double* hA, double*
 
 int scs_waveform_aet(scs_ctx* ctx, int sid, const double* theta, double* hA, double* hE,
                      double* hT, void* cuda_stream) {
+  SCS_TRACE("scs_waveform_aet");
   if (!ctx) return SCS_EINVAL;
   if (!theta || !hA || !hE || !hT) return fail(ctx, SCS_EINVAL, "null pointer");
   int rc = bind(ctx);
@@ -1120,6 +1145,7 @@ int scs_waveform_aet(scs_ctx* ctx, int sid, const double* theta, double* hA, dou
 }
 
 int scs_inject(scs_ctx* ctx, int sid, const double* theta, double snr, double* hh_out) {
+  SCS_TRACE("scs_inject");
   if (!ctx) return SCS_EINVAL;
   if (!theta || !std::isfinite(snr)) return fail(ctx, SCS_EINVAL, "bad arguments");
   int rc = bind(ctx);
@@ -1221,6 +1247,7 @@ extern "C" {
 
 int scs_eval_stat_noalloc(scs_ctx* ctx, int sid, const double* params, int64_t P,
                           double* stat, void* cuda_stream) {
+  SCS_TRACE("scs_eval_stat_noalloc");
   if (!ctx) return SCS_EINVAL;
   if (!params || !stat) return fail(ctx, SCS_EINVAL, "null params or stat");
   if (P < 1 || P > (1 << 24)) return fail(ctx, SCS_EINVAL, "P = %lld out of range", (long long)P);
@@ -1381,6 +1408,7 @@ extern "C" {
 int scs_pso_create(scs_ctx* ctx, int n_swarms, const int* stream_ids,
                    const int64_t* swarm_offsets, const double* prior_lo,
                    const double* prior_hi, uint64_t seed, void* cuda_stream) {
+  SCS_TRACE("scs_pso_create");
   if (!ctx) return SCS_EINVAL;
   if (n_swarms < 1 || n_swarms > 1024 || !stream_ids || !swarm_offsets || !prior_lo ||
       !prior_hi)
@@ -1484,6 +1512,7 @@ int scs_pso_set_hyper(scs_ctx* ctx, int swarm, double Omega, double PhiP, double
 }
 
 int scs_pso_run(scs_ctx* ctx, int iters, int use_graph, void* cuda_stream) {
+  SCS_TRACE("scs_pso_run");
   int rc = pso_check(ctx);
   if (rc) return rc;
   if (iters < 0 || iters > 100000) return fail(ctx, SCS_EINVAL, "iters = %d out of range", iters);
@@ -1557,6 +1586,7 @@ int scs_pso_run(scs_ctx* ctx, int iters, int use_graph, void* cuda_stream) {
 int scs_pso_get(scs_ctx* ctx, double* pos, double* vel, double* best_pos, double* best_val,
                 double* swarm_pos, double* swarm_val, double* stat, int64_t* iter,
                 void* cuda_stream) {
+  SCS_TRACE("scs_pso_get");
   int rc = pso_check(ctx);
   if (rc) return rc;
   auto& q = ctx->pso;
@@ -1577,6 +1607,7 @@ int scs_pso_get(scs_ctx* ctx, double* pos, double* vel, double* best_pos, double
 int scs_pso_set(scs_ctx* ctx, const double* pos, const double* vel, const double* best_pos,
                 const double* best_val, const double* swarm_pos, const double* swarm_val,
                 int64_t iter, void* cuda_stream) {
+  SCS_TRACE("scs_pso_set");
   int rc = pso_check(ctx);
   if (rc) return rc;
   if (iter < 0 || iter > 0xffffffffLL) return fail(ctx, SCS_EINVAL, "iteration out of range");
@@ -1821,6 +1852,7 @@ extern "C" {
 int scs_kmeans(scs_ctx* ctx, const double* pos, int64_t P, const double* prior_lo,
                const double* prior_hi, int k, int iters, int* labels, double* centroids,
                void* cuda_stream) {
+  SCS_TRACE("scs_kmeans");
   if (!ctx) return SCS_EINVAL;
   if (!pos || !prior_lo || !prior_hi || !labels || P < 1 || P > (1 << 24) || k < 1 || k > P ||
       k > 1024 || iters < 0 || iters > 1000)
@@ -1850,6 +1882,7 @@ int scs_kmeans(scs_ctx* ctx, const double* pos, int64_t P, const double* prior_l
 }
 
 int scs_pso_regroup(scs_ctx* ctx, int n_clusters, int iters, void* cuda_stream) {
+  SCS_TRACE("scs_pso_regroup");
   int rc = pso_check(ctx);
   if (rc) return rc;
   if (n_clusters < 1 || n_clusters > 1024 || iters < 0 || iters > 1000)
@@ -1949,6 +1982,7 @@ int scs_pso_regroup(scs_ctx* ctx, int n_clusters, int iters, void* cuda_stream) 
 int scs_pso_search(scs_ctx* ctx, const int* ladder, int n_rungs, const double* hyper_rows,
                    int n_clusters, int chunk_iters, int max_iters, int64_t* iters_out,
                    void* cuda_stream) {
+  SCS_TRACE("scs_pso_search");
   int rc = pso_check(ctx);
   if (rc) return rc;
   if (!ladder || !hyper_rows || n_rungs < 1 || n_rungs > 64 || chunk_iters < 1 ||
