@@ -69,7 +69,7 @@ LAUNCHES_PER_STEP = 9   # setup, scan, chunk table, fill, sort, edges, main, 2 x
 # DRAM bytes (read + write) of one two-channel k_main_mixed launch on the
 # one-year workload at full size, per work tile (log2 bins), from an ncu
 # capture of the kernel as built now; emptied whenever the kernel changes.
-MAIN_TRAFFIC_BYTES: dict[int, float] = {}
+MAIN_TRAFFIC_BYTES: dict[int, float] = {11: 73.881856e6 + 24.901888e6}
 
 
 def parse(argv=None):

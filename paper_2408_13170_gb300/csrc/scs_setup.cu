@@ -53,7 +53,164 @@ __device__ bool phase_check(const Part& p, int B, int s, int t, double f_first, 
   return fabs(d) <= kTolPhase;
 }
 
-// Response: the quadratic through the exact FP64 nodes at 0, Br/2, Br of the
+// Per-particle constants of the double-float anchor power.
+struct PowDf {
+  dfl k[3], up[3], vp[3];
+  dfl A1, A2;   // ap / 48 and 2 ax / 48 (48 = (4 sqrt3)^2, see below)
+};
+
+__device__ inline void pow_consts(const Part& p, PowDf& c) {
+  c.k[0] = df_split(p.kx);
+  c.k[1] = df_split(p.ky);
+  c.k[2] = df_split(p.kz);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    c.up[i] = df_split(p.up[i]);
+    c.vp[i] = df_split(p.vp[i]);
+  }
+  c.A1 = df_split(p.ap * (1.0 / 48.0));
+  c.A2 = df_split(p.ax * (1.0 / 24.0));
+}
+
+// sin(x)/x given sin(x) (double-float)
+__device__ __forceinline__ dfl df_sinc_of(dfl x, dfl sx) {
+  return fabsf(x.hi) < 0.3f ? df_sinc_small(x) : df_div(sx, x);
+}
+
+// |R_A|^2, |R_E|^2 and |R_T|^2 of the residual response (the model of
+// response_residual) at a = pi f L and orbit angle alpha, in double-float.
+// Craft offsets from the guiding centre are d_i = (L / (4 sqrt3)) g_i with
+//   g_i = (cos(2 alpha - b_i) - 3 cos b_i, sin(2 alpha - b_i) - 3 sin b_i,
+//          -2 sqrt3 cos(alpha - b_i)),  b_i = 2 pi i / 3,  sum_i g_i = 0,
+// so arm (s, r) has n = (g_r - g_s)/(4 sqrt3), link phase factors
+// e_i = e^{i ph_i}, ph_i = -(a/(4 sqrt3)) k.g_i with e_0 e_1 e_2 = 1, and
+// n.P.n = (ap/48)(dmu^2 - dnu^2) - i (2 ax/48) dmu dnu with dmu, dnu the
+// differences of u'.g and v'.g.  With F = sinc(a - b), K = sinc(a + b),
+// b = ph_s - ph_r and base = conj(e_k) n.P.n (k the third craft), the links
+// are G_{s->r} = -i a F base, G_{r->s} = -i a K base, and with
+// U = base (K + D F), V = base (F + D K), D = e^{-2ia}:
+//   X = -i a W (U_02 - U_01), Y = -i a W (V_01 - U_12), Z = -i a W (V_12 - V_02),
+// W = 1 - D^2, |a W|^2 = 16 (a sin a cos a)^2.
+__device__ inline void response_xyz_df(const PowDf& c, dfl a, dfl al, cdfl& X, cdfl& Y, cdfl& Z,
+                                       dfl& s_a, dfl& c_a) {
+  dfl sa, ca;
+  df_sincos(al, &sa, &ca);
+  const dfl c2a = ca * ca - sa * sa;
+  const dfl s2a = df_scale2(ca * sa, 2.f);
+  constexpr dfl h3 = df_const(0.86602540378443865);    // sqrt3 / 2
+  constexpr dfl k33 = df_const(2.5980762113533160);    // 3 sqrt3 / 2
+  constexpr dfl m2s3 = df_const(-3.4641016151377546);  // -2 sqrt3
+  const dfl P = s2a * h3, Q = c2a * h3, R = sa * h3;
+  const dfl hc2 = df_scale2(c2a, 0.5f), hs2 = df_scale2(s2a, 0.5f), hca = df_scale2(ca, 0.5f);
+  dfl g[2][3];
+  g[0][0] = c2a - df_f(3.f);
+  g[0][1] = s2a;
+  g[0][2] = ca * m2s3;
+  g[1][0] = (P - hc2) + df_f(1.5f);
+  g[1][1] = -(hs2 + Q) - k33;
+  g[1][2] = (R - hca) * m2s3;
+  dfl kap[3], mu[3], nu[3];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    kap[i] = c.k[0] * g[i][0] + c.k[1] * g[i][1] + c.k[2] * g[i][2];
+    mu[i] = c.up[0] * g[i][0] + c.up[1] * g[i][1] + c.up[2] * g[i][2];
+    nu[i] = c.vp[0] * g[i][0] + c.vp[1] * g[i][1] + c.vp[2] * g[i][2];
+  }
+  kap[2] = -(kap[0] + kap[1]);
+  mu[2] = -(mu[0] + mu[1]);
+  nu[2] = -(nu[0] + nu[1]);
+  constexpr dfl i4s3 = df_const(0.14433756729740644);   // 1 / (4 sqrt3)
+  const dfl ah = a * i4s3;
+  dfl ph[3];
+  ph[0] = -(ah * kap[0]);
+  ph[1] = -(ah * kap[1]);
+  ph[2] = -(ph[0] + ph[1]);
+  cdfl e[3];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) df_sincos(ph[i], &e[i].im, &e[i].re);
+  e[2] = cdf_conj(e[0] * e[1]);
+  df_sincos(a, &s_a, &c_a);
+  const cdfl D{c_a * c_a - s_a * s_a, -df_scale2(s_a * c_a, 2.f)};
+  // arms (s, r) with third craft k: (0,1;2), (0,2;1), (1,2;0)
+  cdfl U[3], V[3];
+  const int as[3] = {0, 0, 1}, ar[3] = {1, 2, 2}, ak[3] = {2, 1, 0};
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    const int s = as[m], r = ar[m], k = ak[m];
+    const dfl dmu = mu[r] - mu[s], dnu = nu[r] - nu[s];
+    const cdfl nPn{c.A1 * ((dmu - dnu) * (dmu + dnu)), -(c.A2 * (dmu * dnu))};
+    const cdfl base = cdf_conj(e[k]) * nPn;
+    const cdfl eb = e[s] * cdf_conj(e[r]);    // e^{i b}
+    const dfl b = ph[s] - ph[r];
+    const dfl sc = s_a * eb.re, cs = c_a * eb.im;
+    const dfl F = df_sinc_of(a - b, sc - cs), K = df_sinc_of(a + b, sc + cs);
+    U[m] = base * cdfl{K + F * D.re, F * D.im};
+    V[m] = base * cdfl{F + K * D.re, K * D.im};
+  }
+  X = U[1] - U[0];
+  Y = V[0] - U[2];
+  Z = V[2] - V[1];
+}
+
+__device__ inline void response_power_df(const PowDf& c, dfl a, dfl al, dfl& qA, dfl& qE,
+                                         dfl& qT) {
+  cdfl X, Y, Z;
+  dfl s_a, c_a;
+  response_xyz_df(c, a, al, X, Y, Z, s_a, c_a);
+  const dfl w = (a * s_a) * c_a;
+  const dfl fac = df_scale2(w * w, 16.f);
+  constexpr dfl i6 = df_const(1.0 / 6.0), i3 = df_const(1.0 / 3.0);
+  qA = df_scale2(fac * cdf_norm2(Z - X), 0.5f);
+  const cdfl Y2{df_scale2(Y.re, 2.f), df_scale2(Y.im, 2.f)};
+  qE = (fac * cdf_norm2((X - Y2) + Z)) * i6;
+  qT = (fac * cdf_norm2((X + Y) + Z)) * i3;
+}
+
+// The complex residual response R_A, R_E, R_T (the values of
+// response_residual, the common factor included): with the link factor
+// -i a e^{-ia} and W = 1 - e^{-4ia}, X = -i a e^{-ia} W X' etc.
+__device__ inline void response_complex_df(const PowDf& c, dfl a, dfl al, cdfl& RA, cdfl& RE,
+                                           cdfl& RT) {
+  cdfl X, Y, Z;
+  dfl s_a, c_a;
+  response_xyz_df(c, a, al, X, Y, Z, s_a, c_a);
+  const dfl c2 = c_a * c_a - s_a * s_a, s2 = df_scale2(s_a * c_a, 2.f);
+  const dfl c4 = c2 * c2 - s2 * s2, s4 = df_scale2(s2 * c2, 2.f);
+  const cdfl W{df_f(1.f) - c4, s4};                        // 1 - e^{-4ia}
+  const cdfl ea{c_a, -s_a};                                // e^{-ia}
+  const cdfl Kf = cdfl{df_f(0.f), -a} * (ea * W);          // -i a e^{-ia} W
+  constexpr dfl is2 = df_const(0.70710678118654752), is6 = df_const(0.40824829046386302),
+                is3 = df_const(0.57735026918962576);
+  const cdfl A = Z - X, E = (X - cdfl{df_scale2(Y.re, 2.f), df_scale2(Y.im, 2.f)}) + Z,
+             T = (X + Y) + Z;
+  RA = Kf * cdfl{A.re * is2, A.im * is2};
+  RE = Kf * cdfl{E.re * is6, E.im * is6};
+  RT = Kf * cdfl{T.re * is3, T.im * is3};
+}
+
+// G_alpha at bin offset x from k_a (out[0..3] = G_A, G_E re/im, out[4..5] =
+// G_T): f, t(f) and the orbit angle in FP64, the response in double-float
+// (relative error ~1e-13; the stride checks compare against 3e-7).
+__device__ void g_df(const Part& p, const PowDf& pc, double fa, double df, double x,
+                     double out[6]) {
+  const double f = fma(x, df, fa);
+  double u = (double)rcbrtf((float)f);
+#pragma unroll
+  for (int it = 0; it < 2; ++it) u = fma(u * fma(-f, u * u * u, 1.0), 1.0 / 3.0, u);
+  const double t = time_of_freq_fu(p, f, u);
+  cdfl RA{df_f(1.f), df_f(0.f)}, RE{df_f(0.f), df_f(0.f)}, RT{df_f(0.f), df_f(0.f)};
+  if (!p.ident) response_complex_df(pc, df_split((kPi * kArm) * f), df_split(orbit_angle(t)), RA, RE, RT);
+  const double amp = p.model == kModelLinearChirp ? 1.0 : u * u * u * sqrt(u);
+  const dfl am = df_split(amp);
+  const cdfl R[3] = {RA, RE, RT};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    out[2 * c] = df_join(am * R[c].re);
+    out[2 * c + 1] = df_join(am * R[c].im);
+  }
+}
+
+// Response: the quadratic through the exact nodes at 0, Br/2, Br of the
 // span against the exact G at the offset (G_A, G_E, and G_T if withT).
 __device__ bool resp_check(const Part& p, int Br, int s, int t, double f_first, double df,
                            bool withT) {
@@ -63,14 +220,16 @@ __device__ bool resp_check(const Part& p, int Br, int s, int t, double f_first, 
   if (jhi < jlo) return true;
   const double h = 0.5 * (double)Br;
   double fa = f_first + (double)ka * df;
+  PowDf pc;
+  pow_consts(p, pc);
   double y0[6], y1[6], y2[6];
-  g_exact64(p, fa, df, 0.0, y0);
-  g_exact64(p, fa, df, h, y1);
-  g_exact64(p, fa, df, 2.0 * h, y2);
+  g_df(p, pc, fa, df, 0.0, y0);
+  g_df(p, pc, fa, df, h, y1);
+  g_df(p, pc, fa, df, 2.0 * h, y2);
   const int jt = t == 0 ? Br / 4 : (t == 1 ? (3 * Br) / 4 : Br - 1);
   double x = (double)min(max(jt, jlo), jhi);
   double g[6];
-  g_exact64(p, fa, df, x, g);
+  g_df(p, pc, fa, df, x, g);
   double l0 = (x - h) * (x - 2.0 * h) / (2.0 * h * h);
   double l1 = -x * (x - 2.0 * h) / (h * h);
   double l2 = x * (x - h) / (2.0 * h * h);
@@ -388,111 +547,6 @@ __global__ void k_sort_chunks(const Part* part, const int* cnt, const int* list_
 // interpolation (~1e-15 of C per operation on the offset).
 constexpr float kEpsPowerDf = 5e-13f;
 constexpr float kEpsInterp = 1e-13f;
-
-// Per-particle constants of the double-float anchor power.
-struct PowDf {
-  dfl k[3], up[3], vp[3];
-  dfl A1, A2;   // ap / 48 and 2 ax / 48 (48 = (4 sqrt3)^2, see below)
-};
-
-__device__ inline void pow_consts(const Part& p, PowDf& c) {
-  c.k[0] = df_from(p.kx);
-  c.k[1] = df_from(p.ky);
-  c.k[2] = df_from(p.kz);
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    c.up[i] = df_from(p.up[i]);
-    c.vp[i] = df_from(p.vp[i]);
-  }
-  c.A1 = df_from(p.ap * (1.0 / 48.0));
-  c.A2 = df_from(p.ax * (1.0 / 24.0));
-}
-
-// sin(x)/x given sin(x) (double-float)
-__device__ __forceinline__ dfl df_sinc_of(dfl x, dfl sx) {
-  return fabsf(x.hi) < 0.3f ? df_sinc_small(x) : df_div(sx, x);
-}
-
-// |R_A|^2, |R_E|^2 and |R_T|^2 of the residual response (the model of
-// response_residual) at a = pi f L and orbit angle alpha, in double-float.
-// Craft offsets from the guiding centre are d_i = (L / (4 sqrt3)) g_i with
-//   g_i = (cos(2 alpha - b_i) - 3 cos b_i, sin(2 alpha - b_i) - 3 sin b_i,
-//          -2 sqrt3 cos(alpha - b_i)),  b_i = 2 pi i / 3,  sum_i g_i = 0,
-// so arm (s, r) has n = (g_r - g_s)/(4 sqrt3), link phase factors
-// e_i = e^{i ph_i}, ph_i = -(a/(4 sqrt3)) k.g_i with e_0 e_1 e_2 = 1, and
-// n.P.n = (ap/48)(dmu^2 - dnu^2) - i (2 ax/48) dmu dnu with dmu, dnu the
-// differences of u'.g and v'.g.  With F = sinc(a - b), K = sinc(a + b),
-// b = ph_s - ph_r and base = conj(e_k) n.P.n (k the third craft), the links
-// are G_{s->r} = -i a F base, G_{r->s} = -i a K base, and with
-// U = base (K + D F), V = base (F + D K), D = e^{-2ia}:
-//   X = -i a W (U_02 - U_01), Y = -i a W (V_01 - U_12), Z = -i a W (V_12 - V_02),
-// W = 1 - D^2, |a W|^2 = 16 (a sin a cos a)^2.
-__device__ inline void response_power_df(const PowDf& c, dfl a, dfl al, dfl& qA, dfl& qE,
-                                         dfl& qT) {
-  dfl sa, ca;
-  df_sincos(al, &sa, &ca);
-  const dfl c2a = ca * ca - sa * sa;
-  const dfl s2a = df_scale2(ca * sa, 2.f);
-  constexpr dfl h3 = df_const(0.86602540378443865);    // sqrt3 / 2
-  constexpr dfl k33 = df_const(2.5980762113533160);    // 3 sqrt3 / 2
-  constexpr dfl m2s3 = df_const(-3.4641016151377546);  // -2 sqrt3
-  const dfl P = s2a * h3, Q = c2a * h3, R = sa * h3;
-  const dfl hc2 = df_scale2(c2a, 0.5f), hs2 = df_scale2(s2a, 0.5f), hca = df_scale2(ca, 0.5f);
-  dfl g[2][3];
-  g[0][0] = c2a - df_f(3.f);
-  g[0][1] = s2a;
-  g[0][2] = ca * m2s3;
-  g[1][0] = (P - hc2) + df_f(1.5f);
-  g[1][1] = -(hs2 + Q) - k33;
-  g[1][2] = (R - hca) * m2s3;
-  dfl kap[3], mu[3], nu[3];
-#pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    kap[i] = c.k[0] * g[i][0] + c.k[1] * g[i][1] + c.k[2] * g[i][2];
-    mu[i] = c.up[0] * g[i][0] + c.up[1] * g[i][1] + c.up[2] * g[i][2];
-    nu[i] = c.vp[0] * g[i][0] + c.vp[1] * g[i][1] + c.vp[2] * g[i][2];
-  }
-  kap[2] = -(kap[0] + kap[1]);
-  mu[2] = -(mu[0] + mu[1]);
-  nu[2] = -(nu[0] + nu[1]);
-  constexpr dfl i4s3 = df_const(0.14433756729740644);   // 1 / (4 sqrt3)
-  const dfl ah = a * i4s3;
-  dfl ph[3];
-  ph[0] = -(ah * kap[0]);
-  ph[1] = -(ah * kap[1]);
-  ph[2] = -(ph[0] + ph[1]);
-  cdfl e[3];
-#pragma unroll
-  for (int i = 0; i < 2; ++i) df_sincos(ph[i], &e[i].im, &e[i].re);
-  e[2] = cdf_conj(e[0] * e[1]);
-  dfl s_a, c_a;
-  df_sincos(a, &s_a, &c_a);
-  const cdfl D{c_a * c_a - s_a * s_a, -df_scale2(s_a * c_a, 2.f)};
-  // arms (s, r) with third craft k: (0,1;2), (0,2;1), (1,2;0)
-  cdfl U[3], V[3];
-  const int as[3] = {0, 0, 1}, ar[3] = {1, 2, 2}, ak[3] = {2, 1, 0};
-#pragma unroll
-  for (int m = 0; m < 3; ++m) {
-    const int s = as[m], r = ar[m], k = ak[m];
-    const dfl dmu = mu[r] - mu[s], dnu = nu[r] - nu[s];
-    const cdfl nPn{c.A1 * ((dmu - dnu) * (dmu + dnu)), -(c.A2 * (dmu * dnu))};
-    const cdfl base = cdf_conj(e[k]) * nPn;
-    const cdfl eb = e[s] * cdf_conj(e[r]);    // e^{i b}
-    const dfl b = ph[s] - ph[r];
-    const dfl sc = s_a * eb.re, cs = c_a * eb.im;
-    const dfl F = df_sinc_of(a - b, sc - cs), K = df_sinc_of(a + b, sc + cs);
-    U[m] = base * cdfl{K + F * D.re, F * D.im};
-    V[m] = base * cdfl{F + K * D.re, K * D.im};
-  }
-  const cdfl X = U[1] - U[0], Y = V[0] - U[2], Z = V[2] - V[1];
-  const dfl w = (a * s_a) * c_a;
-  const dfl fac = df_scale2(w * w, 16.f);
-  constexpr dfl i6 = df_const(1.0 / 6.0), i3 = df_const(1.0 / 3.0);
-  qA = df_scale2(fac * cdf_norm2(Z - X), 0.5f);
-  const cdfl Y2{df_scale2(Y.re, 2.f), df_scale2(Y.im, 2.f)};
-  qE = (fac * cdf_norm2((X - Y2) + Z)) * i6;
-  qT = (fac * cdf_norm2((X + Y) + Z)) * i3;
-}
 
 // Cumulative anchor power and the edges of one particle (one block of
 // kBT threads) from its anchor powers H[0 .. nanch) (FP64, any common

@@ -7,9 +7,9 @@
 //
 // Per particle the nodes are k_lo, k_lo + S, ..., k_hi (the last interval
 // may be shorter), S a power of two <= 2^max_log2S (default 1024 bins),
-// halved while the spline's phase error bound (5/384) S^4 |d^4 Phi / dk^4| exceeds
-// kTolSplinePhase turns, so that the path meets the same accuracy as the
-// others.  Splines: not-a-knot end conditions (slopes from a tridiagonal
+// halved while the spline's phase error bound (5/384) S^4 |d^4 Phi / dk^4|
+// exceeds kTolSplinePhase turns and until the support has at least four
+// nodes, so that the path meets the same accuracy as the others.  Splines: not-a-knot end conditions (slopes from a tridiagonal
 // system, Thomas algorithm, FP64), one per quantity: the unwrapped total
 // phase Phi = Psi/(2 pi) + f k.p0(t(f)) in turns (FP64 coefficients) and
 // the real and imaginary parts of G_A, G_E (and G_T) (FP32 coefficients).
@@ -47,11 +47,16 @@ __device__ int spline_log2S(const Part& p, double f_first, double df, int max_lo
   const double w = kOmega * fabs(T1);
   const double phi4 = fabs(d4) + fhi * p.Rcb * w * w * w * w;
   int l = max_log2;
-  while (l > 3) {
+  while (l > 0) {
     const double S = (double)(1 << l);
     if (2.0 * (5.0 / 384.0) * S * S * S * S * phi4 <= kTolSplinePhase) break;
     --l;
   }
+  // at least four nodes (a cubic; with three or two the spline degrades to a
+  // parabola or a line), unless the support has fewer than four bins (then
+  // every bin is a node)
+  const int span = p.k_hi - p.k_lo;
+  while (l > 0 && (span >> l) < 3) --l;
   return l;
 }
 

@@ -140,3 +140,19 @@ def test_spline_path_refuses_swarm_and_noalloc(scstat, month):
         with pytest.raises(scstat.ScsError) as e:
             scstat.scs_eval_stat_noalloc(ctx.h, 0, dev, len(th), out)
         assert e.value.code == scstat.SCS_EUNSUPPORTED
+
+
+def test_spline_path_short_supports_near_band_end(scstat):
+    """The C1 band (0.015-0.03 Hz, 35 days) with particles up to the band's
+    end: supports of a few bins to a few thousand, where a spline with fewer
+    than four nodes would degrade to a parabola or a line."""
+    d, inj = stream(3e6, 0.015, 0.030, 35, 20.0)
+    rng = np.random.default_rng(12)
+    th = np.vstack([inj, synth.draw_particles(120, rng)])
+    for mode, N in ((oracle.EQUAL_WIDTH, 8), (oracle.EQUAL_SNR2, 16)):
+        ref = oracle.evaluate(d, th, N, mode=mode)
+        with scstat.Context(0, scstat.SCS_SPLINE) as ctx:
+            ctx.set_data(0, d)
+            ctx.set_segments(0, N, mode)
+            got = ctx.eval(0, th)
+        assert rel_err(got, ref) <= TOL
