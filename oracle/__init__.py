@@ -74,6 +74,8 @@ def _load():
         lib.orc_derive.restype = I
         lib.orc_phase_turns.argtypes = [P, I, D, D, I64]
         lib.orc_phase_turns.restype = D
+        lib.orc_pn_terms.argtypes = [P, I, D, P, P]
+        lib.orc_pn_terms.restype = I
         lib.orc_response.argtypes = [P, D, D, P, P]
         lib.orc_response.restype = I
         lib.orc_template.argtypes = [P, I, I, D, D, I64, D, D, D, P, P, P]
@@ -121,6 +123,18 @@ def derive(theta, waveform=TF2):
 def phase_turns(theta, f_first, df, k, waveform=TF2):
     return _load().orc_phase_turns(_ptr(_theta(theta)), waveform, f_first, df,
                                    int(k))
+
+
+def pn_terms(theta, f, waveform=TF2):
+    """The PN phase split by order at frequency f: (status, F[8] turns,
+    T[8] seconds), T = dF/df, for the orders 0, 1, 1.5, 2, 2.5, 3, 3.5PN and
+    the leading eccentric term (Sec. IV, TaylorF2Ecc read as 3.5PN TaylorF2
+    plus the O(e0^2) correction)."""
+    F = np.zeros(8)
+    T = np.zeros(8)
+    st = _load().orc_pn_terms(_ptr(_theta(theta)), waveform, float(f), _ptr(F),
+                              _ptr(T))
+    return st, F, T
 
 
 def response(theta, f, t):

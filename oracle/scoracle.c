@@ -25,9 +25,17 @@
  *                                                  channels, Sec. I)
  *
  * Readings where the paper is silent:
- *   - waveform: non-spinning, circular (e0 = 0) TaylorF2 to 2PN; t(f) is
- *     defined as Psi'(f)/(2 pi); t_c fixed by t(f0) = 0; hard support cut
- *     f >= f0, t(f) <= T_obs, v <= 6^{-1/2};
+ *   - waveform: the paper's TaylorF2Ecc (Sec. IV) is not printed.  Read as
+ *     the non-spinning TaylorF2 phase to 3.5PN (orders v^0..v^7 of the
+ *     energy-balance SPA phase, with the 2.5PN term written
+ *     phi_5 (1 + 3 ln(v/v_lso)), v_lso = 6^{-1/2}, and the 3PN logarithm
+ *     ln(4v)) plus the leading-order eccentric correction
+ *     -(2355/1462) e0^2 chi^{-19/9} times the Newtonian term, chi = f/f0,
+ *     e0 the eccentricity at the particle's initial frequency f0 (Yunes,
+ *     Arun, Berti & Will 2009: the O(e0^2) SPA phase of the Peters-Mathews
+ *     inspiral); 0 <= e0 <= 0.3; t(f) is defined as Psi'(f)/(2 pi); t_c
+ *     fixed by t(f0) = 0; hard support cut f >= f0, t(f) <= T_obs,
+ *     v <= 6^{-1/2};
  *   - response: rigid-adiabatic single-link transfer from the two-pulse
  *     link formula, evaluated at t = t(f), first-generation TDI X,Y,Z and
  *     A = (Z-X)/sqrt2, E = (X-2Y+Z)/sqrt6, T = (X+Y+Z)/sqrt3 (the
@@ -154,6 +162,10 @@ typedef struct {
     /* PN waveform */
     dd eta, Ms;            /* symmetric mass ratio; total mass in seconds */
     dd phi2, phi3, phi4;   /* PN phase coefficients (phi0 = 1) */
+    double phi5;           /* 2.5PN: phi5 (1 + 3 ln(v/v_lso)) */
+    double phi6c, phi6l;   /* 3PN: phi6c + phi6l ln(4v) */
+    double phi7;           /* 3.5PN */
+    dd ecc;                /* -(2355/1462) e0^2 f0^{19/9} (0 when circular) */
     dd piMs;               /* pi * Ms */
     dd tc;                 /* coalescence time, fixed by t(f0) = 0 */
     double fdot;           /* linear-chirp test model: df/dt */
@@ -162,36 +174,75 @@ typedef struct {
     double complex P[3][3];        /* complex polarisation tensor */
 } orc_particle;
 
-/* Sum over k in {0,2,3,4} of c_k phi_k y^{5-k}, y = v^{-1}, i.e. the PN
- * bracket  sum_k c_k phi_k v^{k-5}. */
-static dd pn_series(const orc_particle *p, dd y, const double c[4]) {
+/* The PN phase split by order.  With P = 3/(256 pi eta) and v = (pi M f)^{1/3}
+ * (Sec. IV, TaylorF2 family), in turns:
+ *   F_k = P phi_k v^{k-5}                      k = 0, 2, 3, 4, 7
+ *   F_5 = P phi5 (1 + 3 ln(v/v_lso))
+ *   F_6 = P v (phi6c + phi6l ln(4v))
+ *   F_e = P ecc v^{-5} f^{-19/9}  (= Newtonian x -(2355/1462) e0^2 (f/f0)^{-19/9})
+ * and the time terms t_j = dF_j/df (d v/df = v/(3f)):
+ *   t_k = F_k (k-5)/(3f),   t_5 = P phi5/f,
+ *   t_6 = P v (phi6c + phi6l ln(4v) + phi6l)/(3f),   t_e = -(34/9) F_e/f.
+ * F[j], T[j] for j = 0..7 <-> orders 0, 1, 1.5, 2, 2.5, 3, 3.5PN and the
+ * eccentric term.  The Newtonian model keeps j = 0 only (its other
+ * coefficients are zero).  The large terms (j = 0..3, e) are double-double;
+ * the 2.5-3.5PN terms (|F| below ~1e3 turns) are plain doubles. */
+static void pn_terms(const orc_particle *p, dd f, dd F[8], dd T[8]) {
+    dd y = dd_rcbrt(dd_mul(p->piMs, f));               /* 1/v */
+    dd P = dd_div(from_d(3.0), dd_mul(dd_mul_d(DD_PI, 256.0), p->eta));
     dd y2 = dd_mul(y, y);
     dd y3 = dd_mul(y2, y);
     dd y5 = dd_mul(y3, y2);
-    dd s = dd_mul_d(y5, c[0]);                                  /* phi0 = 1 */
-    s = dd_add(s, dd_mul_d(dd_mul(p->phi2, y3), c[1]));
-    s = dd_add(s, dd_mul_d(dd_mul(p->phi3, y2), c[2]));
-    s = dd_add(s, dd_mul_d(dd_mul(p->phi4, y), c[3]));
+    dd inv3f = dd_div(from_d(1.0), dd_mul_d(f, 3.0));  /* 1/(3f) */
+    const dd pw[4] = {y5, y3, y2, y};                   /* v^{k-5}, k=0,2,3,4 */
+    const dd phk[4] = {from_d(1.0), p->phi2, p->phi3, p->phi4};
+    const double km5[4] = {-5.0, -3.0, -2.0, -1.0};
+    for (int j = 0; j < 4; ++j) {
+        F[j] = dd_mul(dd_mul(P, phk[j]), pw[j]);
+        T[j] = dd_mul_d(dd_mul(F[j], inv3f), km5[j]);
+    }
+    double v = 1.0 / dd_to_d(y), Pd = dd_to_d(P), fd = dd_to_d(f);
+    double lnv = log(v);
+    /* 2.5PN */
+    double F5 = Pd * p->phi5 * (1.0 + 3.0 * (lnv + 0.5 * log(6.0)));
+    F[4] = from_d(F5);
+    T[4] = from_d(Pd * p->phi5 / fd);
+    /* 3PN */
+    double br6 = p->phi6c + p->phi6l * (log(4.0) + lnv);
+    F[5] = from_d(Pd * v * br6);
+    T[5] = from_d(Pd * v * (br6 + p->phi6l) / (3.0 * fd));
+    /* 3.5PN */
+    double F7 = Pd * p->phi7 * v * v;
+    F[6] = from_d(F7);
+    T[6] = from_d(F7 * 2.0 / (3.0 * fd));
+    /* eccentric: f^{-19/9} = f^{-2} f^{-1/9}, f^{-1/9} = (f^{1/3})^{-1/3} */
+    if (p->ecc.hi != 0.0) {
+        dd f13 = dd_div(from_d(1.0), dd_rcbrt(f));
+        dd fm19 = dd_mul(dd_rcbrt(f13), dd_div(from_d(1.0), dd_mul(f, f)));
+        F[7] = dd_mul(dd_mul(dd_mul(P, p->ecc), y5), fm19);
+        T[7] = dd_div(dd_mul_d(F[7], -34.0), dd_mul_d(f, 9.0));
+    } else {
+        F[7] = from_d(0.0);
+        T[7] = from_d(0.0);
+    }
+}
+
+/* t(f) - t_c = sum of the time terms                         [seconds, dd] */
+static dd pn_time_offset(const orc_particle *p, dd f) {
+    dd F[8], T[8];
+    pn_terms(p, f, F, T);
+    dd s = T[0];
+    for (int j = 1; j < 8; ++j) s = dd_add(s, T[j]);
     return s;
 }
 
-/* t(f) - t_c = (1/(256 pi eta f)) sum_k phi_k (k-5) v^{k-5}   [seconds, dd] */
-static dd pn_time_offset(const orc_particle *p, dd f) {
-    static const double ck[4] = {-5.0, -3.0, -2.0, -1.0};     /* (k-5) */
-    dd y = dd_rcbrt(dd_mul(p->piMs, f));
-    dd s = pn_series(p, y, ck);
-    dd den = dd_mul(dd_mul(dd_mul_d(DD_PI, 256.0), p->eta), f);
-    return dd_div(s, den);
-}
-
-/* Psi(f)/(2 pi) in turns, before adding f t_c and -1/8:
- *   (3/(256 pi eta)) sum_k phi_k v^{k-5}                       [turns, dd] */
+/* Psi(f)/(2 pi) in turns, before adding f t_c and -1/8        [turns, dd] */
 static dd pn_phase_turns(const orc_particle *p, dd f) {
-    static const double ck[4] = {1.0, 1.0, 1.0, 1.0};
-    dd y = dd_rcbrt(dd_mul(p->piMs, f));
-    dd s = pn_series(p, y, ck);
-    dd den = dd_mul(dd_mul_d(DD_PI, 256.0), p->eta);
-    return dd_div(dd_mul_d(s, 3.0), den);
+    dd F[8], T[8];
+    pn_terms(p, f, F, T);
+    dd s = F[0];
+    for (int j = 1; j < 8; ++j) s = dd_add(s, F[j]);
+    return s;
 }
 
 static int finite8(const double *th) {
@@ -209,8 +260,11 @@ static int particle_init(orc_particle *p, const double *th, int waveform,
     memcpy(p->th, th, sizeof(p->th));
     if (!finite8(th)) return ORC_INVALID;
     double Mc = th[0], q = th[1], f0 = th[2];
-    if (th[7] != 0.0) return ORC_INVALID;          /* eccentric: not modelled */
+    double e0 = th[7];
     if (f0 <= 0.0) return ORC_INVALID;
+    /* eccentricity: TaylorF2 only, 0 <= e0 <= 0.3 */
+    if (e0 != 0.0 && (waveform != ORC_TF2 || !(e0 > 0.0 && e0 <= 0.3)))
+        return ORC_INVALID;
     if (waveform == ORC_LINEAR_CHIRP) {
         if (Mc <= 0.0) return ORC_INVALID;
         p->fdot = Mc;
@@ -230,6 +284,25 @@ static int particle_init(orc_particle *p, const double *th, int waveform,
                 dd_add(dd_div(from_d(15293365.0), from_d(508032.0)),
                        dd_mul(dd_div(from_d(27145.0), from_d(504.0)), e)),
                 dd_mul(dd_div(from_d(3085.0), from_d(72.0)), dd_mul(e, e)));
+            double et = dd_to_d(e), pi = M_PI, gE = 0.57721566490153286061;
+            p->phi5 = pi * (38645.0 / 756.0 - 65.0 / 9.0 * et);
+            p->phi6c = 11583231236531.0 / 4694215680.0 - 640.0 / 3.0 * pi * pi
+                       - 6848.0 / 21.0 * gE
+                       + (-15737765635.0 / 3048192.0 + 2255.0 / 12.0 * pi * pi) * et
+                       + 76055.0 / 1728.0 * et * et
+                       - 127825.0 / 1296.0 * et * et * et;
+            p->phi6l = -6848.0 / 21.0;
+            p->phi7 = pi * (77096675.0 / 254016.0 + 378515.0 / 1512.0 * et
+                            - 74045.0 / 756.0 * et * et);
+            /* -(2355/1462) e0^2 f0^{19/9}; f0^{19/9} = f0^2 (f0^{1/3})^{1/3} */
+            if (e0 != 0.0) {
+                dd f0d = from_d(f0);
+                dd f013 = dd_div(from_d(1.0), dd_rcbrt(f0d));
+                dd f019 = dd_div(from_d(1.0), dd_rcbrt(f013));
+                dd c = dd_div(from_d(-2355.0), from_d(1462.0));
+                p->ecc = dd_mul(dd_mul(c, dd_mul(from_d(e0), from_d(e0))),
+                                dd_mul(dd_mul(f0d, f0d), f019));
+            }
         } else {
             p->phi2 = from_d(0.0);
             p->phi3 = from_d(0.0);
@@ -426,6 +499,25 @@ double orc_time_of_freq(const double *th, int waveform, double f) {
     orc_particle p;
     if (particle_init(&p, th, waveform, ORC_IDENTITY) != ORC_OK) return NAN;
     return time_of_freq(&p, from_d(f));
+}
+
+/* The PN phase and time split by order at frequency f (pins only):
+ * F[j] [turns] and T[j] = dF[j]/df [s] for j = 0..7 (orders 0, 1, 1.5, 2,
+ * 2.5, 3, 3.5PN, eccentric).  ORC_INVALID for an invalid particle or a
+ * model without a PN phase. */
+int orc_pn_terms(const double *th, int waveform, double f, double *Fo,
+                 double *To) {
+    orc_particle p;
+    if (waveform == ORC_LINEAR_CHIRP) return ORC_INVALID;
+    if (particle_init(&p, th, waveform, ORC_IDENTITY) != ORC_OK)
+        return ORC_INVALID;
+    dd F[8], T[8];
+    pn_terms(&p, from_d(f), F, T);
+    for (int j = 0; j < 8; ++j) {
+        Fo[j] = dd_to_d(F[j]);
+        To[j] = dd_to_d(T[j]);
+    }
+    return ORC_OK;
 }
 
 /* derived: out[0]=eta, out[1]=M [s], out[2]=t_c [s], out[3]=t_c low part */

@@ -198,6 +198,8 @@ def test_newtonian_time_closed_form():
     (10.0, 1.0, 0.0101, 0.3, -0.2, 1.0, 0.4, 0.0),   # the largest phase on the grid
     (30.0, 1.5, 0.018, 1.1, 0.4, 1.2, 0.7, 0.0),
     (70.0, 6.0, 0.013, 4.0, 1.0, 2.5, 2.9, 0.0),
+    (30.0, 1.5, 0.018, 1.1, 0.4, 1.2, 0.7, 0.1),     # eccentric
+    (10.0, 1.0, 0.0101, 0.3, -0.2, 1.0, 0.4, 0.3),   # the largest eccentric term
 ])
 def test_tf2_time_is_phase_derivative(theta):
     """t(f) is defined as Psi'(f)/(2 pi) (Sec. IV reading of the SPA): over
@@ -205,8 +207,9 @@ def test_tf2_time_is_phase_derivative(theta):
     the midpoint rule gives as t(f_k + df/2) df up to t'' df^3/24 (< 1e-11
     turns here).  The phase (pn_phase_turns, weights 1) and the time
     (pn_time_offset, weights k - 5) come from separate series, so a wrong
-    weight, sign or power on any PN term of t(f) shows as a mismatch of order
-    1e-5 turns or more; the tolerance is 1e-9 turns."""
+    weight, sign or power on any PN term of t(f), or on the eccentric term,
+    shows as a mismatch of order 1e-5 turns or more; the tolerance is 1e-9
+    turns."""
     th = np.array(theta)
     f_first, df, K = synth.grid(0.01, 0.05, 3.15e7)
     st, lo, hi = oracle.support(th, f_first, df, K, 3.15e7)
@@ -224,9 +227,10 @@ def test_tf2_time_is_phase_derivative(theta):
 
 def test_table1_time_to_merger():
     """Table I: the GW150914-like source (Mc = 28.095555, eta = 0.2471,
-    f_low = 0.018 Hz) merges 43.28 months after the start.  The circular 2PN
-    t(f) must land within a few per cent (the paper's waveform adds
-    eccentricity and higher orders); the Newtonian value is lower still."""
+    f_low = 0.018 Hz) merges 43.28 months after the start.  The PN t(f)
+    must land within a few per cent (at v ~ 0.03 the orders beyond 1PN and
+    the eccentricity move t_c by < 0.1%); the Newtonian value is lower
+    still."""
     g = json.load(open(os.path.join(GOLDEN, "table1_gw150914.json")))
     eta = g["eta"]
     q = ((1 - 2 * eta) + math.sqrt(1 - 4 * eta)) / (2 * eta)
@@ -237,6 +241,129 @@ def test_table1_time_to_merger():
     assert tc / month == pytest.approx(g["t_c_months"], rel=0.03)
     assert tcN / month == pytest.approx(g["t_c_months"], rel=0.03)
     assert tcN < tc   # 1PN terms lengthen the inspiral at this mass ratio
+
+
+def _spa_from_energy_balance():
+    """TaylorF2 derived here from scratch, not from the oracle's coefficients:
+    the 3PN binding energy E(v) and the 3.5PN flux F(v) of a non-spinning
+    circular binary (Blanchet, Living Rev. Relativ. 17 (2014) 2), the balance
+    dE/dt = -F, and the SPA phase Psi = 2 pi f t(f) - 2 phi(f) - pi/4 with
+    dphi/dt = v^3/M and 2 pi f = 2 v^3/M.  Returns, per order k = 0..7,
+    functions (v, eta) -> the phase term Psi_k/(2 pi) [turns] and the time
+    term t_k [units of M], both without the integration constants."""
+    sp = pytest.importorskip("sympy")
+    v, eta, L = sp.symbols("v eta L")   # L stands for ln v
+    R, pi, gE = sp.Rational, sp.pi, sp.EulerGamma
+    e = [1, -R(3, 4) - eta / 12, -R(27, 8) + R(19, 8) * eta - eta ** 2 / 24,
+         -R(675, 64) + (R(34445, 576) - R(205, 96) * pi ** 2) * eta
+         - R(155, 96) * eta ** 2 - R(35, 5184) * eta ** 3]
+    fl = [1, 0, -R(1247, 336) - R(35, 12) * eta, 4 * pi,
+          -R(44711, 9072) + R(9271, 504) * eta + R(65, 18) * eta ** 2,
+          (-R(8191, 672) - R(583, 24) * eta) * pi,
+          R(6643739519, 69854400) + R(16, 3) * pi ** 2 - R(1712, 105) * gE
+          - R(856, 105) * (sp.log(16) + 2 * L)
+          + (-R(134543, 7776) + R(41, 48) * pi ** 2) * eta - R(94403, 3024) * eta ** 2
+          - R(775, 324) * eta ** 3,
+          (-R(16285, 504) + R(214745, 1728) * eta + R(193385, 3024) * eta ** 2) * pi]
+    # -dE/dv = eta v sum_j (j+1) e_j v^{2j};  F = (32/5) eta^2 v^10 sum_k fl_k v^k
+    num = [0] * 8
+    for j in range(4):
+        num[2 * j] = (j + 1) * e[j]
+    qs = []   # dt/dv = (5/(32 eta)) v^{-9} sum_k q_k v^k   (M = 1)
+    for k in range(8):
+        qs.append(sp.expand(num[k] - sum(qs[j] * fl[k - j] for j in range(k))))
+
+    def integ(c, n):   # int c(L) v^n dv, L = ln v, n != -1
+        c1 = sp.expand(c).coeff(L, 1)
+        c0 = sp.expand(c - c1 * L)
+        return c0 * v ** (n + 1) / (n + 1) + c1 * v ** (n + 1) / (n + 1) * (L - R(1, n + 1))
+
+    def integ_log(c):  # n = -1 (only the 2.5PN phase term meets it)
+        return sp.expand(c) * L
+
+    pre = R(5, 32) / eta
+    out = []
+    for k in range(8):
+        tk = pre * integ(qs[k], k - 9)
+        phik = pre * (integ_log(qs[k]) if k == 5 else integ(qs[k], k - 6))
+        psik = sp.expand(2 * v ** 3 * tk - 2 * phik) / (2 * pi)
+        lam = [sp.lambdify((v, eta), expr.subs(L, sp.log(v)), "math") for expr in (psik, tk)]
+        out.append(lam)
+    return out
+
+
+@pytest.mark.parametrize("theta,fs", [
+    ((30.0, 1.5, 0.018, 0, 0, 0, 0, 0.0), (0.018, 0.021, 0.03)),     # LISA band
+    ((1.2188, 1.0, 10.0, 0, 0, 0, 0, 0.0), (10.0, 100.0, 1000.0)),   # 1.4 + 1.4 Msun
+    ((8.0, 3.0, 30.0, 0, 0, 0, 0, 0.0), (30.0, 120.0, 300.0)),       # v up to ~0.36
+])
+def test_pn_orders_follow_from_energy_balance(theta, fs):
+    """Every PN order of the oracle's phase and time (orders 0 to 3.5PN, each
+    returned separately by orc_pn_terms) equals the term the SPA derivation
+    from the binding energy and the flux gives (above), to 1e-12 relative.
+    The 2.5PN phase term is a constant plus a logarithm; its constant is a
+    phase convention (absorbed in phi_c), so that order compares the phase
+    difference between two frequencies."""
+    terms = _spa_from_energy_balance()
+    th = np.array(theta)
+    st, eta, M, _ = oracle.derive(th)
+    assert st == oracle.OK
+    idx = {0: 0, 2: 1, 3: 2, 4: 3, 5: 4, 6: 5, 7: 6}
+    ref = {}
+    for f in fs:
+        v = (math.pi * M * f) ** (1.0 / 3.0)
+        st, F, T = oracle.pn_terms(th, f)
+        assert st == oracle.OK and F[7] == 0.0 and T[7] == 0.0
+        for k, j in idx.items():
+            psi_k, t_k = terms[k]
+            assert T[j] == pytest.approx(t_k(v, eta) * M, rel=1e-12, abs=1e-300)
+            if k != 5:
+                assert F[j] == pytest.approx(psi_k(v, eta), rel=1e-12, abs=1e-300)
+        ref[f] = (F[4], terms[5][0](v, eta))
+    f1, f2 = fs[0], fs[-1]
+    assert ref[f2][0] - ref[f1][0] == pytest.approx(ref[f2][1] - ref[f1][1], rel=1e-11)
+
+
+def test_eccentric_term_follows_peters_mathews():
+    """The leading-order eccentric correction against a direct integration of
+    the Peters-Mathews orbit-averaged evolution (Peters 1964): da/dt and de/dt
+    of the quadrupole inspiral with the full enhancement functions of e, the
+    dominant harmonic at f = 2 x orbital frequency = sqrt(M/a^3)/pi.  The
+    time from f0 to f with e(f0) = e0, minus the circular time, must equal
+    the oracle's eccentric time term T_e(f) - T_e(f0) to O(e0^2) relative
+    (1% at e0 = 0.01), and the circular (e0 = 0) integral must equal its
+    Newtonian time term to 1e-9.  The eccentric phase term is then fixed by
+    t = dF/df (test_tf2_time_is_phase_derivative)."""
+    integrate = pytest.importorskip("scipy.integrate")
+    for e0 in (0.01, 0.02):
+        th = np.array([30.0, 1.5, 0.018, 0, 0, 0, 0, e0])
+        st, eta, M, _ = oracle.derive(th)
+        assert st == oracle.OK
+        f0 = th[2]
+
+        def a_of(f):
+            return (M / (math.pi * f) ** 2) ** (1.0 / 3.0)
+
+        def rhs(a, y):
+            ecc = y[1]
+            e2 = ecc * ecc
+            dadt = -64.0 / 5.0 * eta * M ** 3 / a ** 3 * (
+                1 + 73.0 / 24.0 * e2 + 37.0 / 96.0 * e2 * e2) / (1 - e2) ** 3.5
+            dedt = -304.0 / 15.0 * eta * M ** 3 * ecc / a ** 4 * (
+                1 + 121.0 / 304.0 * e2) / (1 - e2) ** 2.5
+            return [1.0 / dadt, dedt / dadt]
+
+        for f in (0.021, 0.03, 0.05):
+            span = (a_of(f0), a_of(f))
+            te = integrate.solve_ivp(rhs, span, [0.0, e0], rtol=1e-12, atol=1e-30,
+                                     method="DOP853").y[0, -1]
+            tc0 = integrate.solve_ivp(rhs, span, [0.0, 0.0], rtol=1e-12, atol=1e-30,
+                                      method="DOP853").y[0, -1]
+            _, _, T = oracle.pn_terms(th, f)
+            _, _, T0 = oracle.pn_terms(th, f0)
+            assert T[0] - T0[0] == pytest.approx(tc0, rel=1e-9)
+            assert T[7] - T0[7] == pytest.approx(te - tc0, rel=0.01)
+            assert T[7] < T0[7] and te < tc0   # eccentric binaries merge sooner
 
 
 def test_spa_sign_against_time_domain_chirp():
@@ -471,13 +598,14 @@ def test_invalid_and_empty_particles():
         [30.0, 0.5, 0.018, 0, 0, 0, 0, 0],         # q < 1
         [30.0, 1.5, -0.01, 0, 0, 0, 0, 0],         # f0 <= 0
         [30.0, 1.5, np.nan, 0, 0, 0, 0, 0],        # not finite
-        [30.0, 1.5, 0.018, 0, 0, 0, 0, 0.1],       # eccentric
+        [30.0, 1.5, 0.018, 0, 0, 0, 0, 0.35],      # e0 beyond 0.3
+        [30.0, 1.5, 0.018, 0, 0, 0, 0, -0.05],     # e0 < 0
         [2.0e5, 1.0, 0.018, 0, 0, 0, 0, 0],        # past the last stable orbit
         [30.0, 1.5, 0.025, 0, 0, 0, 0, 0],         # starts above the band
     ])
     s = oracle.evaluate(d, bad, 4)
-    assert np.all(np.isneginf(s[:6]))
-    assert s[6] == 0.0
+    assert np.all(np.isneginf(s[:7]))
+    assert s[7] == 0.0
 
 
 def test_support_matches_linear_scan():
@@ -503,34 +631,44 @@ def test_support_matches_linear_scan():
 
 def test_phase_precision_floor():
     """The reduced phase carries double-double accuracy: against a 40-digit
-    evaluation of the same Psi/(2 pi), the turn fraction agrees to 1e-13
-    turns although Psi reaches ~1e7 turns (without double-double, ~1e-9)."""
+    evaluation of the same Psi/(2 pi) (all orders to 3.5PN and the eccentric
+    term), the turn fraction agrees to 1e-13 turns although Psi reaches ~1e7
+    turns (without double-double, ~1e-9)."""
     mpmath = pytest.importorskip("mpmath")
     mpmath.mp.dps = 40
-    th = np.array([12.0, 1.3, 0.0121, 0, 0, 0, 0, 0])
+    th = np.array([12.0, 1.3, 0.0121, 0, 0, 0, 0, 0.08])
     T = 1.26e8
     f_first, df, K = synth.grid(0.01, 0.05, T)
-    q = mpmath.mpf(th[1])
+    mpf = mpmath.mpf
+    q = mpf(th[1])
     eta = q / (1 + q) ** 2
-    M = mpmath.mpf(th[0]) * eta ** (mpmath.mpf(-3) / 5) * mpmath.mpf(TSUN)
-    phi = [mpmath.mpf(1), mpmath.mpf(3715) / 756 + mpmath.mpf(55) / 9 * eta,
-           -16 * mpmath.pi,
-           mpmath.mpf(15293365) / 508032 + mpmath.mpf(27145) / 504 * eta
-           + mpmath.mpf(3085) / 72 * eta ** 2]
-    pw = [0, 2, 3, 4]
+    M = mpf(th[0]) * eta ** (mpf(-3) / 5) * mpf(TSUN)
+    pi, gE = mpmath.pi, mpmath.euler
+    phi = {0: mpf(1), 2: mpf(3715) / 756 + mpf(55) / 9 * eta, 3: -16 * pi,
+           4: mpf(15293365) / 508032 + mpf(27145) / 504 * eta + mpf(3085) / 72 * eta ** 2,
+           7: pi * (mpf(77096675) / 254016 + mpf(378515) / 1512 * eta
+                    - mpf(74045) / 756 * eta ** 2)}
+    phi5 = pi * (mpf(38645) / 756 - mpf(65) / 9 * eta)
+    phi6c = (mpf(11583231236531) / 4694215680 - mpf(640) / 3 * pi ** 2
+             - mpf(6848) / 21 * gE
+             + (mpf(-15737765635) / 3048192 + mpf(2255) / 12 * pi ** 2) * eta
+             + mpf(76055) / 1728 * eta ** 2 - mpf(127825) / 1296 * eta ** 3)
+    phi6l = mpf(-6848) / 21
+    e0, f0 = mpf(th[7]), mpf(th[2])
+    P = 3 / (256 * pi * eta)
 
-    def v(f):
-        return (mpmath.pi * M * f) ** (mpmath.mpf(1) / 3)
+    def Fpn(f):
+        v = (pi * M * f) ** (mpf(1) / 3)
+        s = sum(c * v ** (k - 5) for k, c in phi.items())
+        s += phi5 * (1 + 3 * mpmath.log(v * mpmath.sqrt(6)))
+        s += v * (phi6c + phi6l * mpmath.log(4 * v))
+        s += -mpf(2355) / 1462 * e0 ** 2 * v ** -5 * (f / f0) ** (mpf(-19) / 9)
+        return P * s
 
-    def tminus(f):
-        return sum(phi[i] * (pw[i] - 5) * v(f) ** (pw[i] - 5)
-                   for i in range(4)) / (256 * mpmath.pi * eta * f)
-
-    tc = -tminus(mpmath.mpf(th[2]))
+    tc = -mpmath.diff(Fpn, f0)
     for k in (150000, 900000, 4000000):
-        f = mpmath.mpf(f_first) + k * mpmath.mpf(df)
-        F = f * tc - mpmath.mpf(1) / 8 + 3 * sum(
-            phi[i] * v(f) ** (pw[i] - 5) for i in range(4)) / (256 * mpmath.pi * eta)
+        f = mpf(f_first) + k * mpf(df)
+        F = f * tc - mpf(1) / 8 + Fpn(f)
         frac = float(F - mpmath.nint(F))
         got = oracle.phase_turns(th, f_first, df, k)
         assert abs(got - frac) < 1e-13
