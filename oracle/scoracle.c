@@ -43,7 +43,11 @@
  *     orbit with the constellation centre at (R cos Omega t, R sin Omega t, 0);
  *   - equal-SNR^2 segments: trapezoid cumulative of the exact template
  *     power on an anchor grid of stride 1024 bins, linear inverse
- *     interpolation, bin k in segment n iff kappa_n <= k < kappa_{n+1};
+ *     interpolation, bin k in segment n iff kappa_n <= k < kappa_{n+1},
+ *     with each interior kappa_n lowered by 2^-20 bins: a kappa that is an
+ *     integer in exact arithmetic (a support shorter than one anchor stride
+ *     makes kappa_n = k_lo + n (k_hi - k_lo)/N) then starts its segment at
+ *     that integer whatever the last bit of its FP64 rounding;
  *   - the large waveform phase (up to ~1e8 rad) is evaluated in
  *     double-double arithmetic, reduced modulo one turn, then rounded.
  *
@@ -597,6 +601,7 @@ int orc_template(const double *th, int waveform, int response, double f_first,
  * anchor grid k_lo, k_lo + 1024, ..., k_hi.  hhk[j] = sum_alpha w |h|^2 at
  * support bin k_lo + j.  */
 #define ORC_SNR2_STRIDE 1024
+#define ORC_SNR2_SNAP 0x1p-20   /* bins; kappa - 2^-20 is exact below 2^32 */
 static void snr2_bounds(int64_t lo, int64_t hi, const double *hhk, int N,
                         double *kappa) {
     int64_t nanch = (hi - lo) / ORC_SNR2_STRIDE + 1;
@@ -624,6 +629,7 @@ static void snr2_bounds(int64_t lo, int64_t hi, const double *hhk, int N,
         while (a < nanch - 1 && C[a] < cn) ++a;
         kappa[n] = (double)ka[a - 1] + (cn - C[a - 1]) / (C[a] - C[a - 1]) *
                                            (double)(ka[a] - ka[a - 1]);
+        kappa[n] -= ORC_SNR2_SNAP;
     }
     free(ka);
     free(C);

@@ -179,6 +179,35 @@ def test_refinement_monotone(mode):
         prev = (s, kap)
 
 
+
+def test_snr2_edges_of_short_supports_are_exact_rationals():
+    """A support no longer than one anchor stride (1024 bins) has two anchors,
+    so the trapezoid cumulative is linear and kappa_n = k_lo + n span / N
+    exactly: the edges must be k_lo + ceil(n span / N) in integer arithmetic,
+    also where n span / N is an integer (there the FP64 kappa may round to
+    either side of it; the 2^-20-bin snap of the definition takes the
+    integer)."""
+    d = small_stream()
+    rng = np.random.default_rng(17)
+    th = synth.draw_particles(400, rng, lo=[10, 1, 0.0176, 0, -1.5, 0, 0, 0],
+                              hi=[100, 8, 0.0195, 6.28, 1.5, 3.14, 3.14, 0.1])
+    short = []
+    for p in th:
+        st, lo, hi = oracle.support(p, d["f_first"], d["df"], d["K"], d["T_obs"])
+        if st == oracle.OK and 100 < hi - lo <= 1024:
+            short.append((p, lo, hi))
+    assert len(short) >= 5
+    hits = 0
+    for N in (4, 10, 12, 100):   # N = 12 meets an FP64 kappa just above its integer
+        ps = np.array([p for p, _, _ in short])
+        _, kap = oracle.evaluate(d, ps, N, mode=oracle.EQUAL_SNR2, want_kappa=True)
+        for (p, lo, hi), k in zip(short, kap):
+            span = hi - lo
+            want = [lo + (-(-n * span // N)) for n in range(N)] + [hi + 1]
+            np.testing.assert_array_equal(np.ceil(k).astype(np.int64), want)
+            hits += sum(1 for n in range(1, N) if n * span % N == 0)
+    assert hits >= 10   # the integer cases occur
+
 # ----------------------------------------------------------------- waveform
 def test_newtonian_time_closed_form():
     """Newtonian chirp: t_c - t(f) = (5/256) (G Mc/c^3)^{-5/3} (pi f)^{-8/3}."""
