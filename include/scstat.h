@@ -13,8 +13,8 @@
  *   x_{p,n}  = max_phi Re{z e^{-i phi}} = |z_{p,n}|
  *   Upsilon_N(p) = sum_n x_{p,n}^2 / hh_{p,n}      (terms with hh = 0 add 0)
  *
- * with h_alpha the (2,2)-mode frequency-domain inspiral (circular TaylorF2
- * to 2PN) times the LISA TDI A/E (and, on a stream loaded with
+ * with h_alpha the (2,2)-mode frequency-domain inspiral (TaylorF2 to 3.5PN
+ * with the leading eccentric term) times the LISA TDI A/E (and, on a stream loaded with
  * scs_set_data_aet, T) transfer function at t = t(f) (Sec. IV).
  *
  * Conventions shared by all calls
@@ -29,10 +29,15 @@
  *      {Mc [Msun, detector frame], q = m1/m2 >= 1, f0 [Hz, GW frequency at
  *       t = 0, the start of the observation], lambda, beta [ecliptic
  *       longitude/latitude, rad], iota [inclination, rad], psi
- *       [polarisation, rad], e0 [initial eccentricity; must be 0]}.
+ *       [polarisation, rad], e0 [orbital eccentricity at f0, 0 <= e0 <= 0.3]}.
+ *  - Waveform (Sec. IV, TaylorF2Ecc): the non-spinning TaylorF2 phase to
+ *    3.5PN plus the leading-order eccentric term
+ *    -(2355/1462) e0^2 (f/f0)^{-19/9} times the Newtonian term; amplitude
+ *    f^{-7/6}.
  *  - Non-physical particles (Mc <= 0, q < 1, f0 <= 0, a non-finite entry,
- *    e0 != 0, or f0 already past the last stable orbit v = 6^{-1/2}) get
- *    stat = -inf; a particle whose support misses the data band gets 0.
+ *    e0 < 0 or e0 > 0.3, or f0 already past the last stable orbit
+ *    v = 6^{-1/2}) get stat = -inf; a particle whose support misses the data
+ *    band gets 0.
  *  - Support of a particle: grid bins k with f_k >= f0, t(f_k) <= T_obs and
  *    v(f_k) <= 6^{-1/2}.
  */
@@ -105,15 +110,16 @@ int scs_set_spline(scs_ctx *ctx, int max_log2_spacing);
  * Replaces, for every later call on the context (evaluation on both paths,
  * edges, supports, templates, injection, swarm iterations), the waveform and
  * the response by test models that have closed forms:
- *   SCS_MODEL_TF2           the search model (default): circular TaylorF2
- *                           to 2PN, amplitude f^{-7/6} (Sec. IV);
+ *   SCS_MODEL_TF2           the search model (default): TaylorF2 to 3.5PN
+ *                           with the leading eccentric term, amplitude
+ *                           f^{-7/6} (Sec. IV);
  *   SCS_MODEL_NEWTONIAN     the same with the leading (Newtonian) phase term
- *                           only: a power-law chirp;
+ *                           only: a power-law chirp (e0 must be 0);
  *   SCS_MODEL_LINEAR_CHIRP  App. A's constant-amplitude linear chirp
  *                           f(t) = f0 + fdot t: phase (f - f0)^2 / (2 fdot)
  *                           - 1/8 turns, t(f) = (f - f0)/fdot, amplitude 1,
  *                           params[0] read as fdot [Hz/s] > 0, q ignored, no
- *                           last-stable-orbit cut;
+ *                           last-stable-orbit cut, e0 must be 0;
  *   SCS_RESPONSE_TDI        the rigid-adiabatic TDI A, E (and T) response
  *                           (default);
  *   SCS_RESPONSE_IDENTITY   h_A = h, h_E = h_T = 0, no Doppler modulation.
@@ -225,7 +231,10 @@ int scs_batch_eval(scs_ctx *ctx, const int *stream_ids, const int64_t *P_offsets
  *   move           theta <- theta + v; lambda (dimension 3) and psi (6) wrap
  *                  into [lo, hi); the others reflect at a bound that was
  *                  crossed (2 bound - theta, velocity negated) and are then
- *                  clipped to [lo, hi].  Dimension 7 (e0) stays at prior_lo[7].
+ *                  clipped to [lo, hi].  Dimension 7 (e0) is searched (and
+ *                  reflects) when prior_hi[7] > prior_lo[7]; with
+ *                  prior_hi[7] == prior_lo[7] it stays at prior_lo[7] and
+ *                  draws no random numbers.
  * r_P, r_G: outputs 0 and 1 of Philox4x32-10 (Salmon et al., SC'11) with key
  * (seed mod 2^32, seed >> 32) and counter (particle, iteration, dimension, 0),
  * mapped to (x + 1/2) 2^-32.  The iteration counter lives on the device.

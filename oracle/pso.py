@@ -14,7 +14,9 @@ Philox4x32-10 (Salmon et al. 2011, "Parallel random numbers: as easy as
 dimension, 0), outputs 0 and 1 mapped to (x + 1/2) 2^-32; positions leaving
 the prior box wrap in lambda (dimension 3) and psi (dimension 6) and reflect
 (with the velocity component negated) in the other dimensions; dimension 7
-(e0) is not searched.
+(e0) is searched like the others when its prior range has width (Table I
+gives it a prior), and otherwise stays at its lower bound and draws no
+random numbers.
 """
 from __future__ import annotations
 
@@ -24,7 +26,12 @@ M0, M1 = np.uint64(0xD2511F53), np.uint64(0xCD9E8D57)
 W0, W1 = np.uint32(0x9E3779B9), np.uint32(0xBB67AE85)
 MASK = np.uint64(0xFFFFFFFF)
 WRAP_DIMS = (3, 6)
-SEARCH_DIMS = 7
+SEARCH_DIMS = 7          # without e0
+
+
+def search_dims(lo, hi):
+    """Searched dimensions: 0-6, and e0 (7) when its prior range has width."""
+    return 8 if hi[7] > lo[7] else SEARCH_DIMS
 
 
 def philox4x32_10(ctr, key):
@@ -68,7 +75,7 @@ def pso_init(P, lo, hi, seed):
     pos = np.tile(lo, (P, 1))
     vel = np.zeros((P, 8))
     idx = np.arange(P)
-    for d in range(SEARCH_DIMS):
+    for d in range(search_dims(lo, hi)):
         ctr = np.zeros((P, 4), np.uint32)
         ctr[:, 0] = idx
         ctr[:, 1] = 0xFFFFFFFF
@@ -121,7 +128,7 @@ def pso_step(pos, vel, best_pos, swarm_best_pos, swarm_of, hyper, lo, hi, seed, 
     P = pos.shape[0]
     idx = np.arange(P)
     h = hyper[swarm_of]
-    for d in range(SEARCH_DIMS):
+    for d in range(search_dims(lo, hi)):
         rp, rg = uniforms(seed, idx, iteration, d)
         th = pos[:, d]
         u = (h[:, 0] * vel[:, d] + h[:, 1] * rp * (best_pos[:, d] - th)

@@ -49,12 +49,12 @@ __device__ inline uint64_t small_turns_to_fixed(float x) {   // normally |x| << 
 // Taylor coefficients of the phase in the bin offset j about k_a:
 // c[r] = Phi^{(r)} df^r / r!  (c[0] reduced modulo one turn), orders 0-3 in
 // FP64 (c64) and 4-6 in FP32 (c32), plus the node hand-off.
-__device__ inline void phase_taylor(const Part& p, double fa, double df, double idf, double c64[4],
-                                    float c32[7], PhaseAnchor& an) {
-  double u = rcbrt(fa);
-  double u2 = u * u;
-  const double rdf = df * (u2 * u);   // df / f (u^3 = 1/f): d/df of u^n = -(n/3) u^n / f
-  double upow[4] = {u2 * u2 * u, u2 * u, u2, u};
+__device__ inline void phase_taylor(const Part& p, double fa, double2 wl, double df, double idf,
+                                    double c64[4], float c32[7], PhaseAnchor& an) {
+  // u = f^{-1/3} from the grid table's w = f^{-1/9}: u = w^3, one Newton step
+  // on u^3 f = 1
+  const double w = wl.x, u0 = w * w * w;
+  const double u = fma(u0 * fma(-fa, u0 * u0 * u0, 1.0), 1.0 / 3.0, u0);
   // PN part F_pn: bin-unit derivatives F[r] = F_pn^{(r)} df^r (the linear
   // chirp's phase (f - f0)^2 / (2 fdot) is exactly quadratic)
   double F[5] = {0, 0, 0, 0, 0};
@@ -65,23 +65,7 @@ __device__ inline void phase_taylor(const Part& p, double fa, double df, double 
     F[1] = x * df * ifd;
     F[2] = df * df * ifd;
   }
-#pragma unroll
-  for (int m = 0; m < 4; ++m) {
-    double n = (double)kPow[m];
-    double val = p.A[m].hi * upow[m];
-#pragma unroll
-    for (int r = 0; r < 5; ++r) {
-      F[r] += val;
-      val *= -(n + 3.0 * r) * (1.0 / 3.0) * rdf;
-    }
-    float v32 = (float)val;
-    const float rdf32 = (float)rdf;
-#pragma unroll
-    for (int r = 5; r < 8; ++r) {
-      F32[r] += v32;
-      v32 *= -((float)n + 3.0f * r) * (1.0f / 3.0f) * rdf32;
-    }
-  }
+  pn_bin_derivs<5, 8>(p, fa, u, w, wl.y, df, F, F32);
   // t(f) and its bin derivatives T[r] = t^{(r)} df^r (t = F'):  T[r] = F[r+1]/df
   double t0 = p.tc.hi + (p.tc.lo + F[1] * idf);
   double T1 = F[2] * idf, T2 = F[3] * idf, T3 = F[4] * idf;
@@ -155,12 +139,14 @@ __device__ inline void phase_taylor(const Part& p, double fa, double df, double 
 
 // Build the phase state of the span starting at k_a (inlined: a call's
 // register saves cost more than the code size).
+// fz: the stream's grid table (f_k^{-1/9}, ln f_k).
 __device__ __forceinline__ void phase_anchor(const Part& p, int ka, double f_first,
-                                                 double df, double idf, PhaseAnchor& an) {
+                                                 double df, double idf, const double2* fz,
+                                                 PhaseAnchor& an) {
   double fa = f_first + (double)ka * df;
   double c64[4];
   float c32[7];
-  phase_taylor(p, fa, df, idf, c64, c32, an);
+  phase_taylor(p, fa, __ldg(fz + ka), df, idf, c64, c32, an);
   // forward differences Delta_r = sum_{s>=r} c_s r! S(s, r), with r! S(s, r)
   // (S: Stirling numbers of the second kind) the r-th forward difference at
   // 0 of j^s

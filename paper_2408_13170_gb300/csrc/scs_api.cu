@@ -58,6 +58,7 @@ struct DataStream {
   int K = 0;
   DevBuf dA64, dE64, w64, d32, w32;
   DevBuf wdf;           // double-float weights for the equal-SNR^2 edges
+  DevBuf fz;            // grid table (f_k^{-1/9}, ln f_k)
   bool has_T = false;   // the third TDI channel (scs_set_data_aet)
   DevBuf dT64, wT64, t32, wTdf;
   DevBuf wmax;          // max w as the bits of a double (FP32 scale W0)
@@ -111,6 +112,7 @@ struct scs_ctx {
   struct Pso {
     bool made = false;
     int P = 0, S = 0;
+    int ndim = kPsoDimsCirc;
     uint64_t seed = 0;
     std::vector<int> sids;
     std::vector<int64_t> off;
@@ -252,6 +254,7 @@ std::vector<StreamDesc> make_table(const std::vector<BatchPart>& parts, int* n_c
     d.width_edges = ds.width_edges.as<int>();
     d.wdf = ds.wdf.as<float4>();
     d.wTdf = ds.has_T ? ds.wTdf.as<float2>() : nullptr;
+    d.fz = ds.fz.as<double2>();
   }
   *n_chunks_total = cb;
   *edges_total = eb;
@@ -539,7 +542,7 @@ void scs_destroy(scs_ctx* ctx) {
     DataStream& d = kv.second;
     d.dA64.release(); d.dE64.release(); d.w64.release(); d.d32.release(); d.w32.release();
     d.dT64.release(); d.wT64.release(); d.t32.release();
-    d.wdf.release(); d.wTdf.release();
+    d.wdf.release(); d.wTdf.release(); d.fz.release();
     d.wmax.release();
     d.width_edges.release();
   }
@@ -649,6 +652,7 @@ int set_data_impl(scs_ctx* ctx, int sid, const double* A, const double* E, const
   CK(cudaMemsetAsync(ds.d32.as<float4>() + Kz, 0, sizeof(float4) * 32, s));
   CK(cudaMemsetAsync(ds.w32.as<float2>() + Kz, 0, sizeof(float2) * 32, s));
   CK(ds.wdf.reserve(sizeof(float4) * Kz));
+  CK(ds.fz.reserve(sizeof(double2) * Kz));
   ds.has_T = withT;
   if (withT) {
     CK(ds.dT64.reserve(sizeof(double2) * Kz));
@@ -700,6 +704,8 @@ int set_data_impl(scs_ctx* ctx, int sid, const double* A, const double* E, const
   k_to_wdf<<<2048, 256, 0, s>>>(ds.w64.as<double2>(), wT64, (int)K,
                                 ds.wmax.as<unsigned long long>(), ds.wdf.as<float4>(),
                                 withT ? ds.wTdf.as<float2>() : nullptr);
+  CKLAUNCH();
+  k_grid_pow<<<2048, 256, 0, s>>>(f_first, df, (int)K, ds.fz.as<double2>());
   CKLAUNCH();
   unsigned long long wbits = 0;
   CK(cudaMemcpyAsync(&wbits, ds.wmax.ptr, sizeof wbits, cudaMemcpyDeviceToHost, s));
@@ -1312,6 +1318,7 @@ PsoArgs pso_args(scs_ctx* ctx) {
   PsoArgs a;
   a.P = q.P;
   a.S = q.S;
+  a.ndim = q.ndim;
   a.off = q.d_off.as<int64_t>();
   a.pos = q.pos.as<double>();
   a.vel = q.vel.as<double>();
@@ -1422,7 +1429,7 @@ int scs_pso_create(scs_ctx* ctx, int n_swarms, const int* stream_ids,
   for (int d = 0; d < 8; ++d) {
     if (!std::isfinite(prior_lo[d]) || !std::isfinite(prior_hi[d]))
       return fail(ctx, SCS_EINVAL, "prior bound %d not finite", d);
-    if (d < kPsoDims ? !(prior_hi[d] > prior_lo[d]) : !(prior_hi[d] >= prior_lo[d]))
+    if (d < kPsoDimsCirc ? !(prior_hi[d] > prior_lo[d]) : !(prior_hi[d] >= prior_lo[d]))
       return fail(ctx, SCS_EINVAL, "prior box empty in dimension %d", d);
   }
   int rc = bind(ctx);
@@ -1448,6 +1455,8 @@ int scs_pso_create(scs_ctx* ctx, int n_swarms, const int* stream_ids,
     q.lohi[d] = prior_lo[d];
     q.lohi[8 + d] = prior_hi[d];
   }
+  // e0 is searched when its prior has width (Table I), else held at prior_lo[7]
+  q.ndim = prior_hi[7] > prior_lo[7] ? 8 : kPsoDimsCirc;
   // default: the first rung of the ladder in Table III (N = 100), eps in the
   // parameter order of this library (Mc, q, f0, lambda, beta, iota, psi, e0)
   const double row[kPsoHyper] = {0.5, 0.2, 0.3, 0.1, 0.05, 5e-8, 0.1, 0.1, 0.2, 0.1, 0.1};

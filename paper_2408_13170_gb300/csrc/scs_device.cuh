@@ -94,9 +94,18 @@ __device__ inline dd grid_freq_dd(double f_first, double df, int64_t k) {
 }
 
 // ------------------------------------------------------------- the particle
-// Phase in turns: F(f) = Psi(f)/(2 pi) = t_c f - 1/8 + sum_k A_k u^{n_k},
-// u = f^{-1/3}, n = {5, 3, 2, 1} for PN orders k = {0, 2, 3, 4}.  Then
-// d u^n / df = -(n/3) u^{n+3}, so t(f) = F'(f) = t_c - u^3 sum (n_k/3) A_k u^{n_k}.
+// Phase in turns (Sec. IV, TaylorF2Ecc read as the 3.5PN TaylorF2 phase plus
+// the leading O(e0^2) eccentric term), u = f^{-1/3}:
+//   F(f) = Psi(f)/(2 pi) = t_c f - 1/8 + sum_m A_m u^{n_m}     n = 5, 3, 2, 1
+//          + Ah_0 u^{-1} + Ah_1 u^{-2}                         3PN, 3.5PN
+//          + Fc + L5 ln f + L6 u^{-1} ln f                     2.5PN, 3PN logs
+//          + Ae u^{34/3}                                       eccentric
+// (orders 0, 1, 1.5, 2PN; the 3PN and 3.5PN powers; the 2.5PN term
+// phi5 (1 + 3 ln(v/v_lso)) and the 3PN ln(4v) split into constants and ln f;
+// -(2355/1462) e0^2 (f/f0)^{-19/9} times the Newtonian term).  With
+// d u^n/df = -(n/3) u^{n+3}, t(f) = F'(f) = t_c - u^3 sum (n_m/3) A_m u^{n_m}
+//   + (1/3) Ah_0 u^2 + (2/3) Ah_1 u + L5 u^3 + L6 u^2 (1 - ln u)
+//   - (34/9) Ae u^{43/3}.
 struct Part {
   int status;
   int k_lo, k_hi;   // support in grid bins (k_hi < k_lo: empty)
@@ -107,6 +116,9 @@ struct Part {
   double piMs;      // pi G M / c^3 [s]
   dd tc;            // coalescence time [s]
   dd A[4];          // PN phase coefficients for u^5, u^3, u^2, u^1 [turns]
+  double Ah[2];     // 3PN u^{-1} and 3.5PN u^{-2} coefficients [turns]
+  double Fc, L5, L6;   // 2.5PN constant, ln f and u^{-1} ln f coefficients [turns]
+  dd Ae;            // eccentric u^{34/3} coefficient [turns]; 0 when circular
   double kx, ky, kz;            // propagation direction
   double Pr[6], Pi[6];          // polarisation tensor xx, yy, zz, xy, xz, yz
   double Rcb, lam;              // R cos(beta) [s], lambda
@@ -120,20 +132,38 @@ struct Part {
   double lc_f0, lc_fdot;   // linear chirp: f(t) = f0 + fdot t
 };
 
-__device__ constexpr int kPow[4] = {5, 3, 2, 1};
 
 // FP64 t(f) (accurate to ~1e-8 s; enough for the response and the support)
-__device__ inline double time_of_freq_u(const Part& p, double u) {
+// t(f) given u = f^{-1/3}, w = f^{-1/9} and ln f (w and ln f are read by the
+// TaylorF2 model only)
+__device__ inline double time_of_freq_uw(const Part& p, double u, double w, double lnf) {
   double u2 = u * u;
   double s = u * (-(1.0 / 3.0) * p.A[3].hi +
                   u * (-(2.0 / 3.0) * p.A[2].hi +
                        u * (-p.A[1].hi + u2 * (-(5.0 / 3.0) * p.A[0].hi))));
-  return p.tc.hi + (p.tc.lo + u2 * u * s);
+  double t = u2 * u * s;
+  if (p.model == kModelTF2) {
+    // 1 - ln u = 1 + ln f / 3
+    t += u * ((2.0 / 3.0) * p.Ah[1] +
+              u * ((1.0 / 3.0) * p.Ah[0] + p.L6 * fma(lnf, 1.0 / 3.0, 1.0) + u * p.L5));
+    const double u7 = u2 * u2 * u2 * u;
+    t -= (34.0 / 9.0) * p.Ae.hi * (u7 * u7 * w);   // u^{43/3}
+  }
+  return p.tc.hi + (p.tc.lo + t);
+}
+__device__ inline double time_of_freq_u(const Part& p, double u) {
+  if (p.model != kModelTF2) return time_of_freq_uw(p, u, 0.0, 0.0);
+  return time_of_freq_uw(p, u, cbrt(u), -3.0 * log(u));
 }
 // t(f) given f and u = f^{-1/3} (the linear chirp uses f only)
 __device__ inline double time_of_freq_fu(const Part& p, double f, double u) {
   if (p.model == kModelLinearChirp) return (f - p.lc_f0) / p.lc_fdot;
   return time_of_freq_u(p, u);
+}
+// the same with w = f^{-1/9} and ln f from the stream's grid table
+__device__ inline double time_of_freq_fuw(const Part& p, double f, double u, double2 wl) {
+  if (p.model == kModelLinearChirp) return (f - p.lc_f0) / p.lc_fdot;
+  return time_of_freq_uw(p, u, wl.x, wl.y);
 }
 __device__ inline double time_of_freq(const Part& p, double f) {
   if (p.model == kModelLinearChirp) return (f - p.lc_f0) / p.lc_fdot;
@@ -159,8 +189,14 @@ __device__ inline void part_init(Part& p, const double* th, int model = kModelTF
   for (int i = 0; i < 8; ++i) fin = fin && isfinite(th[i]);
   double Mc = th[0], q = th[1], f0 = th[2];
   p.f0 = f0;
+  // eccentricity: circular, or 0 < e0 <= 0.3 (the TaylorF2 model only)
+  const double e0 = th[7];
+  const bool ecc_ok = e0 == 0.0 || (p.model == kModelTF2 && e0 > 0.0 && e0 <= 0.3);
+  p.Ah[0] = p.Ah[1] = 0.0;
+  p.Fc = p.L5 = p.L6 = 0.0;
+  p.Ae = mkdd(0.0);
   if (p.model == kModelLinearChirp) {
-    if (!fin || !(Mc > 0.0) || !(f0 > 0.0) || th[7] != 0.0) return;
+    if (!fin || !(Mc > 0.0) || !(f0 > 0.0) || !ecc_ok) return;
     p.piMs = 0.0;   // no last stable orbit
     p.tc = mkdd(0.0);
     for (int m = 0; m < 4; ++m) p.A[m] = mkdd(0.0);
@@ -169,7 +205,7 @@ __device__ inline void part_init(Part& p, const double* th, int model = kModelTF
     part_sky(p, th);
     return;
   }
-  if (!fin || !(Mc > 0.0) || !(q >= 1.0) || !(f0 > 0.0) || th[7] != 0.0) return;
+  if (!fin || !(Mc > 0.0) || !(q >= 1.0) || !(f0 > 0.0) || !ecc_ok) return;
   // eta = q/(1+q)^2 ; M = Mc eta^{-3/5}
   dd onepq = dd_two_sum(1.0, q);
   dd eta = dd_div(mkdd(q), onepq * onepq);
@@ -204,14 +240,152 @@ __device__ inline void part_init(Part& p, const double* th, int model = kModelTF
   p.A[1] = pre * phi2 * c3;
   p.A[2] = pre * phi3 * c2;
   p.A[3] = pre * phi4 * c;
-  // t_c: t(f0) = 0  =>  t_c = u0^3 sum (n_k/3) A_k u0^{n_k}
   dd u0 = dd_rcbrt(mkdd(f0));
+  if (pn) {
+    // 2.5, 3 and 3.5PN with ln(v/v_lso) = (ln(pi M) + ln f)/3 + (1/2) ln 6 and
+    // ln(4v) = ln 4 + (ln(pi M) + ln f)/3;  v = (pi M)^{1/3} u^{-1}
+    const double et = dd_val(eta), P = dd_val(pre), ic = 1.0 / dd_val(c);
+    const double lpm = log(p.piMs);
+    const double phi5 = kPi * (38645.0 / 756.0 - 65.0 / 9.0 * et);
+    const double phi6c = 11583231236531.0 / 4694215680.0 - 640.0 / 3.0 * kPi * kPi -
+                         6848.0 / 21.0 * 0.57721566490153286061 +
+                         (-15737765635.0 / 3048192.0 + 2255.0 / 12.0 * kPi * kPi) * et +
+                         76055.0 / 1728.0 * et * et - 127825.0 / 1296.0 * et * et * et;
+    const double phi6l = -6848.0 / 21.0;
+    const double phi7 = kPi * (77096675.0 / 254016.0 + 378515.0 / 1512.0 * et -
+                               74045.0 / 756.0 * et * et);
+    p.Fc = P * phi5 * (1.0 + 1.5 * log(6.0) + lpm);
+    p.L5 = P * phi5;
+    p.Ah[0] = P * ic * (phi6c + phi6l * (log(4.0) + lpm * (1.0 / 3.0)));
+    p.L6 = P * ic * phi6l * (1.0 / 3.0);
+    p.Ah[1] = P * phi7 * ic * ic;
+    if (e0 != 0.0) {
+      // -(2355/1462) e0^2 (f/f0)^{-19/9} P v^{-5} = Ae u^{34/3}:
+      // Ae = -(2355/1462) e0^2 P c^5 f0^{19/9}, f0^{19/9} = f0^2 (f0^{1/3})^{1/3}
+      const dd f013 = dd_div(mkdd(1.0), u0);
+      const dd f019 = dd_div(mkdd(1.0), dd_rcbrt(f013));
+      const dd e2 = dd_prod(e0, e0);
+      p.Ae = dd_div(mkdd(-2355.0), mkdd(1462.0)) * e2 * pre * c5 * (mkdd(f0) * f0 * f019);
+    }
+  }
+  // t_c: t(f0) = 0  =>  t_c = -(the u0 terms of t above)
   dd u02 = u0 * u0;
   dd s = u0 * (dd_div(p.A[3], mkdd(3.0)) +
             u0 * (dd_div(p.A[2] * 2.0, mkdd(3.0)) +
                   u0 * (p.A[1] + u02 * dd_div(p.A[0] * 5.0, mkdd(3.0)))));
   p.tc = u02 * u0 * s;
+  if (pn) {
+    const double ud = dd_val(u0);
+    p.tc = p.tc - mkdd(ud * ((2.0 / 3.0) * p.Ah[1] +
+                             ud * ((1.0 / 3.0) * p.Ah[0] + p.L6 * (1.0 - log(ud)) +
+                                   ud * p.L5)));
+    if (e0 != 0.0) {
+      // + (34/9) Ae u0^{43/3}, u0^{1/3} = (f0^{1/3})^{-1/3}
+      const dd w = dd_rcbrt(dd_div(mkdd(1.0), u0));
+      const dd u04 = u02 * u02, u07 = u04 * u02 * u0;
+      p.tc = p.tc + dd_div(p.Ae * 34.0 * (u07 * u07 * w), mkdd(9.0));
+    }
+  }
   part_sky(p, th);
+}
+
+// Compile-time coefficients of the bin-unit derivatives of the PN phase:
+// row m < 7 for the powers f^{p_m} (u^n = f^{-n/3}: p = -5/3, -1, -2/3,
+// -1/3, 1/3, 2/3 and -34/9), whose r-th derivative is f^{p-r} times the
+// falling factorial (p)_r; row 7 for ln f, with r-th derivative
+// (-1)^{r-1} (r-1)! f^{-r}; rows 8, 9 for f^{1/3} ln f, whose r-th
+// derivative is f^{1/3-r} (Q_r + P_r ln f), P_{r+1} = (1/3 - r) P_r,
+// Q_{r+1} = (1/3 - r) Q_r + P_r, P_0 = 1, Q_0 = 0 (row 8: Q, row 9: P).
+struct PnCoef {
+  double c[10][8];
+};
+__host__ __device__ constexpr PnCoef pn_coef() {
+  PnCoef k{};
+  const double pw[7] = {-5.0 / 3.0, -1.0, -2.0 / 3.0, -1.0 / 3.0, 1.0 / 3.0, 2.0 / 3.0,
+                        -34.0 / 9.0};
+  for (int m = 0; m < 7; ++m) {
+    double c = 1.0;
+    for (int r = 0; r < 8; ++r) {
+      k.c[m][r] = c;
+      c *= pw[m] - (double)r;
+    }
+  }
+  double c = 1.0;
+  k.c[7][0] = 0.0;
+  for (int r = 1; r < 8; ++r) {
+    k.c[7][r] = c;
+    c *= -(double)r;
+  }
+  double P = 1.0, Q = 0.0;
+  for (int r = 0; r < 8; ++r) {
+    k.c[8][r] = Q;
+    k.c[9][r] = P;
+    Q = (1.0 / 3.0 - (double)r) * Q + P;
+    P = (1.0 / 3.0 - (double)r) * P;
+  }
+  return k;
+}
+__device__ constexpr PnCoef kPnCoef = pn_coef();
+
+// Bin-unit derivatives of the PN phase (without t_c f - 1/8) at frequency f:
+// F[r] = F_pn^{(r)}(f) df^r for r < R64 in FP64 (added to F) and for
+// R64 <= r < R in FP32 (added to F32), given u = f^{-1/3}, w = f^{-1/9} and
+// ln f.  Each term's value is formed once; order r is then
+// (df/f)^r sum_m c[m][r] b_m with the compile-time coefficients above.
+template <int R64, int R>
+__device__ __forceinline__ void pn_bin_derivs(const Part& p, double f, double u, double w,
+                                              double lnf, double df, double* F, float* F32) {
+  const double rdf = df * (u * u * u);   // df / f
+  const double u2 = u * u, u4 = u2 * u2;
+  constexpr int NB = 10;
+  double b[NB];
+  b[0] = p.A[0].hi * (u4 * u);
+  b[1] = p.A[1].hi * (u2 * u);
+  b[2] = p.A[2].hi * u2;
+  b[3] = p.A[3].hi * u;
+  const bool tf2 = p.model == kModelTF2;
+  if (tf2) {
+    const double iu = f * u2;   // f^{1/3}
+    b[4] = p.Ah[0] * iu;
+    b[5] = p.Ah[1] * (iu * iu);
+    b[6] = p.Ae.hi * (u4 * u4 * u2 * u * w);   // u^{34/3}
+    b[7] = p.L5;
+    b[8] = p.L6 * iu;
+    b[9] = b[8] * lnf;
+    F[0] += ((b[0] + b[1]) + (b[2] + b[3])) + ((b[4] + b[5]) + b[6]) +
+            ((p.Fc + p.L5 * lnf) + b[9]);
+  } else {
+#pragma unroll
+    for (int m = 4; m < NB; ++m) b[m] = 0.0;
+    F[0] += (b[0] + b[1]) + (b[2] + b[3]);
+  }
+  double rp = 1.0;
+#pragma unroll
+  for (int r = 1; r < R64; ++r) {
+    rp *= rdf;
+    double sr = 0.0;
+#pragma unroll
+    for (int m = 0; m < NB; ++m) sr = fma(kPnCoef.c[m][r], b[m], sr);
+    F[r] += sr * rp;
+  }
+  if constexpr (R > R64) {
+    float b32[NB];
+#pragma unroll
+    for (int m = 0; m < NB; ++m) b32[m] = (float)b[m];
+    const float rdf32 = (float)rdf;
+    float rp32 = (float)(rp * rdf);   // (df/f)^R64, normal in FP32 for df/f > 1e-7
+#pragma unroll
+    for (int r = R64; r < R; ++r) {
+      float sr = 0.f;
+#pragma unroll
+      for (int m = 0; m < NB; ++m) sr = fmaf((float)kPnCoef.c[m][r], b32[m], sr);
+      // (sum) (df/f)^R64 (df/f)^{r-R64}: the sum first keeps it normal
+      float v = sr * rp32;
+#pragma unroll
+      for (int q = R64; q < r; ++q) v *= rdf32;
+      F32[r] += v;
+    }
+  }
 }
 
 // Sky position and polarisation of a particle (theta[3..6]); marks it valid.
@@ -593,17 +767,32 @@ __device__ inline double doppler_delay(const Part& p, double t) {
 // ------------------------------------------------------ per-bin FP64 model
 // Reduced total phase (turns, in [-1/2, 1/2)) of bin f (dd) together with
 // t(f): Phi = F(f) + f k.p0(t(f)); the large F is summed in double-double.
-__device__ inline double phase_turns_fp64(const Part& p, dd f, double& t_out) {
-  dd F;
+// Unreduced phase F(f) = Psi(f)/(2 pi) in turns, double-double, without the
+// Doppler term: the terms of up to ~1e7 turns (orders 0-2PN, the eccentric
+// one, t_c f) in double-double, the 2.5-3.5PN ones (< 1e3 turns) in FP64.
+__device__ inline dd pn_phase_dd(const Part& p, dd f) {
   if (p.model == kModelLinearChirp) {   // (f - f0)^2 / (2 fdot) - 1/8
     const dd x = f - mkdd(p.lc_f0);
-    F = dd_div(x * x, mkdd(2.0 * p.lc_fdot)) - mkdd(0.125);
-  } else {
-    dd u = dd_rcbrt(f);
-    dd u2 = u * u;
-    dd Fp = u * (p.A[3] + u * (p.A[2] + u * (p.A[1] + u2 * p.A[0])));
-    F = f * p.tc + Fp - mkdd(0.125);
+    return dd_div(x * x, mkdd(2.0 * p.lc_fdot)) - mkdd(0.125);
   }
+  const dd u = dd_rcbrt(f);
+  const dd u2 = u * u;
+  const dd Fp = u * (p.A[3] + u * (p.A[2] + u * (p.A[1] + u2 * p.A[0])));
+  dd F = f * p.tc + Fp - mkdd(0.125);
+  if (p.model != kModelTF2) return F;
+  const double iu = 1.0 / dd_val(u), lnf = log(dd_val(f));
+  F = F + mkdd(p.Fc + p.L5 * lnf + iu * (p.Ah[0] + p.L6 * lnf + iu * p.Ah[1]));
+  if (p.Ae.hi != 0.0) {
+    // u^{34/3} = u^11 u^{1/3}, u^{1/3} = (f^{1/3})^{-1/3}
+    const dd w = dd_rcbrt(dd_div(mkdd(1.0), u));
+    const dd u4 = u2 * u2;
+    F = F + p.Ae * (u4 * u4 * u2 * u * w);
+  }
+  return F;
+}
+
+__device__ inline double phase_turns_fp64(const Part& p, dd f, double& t_out) {
+  const dd F = pn_phase_dd(p, f);
   double n = rint(F.hi);
   double fr = dd_val(F - mkdd(n));
   double fd = dd_val(f);

@@ -65,6 +65,9 @@ struct StreamDesc {
   // 2^e <= W0 < 2^(e+1)
   const float4* wdf;
   const float2* wTdf;
+  // grid table: (f_k^{-1/9}, ln f_k) per bin, FP64 (the TaylorF2 phase's
+  // eccentric power and logarithms at phase anchors)
+  const double2* fz;
 };
 
 // Everything a main kernel needs; all pointers are device memory.
@@ -100,10 +103,11 @@ __host__ __device__ inline const int* edges_of(const StreamDesc& d, const int* e
 
 // Swarm state on the device (all arrays device memory).  Particles of swarm
 // s are off[s] .. off[s+1]-1.
-constexpr int kPsoDims = 7;      // searched dimensions (e0 stays 0)
+constexpr int kPsoDimsCirc = 7;  // searched dimensions without e0 (dimension 7)
 constexpr int kPsoHyper = 11;    // Omega, Phi_P, Phi_G, eps[8] per swarm
 struct PsoArgs {
   int P, S;
+  int ndim;           // searched dimensions: 7, or 8 when e0's prior has width
   const int64_t* off;
   double* pos;        // P x 8
   double* vel;        // P x 8

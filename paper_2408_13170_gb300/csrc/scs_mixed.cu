@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(128, kT ? 3 : 4) k_main_mixed(EvalArgs a) {
       nb = min(nb, warp_min(L.e_cut2 == kNoEdge ? kNoEdge : L.e_cut2 - k0));
       if (L.act && k0 == L.next_phase && k0 < L.ke) {
         PhaseAnchor an;
-        phase_anchor(*L.pp, k0, f_first, df, sd.idf, an);
+        phase_anchor(*L.pp, k0, f_first, df, sd.idf, sd.fz, an);
 #pragma unroll
         for (int r = 0; r <= kOrd; ++r) L.d[r] = an.d[r];
         L.al0 = an.al0;

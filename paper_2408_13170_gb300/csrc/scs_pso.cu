@@ -51,7 +51,7 @@ __global__ void k_pso_init(const PsoArgs a) {
   if (p >= a.P) return;
   for (int d = 0; d < 8; ++d) {
     double x = a.lo[d], v = 0.0;
-    if (d < kPsoDims) {
+    if (d < a.ndim) {
       uint32_t c[4] = {(uint32_t)p, 0xFFFFFFFFu, (uint32_t)d, 1u};
       philox4x32_10(c, a.key0, a.key1);
       double w = a.hi[d] - a.lo[d];
@@ -283,7 +283,7 @@ __global__ void k_pso_move(const PsoArgs a) {
   const int s = swarm_of(a.off, a.S, p);
   const double* h = a.hyper + kPsoHyper * s;   // Omega, Phi_P, Phi_G, eps[8]
   const uint32_t it = (uint32_t)*a.iter;
-  for (int d = 0; d < kPsoDims; ++d) {
+  for (int d = 0; d < a.ndim; ++d) {
     uint32_t c[4] = {(uint32_t)p, it, (uint32_t)d, 0u};
     philox4x32_10(c, a.key0, a.key1);
     const double rp = unit_open(c[0]), rg = unit_open(c[1]);

@@ -36,13 +36,14 @@ __device__ inline int span_start(int k, int B) { return (k / B) * B; }
 // support, offset t in {B/4, 3B/4, B-1} (clamped to the support).  A span
 // outside the support passes.  Phase: the kernel's own fixed-point
 // polynomial against the exact (double-double) phase.
-__device__ bool phase_check(const Part& p, int B, int s, int t, double f_first, double df) {
+__device__ bool phase_check(const Part& p, int B, int s, int t, double f_first, double df,
+                            const double2* fz) {
   const int k = s == 0 ? p.k_lo : (s == 1 ? (p.k_lo + p.k_hi) / 2 : p.k_hi);
   const int ka = span_start(k, B);
   const int jlo = max(0, p.k_lo - ka), jhi = min(B - 1, p.k_hi - ka);
   if (jhi < jlo) return true;
   PhaseAnchor an;
-  phase_anchor(p, ka, f_first, df, 1.0 / df, an);
+  phase_anchor(p, ka, f_first, df, 1.0 / df, fz, an);
   const int jt = t == 0 ? B / 4 : (t == 1 ? (3 * B) / 4 : B - 1);
   const int j = min(max(jt, jlo), jhi);
   double tt;
@@ -254,18 +255,10 @@ __device__ int log2_floor_clamp(double x) {
 __device__ void stride_estimates(const Part& p, double f_first, double df, int* l0, int* lr_cap) {
   double flo = f_first + (double)p.k_lo * df;
   double fhi = f_first + (double)p.k_hi * df;
-  double rdf = df / flo, u = rcbrt(flo), u2 = u * u;
-  double upow[4] = {u2 * u2 * u, u2 * u, u2, u};
-  double d7 = 0.0, T1 = 0.0;
-  for (int m = 0; m < 4; ++m) {
-    double n = (double)kPow[m];
-    double val = p.A[m].hi * upow[m];
-    for (int r = 0; r < 7; ++r) {
-      if (r == 2) T1 += val / df;   // t' df = F'' df^2 / df
-      val *= -(n + 3.0 * r) * (1.0 / 3.0) * rdf;
-    }
-    d7 += val;
-  }
+  double Fd[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  const double ulo = rcbrt(flo);
+  pn_bin_derivs<8, 8>(p, flo, ulo, cbrt(ulo), log(flo), df, Fd, nullptr);
+  const double d7 = Fd[7], T1 = Fd[2] / df;   // t' df = F'' df^2 / df
   double Bpn = pow(5040.0 * 0.5 * kTolPhase / fmax(fabs(d7), 1e-300), 1.0 / 7.0);
   double wdop = kOmega * fabs(T1);
   double Bdop = pow(5040.0 * 0.5 * kTolPhase / (fhi * p.Rcb + 1e-30), 1.0 / 7.0) /
@@ -323,6 +316,7 @@ __global__ void __launch_bounds__(kSetupThreads) k_setup(const double* params, i
     const double f_first = mine ? streams[p.sid].f_first : 0.0;
     const double df = mine ? streams[p.sid].df : 0.0;
     const bool withT = mine && streams[p.sid].t32 != nullptr;
+    const double2* fz = mine ? streams[p.sid].fz : nullptr;
     for (int pass = 0; pass < 2; ++pass) {   // 0: phase stride, 1: response sub-span
       if (warp == 0) s_done[lane] = !(mine && s_l[lane] > 0);   // 2^0 needs no check
       for (;;) {
@@ -330,7 +324,7 @@ __global__ void __launch_bounds__(kSetupThreads) k_setup(const double* params, i
         __syncthreads();
         const int l = s_l[lane];
         if (!s_done[lane]) {
-          const bool ok = pass == 0 ? phase_check(p, 1 << l, warp / 3, warp % 3, f_first, df)
+          const bool ok = pass == 0 ? phase_check(p, 1 << l, warp / 3, warp % 3, f_first, df, fz)
                                     : resp_check(p, 1 << l, warp / 3, warp % 3, f_first, df,
                                                  withT);
           if (!ok) atomicOr(&s_fail[lane], 1u << warp);
@@ -554,11 +548,17 @@ constexpr float kEpsInterp = 1e-13f;
 // contiguous run of anchors, joined by a block scan), then per thread a
 // contiguous run of interior edges: the offset c_n - C[a-1] is carried in
 // double-float from one target to the next and
-// kappa_n - k_{a-1} = (c_n - C[a-1]) (k_a - k_{a-1}) / (C[a] - C[a-1]).
-// An edge within eps Cl / slope bins of an integer is either reported
+// kappa_n - k_{a-1} = (c_n - C[a-1]) (k_a - k_{a-1}) / (C[a] - C[a-1]);
+// the edge is ceil(kappa_n - 2^-20): a kappa that is an integer in exact
+// arithmetic (a support shorter than one anchor stride gives
+// kappa_n = k_lo + n (k_hi - k_lo) / N) starts its segment at that integer
+// whatever the last bit of its rounding.
+// An edge whose kappa_n - 2^-20 lies within eps Cl / slope bins of an
+// integer is either reported
 // (returns true, block-uniform; exact = false) or recomputed with the
 // definition's FP64 arithmetic (exact = true).
 constexpr int kBT = 128;
+constexpr double kSnap = 0x1p-20;   // bins
 
 __device__ bool bounds_edges(const Part& p, int N, int nanch, const double* H, double* C,
                              int* e, bool exact, float eps, double* s_warp) {
@@ -645,7 +645,7 @@ __device__ bool bounds_edges(const Part& p, int N, int nanch, const double* H, d
       }
       const dfl kap = num * rec;   // kappa_n - k1 in bins
       const float r = rintf(kap.hi);
-      const float d = (kap.hi - r) + kap.lo;
+      const float d = ((kap.hi - r) + kap.lo) - (float)kSnap;   // kappa - 2^-20 - (k1 + r)
       int ek = k1 + (int)r + (d > 0.f ? 1 : 0);
       if (!(fabsf(d) >= guard)) {
         if (exact) {   // the definition's arithmetic for this edge
@@ -655,7 +655,7 @@ __device__ bool bounds_edges(const Part& p, int N, int nanch, const double* H, d
           const int e2 = min(p.k_lo + ae * kSnr2Stride, p.k_hi);
           const double nm = __dsub_rn(cn, C[ae - 1]), dn = __dsub_rn(C[ae], C[ae - 1]);
           const double fr = dn > 0.0 ? __ddiv_rn(nm, dn) : 0.0;
-          ek = (int)ceil(__dadd_rn((double)e1, __dmul_rn(fr, (double)(e2 - e1))));
+          ek = (int)ceil(__dsub_rn(__dadd_rn((double)e1, __dmul_rn(fr, (double)(e2 - e1))), kSnap));
         } else {
           flag = true;
         }
@@ -709,7 +709,7 @@ __global__ void __launch_bounds__(kBT) k_bounds_df(const Part* part, int P,
     const dfl u1 = df_f(u0) + (r0 * df_f(u0)) * df_const(1.0 / 3.0);
     double u = df_join(u1);
     u = fma(u * fma(-f, u * u * u, 1.0), 1.0 / 3.0, u);
-    const double t = time_of_freq_fu(p, f, u);
+    const double t = time_of_freq_fuw(p, f, u, __ldg(sd.fz + ka));
     const double al = orbit_angle(t);
     const double a64 = (kPi * kArm) * f;
     bad = bad || !(a64 < 3.9);   // beyond the double-float sin/cos reduction
@@ -752,7 +752,7 @@ __global__ void __launch_bounds__(128) k_bounds_h64(const Part* part, const Stre
     const int ka = min(p.k_lo + a * kSnr2Stride, p.k_hi);
     const double f = dd_val(grid_freq_dd(sd.f_first, sd.df, ka));
     const double u = rcbrt(f), u2 = u * u;
-    const double t = time_of_freq_fu(p, f, u);
+    const double t = time_of_freq_fuw(p, f, u, __ldg(sd.fz + ka));
     double sa, ca;
     sincos_small(orbit_angle(t), &sa, &ca);
     double pA, pE, pT = 0.0;
@@ -987,6 +987,15 @@ __global__ void k_to_fp32(const double2* dA64, const double2* dE64, const double
 // Double-float copies of the weights for the equal-SNR^2 anchor power,
 // scaled by 2^-e with 2^e <= W0 < 2^(e+1) (exact scaling; the edges do not
 // depend on a common factor of the template power).
+// Grid table of the powers the TaylorF2 phase needs beyond f^{-1/3}: per bin
+// (f_k^{-1/9}, ln f_k), f_k = f_first + k df, FP64.
+__global__ void k_grid_pow(double f_first, double df, int K, double2* fz) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
+    const double f = f_first + (double)k * df;
+    fz[k] = make_double2(rcbrt(cbrt(f)), log(f));
+  }
+}
+
 __global__ void k_to_wdf(const double2* w64, const double* wT64, int K,
                          const unsigned long long* wmax, float4* wdf, float2* wTdf) {
   const double W0 = __longlong_as_double((long long)*wmax);

@@ -28,6 +28,7 @@ __global__ void __launch_bounds__(128) k_bounds_fix(const Part* part, const Stre
                                                     int* edges_all, double* Hs, double* Cs,
                                                     const int* fb_list, const int* fb_count);
 // double-float copies of the weights for the edges: w / 2^e (A, E) and w_T / 2^e
+__global__ void k_grid_pow(double f_first, double df, int K, double2* fz);
 __global__ void k_to_wdf(const double2* w64, const double* wT64, int K,
                          const unsigned long long* wmax, float4* wdf, float2* wTdf);
 __global__ void k_fixup_slices(const Part* part, const int2* crange, const int64_t* rec_off,

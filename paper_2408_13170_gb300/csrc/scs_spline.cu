@@ -31,18 +31,11 @@ constexpr double kTolSplinePhase = 1e-6;   // turns
 // with a factor 2 for the not-a-knot ends and the lower-order Doppler terms.
 __device__ int spline_log2S(const Part& p, double f_first, double df, int max_log2) {
   const double flo = f_first + (double)p.k_lo * df, fhi = f_first + (double)p.k_hi * df;
-  const double rdf = df / flo, u = rcbrt(flo), u2 = u * u;
-  const double upow[4] = {u2 * u2 * u, u2 * u, u2, u};
-  double d4 = 0.0, T1 = 0.0;
-  for (int m = 0; m < 4; ++m) {
-    const double n = (double)kPow[m];
-    double val = p.A[m].hi * upow[m];
-    for (int r = 0; r < 4; ++r) {
-      if (r == 2) T1 += val / df;
-      val *= -(n + 3.0 * r) * (1.0 / 3.0) * rdf;
-    }
-    d4 += val;
-  }
+  double Fd[5] = {0, 0, 0, 0, 0};
+  const double ulo = rcbrt(flo);
+  pn_bin_derivs<5, 5>(p, flo, ulo, cbrt(ulo), log(flo), df, Fd, nullptr);
+  const double d4 = Fd[4];
+  double T1 = Fd[2] / df;
   if (p.model == kModelLinearChirp) T1 = df / p.lc_fdot;   // its phase is quadratic
   const double w = kOmega * fabs(T1);
   const double phi4 = fabs(d4) + fhi * p.Rcb * w * w * w * w;
@@ -86,16 +79,7 @@ __global__ void k_spline_count(const Part* part, int P, const StreamDesc* stream
 __device__ void node_exact(const Part& p, double f_first, double df, int k, double& phi,
                            double G[6]) {
   const dd f = grid_freq_dd(f_first, df, k);
-  dd F;
-  if (p.model == kModelLinearChirp) {
-    const dd x = f - mkdd(p.lc_f0);
-    F = dd_div(x * x, mkdd(2.0 * p.lc_fdot)) - mkdd(0.125);
-  } else {
-    const dd u = dd_rcbrt(f);
-    const dd u2 = u * u;
-    const dd Fp = u * (p.A[3] + u * (p.A[2] + u * (p.A[1] + u2 * p.A[0])));
-    F = f * p.tc + Fp - mkdd(0.125);
-  }
+  const dd F = pn_phase_dd(p, f);
   const double fd = dd_val(f);
   const double t = time_of_freq(p, fd);
   phi = dd_val(F) + fd * doppler_delay(p, t);

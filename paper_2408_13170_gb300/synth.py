@@ -69,28 +69,28 @@ def noise(S, T_obs, rng):
 
 PRIOR_BOX = {
     # Mc [Msun], q, f0 [Hz], lambda, beta, iota, psi, e0
-    "lo": np.array([10.0, 1.0, 0.012, 0.0, -np.pi / 2, 0.0, 0.0, 0.0]),
-    "hi": np.array([100.0, 8.0, 0.03, 2 * np.pi, np.pi / 2, np.pi, np.pi, 0.0]),
+    "lo": np.array([10.0, 1.0, 0.012, 0.0, -np.pi / 2, 0.0, 0.0, 0.005]),
+    "hi": np.array([100.0, 8.0, 0.03, 2 * np.pi, np.pi / 2, np.pi, np.pi, 0.1]),
 }
 
 
 def draw_particles(P: int, rng, lo=None, hi=None):
     """P particles uniform in the prior box (uniform-in-parameter priors,
-    Table I); e0 = 0."""
+    Table I, e0 in [0.005, 0.1]); a box with lo[7] = hi[7] = 0 gives
+    circular particles."""
     lo = PRIOR_BOX["lo"] if lo is None else np.asarray(lo, dtype=np.float64)
     hi = PRIOR_BOX["hi"] if hi is None else np.asarray(hi, dtype=np.float64)
     u = rng.random((P, 8))
-    th = lo + u * (hi - lo)
-    th[:, 7] = 0.0
-    return th
+    return lo + u * (hi - lo)
 
 
-def injection_params(rng, Mc, q, f0):
-    """Injected source: intrinsic parameters fixed, sky / inclination /
-    polarisation uniform (the phase is maximised away)."""
+def injection_params(rng, Mc, q, f0, e0=0.01):
+    """Injected source: intrinsic parameters fixed (e0 = 0.01 as Table I's
+    GW150914-like source), sky / inclination / polarisation uniform (the
+    phase is maximised away)."""
     return np.array([Mc, q, f0, rng.uniform(0, 2 * np.pi),
                      rng.uniform(-np.pi / 2, np.pi / 2), rng.uniform(0, np.pi),
-                     rng.uniform(0, np.pi), 0.0])
+                     rng.uniform(0, np.pi), e0])
 
 
 # Benchmark / test configurations (sizes, segment counts, seeds).

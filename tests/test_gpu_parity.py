@@ -40,9 +40,9 @@ def stream(T=3e6, fmin=0.0175, fmax=0.0200, seed=21, snr=18.0, inj=(30.0, 1.5, 0
     return d, th
 
 
-def particles(rng, n, f_lo=0.0176, f_hi=0.019, mc=(10, 100), q=(1, 8)):
-    return synth.draw_particles(n, rng, lo=[mc[0], q[0], f_lo, 0, -1.5, 0, 0, 0],
-                                hi=[mc[1], q[1], f_hi, 6.28, 1.5, 3.14, 3.14, 0])
+def particles(rng, n, f_lo=0.0176, f_hi=0.019, mc=(10, 100), q=(1, 8), e0=(0.0, 0.1)):
+    return synth.draw_particles(n, rng, lo=[mc[0], q[0], f_lo, 0, -1.5, 0, 0, e0[0]],
+                                hi=[mc[1], q[1], f_hi, 6.28, 1.5, 3.14, 3.14, e0[1]])
 
 
 @pytest.fixture(scope="module")
@@ -119,10 +119,15 @@ def test_edge_cases(scstat, small):
     d, th, ctx = small
     ctx.set_path(scstat.SCS_MIXED)
     bad = np.array([[-1, 1.5, .018, 0, 0, 0, 0, 0], [30, 1.5, np.inf, 0, 0, 0, 0, 0],
-                    [30, 1.5, 0.025, 0, 0, 0, 0, 0], [30, 1.5, .018, 0, 0, 0, 0, 0.2]])
+                    [30, 1.5, 0.025, 0, 0, 0, 0, 0], [30, 1.5, .018, 0, 0, 0, 0, 0.35],
+                    [30, 1.5, .018, 0, 0, 0, 0, -0.01], [30, 1.5, .018, 0, 0, 0, 0, 0.3]])
     ctx.set_segments(0, 4, scstat.SCS_EQUAL_WIDTH)
     s = ctx.eval(0, bad)
     assert np.isneginf(s[0]) and np.isneginf(s[1]) and s[2] == 0.0 and np.isneginf(s[3])
+    assert np.isneginf(s[4]) and s[5] > 0.0   # e0 in [0, 0.3]
+    ref = oracle.evaluate(d, bad, 4)
+    assert np.array_equal(np.isneginf(s), np.isneginf(ref))
+    assert abs(s[5] - ref[5]) <= TOL32 * abs(ref[5])
     for path in (scstat.SCS_FP64, scstat.SCS_MIXED):
         ctx.set_path(path)
         one = ctx.eval(0, th[:1])

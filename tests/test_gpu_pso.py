@@ -17,8 +17,8 @@ from paper_2408_13170_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 TOL = {"fp64": 1e-10, "mixed": 1e-5}
-LO = np.array([10.0, 1.0, 0.0176, 0.0, -math.pi / 2, 0.0, 0.0, 0.0])
-HI = np.array([100.0, 8.0, 0.0190, 2 * math.pi, math.pi / 2, math.pi, math.pi, 0.0])
+LO = np.array([10.0, 1.0, 0.0176, 0.0, -math.pi / 2, 0.0, 0.0, 0.005])   # e0 searched
+HI = np.array([100.0, 8.0, 0.0190, 2 * math.pi, math.pi / 2, math.pi, math.pi, 0.1])
 SIZES = [40, 72]
 SEED = 0x1234_5678_9ABC
 
@@ -120,7 +120,7 @@ def test_iterations_match_reference(scstat, datas, path):
                                      SEED, it)
             np.testing.assert_array_equal(cur["pos"], pos)
             np.testing.assert_array_equal(cur["vel"], vel)
-            assert np.all(cur["pos"][:, :7] >= LO[:7]) and np.all(cur["pos"][:, :7] <= HI[:7])
+            assert np.all(cur["pos"] >= LO) and np.all(cur["pos"] <= HI)
             prev = cur
         assert P == len(cur["stat"])
 
@@ -288,7 +288,7 @@ def test_search_ladder_finds_the_injection(scstat):
     hi[:3] = th[:3] * np.array([1.1, 1.2, 1.001])
     lo[3:7] = [0, -math.pi / 2, 0, 0]
     hi[3:7] = [2 * math.pi, math.pi / 2, math.pi, math.pi]
-    lo[7] = hi[7] = 0.0
+    lo[7] = hi[7] = th[7]   # e0 held at the injected value
     with scstat.Context(0, scstat.SCS_MIXED) as ctx:
         ctx.set_data(0, d)
         ctx.set_segments(0, 1, scstat.SCS_EQUAL_SNR2)

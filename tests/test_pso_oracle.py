@@ -162,6 +162,30 @@ def test_init_inside_box():
     assert np.allclose(pos[:, :7].mean(0), (LO + HI)[:7] / 2, atol=0.02 * w[:7].max())
 
 
+
+def test_e0_is_searched_when_its_prior_has_width():
+    """Table I gives e0 a prior range: with lo[7] < hi[7] dimension 7 is
+    drawn, moved and reflected like the others, from its own counters
+    (dimension 7), so dimensions 0-6 are bit for bit those of the run with
+    e0 held fixed."""
+    lo8, hi8 = LO.copy(), HI.copy()
+    lo8[7], hi8[7] = 0.005, 0.1
+    p7, v7 = pso.pso_init(300, LO, HI, 11)
+    p8, v8 = pso.pso_init(300, lo8, hi8, 11)
+    np.testing.assert_array_equal(p7[:, :7], p8[:, :7])
+    np.testing.assert_array_equal(v7[:, :7], v8[:, :7])
+    assert np.all(p8[:, 7] > lo8[7]) and np.all(p8[:, 7] < hi8[7])
+    assert np.all(np.abs(v8[:, 7]) <= 0.1 * (hi8[7] - lo8[7])) and np.all(v8[:, 7] != 0.0)
+    h = _hyper(1, 0.5, 0.2, 0.3, np.array([0.1, 0.05, 5e-8, 0.1, 0.1, 0.2, 0.1, 0.1]))
+    s7, s8 = (p7, v7), (p8, v8)
+    for it in range(5):
+        s7 = pso.pso_step(s7[0], s7[1], s7[0], s7[0][:1], np.zeros(300, int), h, LO, HI, 11, it)
+        s8 = pso.pso_step(s8[0], s8[1], s8[0], s8[0][:1], np.zeros(300, int), h, lo8, hi8, 11, it)
+        np.testing.assert_array_equal(s7[0][:, :7], s8[0][:, :7])
+        assert np.all(s7[0][:, 7] == LO[7])
+        assert np.all(s8[0][:, 7] >= lo8[7]) and np.all(s8[0][:, 7] <= hi8[7])
+        assert np.all(np.abs(s8[1][:, 7]) >= 0.1)   # eps_e0 = 0.1 (Table III)
+
 def test_swarm_climbs_a_concave_objective():
     """Any correct PSO update climbs to the maximum of a smooth concave
     function; a sign error in a pull term or in the bests makes it wander."""
