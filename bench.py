@@ -12,6 +12,12 @@ Workloads (`--workload`, default C2):
       launch.
   C4  the uneven batch: eight streams of 1-4 years, one swarm each; one
       step = one CUDA-graph launch of --pso-iters whole swarm iterations.
+  C5  the false-alarm campaign: four-year streams (noise-only, and with an
+      injection at SNR 15-30, alternating), 65 536 particles on each of the
+      seven ladder levels; one step = one stream, all levels in one batched
+      launch; --streams of the campaign's 128 (default 4).  Per stream and
+      level: the maximum statistic and its particle index, certified by the
+      FP64 path on every particle within twice the error bound of it.
 One step (C1-C3) is one evaluation of every particle of the workload through
 the C ABI, inputs resident on the device; the JSON line also carries the
 same metric end to end (host buffers), the plain FP64 GPU path on the same
@@ -41,7 +47,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "SC-stat particle-evals/s, mixed vs plain FP64 path on GB300, at rel err ≤1e-5"
 DEFAULT_WORKLOAD = "C2"
-WORKLOADS = ("C1", "C2", "C3", "C4")
+WORKLOADS = ("C1", "C2", "C3", "C4", "C5")
 # Algorithmic work of the mixed path per support bin-evaluation (the scope
 # table's count): FP32 issue slots -- phase cubic 3, amplitude 2, response
 # interpolation 8, forming h_A, h_E 12, two complex MACs with d~ 8, norms 5,
@@ -69,7 +75,7 @@ LAUNCHES_PER_STEP = 9   # setup, scan, chunk table, fill, sort, edges, main, 2 x
 # DRAM bytes (read + write) of one two-channel k_main_mixed launch on the
 # one-year workload at full size, per work tile (log2 bins), from an ncu
 # capture of the kernel as built now; emptied whenever the kernel changes.
-MAIN_TRAFFIC_BYTES: dict[int, float] = {11: 73.881856e6 + 24.901888e6}
+MAIN_TRAFFIC_BYTES: dict[int, float] = {11: 74.412032e6 + 25.629952e6}
 
 
 def parse(argv=None):
@@ -97,6 +103,8 @@ def parse(argv=None):
                     help="skip the pipe-rate probes (roofline peaks then nominal)")
     ap.add_argument("--pso-iters", type=int, default=10,
                     help="C4: swarm iterations per captured graph (one step = one graph launch)")
+    ap.add_argument("--streams", type=int, default=4,
+                    help="C5: streams of the campaign evaluated (one timed step each)")
     args = ap.parse_args(argv)
     if args.steps is None:
         args.steps = 5 if args.workload == "C3" else 30
@@ -197,11 +205,15 @@ def oracle_threads():
 class Workload:
     """One data stream and its levels: levels[i] = (N, mode, params[P, 8])."""
 
-    def __init__(self, name, seed_offset=0, channels="AE", particles=None):
+    def __init__(self, name, seed_offset=0, channels="AE", particles=None, stream=1):
         from paper_2408_13170_gb300 import synth
         self.name = name
         self.cfg = dict(synth.CONFIGS[name])
         self.cfg["seed"] = self.cfg["seed"] + seed_offset
+        self.injected = True
+        if name == "C5":   # one stream of the campaign
+            seed, self.injected, snr = synth.c5_stream(stream)
+            self.cfg["seed"], self.cfg["snr"] = seed + seed_offset, snr
         self.channels = channels
         self.d = synth.make_stream(self.cfg, channels=channels)
         self.inj = synth.injection_params(self.d["rng"], *self.cfg["inj"])
@@ -230,6 +242,11 @@ class Workload:
             return (f"C3: four-year stream T={c['T_obs']:.3g} s, K={self.K} bins x TDI {ch}; "
                     f"hierarchy N={self.Ns} {seg}, {self.P} particles per level uniform in "
                     f"the prior box (one batched launch); injection SNR {c['snr']}")
+        if self.name == "C5":
+            return (f"C5: false-alarm campaign, four-year streams T={c['T_obs']:.3g} s, "
+                    f"K={self.K} bins x TDI {ch}; hierarchy N={self.Ns} {seg}, {self.P} "
+                    f"particles per level uniform in the prior box (one batched launch per "
+                    f"stream); noise-only streams alternating with injections at SNR 15-30")
         span = "one-year stream" if self.name == "C2" else "short stream"
         return (f"{self.name}: {span} T={c['T_obs']:.3g} s, K={self.K} bins x TDI {ch}; "
                 f"P={self.P} particles uniform in the prior box; N={self.Ns[0]} {seg} "
@@ -244,12 +261,14 @@ class Workload:
         dh["E"] = d["E"].copy()
         if d.get("T") is not None:
             dh["T"] = d["T"].copy()
-        oracle.inject(self.inj, d["f_first"], d["df"], d["K"], d["T_obs"], d["SA"], d["SE"],
-                      self.cfg["snr"], dh["A"], dh["E"], T=dh.get("T"), ST=d.get("ST"))
+        if self.injected:
+            oracle.inject(self.inj, d["f_first"], d["df"], d["K"], d["T_obs"], d["SA"],
+                          d["SE"], self.cfg["snr"], dh["A"], dh["E"], T=dh.get("T"),
+                          ST=d.get("ST"))
         return dh
 
 
-DEFAULT_CPU_SAMPLE = {"C1": 256, "C2": 48, "C3": 112}
+DEFAULT_CPU_SAMPLE = {"C1": 256, "C2": 48, "C3": 112, "C5": 112}
 
 
 def run_reference(args, rank, world):
@@ -588,6 +607,152 @@ def run_ours(args, rank, world, local):
     print(json.dumps(out))
 
 
+def run_campaign(args, rank, world, local):
+    """C5, the false-alarm campaign: --streams four-year streams (rank r of N
+    takes streams r, r + N, ...), each one timed step: 65 536 particles on
+    each of the seven ladder levels in one batched launch, inputs resident on
+    the device, L2 flushed before it.  Per stream and level the maximum and
+    its index; every particle within twice the 1e-5 error bound of the
+    maximum is re-scored by the FP64 path (certified argmax).  The same
+    streams are then evaluated end to end with host buffers."""
+    import torch
+    from paper_2408_13170_gb300 import scstat, synth
+    assert torch.cuda.is_available(), "bench needs a CUDA device"
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    mine = list(range(rank, args.streams, world))
+    ctx = scstat.Context(local, scstat.SCS_MIXED)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    tile = None
+    times, e2e_times, per_stream, stage = [], [], [], []
+    bin_evals, anchors = [], []
+    n_part = 0
+    clocks = ClockSampler(local)
+    clocks_on = False
+    for j in mine:
+        w = Workload("C5", channels=args.channels, particles=args.particles, stream=j)
+        P_level, nl = w.P, len(w.Ns)
+        P = P_level * nl
+        sids = list(range(nl))
+        offs = np.arange(nl + 1, dtype=np.int64) * P_level
+        for s, N in zip(sids, w.Ns):
+            ctx.set_data(s, w.d)
+            if w.injected:
+                ctx.inject(s, w.inj, w.cfg["snr"])
+            ctx.set_segments(s, N, w.mode)
+        hb = w.draw(w.d["rng"])
+        if not w.injected:   # noise-only: no particle sits on a signal
+            hb = np.concatenate([synth.draw_particles(P_level, w.d["rng"]) for _ in w.Ns])
+        params = torch.tensor(hb, device=dev)
+        out = torch.empty(P, dtype=torch.float64, device=dev)
+        if tile is None:     # the autotuner's tile on a middle level of the first stream
+            tl = min(2, nl - 1)
+            tile, _ = scstat.scs_autotune(ctx.h, tl, params[tl * P_level:(tl + 1) * P_level],
+                                          P_level, cuda_stream=stream)
+            scstat.scs_batch_eval(ctx.h, sids, offs, params, out, cuda_stream=stream)  # warm
+        for s in sids:
+            scstat.scs_set_tile(ctx.h, s, tile)
+        scstat.scs_set_profiling(ctx.h, True)
+        if not clocks_on:
+            clocks.start()
+            clocks_on = True
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        scstat.scs_batch_eval(ctx.h, sids, offs, params, out, cuda_stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+        stage.append(scstat.scs_last_timings(ctx.h))
+        scstat.scs_set_profiling(ctx.h, False)
+        n_part += P
+        mixed = out.cpu().numpy().reshape(nl, P_level)
+        # end to end: host params in, host stat out, through the same call
+        host_stat = np.empty(P)
+        pinned = torch.from_numpy(hb).pin_memory().numpy()
+        t0 = time.perf_counter()
+        scstat.scs_batch_eval(ctx.h, sids, offs, pinned, host_stat, cuda_stream=None)
+        e2e_times.append(time.perf_counter() - t0)
+        # units for the roofline
+        be = an = 0.0
+        for s in sids:
+            lo, hi, l2 = ctx.support(s, hb[s * P_level:(s + 1) * P_level])
+            ok = hi >= lo
+            be += float(np.sum(np.where(ok, hi - lo + 1, 0)))
+            lb = (l2 & 0xff).astype(np.int64)
+            an += float(np.sum(np.where(ok, (hi >> lb) - (lo >> lb) + 1, 0)))
+        bin_evals.append(be)
+        anchors.append(an)
+        # per level: maximum, index, FP64-certified argmax
+        levels = []
+        ctx.set_path(scstat.SCS_FP64)
+        for s, N in zip(sids, w.Ns):
+            m = mixed[s]
+            i = int(np.argmax(m))
+            cand = np.flatnonzero(m >= m[i] - 2e-5 * max(abs(m[i]), 1.0))
+            th = hb[s * P_level + cand]
+            f64 = ctx.eval(s, th)
+            best64 = int(cand[int(np.argmax(f64))])
+            err = float(np.max(np.abs(m[cand] - f64) / np.maximum(np.abs(f64), 1.0)))
+            levels.append({"N": N, "max": float(m[i]), "argmax": i,
+                           "candidates": int(len(cand)), "fp64_argmax": best64,
+                           "agree": best64 == i, "max_rel_err_candidates": err})
+        ctx.set_path(scstat.SCS_MIXED)
+        per_stream.append({"stream": j, "seed": w.cfg["seed"], "injected": w.injected,
+                           "snr": w.cfg["snr"] if w.injected else None, "levels": levels,
+                           "ms": 1e3 * times[-1]})
+    ck = clocks.stop() if clocks_on else None
+    t_dev = max_over_ranks(float(np.sum(times)), world, dev)
+    n_all = max_over_ranks(float(n_part), world, dev) * world
+    value = n_all / t_dev
+    e2e_t = max_over_ranks(float(np.sum(e2e_times)), world, dev)
+    if rank != 0:
+        return
+    stages = np.array(stage)
+    sm_mhz = (ck or {}).get("sm_mhz") or 2070.0
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peaks = None
+    if not args.no_peaks:
+        from paper_2408_13170_gb300 import peaks as pk
+        peaks = pk.measure(local)
+    if peaks is None:
+        peaks = {"ffma": {"ops_per_clk_sm": 128.0}, "mufu": {"ops_per_clk_sm": 16.0},
+                 "dfma": {"ops_per_clk_sm": 2.0}, "iadd": {"ops_per_clk_sm": 64.0}}
+    hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+    roof = roofline(peaks, sms, sm_mhz, np.array(bin_evals), np.array(anchors), w.K,
+                    stages[:, 2] / 1e3, args.channels == "AET", hbm)
+    roof["traffic"] = None
+    roof["peak_sm_mhz"] = sm_mhz
+    agree = all(l["agree"] for s in per_stream for l in s["levels"])
+    out = {
+        "metric": METRIC, "value": value, "unit": "particle-evals/s", "n_gpus": world,
+        "steps": len(mine), "warmup": 1, "ms_per_step": 1e3 * t_dev / max(len(mine), 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "dtype_note": "f32/int32 per bin; f64 anchors, edges and segment totals",
+        "data": "synthetic",
+        "config": {"workload": w.describe(), "streams": args.streams,
+                   "P_per_stream": P, "P_per_level": P_level, "K": w.K, "N": w.Ns,
+                   "path": "mixed", "channels": args.channels, "tile_bins": 1 << tile,
+                   "l2": "256 MB buffer written before each timed stream",
+                   "parallelism": f"streams split over {world} rank(s)"},
+        "bin_evals_per_s": float(world * np.sum(bin_evals) / t_dev),
+        "stage_ms": {k: float(v) for k, v in zip(
+            ("setup_worklist", "segment_edges", "main", "fixup"), stages.mean(axis=0))},
+        "roofline": roof,
+        "e2e": {"value": n_all / e2e_t, "unit": "particle-evals/s",
+                "h2d_bytes_per_step": P * 8 * 8, "d2h_bytes_per_step": P * 8},
+        "gpu_launches": LAUNCHES_PER_STEP * len(mine),
+        "clocks": ck,
+        "accuracy": {"certified_argmax_agrees_all": agree},
+        "per_stream": per_stream,
+        "cpu_baseline": None,
+    }
+    print(json.dumps(out))
+
+
 def fp64_leg(args, ctx, w, batches, stat, stream, sids, P_level, mixed_value):
     """The plain FP64 GPU path on the first timed batch: all particles (C1,
     C2) or, per level, a seeded random subset plus every particle whose mixed
@@ -709,6 +874,9 @@ def main():
         if args.channels != "AE":
             raise SystemExit("the uneven-batch workload is defined on TDI A and E only")
         run_swarm(args, rank, world, local)
+        return
+    if args.workload == "C5":
+        run_campaign(args, rank, world, local)
         return
     run_ours(args, rank, world, local)
 

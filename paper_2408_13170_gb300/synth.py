@@ -102,7 +102,25 @@ CONFIGS = {
     "C3": dict(T_obs=1.26e8, f_min=0.01, f_max=0.05, P=16384,
                N=(16384, 4096, 1024, 256, 64, 16, 1), mode="equal_snr2",
                inj=(30.0, 1.5, 0.018), snr=25.0, seed=0),
+    # the false-alarm campaign: 128 four-year streams (noise seeds 1-64;
+    # seeds 65-128 carry an injection at SNR ~ U[15, 30]), 65 536 particles
+    # per ladder level
+    "C5": dict(T_obs=1.26e8, f_min=0.01, f_max=0.05, P=65536,
+               N=(16384, 4096, 1024, 256, 64, 16, 1), mode="equal_snr2",
+               inj=(30.0, 1.5, 0.018), snr=(15.0, 30.0), seed=0, streams=128),
 }
+
+
+def c5_stream(j: int):
+    """Stream j of the false-alarm campaign, in an order that alternates the
+    two kinds so that any prefix holds both: (seed, injected, snr).  Even j:
+    noise-only seed 1 + j/2; odd j: seed 65 + (j-1)/2 with an injection whose
+    SNR is drawn from U[15, 30] by a generator of its own seed."""
+    if j % 2 == 0:
+        return 1 + j // 2, False, 0.0
+    seed = 65 + j // 2
+    lo, hi = CONFIGS["C5"]["snr"]
+    return seed, True, float(np.random.Generator(np.random.PCG64(5000 + seed)).uniform(lo, hi))
 
 
 YEAR = 3.15e7          # seconds (the one-year stream's duration)

@@ -7,7 +7,8 @@ import pytest
 from paper_2408_13170_gb300 import synth
 
 
-@pytest.mark.parametrize("name,K", [("C1", 45001), ("C2", 1260001), ("C3", 5040001)])
+@pytest.mark.parametrize("name,K", [("C1", 45001), ("C2", 1260001), ("C3", 5040001),
+                                    ("C5", 5040001)])
 def test_config_grids(name, K):
     cfg = synth.CONFIGS[name]
     f_first, df, k = synth.grid(cfg["f_min"], cfg["f_max"], cfg["T_obs"])
@@ -51,3 +52,13 @@ def test_three_channel_stream_extends_the_two_channel_one():
     assert not np.any(z["T"])
     with pytest.raises(ValueError):
         synth.make_stream(cfg, channels="XYZ")
+
+
+def test_false_alarm_campaign_order():
+    """The campaign's 128 streams: seeds 1-64 noise-only, 65-128 injected at
+    SNR in [15, 30], each seed once, the two kinds alternating."""
+    st = [synth.c5_stream(j) for j in range(synth.CONFIGS["C5"]["streams"])]
+    assert sorted(s for s, _, _ in st) == list(range(1, 129))
+    assert all(inj == (s > 64) for s, inj, _ in st)
+    assert all(15.0 <= snr <= 30.0 for s, inj, snr in st if inj)
+    assert [inj for _, inj, _ in st[:4]] == [False, True, False, True]
