@@ -419,6 +419,23 @@ int scs_last_timings(scs_ctx *ctx, double *ms);
  * Errors: SCS_EINVAL, SCS_ENODATA (nothing profiled yet), SCS_ECUDA. */
 int scs_last_counters(scs_ctx *ctx, int64_t *out, int n);
 
+/* Index checks of the debug build.  A library compiled with -DSCS_DEBUG
+ * (the package's build.build(debug=True): _build/libscstat_debug.so; the
+ * Python binding loads it when the environment has SCS_DEBUG=1) tests the
+ * indices of the evaluation kernels' accesses -- data and weight loads,
+ * work-list slots, (particle, chunk) records, edge tables, the grid table and
+ * the equal-SNR^2 anchor slots -- against the sizes of their arrays; a
+ * failing test skips its access (so a bad index is reported instead of
+ * reading or writing out of bounds) and the first failure is kept.  This call
+ * waits for the device, then reads and clears that record:
+ *   check  0 if no test failed, else which: 1 data or weight load, 2 work-list
+ *          slot, 3 record, 4 edge table, 5 grid table, 6 anchor slots;
+ *   index  the failing index, clamped to [0, 2^48 - 1] (-1 if none).
+ * Returns SCS_OK in a debug build; otherwise SCS_EUNSUPPORTED with check = 0
+ * (the normal build has no tests).  Errors: SCS_EINVAL (null argument),
+ * SCS_ECUDA. */
+int scs_debug_error(scs_ctx *ctx, int *check, long long *index);
+
 /* scs_eval_stat without any device allocation.  The paper has no
  * counterpart: this entry point exists for callers that cannot call
  * cudaMalloc at evaluation time -- services whose device memory is entirely

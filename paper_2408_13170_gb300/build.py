@@ -15,6 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libscstat.so")
+LIB_DEBUG = os.path.join(OUT, "libscstat_debug.so")   # -DSCS_DEBUG: index checks
 UNITS = ["scs_api", "scs_setup", "scs_mixed", "scs_fp64", "scs_pso", "scs_peaks", "scs_spline"]
 HEADERS = ["scs_device.cuh", "scs_internal.cuh", "scs_anchor.cuh", "scs_setup.cuh", "scs_df.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -37,17 +38,21 @@ def _newest_input() -> float:
     return max(os.path.getmtime(p) for p in paths)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile (if stale) and return the path of libscstat.so."""
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _newest_input():
-        return LIB
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    """Compile (if stale) and return the path of libscstat.so, or with
+    debug=True of libscstat_debug.so (the kernels' index checks compiled in,
+    read by scs_debug_error)."""
+    lib = LIB_DEBUG if debug else LIB
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= _newest_input():
+        return lib
     os.makedirs(OUT, exist_ok=True)
     nvcc = _nvcc()
-    tag = f"{os.getpid()}"
+    tag = f"{os.getpid()}{'d' if debug else ''}"
+    flags = FLAGS + (["-DSCS_DEBUG"] if debug else [])
 
     def compile_unit(u):
         obj = os.path.join(OUT, f"{u}.{tag}.o")
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", os.path.join(SRC, u + ".cu"), "-o", obj]
+        cmd = [nvcc, *ARCH, *flags, "-c", os.path.join(SRC, u + ".cu"), "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -55,21 +60,28 @@ def build(force: bool = False, verbose: bool = False) -> str:
             raise RuntimeError(f"nvcc failed on {u}.cu:\n{r.stderr}")
         return obj, r.stderr
 
-    with ThreadPoolExecutor(len(UNITS)) as ex:
-        results = list(ex.map(compile_unit, UNITS))
+    try:
+        with ThreadPoolExecutor(len(UNITS)) as ex:
+            results = list(ex.map(compile_unit, UNITS))
+    except RuntimeError:
+        for u in UNITS:   # objects of the units that did compile
+            o = os.path.join(OUT, f"{u}.{tag}.o")
+            if os.path.exists(o):
+                os.remove(o)
+        raise
     objs = [o for o, _ in results]
-    tmp = LIB + f".{tag}.tmp"
+    tmp = lib + f".{tag}.tmp"
     r = subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True,
                        text=True)
     for o in objs:
         os.remove(o)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     if verbose:
         for _, log in results:
             print(log)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":

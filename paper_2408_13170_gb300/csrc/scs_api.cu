@@ -301,6 +301,7 @@ struct Prepared {
   int* item_off = nullptr;
   int* list = nullptr;
   int* edges = nullptr;     // equal-SNR^2 edge tables
+  int64_t edges_cap = 0;    // their entries
   bool any_snr2 = false;
   bool any_ae = false, any_t = false;   // streams without / with the third channel
   int s_max = 1;            // record slices per particle in the fix-up
@@ -349,6 +350,7 @@ int prepare_batch(scs_ctx* ctx, const std::vector<BatchPart>& parts, const doubl
   for (const StreamDesc& d : table) max_amax = std::max(max_amax, d.amax);
   if (out.any_snr2 && want_edges) {
     out.edges = (int*)src.get(kSlotEdges, sizeof(int) * etot);
+    out.edges_cap = etot;
     Hs = (double*)src.get(kSlotHs, sizeof(double) * htot);
     Cs = (double*)src.get(kSlotCs, sizeof(double) * htot);
     fb = (int*)src.get(kSlotFb, sizeof(int) * (P + 1));
@@ -425,6 +427,11 @@ int run_batch(scs_ctx* ctx, const Prepared& pr, int P, double* dstat, double* ds
   a.chunk_lo = 0;
   a.chunk_hi = pr.n_chunks;
   a.item_counter = counter;
+#ifdef SCS_DEBUG
+  a.list_cap = pr.bound;
+  a.rec_cap = pr.bound;
+  a.edges_cap = pr.edges_cap;
+#endif
   if (ctx->prof) CK(cudaEventRecord(ctx->ev[2], s));
   if (ctx->path == SCS_MIXED) {
     // one kernel per channel set, each with its own item counter
@@ -473,7 +480,7 @@ int run_batch(scs_ctx* ctx, const Prepared& pr, int P, double* dstat, double* ds
     return SCS_ENOMEM;
   }
   k_fixup_slices<<<(int)(((int64_t)P * pr.s_max + 127) / 128), 128, 0, s>>>(
-      pr.part, pr.crange, pr.nrec, rec, P, pr.s_max, pr.streams, slices, dsx, dsh);
+      pr.part, pr.crange, pr.nrec, rec, pr.bound, P, pr.s_max, pr.streams, slices, dsx, dsh);
   CKLAUNCH();
   k_fixup<<<(P + 31) / 32, 32, 0, s>>>(pr.part, pr.crange, P, pr.s_max, pr.streams, slices,
                                        dstat, dsx, dsh);
@@ -1211,6 +1218,23 @@ int scs_last_counters(scs_ctx* ctx, int64_t* out, int n) {
   const int64_t c[2] = {ctx->prof_P, ctx->prof_edges ? (int64_t)*ctx->prof_host : -1};
   for (int i = 0; i < n; ++i) out[i] = i < 2 ? c[i] : 0;
   return SCS_OK;
+}
+
+int scs_debug_error(scs_ctx* ctx, int* check, long long* index) {
+  if (!ctx || !check || !index) return SCS_EINVAL;
+  int rc = bind(ctx);
+  if (rc) return rc;
+  CK(cudaDeviceSynchronize());
+  unsigned long long v = 0;
+  const unsigned long long u[3] = {dbg_take_setup(), dbg_take_mixed(), dbg_take_fp64()};
+  for (unsigned long long x : u) v = v ? v : x;
+  *check = (int)(v >> 48);
+  *index = v ? (long long)(v & ((1ull << 48) - 1)) : -1;
+#ifdef SCS_DEBUG
+  return SCS_OK;
+#else
+  return SCS_EUNSUPPORTED;
+#endif
 }
 
 int scs_last_timings(scs_ctx* ctx, double* ms) {

@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(128) k_main_fp64(EvalArgs a) {
     const int N = sd.N;
     const int g = item - a.item_off[cg];
     const int slot = g * 32 + lane;
-    const bool has = slot < a.cnt[cg];
+    const bool has = slot < a.cnt[cg] && SCS_IN_BOUNDS(a.list_off[cg] + slot, a.list_cap, kDbgList);
     const int p = has ? a.list[a.list_off[cg] + slot] : -1;
     const int kc0 = c << sd.log2_chunk;
     const int kc1 = min(kc0 + (1 << sd.log2_chunk), sd.K);
@@ -41,6 +41,10 @@ __global__ void __launch_bounds__(128) k_main_fp64(EvalArgs a) {
       pp = a.part[p];
       kb = max(kc0, pp.k_lo);
       ke = min(kc1, pp.k_hi + 1);
+      if (sd.mode == 1 &&
+          !SCS_IN_BOUNDS(sd.edge_base + (int64_t)(p - sd.p_off + 1) * (N + 1) - 1, a.edges_cap,
+                         kDbgEdge))
+        ke = kb;
     }
     const bool act = has && kb < ke;
     const int* e = act ? edges_of(sd, a.edges_all, p) : sd.width_edges;
@@ -57,7 +61,7 @@ __global__ void __launch_bounds__(128) k_main_fp64(EvalArgs a) {
     const int kw0 = warp_min(act ? kb : 0x7fffffff);
     const int kw1 = warp_max(act ? ke : -1);
     for (int k = kw0; k < kw1; ++k) {
-      if (act && k >= kb && k < ke) {
+      if (act && k >= kb && k < ke && SCS_IN_BOUNDS(k, sd.K, kDbgData)) {
         if (k == e_next) {
           // close segment n_cur
           if (head) {
@@ -152,5 +156,7 @@ int occupancy_fp64(int* blocks_per_sm) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_main_fp64, 128, 0) !=
          cudaSuccess;
 }
+
+SCS_DBG_UNIT(fp64)
 
 }  // namespace scs

@@ -92,6 +92,9 @@ struct EvalArgs {
   // per-segment outputs (single-stream calls only; NULL otherwise)
   double* seg_x;
   double* seg_hh;
+#ifdef SCS_DEBUG
+  int64_t list_cap, rec_cap, edges_cap;   // entries of list, rec, edges_all (checks)
+#endif
 };
 
 // segment edge table of particle p (e_0 .. e_N, non-decreasing)
@@ -250,5 +253,47 @@ __device__ inline int advance_segment(const int* e, int N, int n, int k) {
   while (n + 1 <= N && __ldg(e + n + 1) <= k) ++n;
   return n;
 }
+
+// ---- index checks of the debug build (-DSCS_DEBUG) -------------------------
+// SCS_IN_BOUNDS(i, n, id) tests 0 <= i < n.  In a debug build a failing test
+// records (id << 48) | min(i, 2^48 - 1) in its translation unit's error word
+// (the first failure wins), returns false and the caller skips the access, so
+// a bad index is reported instead of faulting; scs_debug_error reads and
+// clears the words.  In the normal build the test is the constant true.
+enum DbgCheck : int {
+  kDbgData = 1,   // a data or weight load: bin < K (+ the FP32 arrays' 32-bin tail)
+  kDbgList,       // a work-list slot inside the call's list
+  kDbgRec,        // a (particle, chunk) record inside the record scratch
+  kDbgEdge,       // a particle's edge table inside the edge scratch
+  kDbgGrid,       // a grid-table read: bin < K
+  kDbgAnchor,     // a particle's equal-SNR^2 anchors fit its anchor slots
+};
+#ifdef SCS_DEBUG
+static __device__ unsigned long long g_dbg_err;
+__device__ __forceinline__ bool dbg_in_bounds(long long i, long long n, int id) {
+  if (i >= 0 && i < n) return true;
+  const unsigned long long m = (1ull << 48) - 1;
+  const unsigned long long ix =
+      i < 0 ? m : ((unsigned long long)i > m ? m : (unsigned long long)i);
+  atomicCAS(&g_dbg_err, 0ull, ((unsigned long long)id << 48) | ix);
+  return false;
+}
+static inline unsigned long long dbg_take_unit() {
+  unsigned long long v = 0, z = 0;
+  if (cudaMemcpyFromSymbol(&v, g_dbg_err, sizeof v) != cudaSuccess) return 0;
+  cudaMemcpyToSymbol(g_dbg_err, &z, sizeof z);
+  return v;
+}
+#define SCS_IN_BOUNDS(i, n, id) ::scs::dbg_in_bounds((long long)(i), (long long)(n), (id))
+#else
+static inline unsigned long long dbg_take_unit() { return 0ull; }
+#define SCS_IN_BOUNDS(i, n, id) true
+#endif
+// the error word of each translation unit with checks, read and cleared
+#define SCS_DBG_UNIT(name) \
+  unsigned long long dbg_take_##name() { return dbg_take_unit(); }
+unsigned long long dbg_take_setup();
+unsigned long long dbg_take_mixed();
+unsigned long long dbg_take_fp64();
 
 }  // namespace scs

@@ -65,6 +65,7 @@ struct Lane {
 
 // the data stream of a work item, as the hot loop needs it
 struct ItemStream {
+  int K;                  // bins of the stream (index checks of the debug build)
   const float4* d32;
   const float2* w32;
   const float4* t32;      // (d~_T, w_T), streams with the third channel
@@ -126,22 +127,25 @@ __device__ __forceinline__ void finish_close(Lane& L, const ItemStream& a, doubl
 template <bool kT, bool kMask>
 __device__ __forceinline__ void run_block(Lane& L, const ItemStream& a, double zs, int k0,
                                           int nb) {
-  float4 dn = __ldg(a.d32 + k0);
-  float2 wn = __ldg(a.w32 + k0);
-  float4 tn;
-  if constexpr (kT) tn = __ldg(a.t32 + k0);
+  float4 dn = make_float4(0.f, 0.f, 0.f, 0.f);
+  float2 wn = make_float2(0.f, 0.f);
+  float4 tn = dn;
+  if (SCS_IN_BOUNDS(k0, a.K + 32, kDbgData)) {
+    dn = __ldg(a.d32 + k0);
+    wn = __ldg(a.w32 + k0);
+    if constexpr (kT) tn = __ldg(a.t32 + k0);
+  }
   const unsigned span = kMask && L.act ? (unsigned)(L.ke - L.kb) : 0u;
 #pragma unroll 2
   for (int i = 0; i < nb; ++i) {
     const int k = k0 + i;
     const float4 dv = dn;
     const float2 wv = wn;
-    dn = __ldg(a.d32 + k + 1);
-    wn = __ldg(a.w32 + k + 1);
-    float4 tv;
-    if constexpr (kT) {
-      tv = tn;
-      tn = __ldg(a.t32 + k + 1);
+    float4 tv = tn;
+    if (SCS_IN_BOUNDS(k + 1, a.K + 32, kDbgData)) {
+      dn = __ldg(a.d32 + k + 1);
+      wn = __ldg(a.w32 + k + 1);
+      if constexpr (kT) tn = __ldg(a.t32 + k + 1);
     }
     const bool m = kMask ? (unsigned)(k - L.kb) < span : true;
     // a segment ends before bin k: keep its block sums, restart them (at
@@ -200,6 +204,7 @@ __global__ void __launch_bounds__(128, kT ? 3 : 4) k_main_mixed(EvalArgs a) {
     const StreamDesc& sd = a.streams[stream_of_chunk(a.streams, a.n_streams, cg)];
     if ((sd.t32 != nullptr) != kT) continue;   // the other kernel's item
     ItemStream is;
+    is.K = sd.K;
     is.d32 = sd.d32;
     is.w32 = sd.w32;
     is.t32 = sd.t32;
@@ -214,7 +219,7 @@ __global__ void __launch_bounds__(128, kT ? 3 : 4) k_main_mixed(EvalArgs a) {
     const int c = cg - sd.chunk_base;   // chunk within the stream
     const int g = item - a.item_off[cg];
     const int slot = g * 32 + lane;
-    const bool has = slot < a.cnt[cg];
+    const bool has = slot < a.cnt[cg] && SCS_IN_BOUNDS(a.list_off[cg] + slot, a.list_cap, kDbgList);
     const int kc0 = c << sd.log2_chunk;
     const int kc1 = min(kc0 + (1 << sd.log2_chunk), sd.K);
     Lane L;
@@ -233,7 +238,14 @@ __global__ void __launch_bounds__(128, kT ? 3 : 4) k_main_mixed(EvalArgs a) {
       L.log2B = L.pp->log2B;
       L.log2Br = L.pp->log2Br;
       first = (L.kb >> L.log2B) << L.log2B;
-      L.rec = a.rec + a.rec_off[L.p] + (c - chunk_of(sd, klo));
+      const int64_t ri = a.rec_off[L.p] + (c - chunk_of(sd, klo));
+      L.rec = a.rec + ri;
+      // debug build: a record or edge table outside its scratch drops the lane
+      if (!SCS_IN_BOUNDS(ri, a.rec_cap, kDbgRec)) L.ke = L.kb;
+      if (sd.mode == 1 &&
+          !SCS_IN_BOUNDS(sd.edge_base + (int64_t)(L.p - sd.p_off + 1) * (sd.N + 1) - 1,
+                         a.edges_cap, kDbgEdge))
+        L.ke = L.kb;
     }
     L.act = has && L.kb < L.ke;
     if (!L.act) first = kNoEdge;
@@ -278,7 +290,7 @@ __global__ void __launch_bounds__(128, kT ? 3 : 4) k_main_mixed(EvalArgs a) {
       // lane's second segment end (one end per lane and block)
       nb = min(BW - (k0 & (BW - 1)), kw1 - k0);
       nb = min(nb, warp_min(L.e_cut2 == kNoEdge ? kNoEdge : L.e_cut2 - k0));
-      if (L.act && k0 == L.next_phase && k0 < L.ke) {
+      if (L.act && k0 == L.next_phase && k0 < L.ke && SCS_IN_BOUNDS(k0, sd.K, kDbgGrid)) {
         PhaseAnchor an;
         phase_anchor(*L.pp, k0, f_first, df, sd.idf, sd.fz, an);
 #pragma unroll
@@ -387,5 +399,7 @@ int occupancy_mixed(int with_t, int* blocks_per_sm) {
                                                                   k_main_mixed<false>, 128, 0)) !=
          cudaSuccess;
 }
+
+SCS_DBG_UNIT(mixed)
 
 }  // namespace scs

@@ -690,6 +690,10 @@ __global__ void __launch_bounds__(kBT) k_bounds_df(const Part* part, int P,
   }
   const int span = p.k_hi - p.k_lo;
   const int nanch = span / kSnr2Stride + 1 + (span % kSnr2Stride != 0 ? 1 : 0);
+  if (!SCS_IN_BOUNDS(nanch - 1, sd.amax, kDbgAnchor)) {   // debug build only
+    for (int n = tid; n <= N; n += kBT) e[n] = 0;
+    return;
+  }
   double* H = Hs + sd.hc_base + lp * sd.amax;
   double* C = Cs + sd.hc_base + lp * sd.amax;
   PowDf pc;
@@ -700,6 +704,7 @@ __global__ void __launch_bounds__(kBT) k_bounds_df(const Part* part, int P,
   bool bad = false;
   for (int a = tid; a < nanch; a += kBT) {
     const int ka = min(p.k_lo + a * kSnr2Stride, p.k_hi);
+    if (!SCS_IN_BOUNDS(ka, sd.K, kDbgGrid)) continue;
     const double f = fma((double)ka, df, f_first);
     // u = f^{-1/3}: FP32 estimate, one Newton step in double-float, one in FP64
     const dfl fd = df_split(f);
@@ -750,6 +755,7 @@ __global__ void __launch_bounds__(128) k_bounds_h64(const Part* part, const Stre
     if (a >= nanch) continue;
     double* H = Hs + sd.hc_base + (int64_t)(gw - sd.p_off) * sd.amax;
     const int ka = min(p.k_lo + a * kSnr2Stride, p.k_hi);
+    if (!SCS_IN_BOUNDS(a, sd.amax, kDbgAnchor) || !SCS_IN_BOUNDS(ka, sd.K, kDbgGrid)) continue;
     const double f = dd_val(grid_freq_dd(sd.f_first, sd.df, ka));
     const double u = rcbrt(f), u2 = u * u;
     const double t = time_of_freq_fuw(p, f, u, __ldg(sd.fz + ka));
@@ -806,8 +812,9 @@ __device__ inline void close_run(int n, double zr, double zi, double hh, int i, 
 }
 
 __global__ void k_fixup_slices(const Part* part, const int2* crange, const int64_t* rec_off,
-                               const Rec* rec, int P, int S_max, const StreamDesc* streams,
-                               SliceSum* out, double* seg_x, double* seg_hh) {
+                               const Rec* rec, int64_t rec_cap, int P, int S_max,
+                               const StreamDesc* streams, SliceSum* out, double* seg_x,
+                               double* seg_hh) {
   constexpr int kBatch = 4;
   constexpr int kVec = sizeof(Rec) / 16;   // 16-byte vectors per record
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -819,6 +826,7 @@ __global__ void k_fixup_slices(const Part* part, const int2* crange, const int64
   const int nrec = cr.y - cr.x + 1;
   const int c0 = j * kSlice, c1 = min(nrec, c0 + kSlice);
   if (c0 >= c1) return;
+  if (!SCS_IN_BOUNDS(rec_off[i] + c1 - 1, rec_cap, kDbgRec)) return;   // debug build only
   const int N = streams[p.sid].N;
   SliceSum sl;
   sl.ups = 0.0;
@@ -1166,5 +1174,7 @@ __global__ void k_edges_out(const Part* part, const StreamDesc* streams, const i
   const Part& pp = part[p];
   out[idx] = pp.status == kInvalid ? -1 : edges_of(streams[pp.sid], edges_all, p)[n];
 }
+
+SCS_DBG_UNIT(setup)
 
 }  // namespace scs

@@ -32,8 +32,9 @@ __global__ void k_grid_pow(double f_first, double df, int K, double2* fz);
 __global__ void k_to_wdf(const double2* w64, const double* wT64, int K,
                          const unsigned long long* wmax, float4* wdf, float2* wTdf);
 __global__ void k_fixup_slices(const Part* part, const int2* crange, const int64_t* rec_off,
-                               const Rec* rec, int P, int S_max, const StreamDesc* streams,
-                               SliceSum* out, double* seg_x, double* seg_hh);
+                               const Rec* rec, int64_t rec_cap, int P, int S_max,
+                               const StreamDesc* streams, SliceSum* out, double* seg_x,
+                               double* seg_hh);
 __global__ void __launch_bounds__(32) k_fixup(const Part* part, const int2* crange, int P,
                                               int S_max, const StreamDesc* streams,
                                               const SliceSum* sl, double* stat, double* seg_x,

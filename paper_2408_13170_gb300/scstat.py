@@ -9,6 +9,7 @@ there is no CPU fallback.
 from __future__ import annotations
 
 import ctypes
+import os
 import threading
 
 import numpy as np
@@ -39,7 +40,8 @@ def lib():
     with _lock:
         if _lib is not None:
             return _lib
-        path = _build.build()
+        # SCS_DEBUG=1: the build with index checks (scs_debug_error)
+        path = _build.build(debug=os.environ.get("SCS_DEBUG") == "1")
         L = ctypes.CDLL(path)
         P, I, I64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
         L.scs_create.argtypes = [ctypes.POINTER(P), I, I]
@@ -78,6 +80,8 @@ def lib():
         L.scs_last_timings.restype = I
         L.scs_last_counters.argtypes = [P, P, I]
         L.scs_last_counters.restype = I
+        L.scs_debug_error.argtypes = [P, P, P]
+        L.scs_debug_error.restype = I
         L.scs_eval_stat_noalloc.argtypes = [P, I, P, I64, P, P]
         L.scs_eval_stat_noalloc.restype = I
         L.scs_batch_eval.argtypes = [P, P, P, I, P, P, P]
@@ -393,6 +397,16 @@ def scs_last_counters(ctx):
     out = np.zeros(2, np.int64)
     _check(ctx, lib().scs_last_counters(ctx, _ptr(out), 2))
     return int(out[0]), int(out[1])
+
+
+def scs_debug_error(ctx):
+    """(is a debug build, failed check number or 0, its index or -1): reads
+    and clears the index-check record of the debug build."""
+    chk, idx = ctypes.c_int(0), ctypes.c_longlong(-1)
+    rc = lib().scs_debug_error(ctx, ctypes.byref(chk), ctypes.byref(idx))
+    if rc not in (SCS_OK, SCS_EUNSUPPORTED):
+        _check(ctx, rc)
+    return rc == SCS_OK, chk.value, idx.value
 
 
 def scs_last_timings(ctx):

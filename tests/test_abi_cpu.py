@@ -39,6 +39,20 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(lib, name), name
 
 
+def test_debug_build_compiles_and_exports_the_boundary():
+    """The -DSCS_DEBUG variant (index checks, scs_debug_error) builds for
+    sm_103a and exports the same entry points; its error reader refuses
+    null arguments before touching a device."""
+    from paper_2408_13170_gb300 import build
+    path = build.build(debug=True)
+    assert path.endswith("libscstat_debug.so")
+    lib = ctypes.CDLL(path)
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    lib.scs_debug_error.argtypes = [ctypes.c_void_p] * 3
+    assert lib.scs_debug_error(None, None, None) == -1   # SCS_EINVAL
+
+
 def test_peak_probe_rejects_bad_arguments():
     """The probe checks its arguments before touching a device."""
     from paper_2408_13170_gb300 import scstat
