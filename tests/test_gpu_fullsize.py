@@ -82,6 +82,13 @@ def test_four_year_stream_levels(scstat, N):
         s32 = ctx.eval(0, th)
         ctx.set_path(scstat.SCS_FP64)
         s64 = ctx.eval(0, th[:48])
+        # the best particle, certified (S-c): every particle within twice the
+        # error bound of the mixed maximum, re-scored by the FP64 path
+        best = int(np.argmax(s32))
+        cand = np.flatnonzero(s32 >= s32[best] - 2 * TOL32 * max(abs(s32[best]), 1.0))
+        c64 = ctx.eval(0, th[cand])
+    assert int(cand[np.argmax(c64)]) == best
+    assert rel(s32[cand], c64) <= TOL32
     assert rel(s32[sample], ref) <= TOL32
     assert rel(s64[sample[:2]], ref[:2]) <= TOL64
     assert rel(s32[:48], s64) <= TOL32
