@@ -73,10 +73,12 @@ __device__ inline void pow_consts(const Part& p, PowDf& c) {
   c.A2 = df_split(p.ax * (1.0 / 24.0));
 }
 
-// sin(x)/x given sin(x) (double-float)
-__device__ __forceinline__ dfl df_sinc_of(dfl x, dfl sx) {
+// sin(x)/x given sin(x) (double-float); one copy for all callers (the code of
+// an anchor power otherwise outgrows the instruction cache)
+__device__ __noinline__ dfl df_sinc_of(dfl x, dfl sx) {
   return fabsf(x.hi) < 0.3f ? df_sinc_small(x) : df_div(sx, x);
 }
+__device__ __noinline__ void df_sincos_one(dfl x, dfl* s, dfl* c) { df_sincos(x, s, c); }
 
 // |R_A|^2, |R_E|^2 and |R_T|^2 of the residual response (the model of
 // response_residual) at a = pi f L and orbit angle alpha, in double-float.
@@ -95,7 +97,7 @@ __device__ __forceinline__ dfl df_sinc_of(dfl x, dfl sx) {
 __device__ inline void response_xyz_df(const PowDf& c, dfl a, dfl al, cdfl& X, cdfl& Y, cdfl& Z,
                                        dfl& s_a, dfl& c_a) {
   dfl sa, ca;
-  df_sincos(al, &sa, &ca);
+  df_sincos_one(al, &sa, &ca);
   const dfl c2a = ca * ca - sa * sa;
   const dfl s2a = df_scale2(ca * sa, 2.f);
   constexpr dfl h3 = df_const(0.86602540378443865);    // sqrt3 / 2
@@ -128,9 +130,9 @@ __device__ inline void response_xyz_df(const PowDf& c, dfl a, dfl al, cdfl& X, c
   ph[2] = -(ph[0] + ph[1]);
   cdfl e[3];
 #pragma unroll
-  for (int i = 0; i < 2; ++i) df_sincos(ph[i], &e[i].im, &e[i].re);
+  for (int i = 0; i < 2; ++i) df_sincos_one(ph[i], &e[i].im, &e[i].re);
   e[2] = cdf_conj(e[0] * e[1]);
-  df_sincos(a, &s_a, &c_a);
+  df_sincos_one(a, &s_a, &c_a);
   const cdfl D{c_a * c_a - s_a * s_a, -df_scale2(s_a * c_a, 2.f)};
   // arms (s, r) with third craft k: (0,1;2), (0,2;1), (1,2;0)
   cdfl U[3], V[3];
