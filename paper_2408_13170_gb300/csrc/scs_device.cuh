@@ -783,10 +783,10 @@ __device__ inline dd pn_phase_dd(const Part& p, dd f) {
   const double iu = 1.0 / dd_val(u), lnf = log(dd_val(f));
   F = F + mkdd(p.Fc + p.L5 * lnf + iu * (p.Ah[0] + p.L6 * lnf + iu * p.Ah[1]));
   if (p.Ae.hi != 0.0) {
-    // u^{34/3} = u^11 u^{1/3}, u^{1/3} = (f^{1/3})^{-1/3}
-    const dd w = dd_rcbrt(dd_div(mkdd(1.0), u));
+    // u^{34/3} = u^12 z^2 with z = u^{-1/3} (no double-double division)
+    const dd z = dd_rcbrt(u);
     const dd u4 = u2 * u2;
-    F = F + p.Ae * (u4 * u4 * u2 * u * w);
+    F = F + p.Ae * ((u4 * u4 * u4) * (z * z));
   }
   return F;
 }
