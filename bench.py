@@ -71,7 +71,12 @@ IMPL_OPS_PER_BIN_AET = 48
 # d~ + float2 w, and a float4 (d~_T, w_T) with the third channel)
 DATA_BYTES_PER_BIN = 24
 DATA_BYTES_PER_BIN_AET = 40
-LAUNCHES_PER_STEP = 9   # setup, scan, chunk table, fill, sort, edges, main, 2 x fix-up
+# kernels of one evaluation: set-up, scan, chunk table, fill, sort, main, two
+# fix-ups, and with equal-SNR^2 segments the three edge kernels (double-float
+# powers, FP64 fallback powers, fallback edges); a swarm iteration adds four
+# (personal bests, swarm bests, move, iteration counter)
+LAUNCHES_EVAL = {0: 8, 1: 11}   # by segmentation: 0 equal width, 1 equal SNR^2
+LAUNCHES_SWARM_UPDATE = 4
 # DRAM bytes (read + write) of one two-channel k_main_mixed launch on the
 # one-year workload at full size, per work tile (log2 bins), from an ncu
 # capture of the kernel as built now; emptied whenever the kernel changes.
@@ -152,13 +157,21 @@ class ClockSampler:
         self.path = f"/tmp/scs_clocks_{os.getpid()}.csv"
 
     def start(self):
+        """Starts sampling every 50 ms and waits (up to 2 s) for the first
+        sample, so that the timed region that follows is covered."""
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, ValueError):
             self.proc = None
+            return
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < 2.0 and self.proc.poll() is None:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.01)
 
     def stop(self):
         if self.proc is None:
@@ -392,7 +405,7 @@ def run_swarm(args, rank, world, local):
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": world * P * G * args.steps / e2e_t, "unit": "particle-evals/s",
                 "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 8 * len(cfgs)},
-        "gpu_launches": (LAUNCHES_PER_STEP + 4) * G * args.steps,
+        "gpu_launches": (LAUNCHES_EVAL[1] + LAUNCHES_SWARM_UPDATE) * G * args.steps,
         "clocks": ck,
         "swarm_best": [float(x) for x in st["swarm_val"]],
         "iterations_run": int(st["iteration"]),
@@ -596,7 +609,7 @@ def run_ours(args, rank, world, local):
         "edge_fp64_fallback_particles": (float(np.mean(fb_counts)) if w.mode == 1 else None),
         "roofline": roof,
         "e2e": e2e,
-        "gpu_launches": LAUNCHES_PER_STEP * args.steps,
+        "gpu_launches": LAUNCHES_EVAL[w.mode] * args.steps,
         "clocks": ck,
         "fp64_path": fp64,
         "spline_path": spline,
@@ -744,7 +757,7 @@ def run_campaign(args, rank, world, local):
         "roofline": roof,
         "e2e": {"value": n_all / e2e_t, "unit": "particle-evals/s",
                 "h2d_bytes_per_step": P * 8 * 8, "d2h_bytes_per_step": P * 8},
-        "gpu_launches": LAUNCHES_PER_STEP * len(mine),
+        "gpu_launches": LAUNCHES_EVAL[1] * len(mine),
         "clocks": ck,
         "accuracy": {"certified_argmax_agrees_all": agree},
         "per_stream": per_stream,
