@@ -21,7 +21,7 @@ struct Rec {
 };
 // Summary of one slice of kSlice consecutive records of a particle (the
 // fix-up merges slices in parallel, then the slices of each particle in order)
-constexpr int kSlice = 32;
+constexpr int kSlice = 16;
 struct SliceSum {
   double ups;          // record sums plus the runs closed inside the slice
   double fz[3], lz[3]; // (zr, zi, hh) of the first and of the last run
