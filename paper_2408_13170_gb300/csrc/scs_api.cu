@@ -375,8 +375,8 @@ int prepare_batch(scs_ctx* ctx, const std::vector<BatchPart>& parts, const doubl
   CKLAUNCH();
   k_fill<<<(P + 31) / 32, 32, 0, s>>>(out.crange, P, out.list_off, fill, list_tmp);
   CKLAUNCH();
-  k_sort_chunks<<<nct < 1024 ? nct : 1024, 256, 0, s>>>(out.part, out.cnt, out.list_off,
-                                                          list_tmp, out.list, nct);
+  k_sort_chunks<<<nct < 1024 ? nct : 1024, kSortThreads, 0, s>>>(out.part, out.streams, ns, out.cnt,
+                                                          out.list_off, list_tmp, out.list, nct);
   CKLAUNCH();
   if (ctx->prof) CK(cudaEventRecord(ctx->ev[1], s));
   if (out.any_snr2 && want_edges) {

@@ -478,30 +478,54 @@ __global__ void k_fill(const int2* crange, int P, const int* list_off, int* fill
 }
 
 // Order each chunk's particle list by the mixed path's strides (response
-// sub-span first, then phase stride, both descending), so that the 32 lanes
-// of a work item share their span boundaries: a warp then runs blocks as
-// wide as its particles allow and calls the node and anchor code together
-// instead of once per lane.  Counting sort per chunk, one block per chunk;
-// the order within a key is arbitrary (results do not depend on it).
-__global__ void k_sort_chunks(const Part* part, const int* cnt, const int* list_off,
-                              const int* list_in, int* list_out, int n_chunks) {
-  constexpr int kKeys = (kMaxLog2B + 1) * (kMaxLog2B + 1);
+// sub-span first, then phase stride, both descending), then by where the
+// particle's range starts in the chunk (eighths), so that the 32 lanes of a
+// work item share their span boundaries and cover neighbouring bins: a warp
+// then runs blocks as wide as its particles allow, calls the node and anchor
+// code together instead of once per lane, and walks a short union of ranges
+// when its particles' supports are short.  Counting sort per chunk, one block
+// per chunk; the order within a key is arbitrary (results do not depend on it).
+__global__ void __launch_bounds__(kSortThreads) k_sort_chunks(const Part* part,
+                                                              const StreamDesc* streams,
+                                                              int n_streams,
+                              const int* cnt, const int* list_off, const int* list_in,
+                              int* list_out, int n_chunks) {
+  constexpr int kPos = 8;
+  constexpr int kKeys = (kMaxLog2B + 1) * (kMaxLog2B + 1) * kPos;
   __shared__ int hist[kKeys];
-  auto key_of = [&](int p) {
-    const Part& q = part[p];
-    int br = min(max(q.log2Br, 0), kMaxLog2B), b = min(max(q.log2B, 0), kMaxLog2B);
-    return (kMaxLog2B - br) * (kMaxLog2B + 1) + (kMaxLog2B - b);
-  };
+  __shared__ int s_scan[kSortThreads];
   for (int c = blockIdx.x; c < n_chunks; c += gridDim.x) {
+    const StreamDesc& sd = streams[stream_of_chunk(streams, n_streams, c)];
+    const int kc0 = (c - sd.chunk_base) << sd.log2_chunk;
+    auto key_of = [&](int p) {
+      const Part& q = part[p];
+      int br = min(max(q.log2Br, 0), kMaxLog2B), b = min(max(q.log2B, 0), kMaxLog2B);
+      const int pos = (max(kc0, q.k_lo) - kc0) >> (sd.log2_chunk - 3);   // 0 .. 7
+      return ((kMaxLog2B - br) * (kMaxLog2B + 1) + (kMaxLog2B - b)) * kPos + min(pos, kPos - 1);
+    };
     const int n = cnt[c], off = list_off[c];
     for (int i = threadIdx.x; i < kKeys; i += blockDim.x) hist[i] = 0;
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&hist[key_of(list_in[off + i])], 1);
     __syncthreads();
-    if (threadIdx.x == 0) {
-      int run = 0;
-      for (int k = 0; k < kKeys; ++k) {
-        int h = hist[k];
+    {
+      // exclusive prefix of hist: kPer consecutive keys per thread, then a
+      // scan of the 256 thread totals
+      constexpr int kPer = (kKeys + kSortThreads - 1) / kSortThreads;
+      const int k0 = threadIdx.x * kPer;
+      int tot = 0;
+      for (int k = k0; k < min(k0 + kPer, kKeys); ++k) tot += hist[k];
+      s_scan[threadIdx.x] = tot;
+      __syncthreads();
+      for (int o = 1; o < kSortThreads; o <<= 1) {
+        const int v = threadIdx.x >= o ? s_scan[threadIdx.x - o] : 0;
+        __syncthreads();
+        s_scan[threadIdx.x] += v;
+        __syncthreads();
+      }
+      int run = s_scan[threadIdx.x] - tot;
+      for (int k = k0; k < min(k0 + kPer, kKeys); ++k) {
+        const int h = hist[k];
         hist[k] = run;
         run += h;
       }

@@ -13,8 +13,11 @@ __global__ void k_scan64(int64_t* v, int64_t n, int64_t* total);
 __global__ void k_chunk_table(const int* diff, int n_chunks, int* cnt, int* list_off,
                               int* item_off);
 __global__ void k_fill(const int2* crange, int P, const int* list_off, int* fill, int* list);
-__global__ void k_sort_chunks(const Part* part, const int* cnt, const int* list_off,
-                              const int* list_in, int* list_out, int n_chunks);
+constexpr int kSortThreads = 256;
+__global__ void __launch_bounds__(kSortThreads)
+    k_sort_chunks(const Part* part, const StreamDesc* streams, int n_streams,
+                              const int* cnt, const int* list_off, const int* list_in,
+                              int* list_out, int n_chunks);
 // equal-SNR^2 edges: double-float pass over all particles, then the FP64
 // fallback for the particles it lists (anchor powers, then cumulative + edges)
 __global__ void __launch_bounds__(128) k_bounds_df(const Part* part, int P,
