@@ -453,7 +453,8 @@ int scs_debug_error(scs_ctx *ctx, int *check, long long *index);
  *   (roughly 20 + 75 C bytes per particle, C = ceil(K/4096) chunks, plus
  *   4 (N+1) + 16 (K/1024 + 2) bytes per particle for equal-SNR^2 segments).
  *   The first call on each device looks up the array's device address
- *   (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   (cudaGetSymbolAddress, a synchronous runtime call); later calls on that
+ *   device reuse it.
  *   The stream table of the call is handed to the device as a kernel
  *   argument, so no host buffer is read after the call returns.
  *   Every call shares the array and it keeps the previous call's contents:
