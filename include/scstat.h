@@ -181,6 +181,9 @@ int scs_set_segments(scs_ctx *ctx, int stream_id, int N, int mode);
  *   seg_x    NULL, or P x N doubles: x_{p,n} = |z_{p,n}| (row-major).
  *   seg_hh   NULL, or P x N doubles: hh_{p,n} = [h|h]_n.
  *   cuda_stream  cudaStream_t to run on (NULL: the context's stream).
+ * A call holds at most 2^31 - 1 (particle, work chunk) pairs: P times the
+ * stream's ceil(K / tile) chunks (scs_set_tile); a larger call is rejected
+ * with SCS_EINVAL and must be split.
  * Errors: SCS_EINVAL, SCS_ENODATA, SCS_ENOMEM, SCS_ECUDA, SCS_ETIMEOUT. */
 int scs_eval_stat(scs_ctx *ctx, int stream_id, const double *params,
                   int64_t P, double *stat, double *seg_x, double *seg_hh,
@@ -210,6 +213,8 @@ int scs_eval_loglike(scs_ctx *ctx, int stream_id, const double *params, int64_t 
  *               non-decreasing, P = P_offsets[n_items] in [1, 2^24].
  *   params      P x 8 doubles; stat  P doubles (host or device).
  * Per-particle results are identical to scs_eval_stat on the same stream.
+ * The (particle, work chunk) pairs of all items together are limited as in
+ * scs_eval_stat.
  * Errors: SCS_EINVAL, SCS_ENODATA, SCS_ENOMEM, SCS_ECUDA. */
 int scs_batch_eval(scs_ctx *ctx, const int *stream_ids, const int64_t *P_offsets,
                    int n_items, const double *params, double *stat, void *cuda_stream);

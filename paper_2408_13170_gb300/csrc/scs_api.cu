@@ -329,6 +329,11 @@ int prepare_batch(scs_ctx* ctx, const std::vector<BatchPart>& parts, const doubl
     }
     max_chunks = std::max(max_chunks, d.n_chunks);
   }
+  // the work lists are indexed with 32-bit offsets
+  if (bound > 0x7fffffffLL)
+    return fail(ctx, SCS_EINVAL,
+                "%lld (particle, work chunk) pairs in one call, above 2^31 - 1: split the call",
+                (long long)bound);
   out.s_max = std::max(1, (max_chunks + kSlice - 1) / kSlice);
   out.bound = bound;
   out.streams = dev_table ? dev_table
