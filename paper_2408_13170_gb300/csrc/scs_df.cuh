@@ -29,13 +29,13 @@ __device__ __forceinline__ dfl df_from(double x) {
   const float h = __double2float_rn(x);
   return dfl{h, __double2float_rn(x - (double)h)};
 }
-__device__ __forceinline__ double df_to(dfl a) { return (double)a.hi + (double)a.lo; }
 
-// The same two conversions with integer operations on the bit patterns
-// instead of FP64 conversion instructions (which GB300 issues at its FP64
-// rate).  Valid for 0 and for magnitudes whose parts are normal floats
-// (about 1e-30 .. 1e38).  df_split: hi = x rounded to 24 significant bits
-// (ties away from zero), lo = x - hi rounded to FP32.
+// The split (df_split) and the join back to a double (df_join) with integer
+// operations on the bit patterns instead of FP64 conversion instructions
+// (which GB300 issues at its FP64 rate).  Valid for 0 and for magnitudes
+// whose parts are normal floats (about 1e-30 .. 1e38).  df_split: hi = x
+// rounded to 24 significant bits (ties away from zero), lo = x - hi rounded
+// to FP32.
 __device__ __forceinline__ dfl df_split(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const unsigned long long m = b & 0x7fffffffffffffffULL;
@@ -94,9 +94,6 @@ __device__ __forceinline__ dfl operator*(dfl a, float b) {
   e = __fmaf_rn(a.lo, b, e);
   return df_fast(p, e);
 }
-// a * b + c with one renormalisation (c of at most the product's size or
-// smaller; used in Horner steps)
-__device__ __forceinline__ dfl df_fma(dfl a, dfl b, dfl c) { return a * b + c; }
 // exact scaling by a power of two
 __device__ __forceinline__ dfl df_scale2(dfl a, float p2) { return dfl{a.hi * p2, a.lo * p2}; }
 
