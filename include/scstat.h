@@ -294,7 +294,11 @@ int scs_pso_set(scs_ctx *ctx, const double *pos, const double *vel, const double
  * bytes written on output.  scs_pso_load recreates the swarm from such a
  * buffer (the referenced streams must exist in this context); the run then
  * continues bit for bit as it would have without the checkpoint.
- * Errors: SCS_EINVAL (small buffer, not a checkpoint), as create. */
+ * A checkpoint whose sizes, swarm coefficients (finite, eps >= 0) or
+ * convergence rule (delta >= 0, window >= 1) fail the checks of the setters
+ * is refused before the current swarm is touched.
+ * Errors: SCS_EINVAL (small buffer, not a checkpoint or a corrupt one), as
+ * create. */
 int scs_pso_save(scs_ctx *ctx, void *buf, size_t *len, void *cuda_stream);
 int scs_pso_load(scs_ctx *ctx, const void *buf, size_t len, void *cuda_stream);
 

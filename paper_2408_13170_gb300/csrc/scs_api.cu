@@ -1749,6 +1749,19 @@ int scs_pso_load(scs_ctx* ctx, const void* buf, size_t len, void* cuda_stream) {
   std::memcpy(hyper.data(), o, 8 * kPsoHyper * S);
   o += 8 * kPsoHyper * S;
   if (off[S] != P) return fail(ctx, SCS_EINVAL, "corrupt swarm checkpoint");
+  // the checks of scs_pso_set_hyper and scs_pso_set_convergence
+  for (size_t j = 0; j < hyper.size(); ++j)
+    if (!std::isfinite(hyper[j]) || (j % kPsoHyper >= 3 && hyper[j] < 0.0))
+      return fail(ctx, SCS_EINVAL, "corrupt swarm checkpoint (swarm coefficients)");
+  {
+    const unsigned char* r = o + 8 * (3 * 8 * P + P + 8 * S + S) + 16 * S;
+    double delta = 0.0;
+    int64_t win = 0;
+    std::memcpy(&delta, r, 8);
+    std::memcpy(&win, r + 8, 8);
+    if (!std::isfinite(delta) || delta < 0.0 || win < 1 || win > 0x7fffffffLL)
+      return fail(ctx, SCS_EINVAL, "corrupt swarm checkpoint (convergence rule)");
+  }
   int rc = scs_pso_create(ctx, (int)S, sids.data(), off.data(), lohi, lohi + 8, seed,
                           cuda_stream);
   if (rc) return rc;

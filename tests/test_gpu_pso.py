@@ -169,6 +169,32 @@ def test_checkpoint_resume_is_bitwise(scstat, datas):
         _same(a.pso_get(), ref)
 
 
+def test_corrupt_checkpoint_is_refused(scstat, datas):
+    """A checkpoint whose swarm coefficients or convergence rule fail the
+    setters' checks is refused, and the context keeps its swarm."""
+    with _ctx(scstat, datas, scstat.SCS_MIXED) as ctx:
+        _setup(scstat, ctx)
+        ctx.pso_run(2, use_graph=False)
+        blob = ctx.pso_save()
+        before = ctx.pso_get()
+        S = int(np.frombuffer(blob, np.int64, 1, 16)[0])
+        hyper_at = 40 + 8 * (S + 1) + 8 * ((4 * S + 7) // 8) + 16 * 8
+        n = len(blob)   # the last 16 bytes: the rule's delta (double) and window (int64)
+        for at, raw in ((hyper_at, np.float64(np.nan)), (hyper_at + 8 * 3, np.float64(-1.0)),
+                        (n - 16, np.float64(-0.5)), (n - 8, np.int64(0))):
+            bad = bytearray(blob)
+            bad[at:at + 8] = raw.tobytes()
+            with pytest.raises(scstat.ScsError) as e:
+                ctx.pso_load(bytes(bad))
+            assert e.value.code == scstat.SCS_EINVAL
+            _same(ctx.pso_get(), before)
+        ctx.pso_load(blob)   # the checkpoint holds the state, not the last statistic
+        after = ctx.pso_get()
+        for k in ("pos", "vel", "best_pos", "best_val", "swarm_pos", "swarm_val"):
+            np.testing.assert_array_equal(after[k], before[k], err_msg=k)
+        assert after["iteration"] == before["iteration"]
+
+
 def test_swarm_best_ties_take_lowest_index(scstat, datas):
     with _ctx(scstat, datas, scstat.SCS_MIXED) as ctx:
         _setup(scstat, ctx)
