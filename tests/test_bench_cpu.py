@@ -60,3 +60,32 @@ def test_roofline_legs_bound_and_fraction():
     r = b.roofline(peaks, sms, mhz, bin_evals, anchors, 1000, t, True, 1000.0)
     assert np.isclose(r["legs_ms"]["fp32"], 1e3 * 1.0e8 * 72 / 1.28e13)
     assert np.isclose(r["legs_ms"]["hbm"], 1e3 * 1000 * 40 / 1.0e12)
+
+
+def test_clock_samples_parsed():
+    """The clock record of the JSON line from nvidia-smi's CSV samples: the
+    median SM clock, the maximum clock, the sample count and every throttle
+    reason seen active; lines that are not samples are skipped."""
+    b = _bench()
+    cs = b.ClockSampler(0)
+
+    class Finished:   # stands in for the sampling process
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    cs.proc = Finished()
+    with open(cs.path, "w") as f:
+        f.write("0, 2070, 2070, 900.50, 0x0000000000000000, Not Active, Not Active, "
+                "Not Active, Not Active\n")
+        f.write("0, 1980, 2070, 1390.00, 0x0000000000000004, Not Active, Not Active, "
+                "Not Active, Active\n")
+        f.write("[N/A]\n")
+        f.write("0, 2070, 2070, 1200.00, 0x0000000000000000, Not Active, Not Active, "
+                "Not Active, Not Active\n")
+    r = cs.stop()
+    assert r == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "samples": 3,
+                 "reasons": ["sw_power_cap"]}
+    assert not os.path.exists(cs.path)
