@@ -17,6 +17,22 @@ def test_config_grids(name, K):
     assert f_first == pytest.approx(cfg["f_min"], abs=df)
 
 
+LADDER7 = (16384, 4096, 1024, 256, 64, 16, 1)
+
+
+@pytest.mark.parametrize("name,P,N,mode,snr", [
+    ("C1", 256, 8, "equal_width", 20.0),
+    ("C2", 4096, 2048, "equal_snr2", 17.0),
+    ("C3", 16384, LADDER7, "equal_snr2", 25.0),
+    ("C5", 65536, LADDER7, "equal_snr2", (15.0, 30.0))])
+def test_config_sizes(name, P, N, mode, snr):
+    """Particles (per level), segment counts, segmentation and injection SNR
+    of the named workloads; every injection is M_c = 30, q = 1.5, f0 = 0.018 Hz."""
+    cfg = synth.CONFIGS[name]
+    assert (cfg["P"], cfg["N"], cfg["mode"], cfg["snr"]) == (P, N, mode, snr)
+    assert cfg["inj"] == (30.0, 1.5, 0.018)
+
+
 def test_noise_convention():
     """One-sided PSD: Re and Im ~ N(0, S T/4), so E|n|^2 = S T/2."""
     rng = np.random.Generator(np.random.PCG64(1))
