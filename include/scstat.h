@@ -80,15 +80,19 @@ typedef struct scs_ctx scs_ctx; /* opaque, owned by the library */
  * Errors: SCS_EINVAL (bad device/path/out), SCS_ECUDA, SCS_ENOMEM. */
 int scs_create(scs_ctx **out, int device, int path);
 
-/* Release every device buffer of the context.  NULL is ignored. */
+/* Wait for the work queued on the context's stream, then release every
+ * device buffer of the context and the context itself (no counterpart in
+ * the paper).  NULL is ignored; no error is returned. */
 void scs_destroy(scs_ctx *ctx);
 
 /* NUL-terminated text of the last error on this context (owned by the
- * context, valid until the next call on it). */
+ * context, valid until the next call on it; "null context" for NULL).
+ * Never fails. */
 const char *scs_last_error(const scs_ctx *ctx);
 
 /* Switch the evaluation path of later calls (SCS_FP64, SCS_MIXED or
- * SCS_SPLINE; the swarm calls refuse SCS_SPLINE with SCS_EUNSUPPORTED). */
+ * SCS_SPLINE; the swarm calls refuse SCS_SPLINE with SCS_EUNSUPPORTED).
+ * Errors: SCS_EINVAL (unknown path). */
 int scs_set_path(scs_ctx *ctx, int path);
 
 /* Node grid of the SCS_SPLINE path.  Sec. IV evaluates the waveform and the
@@ -259,9 +263,12 @@ int scs_pso_create(scs_ctx *ctx, int n_swarms, const int *stream_ids,
                    const int64_t *swarm_offsets, const double *prior_lo,
                    const double *prior_hi, uint64_t seed, void *cuda_stream);
 
-/* Set Omega, Phi_P, Phi_G and eps[8] (minimum speeds, parameter order of
- * params, >= 0) of one swarm, or of every swarm if swarm = -1.  Waits for the
- * work on cuda_stream first.  Errors: SCS_EINVAL, SCS_ENODATA (no swarm). */
+/* Set Omega, Phi_P, Phi_G (Eq. PSO_velocity_rule) and eps[8] (minimum
+ * speeds, Eq. PSO_min_velocity; parameter order of params, >= 0) of one
+ * swarm, or of every swarm if swarm = -1 (Table III gives them per segment
+ * count).  Waits for the work on cuda_stream first.
+ * Errors: SCS_EINVAL (swarm out of range, non-finite coefficient, eps < 0),
+ * SCS_ENODATA (no swarm), SCS_EUNSUPPORTED (spline path). */
 int scs_pso_set_hyper(scs_ctx *ctx, int swarm, double Omega, double PhiP, double PhiG,
                       const double *eps, void *cuda_stream);
 
@@ -277,13 +284,16 @@ int scs_pso_run(scs_ctx *ctx, int iters, int use_graph, void *cuda_stream);
 /* Copy the state out (each pointer may be NULL to skip; host or device):
  * pos, vel, best_pos P x 8; best_val P; swarm_pos S x 8; swarm_val S;
  * stat P (statistic of the positions evaluated last, i.e. before the last
- * move); iteration = iterations run since create.  Synchronous. */
+ * move); iteration = iterations run since create.  Synchronous.
+ * Errors: SCS_ENODATA (no swarm), SCS_EUNSUPPORTED (spline path), SCS_ECUDA. */
 int scs_pso_get(scs_ctx *ctx, double *pos, double *vel, double *best_pos, double *best_val,
                 double *swarm_pos, double *swarm_val, double *stat, int64_t *iteration,
                 void *cuda_stream);
 
 /* Overwrite parts of the state (NULL pointers keep that part; host or
- * device) and set the iteration counter (0 .. 2^32 - 1).  Synchronous. */
+ * device) and set the iteration counter (0 .. 2^32 - 1).  Synchronous.
+ * Errors: SCS_EINVAL (iteration out of range), SCS_ENODATA (no swarm),
+ * SCS_EUNSUPPORTED (spline path), SCS_ECUDA. */
 int scs_pso_set(scs_ctx *ctx, const double *pos, const double *vel, const double *best_pos,
                 const double *best_val, const double *swarm_pos, const double *swarm_val,
                 int64_t iteration, void *cuda_stream);
@@ -324,7 +334,9 @@ int scs_autotune(scs_ctx *ctx, int stream_id, const double *params, int64_t P,
 /* ---- The hierarchical multi-swarm search on the device (Sec. III.B, App. B) ----
  * Convergence rule: a swarm has converged when its best value has not grown by
  * more than delta over the last `window` evaluations (the paper: 2 over 50,
- * the default).  The record is kept on the device by every iteration. */
+ * the default).  The record is kept on the device by every iteration.
+ * Errors: SCS_EINVAL (delta negative or not finite, window < 1), SCS_ENODATA
+ * (no swarm), SCS_EUNSUPPORTED (spline path). */
 int scs_pso_set_convergence(scs_ctx *ctx, double delta, int window);
 
 /* converged[S] (may be NULL): 1 for each converged swarm; *iteration (may be
@@ -334,11 +346,14 @@ int scs_pso_status(scs_ctx *ctx, int *converged, int64_t *iteration, void *cuda_
 
 /* Forget the personal and swarm bests and the convergence records (positions
  * and velocities are kept): for a new objective, e.g. the next rung of the
- * segment ladder.  Synchronous. */
+ * segment ladder (App. B).  Synchronous.
+ * Errors: SCS_ENODATA (no swarm), SCS_EUNSUPPORTED (spline path), SCS_ECUDA. */
 int scs_pso_reset_bests(scs_ctx *ctx, void *cuda_stream);
 
-/* The current swarm layout (it changes with scs_pso_regroup): *n_swarms, and
- * if not NULL stream_ids[S] and swarm_offsets[S + 1]. */
+/* The current swarm layout (it changes with scs_pso_regroup, Sec. III.B):
+ * *n_swarms, stream_ids[S] and swarm_offsets[S + 1] (host; each may be
+ * NULL to skip it).
+ * Errors: SCS_ENODATA (no swarm), SCS_EUNSUPPORTED (spline path). */
 int scs_pso_layout(scs_ctx *ctx, int *n_swarms, int *stream_ids, int64_t *swarm_offsets);
 
 /* k-means of P positions (P x 8, host or device) in the prior box: features
@@ -347,7 +362,10 @@ int scs_pso_layout(scs_ctx *ctx, int *n_swarms, int *stream_ids, int64_t *swarm_
  * farthest from centroids 0 .. j-1 (lowest index among equals); then `iters`
  * Lloyd steps (nearest centroid, lowest index among equals; an empty cluster
  * keeps its centroid).  labels[P] (host) receive the cluster of each
- * particle, centroids (host, may be NULL) k x 9 features.  1 <= k <= P. */
+ * particle, centroids (host, may be NULL) k x 9 features.  1 <= k <= P.
+ * The clustering step of the multi-swarm search (Sec. III.B); usable alone.
+ * Errors: SCS_EINVAL (sizes, k, iters outside 0 .. 1000), SCS_ENOMEM,
+ * SCS_ECUDA. */
 int scs_kmeans(scs_ctx *ctx, const double *pos, int64_t P, const double *prior_lo,
                const double *prior_hi, int k, int iters, int *labels, double *centroids,
                void *cuda_stream);
@@ -359,7 +377,9 @@ int scs_kmeans(scs_ctx *ctx, const double *pos, int64_t P, const double *prior_l
  * cluster, in their previous order), so swarms can merge, split or appear;
  * the total number of particles is kept.  Bests are forgotten; each new
  * swarm takes the hyper-parameters of its stream's first old swarm.
- * Synchronous. */
+ * Synchronous.
+ * Errors: SCS_EINVAL (n_clusters outside 1 .. 1024, iters outside
+ * 0 .. 1000), SCS_ENODATA (no swarm), SCS_ENOMEM, SCS_ECUDA. */
 int scs_pso_regroup(scs_ctx *ctx, int n_clusters, int iters, void *cuda_stream);
 
 /* The hierarchical search (Sec. III.B): for each rung r of the ladder
@@ -368,7 +388,9 @@ int scs_pso_regroup(scs_ctx *ctx, int n_clusters, int iters, void *cuda_stream);
  * hyper_rows[r] (Omega, Phi_P, Phi_G, eps[8]), the bests are reset, and
  * iterations run in CUDA graphs of chunk_iters until all swarms have
  * converged or max_iters have run (iters_out[r], may be NULL); between rungs
- * the swarms are re-clustered into n_clusters per stream (0: not). */
+ * the swarms are re-clustered into n_clusters per stream (0: not).
+ * Errors: SCS_EINVAL (ladder, rows or counts out of range), SCS_ENODATA,
+ * SCS_ENOMEM, SCS_ECUDA. */
 int scs_pso_search(scs_ctx *ctx, const int *ladder, int n_rungs, const double *hyper_rows,
                    int n_clusters, int chunk_iters, int max_iters, int64_t *iters_out,
                    void *cuda_stream);
@@ -398,15 +420,19 @@ int scs_inject(scs_ctx *ctx, int stream_id, const double *theta, double snr,
                double *hh_out);
 
 /* Support and anchor stride of P particles (diagnostics): k_lo[P], k_hi[P]
- * (k_hi < k_lo: empty; both -1: non-physical) and the mixed path's
+ * (the bins with f >= f0, t(f) <= T_obs and v <= 6^{-1/2}, Sec. IV;
+ * k_hi < k_lo: empty; both -1: non-physical) and the mixed path's
  * strides (may be NULL): bits 0-7 log2 of the phase-anchor stride B, bits
- * 8-15 log2 of the response sub-span Br.  Host or device pointers. */
+ * 8-15 log2 of the response sub-span Br.  Host or device pointers.
+ * Errors: SCS_EINVAL, SCS_ENODATA, SCS_ENOMEM, SCS_ECUDA. */
 int scs_support(scs_ctx *ctx, int stream_id, const double *params, int64_t P,
                 int64_t *k_lo, int64_t *k_hi, int32_t *log2_stride,
                 void *cuda_stream);
 
-/* Segment edges of P particles under the stream's segmentation: e[P x (N+1)]
- * with segment n = [e_n, e_{n+1}) in grid bins (int64, host or device). */
+/* Segment edges of P particles under the stream's segmentation (Sec. II.B:
+ * equal width, or equal squared SNR per segment): e[P x (N+1)] with segment
+ * n = [e_n, e_{n+1}) in grid bins (int64, host or device).
+ * Errors: SCS_EINVAL, SCS_ENODATA, SCS_ENOMEM, SCS_ECUDA. */
 int scs_segment_edges(scs_ctx *ctx, int stream_id, const double *params,
                       int64_t P, int64_t *edges, void *cuda_stream);
 
